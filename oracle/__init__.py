@@ -1,0 +1,240 @@
+"""Python access to the FP64 CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE. The oracle is the slow, plain statement of the
+collapse-time computation of arXiv:2510.02873 (Sec. 3 and Sec. 4.1-4.2) that
+the CUDA library is checked against. Only tests/, __graft_entry__.smoke() and
+the CPU-baseline / reference legs of bench.py may import this package; the
+product path never does. It shares no code with the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+BUILD_DIR = os.path.join(HERE, "_build")
+LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
+SOURCES = [os.path.join(HERE, "oracle.c")]
+
+FLAG_COLLAPSED = 1
+FLAG_EDGE = 4
+FLAG_SIGN0 = 8
+FLAG_EDS = 16
+FLAG_AXIS23 = 32
+# flags whose points sit on a discontinuity of F (either branch is a valid answer)
+FLAGS_AMBIGUOUS = FLAG_EDGE | FLAG_SIGN0
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (plain C11, no FMA contraction, OpenMP)."""
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    newest = max(os.path.getmtime(s) for s in SOURCES + [os.path.join(HERE, "oracle.h")])
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+           "-D_DEFAULT_SOURCE", *SOURCES, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True, cwd=HERE)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class _Tables(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("a", ctypes.POINTER(ctypes.c_double)),
+                ("D", ctypes.POINTER(ctypes.c_double)), ("M", ctypes.POINTER(ctypes.c_double))]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(LIB_PATH)
+            d, i, i64, vp = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+            L.or_growth_table.argtypes = [d, d, i, d, d, vp, vp]
+            L.or_growth_at.argtypes = [d, d, d]
+            L.or_growth_at.restype = d
+            L.or_spline_build.argtypes = [i, vp, vp, d, d, vp]
+            L.or_spline_eval.argtypes = [i, vp, vp, vp, d]
+            L.or_spline_eval.restype = d
+            L.or_bilinear.argtypes = [i, vp, i, vp, vp, d, d]
+            L.or_bilinear.restype = d
+            L.or_eigen_jacobi.argtypes = [vp, vp]
+            L.or_eigen_trig.argtypes = [vp, vp]
+            L.or_axis_stretch.argtypes = [vp, i, d]
+            L.or_axis_stretch.restype = d
+            L.or_axis_coeffs.argtypes = [vp, i, vp]
+            L.or_collapse_D.argtypes = [vp, d, ctypes.POINTER(ctypes.c_int)]
+            L.or_collapse_D.restype = d
+            L.or_tables_init.argtypes = [ctypes.POINTER(_Tables), d, d, i, d, d]
+            L.or_tables_free.argtypes = [ctypes.POINTER(_Tables)]
+            L.or_a_of_D.argtypes = [ctypes.POINTER(_Tables), d, ctypes.POINTER(ctypes.c_int)]
+            L.or_a_of_D.restype = d
+            L.or_F_point.argtypes = [ctypes.POINTER(_Tables), vp, ctypes.POINTER(ctypes.c_int)]
+            L.or_F_point.restype = d
+            L.or_collapse_scale.argtypes = [ctypes.POINTER(_Tables), vp, i64, i64, vp, vp,
+                                            ctypes.c_int32, vp, i]
+            L.or_collapse_scale_f32.argtypes = L.or_collapse_scale.argtypes
+            L.or_F_points.argtypes = [ctypes.POINTER(_Tables), vp, i64, i64, vp, vp, i]
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------- growth / spline
+def growth_table(omega_m=0.3, omega_l=0.7, n_knots=512, a_min=1e-3, a_max=1.0):
+    a = np.empty(n_knots)
+    D = np.empty(n_knots)
+    rc = lib().or_growth_table(omega_m, omega_l, n_knots, a_min, a_max, _p(a), _p(D))
+    if rc:
+        raise ValueError(f"or_growth_table failed: {rc}")
+    return a, D
+
+
+def growth_at(a, omega_m=0.3, omega_l=0.7) -> float:
+    return lib().or_growth_at(omega_m, omega_l, float(a))
+
+
+def spline_build(x, y, M0=0.0, Mn=0.0) -> np.ndarray:
+    x, y = _f64(x), _f64(y)
+    M = np.empty_like(x)
+    rc = lib().or_spline_build(len(x), _p(x), _p(y), M0, Mn, _p(M))
+    if rc:
+        raise ValueError(f"or_spline_build failed: {rc}")
+    return M
+
+
+def spline_eval(x, y, M, t) -> np.ndarray:
+    x, y, M = _f64(x), _f64(y), _f64(M)
+    L = lib()
+    t = np.atleast_1d(np.asarray(t, dtype=np.float64))
+    return np.array([L.or_spline_eval(len(x), _p(x), _p(y), _p(M), float(v)) for v in t])
+
+
+def bilinear(xg, yg, z, x, y) -> np.ndarray:
+    xg, yg, z = _f64(xg), _f64(yg), _f64(z)
+    assert z.shape == (len(xg), len(yg))
+    L = lib()
+    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    y = np.atleast_1d(np.asarray(y, dtype=np.float64))
+    return np.array([L.or_bilinear(len(xg), _p(xg), len(yg), _p(yg), _p(z), float(u), float(v))
+                     for u, v in zip(x, y)])
+
+
+# ---------------------------------------------------------------- eigen / collapse
+def eigen_jacobi(h) -> np.ndarray:
+    h = _f64(h)
+    lam = np.empty(3)
+    lib().or_eigen_jacobi(_p(h), _p(lam))
+    return lam
+
+
+def eigen_trig(h) -> np.ndarray:
+    h = _f64(h)
+    lam = np.empty(3)
+    lib().or_eigen_trig(_p(h), _p(lam))
+    return lam
+
+
+def axis_stretch(lam, axis: int, D: float) -> float:
+    lam = _f64(lam)
+    return lib().or_axis_stretch(_p(lam), axis, float(D))
+
+
+def axis_coeffs(lam, axis: int) -> np.ndarray:
+    lam = _f64(lam)
+    c = np.empty(4)
+    lib().or_axis_coeffs(_p(lam), axis, _p(c))
+    return c
+
+
+def collapse_D(lam, D_top: float):
+    lam = _f64(lam)
+    f = ctypes.c_int(0)
+    Dc = lib().or_collapse_D(_p(lam), float(D_top), ctypes.byref(f))
+    return Dc, f.value
+
+
+class Tables:
+    """Growth table and the natural spline of a(D) (owned by the oracle)."""
+
+    def __init__(self, omega_m=0.3, omega_l=0.7, n_knots=512, a_min=1e-3, a_max=1.0):
+        self._t = _Tables()
+        rc = lib().or_tables_init(ctypes.byref(self._t), omega_m, omega_l, n_knots, a_min, a_max)
+        if rc:
+            raise ValueError(f"or_tables_init failed: {rc}")
+        self.n = n_knots
+        self.a = np.ctypeslib.as_array(self._t.a, shape=(n_knots,)).copy()
+        self.D = np.ctypeslib.as_array(self._t.D, shape=(n_knots,)).copy()
+        self.M = np.ctypeslib.as_array(self._t.M, shape=(n_knots,)).copy()
+
+    def __del__(self):
+        try:
+            lib().or_tables_free(ctypes.byref(self._t))
+        except Exception:
+            pass
+
+    @property
+    def D_top(self) -> float:
+        return float(self.D[-1])
+
+    def a_of_D(self, D):
+        f = ctypes.c_int(0)
+        a = lib().or_a_of_D(ctypes.byref(self._t), float(D), ctypes.byref(f))
+        return a, f.value
+
+    def F_point(self, h):
+        h = _f64(h)
+        f = ctypes.c_int(0)
+        F = lib().or_F_point(ctypes.byref(self._t), _p(h), ctypes.byref(f))
+        return F, f.value
+
+    def F_points(self, hess: np.ndarray, nthreads: int = 0):
+        """hess: (6, n) FP64 planes -> (F, flags)."""
+        hess = _f64(hess)
+        n = hess.shape[1]
+        F = np.empty(n)
+        flags = np.empty(n, dtype=np.int32)
+        lib().or_F_points(ctypes.byref(self._t), _p(hess), n, n, _p(F), _p(flags), nthreads)
+        return F, flags
+
+    def collapse_scale(self, hess: np.ndarray, F_max: np.ndarray, idx: np.ndarray, scale_idx: int,
+                       nthreads: int = 0) -> np.ndarray:
+        """One radius: hess (6, n) FP64 or FP32 planes; updates F_max/idx in place; returns flags."""
+        n = hess.shape[1]
+        assert F_max.dtype == np.float64 and idx.dtype == np.int32
+        assert F_max.flags.c_contiguous and idx.flags.c_contiguous
+        flags = np.empty(n, dtype=np.int32)
+        if hess.dtype == np.float32:
+            h = np.ascontiguousarray(hess)
+            lib().or_collapse_scale_f32(ctypes.byref(self._t), _p(h), n, n, _p(F_max), _p(idx),
+                                        scale_idx, _p(flags), nthreads)
+        else:
+            h = _f64(hess)
+            lib().or_collapse_scale(ctypes.byref(self._t), _p(h), n, n, _p(F_max), _p(idx),
+                                    scale_idx, _p(flags), nthreads)
+        return flags
+
+    def collapse_multi(self, hess_stack: np.ndarray, nthreads: int = 0):
+        """All radii of a (R, 6, n) stack -> (F_max, idx, flags_or)."""
+        R, _, n = hess_stack.shape
+        F_max = np.zeros(n)
+        idx = np.full(n, -1, dtype=np.int32)
+        flags_or = np.zeros(n, dtype=np.int32)
+        for r in range(R):
+            flags_or |= self.collapse_scale(hess_stack[r], F_max, idx, r, nthreads)
+        return F_max, idx, flags_or

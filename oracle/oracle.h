@@ -1,0 +1,116 @@
+/* oracle.h -- plain FP64 CPU oracle of the collapse-time hot path.
+ *
+ * TEST INFRASTRUCTURE. This library is the slow, obviously correct statement
+ * of what the GPU path computes. Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline / reference legs of bench.py may load or call it. It shares no
+ * code with the CUDA library (paper_2510_02873_gb300/csrc), and neither
+ * includes nor links the other.
+ *
+ * Paper: Lepinzan et al., "Accelerating cosmological simulations on GPUs: a
+ * portable approach using OpenMP" (arXiv:2510.02873). Section 3 describes the
+ * computation: per grid point and smoothing radius, the Hessian of the
+ * smoothed potential is diagonalised, a third-order LPT ellipsoidal collapse
+ * condition gives the growth factor at collapse, and the inverse growth
+ * function a(D), a cubic spline through the ODE solution D(a), maps it to the
+ * collapse scale factor; Sec. 4.1 adds the per-element maxima update.
+ *
+ * Readings of the paper (it does not print the collapse condition; see the
+ * repository's design notes for the full list):
+ *   - eigenvalues sorted descending, lambda1 >= lambda2 >= lambda3 (Sec. 3);
+ *   - axis stretch (R-LPT: local third-order LPT with EdS growth ratios
+ *     D2 = -3/7 D^2, D3a = -1/3 D^3, D3b = 10/21 D^3):
+ *       A_i(D) = 1 - D l_i - 3/7 D^2 l_j l_k
+ *                + D^3 [ l1 l2 l3 / 9 - 5/21 l_i (l_j^2 + l_k^2) ]
+ *   - collapse growth factor D_c = smallest root of A_1 in (0, D_top];
+ *     lambda1 <= 0 or no such root: no collapse, F = 0. For sorted
+ *     eigenvalues with lambda1 > 0, A_1 is strictly decreasing on D > 0 (a
+ *     positive D^2 coefficient needs l2 l3 < 0, and then c2^2 < 3 |c3| l1), so
+ *     the root is unique and never tangent;
+ *   - a_c from a natural cubic spline through (D(a_k), a_k); below the first
+ *     knot a_c = a_0 D_c / D_0 (EdS limit); F = 1/a_c = 1 + z_c;
+ *   - running maximum over radii with a strict '>' (ties keep the earlier
+ *     radius), F_max starts at 0 and idx at -1.
+ *
+ * Pins (tests/test_oracle_pins.py): spherical limit against the textbook
+ * Lagrangian and Eulerian 3LPT series; plane wave against Zel'dovich; the
+ * 2LPT density of the product A_1 A_2 A_3; symmetry and homogeneity of the
+ * stretch; uniqueness of the collapse root; Jacobi against LAPACK and known
+ * spectra; spline exactness (knots, lines, cubics with true end curvature) and
+ * agreement with SciPy's natural spline; bilinear exactness; the growth ODE
+ * against the Heath integral and the EdS solution; brute force on 8^3 x 3.
+ *
+ * PARITY UNPINNED (partially): or_axis_coeffs. The per-axis split of the
+ * second- and third-order terms (l_j l_k and l_i (l_j^2 + l_k^2)) is a reading;
+ * only its spherical and plane-wave limits, its symmetry in the other two
+ * axes, its degree and its second-order trace are pinned. Nothing outside the
+ * reading fixes the split itself.
+ */
+#ifndef COLLAPSE_ORACLE_H
+#define COLLAPSE_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Per-evaluation diagnostic flags (bit mask). */
+#define OR_FLAG_COLLAPSED   1  /* a root was found in (0, D_top]                    */
+#define OR_FLAG_EDGE        4  /* |A_1(D_top)| <= 1e-9: collapse by a_max ambiguous    */
+#define OR_FLAG_SIGN0       8  /* |lambda1| <= 1e-9 * max|lambda|: lambda1>0 test ambiguous */
+#define OR_FLAG_EDS        16  /* D_c below the first knot: EdS limit used             */
+#define OR_FLAG_AXIS23     32  /* A_2 or A_3 crosses zero before A_1 does (diagnostic) */
+
+/* ---- linear growth factor (Sec. 3, Sec. 4.2) ---- */
+int or_growth_table(double omega_m, double omega_l, int n_knots, double a_min, double a_max,
+                    double *a_k, double *D_k);
+double or_growth_at(double omega_m, double omega_l, double a); /* D(a)/D(1), same integrator */
+
+/* ---- cubic spline with prescribed end second derivatives (natural: 0, 0) ---- */
+int or_spline_build(int n, const double *x, const double *y, double M0, double Mn, double *M);
+double or_spline_eval(int n, const double *x, const double *y, const double *M, double t);
+
+/* ---- bilinear interpolation on a non-uniform grid, z[ix*ny + iy] ---- */
+double or_bilinear(int nx, const double *xg, int ny, const double *yg, const double *z,
+                   double x, double y);
+
+/* ---- symmetric 3x3 eigenvalues, h = (xx, yy, zz, xy, xz, yz), sorted descending ---- */
+void or_eigen_jacobi(const double h[6], double lam[3]);
+void or_eigen_trig(const double h[6], double lam[3]);
+
+/* ---- collapse condition ---- */
+double or_axis_stretch(const double l[3], int axis, double D);        /* A_axis(D), axis 0..2 */
+void   or_axis_coeffs(const double l[3], int axis, double c[4]);      /* A = c0 + c1 D + c2 D^2 + c3 D^3 */
+double or_collapse_D(const double l[3], double D_top, int *flags);    /* D_c or 0 when none   */
+
+/* ---- tables and the per-point collapse value ---- */
+typedef struct {
+  int n;            /* knots */
+  double *a;        /* a_k, increasing */
+  double *D;        /* D(a_k), increasing */
+  double *M;        /* second derivatives of a(D) at the knots (natural) */
+} or_tables;
+
+int  or_tables_init(or_tables *t, double omega_m, double omega_l, int n_knots, double a_min, double a_max);
+void or_tables_free(or_tables *t);
+double or_a_of_D(const or_tables *t, double D, int *flags);           /* spline + EdS branch */
+double or_F_point(const or_tables *t, const double h[6], int *flags); /* F = 1/a_c or 0 */
+
+/* One radius over n points: hess = 6 planes, component c of point p at hess[c*plane_stride + p].
+ * Updates F_max/idx with a strict '>' and writes per-point flags (may be NULL).
+ * nthreads <= 0: all OpenMP threads. */
+void or_collapse_scale(const or_tables *t, const double *hess, int64_t n, int64_t plane_stride,
+                       double *F_max, int32_t *idx, int32_t scale_idx, int32_t *flags, int nthreads);
+
+/* Same, for FP32 planes (the values are widened exactly to FP64 first). */
+void or_collapse_scale_f32(const or_tables *t, const float *hess, int64_t n, int64_t plane_stride,
+                           double *F_max, int32_t *idx, int32_t scale_idx, int32_t *flags, int nthreads);
+
+/* F of each point (no max), with flags. */
+void or_F_points(const or_tables *t, const double *hess, int64_t n, int64_t plane_stride,
+                 double *F, int32_t *flags, int nthreads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,388 @@
+"""Pins of the FP64 oracle against facts fixed outside it (no GPU).
+
+Each test ties one oracle routine to something the oracle does not compute
+itself: textbook perturbation-theory coefficients, exact invariants,
+closed-form special cases, library routines (numpy/scipy) on cases that reduce
+to them, and brute force on tiny inputs.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import hessgen
+import oracle
+
+
+def _rng(seed=7):
+    return np.random.default_rng(seed)
+
+
+def _sym(h):
+    xx, yy, zz, xy, xz, yz = h
+    return np.array([[xx, xy, xz], [xy, yy, yz], [xz, yz, zz]])
+
+
+# ----------------------------------------------------------------------------- P1
+def test_spherical_limit_lagrangian_series():
+    """Equal eigenvalues l = delta/3: A_1 is the textbook spherical 3LPT series
+    R/R_L = 1 - x/3 - x^2/21 - 23 x^3/1701 (x = D delta; Bernardeau 1994)."""
+    for delta in (0.5, 1.0, 3.0):
+        lam = np.full(3, delta / 3.0)
+        for axis in range(3):
+            c = oracle.axis_coeffs(lam, axis)
+            want = [1.0, -delta / 3, -delta ** 2 / 21, -23 * delta ** 3 / 1701]
+            np.testing.assert_allclose(c, want, rtol=1e-14, atol=0)
+
+
+def test_spherical_limit_eulerian_series():
+    """(R/R_L)^-3 = 1 + delta_E must reproduce the Eulerian spherical series
+    delta_E = x + 17/21 x^2 + 341/567 x^3 (Peebles 1980; Fry 1984)."""
+    c = oracle.axis_coeffs(np.full(3, 1.0 / 3.0), 0)  # delta = 1 -> x = D
+    u = -np.array(c[1:])  # A = 1 - u(x)
+    # (1-u)^-3 = 1 + 3u + 6u^2 + 10u^3 + ...  truncated at x^3
+    poly_u = np.array([0.0, u[0], u[1], u[2]])
+    def mul(a, b):
+        return np.convolve(a, b)[:4]
+    series = np.zeros(4)
+    series[0] = 1.0
+    series += 3 * poly_u + 6 * mul(poly_u, poly_u) + 10 * mul(mul(poly_u, poly_u), poly_u)
+    got = [Fraction(float(v)).limit_denominator(2000) for v in series]
+    assert got == [1, 1, Fraction(17, 21), Fraction(341, 567)]
+
+
+def test_spherical_collapse_root():
+    """delta * D_c for equal eigenvalues is the first positive root of the
+    textbook series (2.0500838...; Zel'dovich would give 3)."""
+    roots = np.roots([-23 / 1701, -1 / 21, -1 / 3, 1.0])
+    x_c = min(r.real for r in roots if abs(r.imag) < 1e-12 and r.real > 0)
+    assert abs(x_c - 2.0500838) < 1e-7
+    for delta in (0.7, 2.0, 9.0):
+        Dc, flags = oracle.collapse_D(np.full(3, delta / 3.0), 10.0 / delta)
+        assert flags & oracle.FLAG_COLLAPSED
+        assert abs(Dc * delta - x_c) <= 1e-13 * x_c
+
+
+# ----------------------------------------------------------------------------- P2
+def test_plane_wave_is_zeldovich():
+    """One non-zero eigenvalue: Zel'dovich is exact for plane-parallel flow, so
+    A_1 = 1 - D l1 and the other axes do not move; D_c = 1/l1."""
+    for l1 in (0.3, 1.7, 12.0):
+        lam = np.array([l1, 0.0, 0.0])
+        np.testing.assert_array_equal(oracle.axis_coeffs(lam, 0), [1.0, -l1, 0.0, 0.0])
+        for ax in (1, 2):
+            np.testing.assert_array_equal(oracle.axis_coeffs(lam, ax), [1.0, 0.0, 0.0, 0.0])
+        Dc, flags = oracle.collapse_D(lam, 10.0)
+        assert flags & oracle.FLAG_COLLAPSED
+        assert abs(Dc - 1.0 / l1) <= 2e-16 / l1 * 4
+
+
+# ---------------------------------------------------------------- 2LPT Jacobian
+def test_second_order_density_matches_2lpt():
+    """1/J - 1 with J = A_1 A_2 A_3 must give, to second order, the textbook
+    Lagrangian-frame density delta_L D + D^2 (17/21 delta^2 + 2/7 s_ij s_ij)
+    (s = traceless tidal tensor; Bernardeau et al. 2002, F2 kernel)."""
+    rng = _rng(1)
+    for _ in range(50):
+        lam = rng.normal(size=3)
+        polys = [oracle.axis_coeffs(lam, ax) for ax in range(3)]
+        J = np.convolve(np.convolve(polys[0], polys[1]), polys[2])[:3]  # 1 + j1 D + j2 D^2
+        # 1/J - 1 to second order: -j1 D + (j1^2 - j2) D^2
+        d1, d2 = -J[1], J[1] ** 2 - J[2]
+        delta = lam.sum()
+        s2 = ((lam - delta / 3) ** 2).sum()
+        assert abs(d1 - delta) < 1e-14 * (1 + abs(delta))
+        assert abs(d2 - (17 / 21 * delta ** 2 + 2 / 7 * s2)) < 1e-13 * (1 + delta ** 2 + s2)
+
+
+def test_axis_stretch_symmetric_in_other_axes():
+    """The stretch of axis i cannot depend on how the other two axes are labelled."""
+    rng = _rng(2)
+    for _ in range(50):
+        lam = rng.normal(size=3)
+        for ax in range(3):
+            j, k = (ax + 1) % 3, (ax + 2) % 3
+            sw = lam.copy()
+            sw[j], sw[k] = lam[k], lam[j]
+            np.testing.assert_allclose(oracle.axis_coeffs(lam, ax), oracle.axis_coeffs(sw, ax),
+                                       rtol=1e-15, atol=1e-15)
+
+
+# ----------------------------------------------------------------------------- P3
+def test_homogeneity_and_monotone_in_contrast(oracle_tables):
+    """D_c(k l) = D_c(l)/k for k > 0 (each LPT order has its own degree), so F
+    is non-decreasing along any ray of growing linear contrast."""
+    rng = _rng(3)
+    for _ in range(40):
+        lam = np.sort(rng.normal(size=3))[::-1].copy()
+        if lam[0] <= 0:
+            lam = -lam[::-1].copy()
+        Dc, f = oracle.collapse_D(lam, 1e6)
+        if not f & oracle.FLAG_COLLAPSED or f & oracle.FLAGS_AMBIGUOUS:
+            continue
+        for k in (0.5, 2.0, 7.0):
+            Dk, fk = oracle.collapse_D(k * lam, 1e6)
+            assert abs(Dk * k - Dc) <= 1e-13 * Dc
+    # monotone F along a ray, through the tables
+    direction = np.array([1.0, 0.4, -0.3])
+    R = np.array([[0.36, 0.48, -0.8], [-0.8, 0.6, 0.0], [0.48, 0.64, 0.6]])
+    last = -1.0
+    for k in np.linspace(0.5, 30.0, 60):
+        H = R @ np.diag(k * direction) @ R.T
+        h = [H[0, 0], H[1, 1], H[2, 2], H[0, 1], H[0, 2], H[1, 2]]
+        F, _ = oracle_tables.F_point(h)
+        assert F >= last
+        last = F
+    assert last > 1.0
+
+
+# ----------------------------------------------------------------------------- P4
+def test_jacobi_matches_library_and_known_spectra():
+    rng = _rng(4)
+    for _ in range(300):
+        h = rng.normal(size=6) * rng.uniform(0.1, 10)
+        ref = np.sort(np.linalg.eigvalsh(_sym(h)))[::-1]
+        got = oracle.eigen_jacobi(h)
+        scale = np.abs(ref).max()
+        assert np.all(np.diff(got) <= 0)
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * scale)
+        np.testing.assert_allclose(oracle.eigen_trig(h), ref, rtol=0, atol=1e-7 * scale)
+    # rotated diagonal matrices with known spectra, including exact degeneracies
+    for spec in ([3.0, 1.0, -2.0], [2.0, 2.0, -1.0], [1.0, -0.5, -0.5], [4.0, 4.0, 4.0], [0.0, 0.0, 0.0]):
+        Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        H = Q @ np.diag(spec) @ Q.T
+        h = [H[0, 0], H[1, 1], H[2, 2], H[0, 1], H[0, 2], H[1, 2]]
+        np.testing.assert_allclose(oracle.eigen_jacobi(h), sorted(spec, reverse=True),
+                                   rtol=0, atol=1e-14 * max(1.0, max(map(abs, spec))))
+
+
+# ----------------------------------------------------------------------------- P5
+def test_spline_interpolates_knots_and_linear_data():
+    rng = _rng(5)
+    x = np.sort(rng.uniform(0, 10, 64))
+    y = rng.normal(size=64)
+    M = oracle.spline_build(x, y)
+    assert M[0] == 0.0 and M[-1] == 0.0
+    np.testing.assert_allclose(oracle.spline_eval(x, y, M, x), y, rtol=0, atol=1e-14)
+    yl = 2.5 * x - 1.0
+    Ml = oracle.spline_build(x, yl)
+    t = rng.uniform(x[0], x[-1], 500)
+    np.testing.assert_allclose(oracle.spline_eval(x, yl, Ml, t), 2.5 * t - 1.0, rtol=0, atol=1e-12)
+
+
+def test_spline_exact_on_cubics_with_true_end_curvature():
+    """A cubic spline with the true end second derivatives reproduces any cubic."""
+    rng = _rng(6)
+    x = np.sort(rng.uniform(-3, 4, 40))
+    p = np.poly1d([0.7, -1.3, 0.2, 2.0])
+    y = p(x)
+    M = oracle.spline_build(x, y, M0=p.deriv(2)(x[0]), Mn=p.deriv(2)(x[-1]))
+    np.testing.assert_allclose(M, p.deriv(2)(x), rtol=0, atol=1e-10 * np.abs(M).max())
+    t = rng.uniform(x[0], x[-1], 1000)
+    np.testing.assert_allclose(oracle.spline_eval(x, y, M, t), p(t), rtol=0, atol=1e-11)
+
+
+def test_spline_matches_scipy_natural():
+    scipy_interp = pytest.importorskip("scipy.interpolate")
+    rng = _rng(8)
+    x = np.sort(rng.uniform(0, 1, 512))
+    y = np.sin(7 * x) + x ** 2
+    M = oracle.spline_build(x, y)
+    ref = scipy_interp.CubicSpline(x, y, bc_type="natural")
+    t = np.concatenate([rng.uniform(x[0], x[-1], 2000), x])
+    np.testing.assert_allclose(oracle.spline_eval(x, y, M, t), ref(t), rtol=0, atol=1e-12)
+
+
+def test_spline_paper_toy_x_squared():
+    """The paper's spline validation toy (Sec. 4.3): y = x^2 on 512 random knots.
+    A natural spline is not exact on x^2 (its end curvature is forced to 0), so
+    the residual is small but not zero and concentrated at the ends."""
+    rng = _rng(9)
+    x = np.sort(rng.uniform(0, 1, 512))
+    M = oracle.spline_build(x, x * x)
+    t = rng.uniform(x[0], x[-1], 20000)
+    rel = np.abs(oracle.spline_eval(x, x * x, M, t) - t * t) / (t * t)
+    inner = (t > 0.1) & (t < 0.9)
+    assert np.median(rel) < 1e-7
+    assert rel[inner].max() < 1e-7
+
+
+# ----------------------------------------------------------------------------- P6
+def test_bilinear_exact_on_bilinear_functions():
+    rng = _rng(10)
+    xg = np.sort(rng.uniform(0, 5, 64))
+    yg = np.sort(rng.uniform(-2, 3, 64))
+    f = lambda x, y: 0.3 - 1.1 * x + 2.2 * y + 0.7 * x * y
+    z = f(xg[:, None], yg[None, :])
+    x = rng.uniform(xg[0], xg[-1], 300)
+    y = rng.uniform(yg[0], yg[-1], 300)
+    np.testing.assert_allclose(oracle.bilinear(xg, yg, z, x, y), f(x, y), rtol=0, atol=1e-12)
+
+
+def test_bilinear_paper_toy_quadratic_error_is_second_order():
+    """z = x^2 + y^2 (Sec. 4.3 toy): bilinear error is bounded by (hx^2 + hy^2)/4."""
+    rng = _rng(11)
+    xg = np.sort(rng.uniform(0, 1, 64))
+    yg = np.sort(rng.uniform(0, 1, 64))
+    z = xg[:, None] ** 2 + yg[None, :] ** 2
+    x = rng.uniform(xg[0], xg[-1], 400)
+    y = rng.uniform(yg[0], yg[-1], 400)
+    got = oracle.bilinear(xg, yg, z, x, y)
+    ix = np.searchsorted(xg, x, side="right") - 1
+    iy = np.searchsorted(yg, y, side="right") - 1
+    hx = xg[ix + 1] - xg[ix]
+    hy = yg[iy + 1] - yg[iy]
+    err = got - (x ** 2 + y ** 2)
+    assert np.all(err >= -1e-14)  # a convex function is over-estimated by linear interpolation
+    assert np.all(err <= (hx ** 2 + hy ** 2) / 4 + 1e-14)
+
+
+# ----------------------------------------------------------------------------- P7
+def test_growth_eds_is_exactly_a():
+    a, D = oracle.growth_table(1.0, 0.0, 64, 1e-3, 1.0)
+    np.testing.assert_allclose(D, a, rtol=1e-12, atol=0)
+
+
+def test_growth_matches_heath_integral():
+    """Growing mode of the growth ODE: D(a) proportional to E(a) int_0^a da'/(a' E)^3
+    (Heath 1977), by numerical quadrature."""
+    quad = pytest.importorskip("scipy.integrate").quad
+    om, ol = 0.3, 0.7
+    E = lambda a: np.sqrt(om / a ** 3 + (1 - om - ol) / a ** 2 + ol)
+    def heath(a):
+        val, _ = quad(lambda x: 1.0 / (x * E(x)) ** 3, 0.0, a, epsabs=0, epsrel=1e-13, limit=200)
+        return E(a) * val
+    a, D = oracle.growth_table(om, ol, 512, 1e-3, 1.0)
+    h1 = heath(1.0)
+    for k in (0, 1, 100, 255, 400, 510, 511):
+        assert abs(D[k] - heath(a[k]) / h1) <= 1e-10 * D[k]
+    # open model (curvature term) at a few epochs
+    om2, ol2 = 0.25, 0.6
+    E2f = lambda a: np.sqrt(om2 / a ** 3 + (1 - om2 - ol2) / a ** 2 + ol2)
+    def heath2(a):
+        val, _ = quad(lambda x: 1.0 / (x * E2f(x)) ** 3, 0.0, a, epsabs=0, epsrel=1e-13, limit=200)
+        return E2f(a) * val
+    for a_ in (0.01, 0.3, 0.8):
+        assert abs(oracle.growth_at(a_, om2, ol2) - heath2(a_) / heath2(1.0)) <= 1e-10 * heath2(a_) / heath2(1.0)
+
+
+# ----------------------------------------------------------------------------- P8
+def test_inverse_spline_round_trip(oracle_tables):
+    t = oracle_tables
+    for k in range(t.n):
+        a, _ = t.a_of_D(t.D[k])
+        assert abs(a - t.a[k]) <= 1e-14 * t.a[k]
+    # mid-interval error against a root-find of D(a) with the same ODE
+    brentq = pytest.importorskip("scipy.optimize").brentq
+    worst = 0.0
+    for k in (3, 50, 200, 400, 505):
+        a_mid = np.sqrt(t.a[k] * t.a[k + 1])
+        D_mid = oracle.growth_at(a_mid)
+        a_spl, _ = t.a_of_D(D_mid)
+        worst = max(worst, abs(a_spl - a_mid) / a_mid)
+    assert worst < 1e-7  # natural end condition: largest near a_max
+
+
+def test_eds_branch_below_table(oracle_tables):
+    t = oracle_tables
+    a, f = t.a_of_D(0.5 * t.D[0])
+    assert f & oracle.FLAG_EDS
+    assert abs(a - 0.5 * t.a[0]) <= 1e-16
+
+
+# ----------------------------------------------------------------------------- P9
+def test_brute_force_restatement_tiny_grid(oracle_tables):
+    """8^3 points x 3 radii: oracle vs an independent NumPy/SciPy restatement
+    (eigvalsh, polynomial roots, SciPy natural spline on a growth table from the
+    Heath integral)."""
+    quad = pytest.importorskip("scipy.integrate").quad
+    CubicSpline = pytest.importorskip("scipy.interpolate").CubicSpline
+    om, ol = 0.3, 0.7
+    E = lambda a: np.sqrt(om / a ** 3 + ol)
+    heath = lambda a: E(a) * quad(lambda x: 1.0 / (x * E(x)) ** 3, 0.0, a, epsrel=1e-13, limit=200)[0]
+    a_k = np.exp(np.linspace(np.log(1e-3), 0.0, 512))
+    a_k[-1] = 1.0
+    D_k = np.array([heath(a) for a in a_k]) / heath(1.0)
+    inv = CubicSpline(D_k, a_k, bc_type="natural")
+
+    def F_ref(h):
+        lam = np.sort(np.linalg.eigvalsh(_sym(h)))[::-1]
+        l1, l2, l3 = lam
+        if l1 <= 0:
+            return 0.0
+        c3 = l1 * l2 * l3 / 9 - 5 / 21 * l1 * (l2 ** 2 + l3 ** 2)
+        c2 = -3 / 7 * l2 * l3
+        r = np.roots([c3, c2, -l1, 1.0]) if c3 != 0 else np.roots([c2, -l1, 1.0])
+        pos = [x.real for x in r if abs(x.imag) <= 1e-9 * abs(x) and 0 < x.real <= D_k[-1]]
+        if not pos:
+            return 0.0
+        Dc = min(pos)
+        a = a_k[0] * Dc / D_k[0] if Dc < D_k[0] else float(inv(Dc))
+        return 1.0 / a
+
+    n = 8 ** 3
+    sig = hessgen.sigma_schedule(3, 0.3, 4.0)
+    stack = hessgen.hessian_stack(2501, 0, sig, n)
+    F_max, idx, flags = oracle_tables.collapse_multi(stack)
+    ref_F = np.zeros(n)
+    ref_idx = np.full(n, -1)
+    for r in range(3):
+        for p in range(n):
+            F = F_ref(stack[r, :, p])
+            if F > ref_F[p]:
+                ref_F[p], ref_idx[p] = F, r
+    ok = (flags & oracle.FLAGS_AMBIGUOUS) == 0
+    assert ok.sum() > n - 3
+    np.testing.assert_allclose(F_max[ok], ref_F[ok], rtol=1e-8, atol=0)
+    assert np.array_equal(idx[ok], ref_idx[ok])
+    assert (idx >= 0).sum() > n // 4  # the case exercises collapse, not only F = 0
+
+
+# ---------------------------------------------------------------------------- P10
+def test_no_collapse_rules(oracle_tables):
+    t = oracle_tables
+    for lam in ([-0.1, -0.5, -2.0], [0.0, -1.0, -1.0], [-1e-3, -1e-3, -1e-3]):
+        H = np.diag(lam)
+        F, f = t.F_point([H[0, 0], H[1, 1], H[2, 2], 0, 0, 0])
+        assert F == 0.0 and not f & oracle.FLAG_COLLAPSED
+    hess = np.zeros((6, 5))
+    hess[0:3] = -1.0
+    F_max = np.zeros(5)
+    idx = np.full(5, -1, dtype=np.int32)
+    t.collapse_scale(hess, F_max, idx, 0)
+    t.collapse_scale(hess, F_max, idx, 1)
+    assert np.all(F_max == 0) and np.all(idx == -1)
+    # collapse after a_max (weak plane wave) also gives F = 0
+    F, f = t.F_point([0.5, 0, 0, 0, 0, 0])
+    assert F == 0.0
+
+
+def test_max_keeps_earliest_radius_on_ties(oracle_tables):
+    t = oracle_tables
+    h = np.array([[3.0], [0.5], [0.2], [0.1], [0.0], [0.0]])
+    F_max = np.zeros(1)
+    idx = np.full(1, -1, dtype=np.int32)
+    t.collapse_scale(h, F_max, idx, 4)
+    t.collapse_scale(h, F_max, idx, 5)
+    assert idx[0] == 4 and F_max[0] > 1.0
+
+
+# ---------------------------------------------------------------------------- P11
+def test_collapse_condition_is_monotone_for_sorted_eigenvalues():
+    """For l1 >= l2 >= l3 with l1 > 0 the stretch A_1(D) has no critical point
+    on D > 0: the collapse root is unique, so no tangency can occur. Checked on
+    random triples spanning extreme anisotropy."""
+    rng = _rng(12)
+    lam = rng.normal(size=(20000, 3)) * rng.lognormal(0, 2, size=(20000, 1))
+    lam *= rng.lognormal(0, 1.5, size=(20000, 3))
+    lam = -np.sort(-lam, axis=1)
+    lam = lam[lam[:, 0] > 0]
+    for l in lam[:4000]:
+        c = oracle.axis_coeffs(l, 0)
+        qa, qb, qc = 3 * c[3], 2 * c[2], c[1]  # A' = qc + qb D + qa D^2
+        assert qc < 0 and qa <= 0
+        if qb > 0:
+            assert qb * qb < 4 * qa * qc * (1 - 1e-12) or qa == 0 and qb == 0
+    # the D^2 coefficient is positive only when l2 l3 < 0
+    c2 = np.array([oracle.axis_coeffs(l, 0)[2] for l in lam[:4000]])
+    assert np.all((c2 > 0) == (lam[:4000, 1] * lam[:4000, 2] < 0))
