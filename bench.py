@@ -1,0 +1,314 @@
+#!/usr/bin/env python
+"""Benchmark of the collapse-time hot path (arXiv:2510.02873, Sec. 3 / Sec. 4.1).
+
+Workload (one step): a 256^3 grid x 25 smoothing radii, six FP64
+structure-of-arrays Hessian planes per radius (20.1 GB, resident in HBM, far
+larger than L2), s(R) log-spaced 0.2 -> 6.0, flat LCDM (Om = 0.3, OL = 0.7),
+512-knot growth table. A step is one pass of the whole path over the grid:
+reset of the two per-point maxima, then the fused launch over all radii
+(eigenvalues, LPT collapse condition, inverse-growth spline, running max).
+
+Metric: collapse evaluations (points x radii) per second on the GPU(s).
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
+(the baseline this project checks against) on bounded samples of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GRID = 256
+N_RADII = 25
+S_LO, S_HI = 0.2, 6.0
+SEED = 2512
+COSMO = dict(omega_m=0.3, omega_l=0.7, n_knots=512, a_min=1e-3, a_max=1.0)
+WORKLOAD = "collapse 256^3 grid x 25 radii, FP64 SoA Hessian planes (20.1 GB resident), 512-knot a(D) spline"
+
+# FP64 floating-point operations per (point, radius) evaluation of the FP64
+# kernel, from ncu thread-instruction counters (dadd + dmul + 2 dfma) divided
+# by the evaluations of the captured launch (profiles/collapse_fp64_kernel_*.md).
+# None until a capture of the current kernel exists.
+FP64_FLOPS_PER_EVAL = None
+# DRAM bytes (read + write) per evaluation from the same capture, or None.
+DRAM_BYTES_PER_EVAL = None
+# FP64 FMA rate of one GB300 SM: 1.25 TFLOP/s nominal at 2070 MHz over 152 SMs
+# = 3.97 flop/clk/SM, i.e. 2 DFMA per clock per SM (confirmed by a DFMA-chain probe).
+FP64_FLOP_PER_CLK_PER_SM = 4.0
+HBM_GBS = None  # filled from MEASURED_PEAKS.json when present
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    # smaller problems for profiler captures only (the benchmark workload is the default)
+    ap.add_argument("--grid", type=int, default=GRID)
+    ap.add_argument("--radii", type=int, default=N_RADII)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def cpu_oracle_rate(seconds: float, first_point: int = 0, points_per_chunk: int = 2048):
+    """The FP64 oracle on consecutive chunks of the workload's points (all 25
+    radii each), until `seconds` of CPU work. Inputs are drawn before timing."""
+    import numpy as np
+
+    import hessgen
+    import oracle
+
+    t = oracle.Tables(**{k: COSMO[k] for k in ("omega_m", "omega_l", "n_knots", "a_min", "a_max")})
+    sig = hessgen.sigma_schedule(N_RADII, S_LO, S_HI)
+    evals, elapsed, p0 = 0, 0.0, first_point
+    while evals == 0 or elapsed < seconds:
+        pts = np.arange(p0, p0 + points_per_chunk, dtype=np.int64)
+        stack = np.stack([hessgen.hessian_points(SEED, 0, r, sig[r], pts) for r in range(N_RADII)])
+        F = np.zeros(len(pts))
+        idx = np.full(len(pts), -1, dtype=np.int32)
+        t0 = time.perf_counter()
+        for r in range(N_RADII):
+            t.collapse_scale(stack[r], F, idx, r)
+        elapsed += time.perf_counter() - t0
+        evals += len(pts) * N_RADII
+        p0 += points_per_chunk
+    cores = os.cpu_count()
+    return {"value": evals / elapsed, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{p0 - first_point} points x {N_RADII} radii of the workload "
+                      f"({evals} evaluations, {elapsed:.1f} s, OpenMP over {cores} threads)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_rate(0.0, first_point=4096 * i, points_per_chunk=4096)
+        if i >= args.warmup:
+            steps.append(r)
+    evals = sum(4096 * N_RADII for _ in steps)
+    secs = sum(4096 * N_RADII / r["value"] for r in steps)
+    value = evals / secs
+    line = {
+        "impl": "reference", "metric": "collapse evals/s (points x radii)", "value": value,
+        "unit": "evals/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / len(steps), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_per_step": f"4096 points x {N_RADII} radii"},
+        "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": value, "unit": "evals/s",
+                         "sample": f"{args.steps} steps of 4096 points x {N_RADII} radii"},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import hessgen
+    import hessgen.device as hdev
+    import paper_2510_02873_gb300 as cc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cc.buildlib.build() if hasattr(cc, "buildlib") else None
+    hdev.build()
+
+    n = args.grid ** 3
+    R = args.radii
+    sig = hessgen.sigma_schedule(R, S_LO, S_HI)
+    ctx = cc.Context(**COSMO, device=local)
+    hess = torch.empty((R, 6, n), dtype=torch.float64, device=dev)
+    for r in range(R):
+        hdev.fill(hess[r], SEED, rank, r, sig[r])  # realization = rank: independent problem per GPU
+    F = torch.empty(n, dtype=torch.float64, device=dev)
+    idx = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        ctx.reset_max(F, idx)
+        if ev is not None:
+            ev[0].record(stream)
+        ctx.collapse_multi(hess, sig, F, idx)
+        if ev is not None:
+            ev[1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.reset_stats()
+    kernel_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                     for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(kernel_events[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    kernel_ms = [a.elapsed_time(b) for a, b in kernel_events]
+    stats = ctx.stats()
+    assert stats["evaluations"] == n * R * args.steps, stats
+    if world > 1:
+        tt = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+    evals_total = float(n) * R * args.steps * world
+    value = evals_total / (elapsed_ms * 1e-3)
+
+    # roofline of the dominant kernel (FP64 ALU bound)
+    kern_avg_s = statistics.mean(kernel_ms) * 1e-3
+    evals_launch = float(n) * R
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_mhz = clk.get("sm_max_mhz") or 2070.0
+    peak_tflops = FP64_FLOP_PER_CLK_PER_SM * sm_count * clk_mhz * 1e6 / 1e12
+    achieved = (FP64_FLOPS_PER_EVAL * evals_launch / kern_avg_s / 1e12) if FP64_FLOPS_PER_EVAL else None
+    roofline = {
+        "bound": "alu", "kernel": "collapse_fp64_kernel", "unit": "TFLOP/s",
+        "achieved": achieved, "peak": peak_tflops,
+        "frac": (achieved / peak_tflops) if achieved else None,
+        "peak_basis": f"FP64 {FP64_FLOP_PER_CLK_PER_SM:g} flop/clk/SM x {sm_count} SMs x {clk_mhz:.0f} MHz (max SM clock)",
+        "flops_per_eval": FP64_FLOPS_PER_EVAL,
+        "evals_per_s_kernel": evals_launch / kern_avg_s,
+        "kernel_ms": statistics.mean(kernel_ms),
+        "traffic": (DRAM_BYTES_PER_EVAL * evals_launch) if DRAM_BYTES_PER_EVAL else None,
+        "algorithmic_bytes": 48.0 * evals_launch + 12.0 * 2 * n,
+    }
+    if clk.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = (achieved / (peak_tflops * clk["sm_mhz"] / clk_mhz)) if achieved else None
+
+    result = {
+        "metric": "collapse evals/s (points x radii)", "value": value, "unit": "evals/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if (args.grid, R) == (GRID, N_RADII) else f"profiling case {args.grid}^3 x {R}", "points": n, "radii": R, "mode": "fp64",
+                   "per_gpu": "one independent realization per GPU",
+                   "l2": f"inputs {48 * n * R / 1e9:.1f} GB per step vs 129 MB L2 (no flush needed)"},
+        "roofline": roofline,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "stats": {k: stats[k] for k in ("evaluations", "collapsed", "eds_branch", "refined", "error_flags")},
+    }
+
+    # end to end through the host-buffer entry point (H2D of every radius inside the timed region)
+    if not args.no_e2e and rank == 0:
+        host = torch.empty((R, 6, n), dtype=torch.float64, pin_memory=True)
+        for r in range(R):
+            host[r].copy_(hess[r], non_blocking=False)
+        del hess
+        torch.cuda.empty_cache()
+        Fh = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        ih = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        e2e_times = []
+        for k in range(args.warmup + args.steps):
+            Fh.zero_()
+            ih.fill_(-1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.collapse_multi_host(host, sig, Fh, ih)
+            dt = time.perf_counter() - t0
+            if k >= args.warmup:
+                e2e_times.append(dt)
+        result["e2e"] = {
+            "value": float(n) * R / statistics.mean(e2e_times), "unit": "evals/s",
+            "h2d_bytes_per_step": int(host.numel() * 8 + n * 12), "d2h_bytes_per_step": int(n * 12),
+            "api": "cc_collapse_multi_host (pinned host planes, per-radius H2D overlapped with compute)",
+            "ms_per_step": 1e3 * statistics.mean(e2e_times),
+        }
+        F_check = F.cpu()
+        assert torch.equal(Fh, F_check), "e2e result differs from the device-resident run"
+        result["gpu_launches"] += R * args.steps
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and (args.grid, R) == (GRID, N_RADII):
+        result["cpu_baseline"] = cpu_oracle_rate(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

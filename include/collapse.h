@@ -1,0 +1,165 @@
+/* collapse.h -- C-ABI of libcollapse, the GB300 (sm_103a) collapse-time library.
+ *
+ * What it computes (Lepinzan et al., arXiv:2510.02873, Sec. 3 and Sec. 4.1):
+ * for every grid point p and smoothing radius r, from the six independent
+ * components of the Hessian of the smoothed potential H[r][c][p]
+ * (c = xx, yy, zz, xy, xz, yz):
+ *   1. the eigenvalues l1 >= l2 >= l3 of the symmetric 3x3 matrix (Sec. 3);
+ *   2. the growth factor at collapse D_c, the smallest positive root of the
+ *      third-order LPT stretch of axis 1 (Sec. 3, "Classic" collapse time):
+ *        A_1(D) = 1 - D l1 - 3/7 D^2 l2 l3 + D^3 [l1 l2 l3/9 - 5/21 l1 (l2^2 + l3^2)];
+ *      l1 <= 0, or D_c beyond the last table entry: no collapse, F = 0;
+ *   3. the collapse scale factor a_c = a(D_c) from a natural cubic spline of
+ *      the inverse growth function through (D(a_k), a_k), D(a) being the
+ *      solution of the linear growth ODE (Sec. 3; spline built once, Sec. 4.2);
+ *      below the first knot a_c = a_0 D_c / D(a_0);
+ *   4. F = 1/a_c = 1 + z_c, and the per-point running maxima
+ *      "F_max[p] = F, idx[p] = r if F > F_max[p]" (Sec. 4.1: read/modify/write
+ *      of two output arrays; ties keep the earlier radius).
+ *
+ * Conventions for every call:
+ *   - Device pointers are caller-owned (e.g. torch tensors); the library never
+ *     frees them and keeps no reference after the call returns. Host pointers
+ *     are read or written during the call only.
+ *   - All device work is enqueued on the caller's stream (a cudaStream_t
+ *     passed as void*, NULL = legacy default stream); calls do not
+ *     synchronise unless stated.
+ *   - Return value: CC_OK (0) or a CC_E* code; no exceptions, no exit().
+ *     cc_strerror() names the code; cc_last_error_message() gives detail.
+ *   - One context per device; a context is not thread-safe (serialise calls
+ *     on one context, or use one context per host thread).
+ *   - Plane layout: component c of point p at radius r is
+ *       hess[r * radius_stride + c * plane_stride + p]   (elements, not bytes);
+ *     plane_stride >= n, radius_stride >= 6 * plane_stride. Each plane must
+ *     start on a 16-byte boundary (so plane_stride * elem_size and
+ *     radius_stride * elem_size are multiples of 16 and hess is 16-byte
+ *     aligned); other layouts return CC_EINVAL.
+ */
+#ifndef COLLAPSE_H
+#define COLLAPSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define CC_API __attribute__((visibility("default")))
+#else
+#define CC_API
+#endif
+
+/* ---- status codes ---- */
+#define CC_OK        0
+#define CC_EINVAL    1  /* bad argument (null pointer, size, stride, alignment, mode) */
+#define CC_ECUDA     2  /* a CUDA runtime call failed (detail in cc_last_error_message) */
+#define CC_ENOMEM    3  /* device or host allocation failed */
+#define CC_ETIMEOUT  4  /* a bounded device-side wait gave up (persistent kernels) */
+#define CC_ERANGE    5  /* input outside the supported range (e.g. table bounds) */
+#define CC_ENOTSUP   6  /* mode or dtype not available in this build */
+
+/* ---- element types of the Hessian planes ---- */
+#define CC_F64 8
+#define CC_F32 4
+
+/* ---- evaluation modes ---- */
+typedef enum {
+  CC_MODE_FP64 = 0,     /* all arithmetic in FP64 (Sec. 3 "Classic" kernel)            */
+  CC_MODE_MIXED = 1,    /* FP32 bulk, FP64 for the sensitive branches                   */
+  CC_MODE_SURROGATE = 2,/* learned surrogate with exact fallback                        */
+  CC_MODE_TABULATED = 3 /* table of log D_c in (delta, x, y) (Sec. 3 "Tabulated" kernel) */
+} cc_mode;
+
+/* Flat LCDM-like background: E^2 = Om a^-3 + (1 - Om - OL) a^-2 + OL.
+ * n_knots log-spaced scale factors in [a_min, a_max] (2 <= n_knots <= 4096,
+ * 1e-5 < a_min < a_max); D is normalised to D(a = 1) = 1. */
+typedef struct {
+  double omega_m;
+  double omega_l;
+  int32_t n_knots;
+  double a_min;
+  double a_max;
+} cc_cosmology;
+
+typedef struct cc_ctx cc_ctx;
+
+/* Device-side counters accumulated by every collapse launch since the last
+ * cc_reset_stats (read with cc_get_stats, which synchronises the stream). */
+typedef struct {
+  uint64_t evaluations;   /* (point, radius) evaluations                                   */
+  uint64_t collapsed;     /* evaluations with F > 0                                         */
+  uint64_t eds_branch;    /* D_c below the first knot (a_c = a_0 D_c / D_0)                 */
+  uint64_t refined;       /* eigenvalue pairs re-solved by deflation (near-degenerate pair) */
+  uint64_t fp64_branch;   /* MIXED: points re-evaluated in FP64                             */
+  uint64_t fallback;      /* SURROGATE: points sent to the exact path                       */
+  uint32_t error_flags;   /* bit 0: bounded wait timed out; bit 1: index out of range        */
+  uint32_t reserved;
+} cc_stats;
+
+/* Create a context on `device`: solves the growth ODE in FP64 on the host,
+ * builds the natural spline of a(D) and uploads it once (Sec. 3, Sec. 4.2).
+ * Allocates device memory for the tables and counters. */
+CC_API int cc_create(cc_ctx **out, const cc_cosmology *cosmo, int device);
+
+/* Release the context and its device memory (synchronises the device). NULL is a no-op. */
+CC_API void cc_destroy(cc_ctx *ctx);
+
+/* Host only (no device needed): the library's growth table for `cosmo`,
+ * a_k and D_k with cosmo->n_knots entries each (Sec. 3: D(a) from its ODE). */
+CC_API int cc_build_growth_table(const cc_cosmology *cosmo, double *a_k, double *D_k);
+
+/* Host copies of the library's growth table: a_k and D_k (n = n_knots entries each). */
+CC_API int cc_get_growth_table(const cc_ctx *ctx, double *a_k, double *D_k, int32_t n);
+
+/* F_max[p] = 0 and idx[p] = -1 for p < n (Sec. 4.1: device array initialisation). */
+CC_API int cc_reset_max(cc_ctx *ctx, double *F_max, int32_t *idx, int64_t n, void *stream);
+
+/* One smoothing radius: evaluates F for n points of one radius and applies the
+ * running-maximum update with index scale_idx (Sec. 4.1).
+ *   hess: device, 6 planes (layout above), dtype CC_F64 or CC_F32;
+ *   sigma_R: rms of tr H at this radius; used only by MIXED (degeneracy
+ *            threshold) and SURROGATE (input normalisation), must be > 0;
+ *   F_max (FP64), idx (int32): device, n entries, updated in place. */
+CC_API int cc_collapse_scale(cc_ctx *ctx, cc_mode mode, const void *hess, int32_t dtype, int64_t n,
+                      int64_t plane_stride, double sigma_R, double *F_max, int32_t *idx,
+                      int32_t scale_idx, void *stream);
+
+/* R radii in one launch, equivalent to R calls of cc_collapse_scale with
+ * scale indices scale_idx0 .. scale_idx0 + R - 1 in that order; the running
+ * maximum is kept in registers and F_max/idx are read and written once.
+ *   sigma: host array of R values (> 0). */
+CC_API int cc_collapse_multi(cc_ctx *ctx, cc_mode mode, const void *hess, int32_t dtype, int64_t n,
+                      int64_t plane_stride, int64_t radius_stride, const double *sigma, int32_t R,
+                      double *F_max, int32_t *idx, int32_t scale_idx0, void *stream);
+
+/* Host-resident variant of cc_collapse_multi (the paper's workflow copies the
+ * Hessian planes to the device for every radius, Sec. 3 and Sec. 5.6):
+ * hess_host, F_max_host and idx_host are HOST pointers (page-locked memory
+ * gives copy/compute overlap; pageable memory works, slower). Radius planes
+ * are copied into a device double buffer on a copy stream while the previous
+ * radius is evaluated on `stream`; F_max/idx are copied in, updated on the
+ * device and copied back. Blocks until the host outputs are written.
+ * Device staging memory (2 radii of planes + outputs) is allocated on first
+ * use, grown when needed and kept by the context until cc_destroy. */
+CC_API int cc_collapse_multi_host(cc_ctx *ctx, cc_mode mode, const void *hess_host, int32_t dtype,
+                           int64_t n, int64_t plane_stride, int64_t radius_stride,
+                           const double *sigma, int32_t R, double *F_max_host, int32_t *idx_host,
+                           int32_t scale_idx0, void *stream);
+
+/* Counters since the last reset (synchronises `stream`). */
+CC_API int cc_get_stats(cc_ctx *ctx, cc_stats *out, void *stream);
+CC_API int cc_reset_stats(cc_ctx *ctx, void *stream);
+
+/* Names of status codes and the detail of the last error on this thread. */
+CC_API const char *cc_strerror(int code);
+CC_API const char *cc_last_error_message(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+CC_API int cc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COLLAPSE_H */

@@ -1,0 +1,213 @@
+"""GB300-native collapse-time library (arXiv:2510.02873 hot path) -- Python binding.
+
+The names mirror the C-ABI of include/collapse.h (cc_create, cc_collapse_scale,
+...); every step of the computation runs in libcollapse's CUDA kernels. This
+module only marshals torch tensors (device memory) and CUDA streams into the
+C calls. There is no CPU fallback: without the built library every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import CC_F32, CC_F64, MODES, CcCosmology, CcStats, CollapseError  # noqa: F401
+
+__all__ = [
+    "Context", "cc_create", "cc_destroy", "cc_reset_max", "cc_collapse_scale", "cc_collapse_multi",
+    "cc_collapse_multi_host",
+    "cc_get_stats", "cc_reset_stats", "cc_get_growth_table", "cc_build_growth_table", "cc_version", "CollapseError", "build",
+]
+
+
+def build(force: bool = False) -> str:
+    from . import buildlib as _b
+    return _b.build(force=force)
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float64:
+        return CC_F64
+    if t.dtype == torch.float32:
+        return CC_F32
+    raise TypeError(f"Hessian planes must be float64 or float32, got {t.dtype}")
+
+
+def _check_outputs(F_max, idx, n: int):
+    import torch
+    if F_max.dtype != torch.float64 or idx.dtype != torch.int32:
+        raise TypeError("F_max must be float64 and idx int32")
+    if F_max.numel() < n or idx.numel() < n or not F_max.is_contiguous() or not idx.is_contiguous():
+        raise ValueError("F_max/idx must be contiguous with at least n elements")
+    if not (F_max.is_cuda and idx.is_cuda):
+        raise ValueError("F_max/idx must be CUDA tensors")
+
+
+# ------------------------------------------------------------------ C-ABI mirrors
+def cc_create(omega_m=0.3, omega_l=0.7, n_knots=512, a_min=1e-3, a_max=1.0, device=0) -> ctypes.c_void_p:
+    L = _lib.load()
+    h = ctypes.c_void_p()
+    cosmo = CcCosmology(omega_m, omega_l, n_knots, a_min, a_max)
+    _lib.check(L.cc_create(ctypes.byref(h), ctypes.byref(cosmo), device), "cc_create")
+    return h
+
+
+def cc_destroy(ctx) -> None:
+    _lib.load().cc_destroy(ctx)
+
+
+def cc_build_growth_table(omega_m=0.3, omega_l=0.7, n_knots=512, a_min=1e-3, a_max=1.0):
+    """Host-only: the library's FP64 growth table (a_k, D_k)."""
+    a = np.empty(n_knots)
+    D = np.empty(n_knots)
+    cosmo = CcCosmology(omega_m, omega_l, n_knots, a_min, a_max)
+    _lib.check(_lib.load().cc_build_growth_table(ctypes.byref(cosmo), a.ctypes.data, D.ctypes.data),
+               "cc_build_growth_table")
+    return a, D
+
+
+def cc_get_growth_table(ctx, n_knots: int):
+    a = np.empty(n_knots)
+    D = np.empty(n_knots)
+    _lib.check(_lib.load().cc_get_growth_table(ctx, a.ctypes.data, D.ctypes.data, n_knots),
+               "cc_get_growth_table")
+    return a, D
+
+
+def cc_reset_max(ctx, F_max, idx, n=None, stream=None) -> None:
+    n = F_max.numel() if n is None else n
+    _check_outputs(F_max, idx, n)
+    _lib.check(_lib.load().cc_reset_max(ctx, F_max.data_ptr(), idx.data_ptr(), n, _stream_ptr(stream)),
+               "cc_reset_max")
+
+
+def cc_collapse_scale(ctx, mode, hess, sigma_R: float, F_max, idx, scale_idx: int, stream=None) -> None:
+    """hess: CUDA tensor (6, n) (any plane stride with unit inner stride)."""
+    if hess.dim() != 2 or hess.shape[0] != 6 or hess.stride(1) != 1:
+        raise ValueError("hess must be a (6, n) tensor with unit stride along points")
+    if not hess.is_cuda:
+        raise ValueError("hess must be a CUDA tensor")
+    n = hess.shape[1]
+    _check_outputs(F_max, idx, n)
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    _lib.check(_lib.load().cc_collapse_scale(ctx, m, hess.data_ptr(), _dtype_code(hess), n, hess.stride(0),
+                                             float(sigma_R), F_max.data_ptr(), idx.data_ptr(),
+                                             int(scale_idx), _stream_ptr(stream)), "cc_collapse_scale")
+
+
+def cc_collapse_multi(ctx, mode, hess, sigma, F_max, idx, scale_idx0: int = 0, stream=None) -> None:
+    """hess: CUDA tensor (R, 6, n) with unit stride along points."""
+    if hess.dim() != 3 or hess.shape[1] != 6 or hess.stride(2) != 1:
+        raise ValueError("hess must be a (R, 6, n) tensor with unit stride along points")
+    if not hess.is_cuda:
+        raise ValueError("hess must be a CUDA tensor")
+    R, _, n = hess.shape
+    sig = (ctypes.c_double * R)(*[float(s) for s in sigma])
+    if len(sigma) != R:
+        raise ValueError("len(sigma) must equal the number of radii")
+    _check_outputs(F_max, idx, n)
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    _lib.check(_lib.load().cc_collapse_multi(ctx, m, hess.data_ptr(), _dtype_code(hess), n, hess.stride(1),
+                                             hess.stride(0), sig, R, F_max.data_ptr(), idx.data_ptr(),
+                                             int(scale_idx0), _stream_ptr(stream)), "cc_collapse_multi")
+
+
+def cc_collapse_multi_host(ctx, mode, hess, sigma, F_max, idx, scale_idx0: int = 0, stream=None) -> None:
+    """Host-resident planes and outputs: hess (R, 6, n) CPU tensor or ndarray
+    (page-locked for copy/compute overlap), F_max float64 (n,), idx int32 (n,)
+    on the host, updated in place. Blocks until the outputs are written."""
+    import torch
+    to_t = (lambda x: torch.from_numpy(x) if isinstance(x, np.ndarray) else x)
+    hess, F_max, idx = to_t(hess), to_t(F_max), to_t(idx)
+    if hess.is_cuda or F_max.is_cuda or idx.is_cuda:
+        raise ValueError("cc_collapse_multi_host takes host tensors")
+    if hess.dim() != 3 or hess.shape[1] != 6 or hess.stride(2) != 1:
+        raise ValueError("hess must be a (R, 6, n) tensor with unit stride along points")
+    R, _, n = hess.shape
+    if len(sigma) != R:
+        raise ValueError("len(sigma) must equal the number of radii")
+    if F_max.dtype != torch.float64 or idx.dtype != torch.int32 or F_max.numel() < n or idx.numel() < n:
+        raise ValueError("F_max must be float64 and idx int32 with at least n elements")
+    sig = (ctypes.c_double * R)(*[float(s) for s in sigma])
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    _lib.check(_lib.load().cc_collapse_multi_host(ctx, m, hess.data_ptr(), _dtype_code(hess), n, hess.stride(1),
+                                                  hess.stride(0), sig, R, F_max.data_ptr(), idx.data_ptr(),
+                                                  int(scale_idx0), _stream_ptr(stream)), "cc_collapse_multi_host")
+
+
+def cc_get_stats(ctx, stream=None) -> dict:
+    st = CcStats()
+    _lib.check(_lib.load().cc_get_stats(ctx, ctypes.byref(st), _stream_ptr(stream)), "cc_get_stats")
+    return st.as_dict()
+
+
+def cc_reset_stats(ctx, stream=None) -> None:
+    _lib.check(_lib.load().cc_reset_stats(ctx, _stream_ptr(stream)), "cc_reset_stats")
+
+
+def cc_version() -> int:
+    return _lib.load().cc_version()
+
+
+# ------------------------------------------------------------------ convenience
+class Context:
+    """Owns one cc_ctx (tables on the device) for the given cosmology."""
+
+    def __init__(self, omega_m=0.3, omega_l=0.7, n_knots=512, a_min=1e-3, a_max=1.0, device=0):
+        self.n_knots = n_knots
+        self.device = device
+        self._h = cc_create(omega_m, omega_l, n_knots, a_min, a_max, device)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            cc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def growth_table(self):
+        return cc_get_growth_table(self._h, self.n_knots)
+
+    def reset_max(self, F_max, idx, stream=None):
+        cc_reset_max(self._h, F_max, idx, None, stream)
+
+    def collapse_scale(self, hess, sigma_R, F_max, idx, scale_idx, mode="fp64", stream=None):
+        cc_collapse_scale(self._h, mode, hess, sigma_R, F_max, idx, scale_idx, stream)
+
+    def collapse_multi(self, hess, sigma, F_max, idx, scale_idx0=0, mode="fp64", stream=None):
+        cc_collapse_multi(self._h, mode, hess, sigma, F_max, idx, scale_idx0, stream)
+
+    def collapse_multi_host(self, hess, sigma, F_max, idx, scale_idx0=0, mode="fp64", stream=None):
+        cc_collapse_multi_host(self._h, mode, hess, sigma, F_max, idx, scale_idx0, stream)
+
+    def stats(self, stream=None) -> dict:
+        return cc_get_stats(self._h, stream)
+
+    def reset_stats(self, stream=None):
+        cc_reset_stats(self._h, stream)

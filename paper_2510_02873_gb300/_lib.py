@@ -1,0 +1,93 @@
+"""ctypes declarations of libcollapse (include/collapse.h). Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import buildlib as _build
+
+CC_OK, CC_EINVAL, CC_ECUDA, CC_ENOMEM, CC_ETIMEOUT, CC_ERANGE, CC_ENOTSUP = range(7)
+CC_F64, CC_F32 = 8, 4
+MODES = {"fp64": 0, "mixed": 1, "surrogate": 2, "tabulated": 3}
+
+# every symbol the public header declares
+EXPORTS = (
+    "cc_create", "cc_destroy", "cc_build_growth_table", "cc_get_growth_table", "cc_reset_max", "cc_collapse_scale",
+    "cc_collapse_multi", "cc_collapse_multi_host", "cc_get_stats", "cc_reset_stats", "cc_strerror",
+    "cc_last_error_message", "cc_version",
+)
+
+
+class CcCosmology(ctypes.Structure):
+    _fields_ = [("omega_m", ctypes.c_double), ("omega_l", ctypes.c_double),
+                ("n_knots", ctypes.c_int32), ("a_min", ctypes.c_double), ("a_max", ctypes.c_double)]
+
+
+class CcStats(ctypes.Structure):
+    _fields_ = [("evaluations", ctypes.c_uint64), ("collapsed", ctypes.c_uint64),
+                ("eds_branch", ctypes.c_uint64), ("refined", ctypes.c_uint64),
+                ("fp64_branch", ctypes.c_uint64), ("fallback", ctypes.c_uint64),
+                ("error_flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "reserved"}
+
+
+class CollapseError(RuntimeError):
+    def __init__(self, code: int, what: str, detail: str):
+        super().__init__(f"{what} failed: {detail or 'status ' + str(code)} (code {code})")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load() -> ctypes.CDLL:
+    """Load the in-tree libcollapse.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"libcollapse.so not found at {path}: build it first "
+                "(python -c 'import __graft_entry__ as g; g.build()'); there is no CPU fallback")
+        L = ctypes.CDLL(path)
+        vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.cc_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(CcCosmology), ctypes.c_int]
+        L.cc_create.restype = ctypes.c_int
+        L.cc_destroy.argtypes = [vp]
+        L.cc_destroy.restype = None
+        L.cc_build_growth_table.argtypes = [ctypes.POINTER(CcCosmology), vp, vp]
+        L.cc_get_growth_table.argtypes = [vp, vp, vp, i32]
+        L.cc_reset_max.argtypes = [vp, vp, vp, i64, vp]
+        L.cc_collapse_scale.argtypes = [vp, ctypes.c_int, vp, i32, i64, i64, d, vp, vp, i32, vp]
+        L.cc_collapse_multi.argtypes = [vp, ctypes.c_int, vp, i32, i64, i64, i64,
+                                        ctypes.POINTER(d), i32, vp, vp, i32, vp]
+        L.cc_collapse_multi_host.argtypes = L.cc_collapse_multi.argtypes
+        L.cc_get_stats.argtypes = [vp, ctypes.POINTER(CcStats), vp]
+        L.cc_reset_stats.argtypes = [vp, vp]
+        L.cc_strerror.argtypes = [ctypes.c_int]
+        L.cc_strerror.restype = ctypes.c_char_p
+        L.cc_last_error_message.argtypes = []
+        L.cc_last_error_message.restype = ctypes.c_char_p
+        L.cc_version.argtypes = []
+        for name in ("cc_build_growth_table", "cc_get_growth_table", "cc_reset_max", "cc_collapse_scale",
+                     "cc_collapse_multi", "cc_collapse_multi_host",
+                     "cc_get_stats", "cc_reset_stats", "cc_version"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def check(code: int, what: str) -> None:
+    if code != CC_OK:
+        detail = load().cc_last_error_message().decode(errors="replace")
+        raise CollapseError(code, what, detail)

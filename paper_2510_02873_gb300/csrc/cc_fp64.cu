@@ -1,0 +1,142 @@
+// cc_fp64.cu -- the plain FP64 collapse kernel (arXiv:2510.02873, Sec. 4.1,
+// "Classic" kernel) and the device-array initialisation kernel.
+//
+// One thread per grid point (Sec. 4.1: "assigning the computation at each grid
+// point to an individual GPU-thread"), structure-of-arrays planes so that
+// consecutive threads read consecutive elements, the spline knots and
+// coefficients staged in shared memory once per block, and the running
+// maximum over the radii of one launch kept in registers: F_max/idx are read
+// and written once per point per launch.
+#include "cc_device.cuh"
+
+namespace cc {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ double ld(const T* p) {
+  return static_cast<double>(__ldg(p));
+}
+
+__device__ __forceinline__ void add_counters(DevCounters* cnt, unsigned evals, unsigned coll,
+                                             unsigned eds, unsigned refined) {
+  evals = __reduce_add_sync(0xffffffffu, evals);
+  coll = __reduce_add_sync(0xffffffffu, coll);
+  eds = __reduce_add_sync(0xffffffffu, eds);
+  refined = __reduce_add_sync(0xffffffffu, refined);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&cnt->evaluations, static_cast<unsigned long long>(evals));
+    if (coll) atomicAdd(&cnt->collapsed, static_cast<unsigned long long>(coll));
+    if (eds) atomicAdd(&cnt->eds_branch, static_cast<unsigned long long>(eds));
+    if (refined) atomicAdd(&cnt->refined, static_cast<unsigned long long>(refined));
+  }
+}
+
+template <typename T, bool kSmem>
+__global__ void __launch_bounds__(kThreads)
+collapse_fp64_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
+                     int64_t radius_stride, int R, int32_t scale_idx0, DevTable tab,
+                     double* __restrict__ F_max, int32_t* __restrict__ idx,
+                     DevCounters* __restrict__ cnt) {
+  extern __shared__ Coef4 smem_tab[];
+  const Coef4* coef = tab.coef;
+  const double* Dk = tab.D;
+  if constexpr (kSmem) {
+    Coef4* s_coef = smem_tab;
+    double* s_D = reinterpret_cast<double*>(smem_tab + (tab.n - 1));
+    for (int i = threadIdx.x; i < tab.n - 1; i += blockDim.x) s_coef[i] = tab.coef[i];
+    for (int i = threadIdx.x; i < tab.n; i += blockDim.x) s_D[i] = tab.D[i];
+    __syncthreads();
+    coef = s_coef;
+    Dk = s_D;
+  }
+  unsigned n_eval = 0, n_coll = 0, n_eds = 0, n_ref = 0;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  // whole warps stay in the loop together so the warp-level counter reduction
+  // at the end sees all 32 lanes
+  const int64_t n_round = (n + 31) & ~static_cast<int64_t>(31);
+  for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n_round;
+       p += stride) {
+    const bool active = p < n;
+    if (active) {
+      double Fm = F_max[p];
+      int32_t im = idx[p];
+      const T* base = hess + p;
+      for (int r = 0; r < R; ++r) {
+        const T* h = base + static_cast<int64_t>(r) * radius_stride;
+        const double xx = ld(h), yy = ld(h + plane_stride), zz = ld(h + 2 * plane_stride);
+        const double xy = ld(h + 3 * plane_stride), xz = ld(h + 4 * plane_stride);
+        const double yz = ld(h + 5 * plane_stride);
+        const PointResult res = collapse_point_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, tab);
+        n_coll += res.collapsed;
+        n_eds += res.eds;
+        n_ref += res.refined;
+        if (res.F > Fm) {
+          Fm = res.F;
+          im = scale_idx0 + r;
+        }
+      }
+      F_max[p] = Fm;
+      idx[p] = im;
+      n_eval += R;
+    }
+  }
+  add_counters(cnt, n_eval, n_coll, n_eds, n_ref);
+}
+
+__global__ void reset_max_kernel(double* __restrict__ F_max, int32_t* __restrict__ idx, int64_t n) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n; p += stride) {
+    F_max[p] = 0.0;
+    idx[p] = -1;
+  }
+}
+
+template <typename T, bool kSmem>
+int launch_typed(const LaunchArgs& a, const DevTable& tab) {
+  auto kern = collapse_fp64_kernel<T, kSmem>;
+  const size_t smem = kSmem ? (sizeof(Coef4) * (tab.n - 1) + sizeof(double) * tab.n) : 0;
+  static thread_local int occ_cache[2] = {0, 0};
+  int& occ = occ_cache[kSmem ? 1 : 0];
+  if (kSmem && smem > 48 * 1024) {
+    if (int rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(smem)),
+                            "cudaFuncSetAttribute"))
+      return rc;
+  }
+  if (occ == 0) {
+    int blocks_per_sm = 0;
+    if (int rc = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern,
+                                                                          kThreads, smem),
+                            "occupancy query"))
+      return rc;
+    occ = blocks_per_sm > 0 ? blocks_per_sm : 1;
+  }
+  const int64_t need = (a.n + kThreads - 1) / kThreads;
+  const int64_t cap = static_cast<int64_t>(a.num_sms) * occ;
+  const int grid = static_cast<int>(need < cap ? need : cap);
+  kern<<<grid, kThreads, smem, a.stream>>>(static_cast<const T*>(a.hess), a.n, a.plane_stride,
+                                           a.radius_stride, a.R, a.scale_idx0, tab, a.F_max, a.idx,
+                                           a.counters);
+  return check_cuda(cudaGetLastError(), "collapse_fp64_kernel launch");
+}
+
+}  // namespace
+
+int launch_fp64(const LaunchArgs& a, const DevTable& tab) {
+  const size_t table_bytes = sizeof(Coef4) * (tab.n - 1) + sizeof(double) * tab.n;
+  const bool smem = table_bytes <= static_cast<size_t>(kSmemTableMaxBytes);
+  if (a.dtype == CC_F64)
+    return smem ? launch_typed<double, true>(a, tab) : launch_typed<double, false>(a, tab);
+  return smem ? launch_typed<float, true>(a, tab) : launch_typed<float, false>(a, tab);
+}
+
+int launch_reset_max(double* F_max, int32_t* idx, int64_t n, cudaStream_t stream, int num_sms) {
+  const int64_t need = (n + 255) / 256;
+  const int64_t cap = static_cast<int64_t>(num_sms) * 8;
+  const int grid = static_cast<int>(need < cap ? need : cap);
+  reset_max_kernel<<<grid, 256, 0, stream>>>(F_max, idx, n);
+  return check_cuda(cudaGetLastError(), "reset_max_kernel launch");
+}
+
+}  // namespace cc

@@ -1,0 +1,94 @@
+// cc_internal.h -- internal types of libcollapse (not part of the C-ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/collapse.h"
+
+namespace cc {
+
+constexpr int kMaxKnots = 4096;
+constexpr int kThreads = 256;            // threads per block of the collapse kernels
+constexpr int kSmemTableMaxBytes = 48 * 1024;
+
+// Device-side counters; same layout as cc_stats.
+struct DevCounters {
+  unsigned long long evaluations;
+  unsigned long long collapsed;
+  unsigned long long eds_branch;
+  unsigned long long refined;
+  unsigned long long fp64_branch;
+  unsigned long long fallback;
+  unsigned int error_flags;
+  unsigned int reserved;
+};
+static_assert(sizeof(DevCounters) == sizeof(cc_stats), "counter layout must match cc_stats");
+
+// Cubic on one spline interval: c0 + c1 t + c2 t^2 + c3 t^3.
+struct alignas(32) Coef4 {
+  double c0, c1, c2, c3;
+};
+
+// Inverse growth spline on the device: knots D_k (n) and per-interval
+// polynomial coefficients a = c0 + c1 t + c2 t^2 + c3 t^3, t = D - D_k (n - 1).
+struct DevTable {
+  const double* D;      // n knots
+  const Coef4* coef;    // n - 1 intervals
+  const float* Df;      // FP32 copy of the knots (mixed mode interval search)
+  int n;
+  int search_steps;     // largest power of two <= n - 2 (branch-free search start)
+  double a0, D0, Dtop;  // first scale factor, first and last knot
+  double eds_slope;     // a0 / D0
+};
+
+// host tables (cc_tables.cpp)
+int build_growth_table(const cc_cosmology& c, std::vector<double>& a_k, std::vector<double>& D_k);
+int build_natural_spline(const std::vector<double>& x, const std::vector<double>& y,
+                         std::vector<double>& coef);
+
+// error reporting (cc_api.cu)
+int set_error(int code, const std::string& msg);
+int check_cuda(cudaError_t e, const char* what);
+
+// kernel launchers (cc_fp64.cu)
+struct LaunchArgs {
+  const void* hess;
+  int dtype;
+  int64_t n;
+  int64_t plane_stride;
+  int64_t radius_stride;
+  int R;
+  int32_t scale_idx0;
+  double* F_max;
+  int32_t* idx;
+  DevCounters* counters;
+  cudaStream_t stream;
+  int num_sms;
+};
+int launch_fp64(const LaunchArgs& a, const DevTable& tab);
+int launch_reset_max(double* F_max, int32_t* idx, int64_t n, cudaStream_t stream, int num_sms);
+
+}  // namespace cc
+
+struct cc_ctx {
+  int device = -1;
+  int num_sms = 0;
+  cc_cosmology cosmo{};
+  std::vector<double> a_k, D_k, coef;
+  void* d_table = nullptr;  // D[n] | coef[4(n-1)] | Df[n]
+  cc::DevCounters* d_counters = nullptr;
+  cc::DevTable tab{};
+  // staging of cc_collapse_multi_host (allocated on first use)
+  void* d_stage[2] = {nullptr, nullptr};
+  size_t stage_bytes = 0;
+  double* d_F = nullptr;
+  int32_t* d_idx = nullptr;
+  int64_t out_cap = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+  cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
+};

@@ -1,0 +1,134 @@
+// cc_tables.cpp -- host-side FP64 tables of libcollapse.
+//
+// The linear growth factor D(a) is the solution of the growth ODE (Sec. 3:
+// "the D(a) function is first computed by solving the ODE governing its
+// evolution, then interpolated with a cubic spline to obtain its inverse
+// a(D)"); the spline is built once on the host and copied to the device once
+// (Sec. 4.2). This file solves the ODE in the variable x = ln a for the state
+// (D, dD/dx):
+//     D_xx + (2 + dlnE/dx) D_x - 3/2 Omega_m(a) D = 0,
+//     Omega_m(a) = Omega_m a^-3 / E^2,
+// with classical RK4 on a uniform grid in x, from the matter-dominated growing
+// mode D = a, D_x = a at a = 1e-5, normalised so that D(1) = 1. The natural
+// cubic spline of a(D) through (D_k, a_k) is stored as per-interval
+// polynomials in t = D - D_k for Horner evaluation on the device.
+#include "cc_internal.h"
+
+#include <cmath>
+#include <vector>
+
+namespace cc {
+
+namespace {
+
+struct Background {
+  double om, ok, ol;
+  double E2(double a) const { return om / (a * a * a) + ok / (a * a) + ol; }
+  // d ln E / d ln a
+  double dlnE(double a) const {
+    return (-3.0 * om / (a * a * a) - 2.0 * ok / (a * a)) / (2.0 * E2(a));
+  }
+  double om_a(double a) const { return om / (a * a * a) / E2(a); }
+};
+
+constexpr double kAStart = 1e-5;
+constexpr double kMaxStep = 5e-5;  // largest RK4 step in ln a
+
+// y = (D, D_x); returns dy/dx at x = ln a
+inline void rhs(const Background& bg, double x, const double y[2], double dy[2]) {
+  const double a = std::exp(x);
+  dy[0] = y[1];
+  dy[1] = -(2.0 + bg.dlnE(a)) * y[1] + 1.5 * bg.om_a(a) * y[0];
+}
+
+// advance y from x0 to x1 with uniform RK4 steps no longer than kMaxStep
+void advance(const Background& bg, double x0, double x1, double y[2]) {
+  if (!(x1 > x0)) return;
+  const long steps = static_cast<long>(std::ceil((x1 - x0) / kMaxStep));
+  const double h = (x1 - x0) / static_cast<double>(steps);
+  for (long s = 0; s < steps; ++s) {
+    const double x = x0 + h * static_cast<double>(s);
+    double k1[2], k2[2], k3[2], k4[2], t[2];
+    rhs(bg, x, y, k1);
+    for (int i = 0; i < 2; ++i) t[i] = y[i] + 0.5 * h * k1[i];
+    rhs(bg, x + 0.5 * h, t, k2);
+    for (int i = 0; i < 2; ++i) t[i] = y[i] + 0.5 * h * k2[i];
+    rhs(bg, x + 0.5 * h, t, k3);
+    for (int i = 0; i < 2; ++i) t[i] = y[i] + h * k3[i];
+    rhs(bg, x + h, t, k4);
+    for (int i = 0; i < 2; ++i) y[i] += h * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]) / 6.0;
+  }
+}
+
+}  // namespace
+
+int build_growth_table(const cc_cosmology& c, std::vector<double>& a_k, std::vector<double>& D_k) {
+  const int n = c.n_knots;
+  if (n < 2 || n > kMaxKnots || !(c.a_min > kAStart) || !(c.a_max > c.a_min) ||
+      !std::isfinite(c.omega_m) || !std::isfinite(c.omega_l) || !(c.omega_m > 0.0))
+    return CC_EINVAL;
+  Background bg{c.omega_m, 1.0 - c.omega_m - c.omega_l, c.omega_l};
+  a_k.resize(n);
+  D_k.resize(n);
+  const double xlo = std::log(c.a_min), xhi = std::log(c.a_max);
+  double y[2] = {kAStart, kAStart};
+  double x = std::log(kAStart);
+  for (int k = 0; k < n; ++k) {
+    const double xk = (k == n - 1) ? xhi : xlo + (xhi - xlo) * k / (n - 1);
+    advance(bg, x, xk, y);
+    x = xk;
+    a_k[k] = (k == n - 1) ? c.a_max : std::exp(xk);
+    D_k[k] = y[0];
+  }
+  // normalisation D(a = 1) = 1
+  double y1[2] = {kAStart, kAStart};
+  advance(bg, std::log(kAStart), 0.0, y1);
+  for (int k = 0; k < n; ++k) D_k[k] /= y1[0];
+  for (int k = 0; k + 1 < n; ++k)
+    if (!(D_k[k + 1] > D_k[k]) || !std::isfinite(D_k[k])) return CC_ERANGE;
+  return CC_OK;
+}
+
+// Natural cubic spline y(x) through (x_k, y_k): solve for the knot slopes'
+// second derivatives s_k (s_0 = s_{n-1} = 0) of the tridiagonal system
+//   (x_k - x_{k-1}) s_{k-1} + 2 (x_{k+1} - x_{k-1}) s_k + (x_{k+1} - x_k) s_{k+1}
+//       = 6 (slope_k - slope_{k-1}),
+// then expand interval k as y_k + b t + c t^2 + d t^3, t = x - x_k.
+int build_natural_spline(const std::vector<double>& x, const std::vector<double>& y,
+                         std::vector<double>& coef /* 4 per interval */) {
+  const int n = static_cast<int>(x.size());
+  if (n < 2) return CC_EINVAL;
+  std::vector<double> h(n - 1), slope(n - 1), s(n, 0.0);
+  for (int k = 0; k + 1 < n; ++k) {
+    h[k] = x[k + 1] - x[k];
+    if (!(h[k] > 0.0)) return CC_EINVAL;
+    slope[k] = (y[k + 1] - y[k]) / h[k];
+  }
+  if (n > 2) {
+    const int m = n - 2;  // unknowns s_1 .. s_{n-2}
+    std::vector<double> diag(m), upper(m), rhs(m);
+    for (int i = 0; i < m; ++i) {
+      diag[i] = 2.0 * (h[i] + h[i + 1]);
+      upper[i] = h[i + 1];
+      rhs[i] = 6.0 * (slope[i + 1] - slope[i]);
+    }
+    // elimination of the sub-diagonal h[i] of row i against row i-1
+    for (int i = 1; i < m; ++i) {
+      const double f = h[i] / diag[i - 1];
+      diag[i] -= f * upper[i - 1];
+      rhs[i] -= f * rhs[i - 1];
+    }
+    s[m] = rhs[m - 1] / diag[m - 1];
+    for (int i = m - 2; i >= 0; --i) s[i + 1] = (rhs[i] - upper[i] * s[i + 2]) / diag[i];
+  }
+  coef.resize(4 * (n - 1));
+  for (int k = 0; k + 1 < n; ++k) {
+    coef[4 * k + 0] = y[k];
+    coef[4 * k + 1] = slope[k] - h[k] * (2.0 * s[k] + s[k + 1]) / 6.0;
+    coef[4 * k + 2] = 0.5 * s[k];
+    coef[4 * k + 3] = (s[k + 1] - s[k]) / (6.0 * h[k]);
+  }
+  return CC_OK;
+}
+
+}  // namespace cc
