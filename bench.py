@@ -37,9 +37,11 @@ WORKLOAD = "collapse 256^3 grid x 25 radii, FP64 SoA Hessian planes (20.1 GB res
 # kernel, from ncu thread-instruction counters (dadd + dmul + 2 dfma) divided
 # by the evaluations of the captured launch (profiles/collapse_fp64_kernel_*.md).
 # None until a capture of the current kernel exists.
-FP64_FLOPS_PER_EVAL = None
-# DRAM bytes (read + write) per evaluation from the same capture, or None.
-DRAM_BYTES_PER_EVAL = None
+FP64_FLOPS_PER_EVAL = 81.0   # profiles/collapse_fp64_kernel_128cube_x4.md
+# DRAM traffic of the same capture, split into per-evaluation (planes) and
+# per-point (F_max/idx read + write) parts to scale it to the full launch.
+DRAM_BYTES_PER_EVAL = 48.4
+DRAM_BYTES_PER_POINT = 24.8
 # FP64 FMA rate of one GB300 SM: 1.25 TFLOP/s nominal at 2070 MHz over 152 SMs
 # = 3.97 flop/clk/SM, i.e. 2 DFMA per clock per SM (confirmed by a DFMA-chain probe).
 FP64_FLOP_PER_CLK_PER_SM = 4.0
@@ -74,11 +76,14 @@ class ClockSampler:
         self.proc = None
 
     def start(self):
+        """Start sampling; returns once the first sample has arrived, so that
+        nvidia-smi's start-up does not fall inside the timed region."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
                 text=True)
+            self.first = self.proc.stdout.readline()
         except OSError:
             self.proc = None
 
@@ -93,7 +98,7 @@ class ClockSampler:
             out, _ = self.proc.communicate()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
+        for line in (self.first + out).strip().splitlines():
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -253,7 +258,8 @@ def main():
         "flops_per_eval": FP64_FLOPS_PER_EVAL,
         "evals_per_s_kernel": evals_launch / kern_avg_s,
         "kernel_ms": statistics.mean(kernel_ms),
-        "traffic": (DRAM_BYTES_PER_EVAL * evals_launch) if DRAM_BYTES_PER_EVAL else None,
+        "traffic": (DRAM_BYTES_PER_EVAL * evals_launch + DRAM_BYTES_PER_POINT * n) if DRAM_BYTES_PER_EVAL else None,
+        "traffic_basis": "ncu dram bytes of a 128^3 x 4 capture, scaled per evaluation and per point",
         "algorithmic_bytes": 48.0 * evals_launch + 12.0 * 2 * n,
     }
     if clk.get("sm_mhz"):

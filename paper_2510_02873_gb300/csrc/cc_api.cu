@@ -165,11 +165,28 @@ int cc_create(cc_ctx** out, const cc_cosmology* cosmo, int device) {
   if ((rc = check_cuda(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device),
                        "cudaDeviceGetAttribute"))) { delete ctx; return rc; }
   const int n = cosmo->n_knots;
-  // device layout: coef[n-1] (32-byte aligned) | D[n] | Df[n]
+  // FP32 interval search: uniform buckets in log2 D, each holding the largest
+  // knot index k with D_k <= the bucket's lower edge
+  const int nb = kBucketsPerKnot * n;
+  const double l2lo = std::log2(ctx->D_k[0]), l2hi = std::log2(ctx->D_k[n - 1]);
+  const double width = (l2hi - l2lo) / nb;
+  std::vector<unsigned short> bucket(nb);
+  {
+    int k = 0;
+    for (int b = 0; b < nb; ++b) {
+      const double edge = std::exp2(l2lo + width * b);
+      while (k + 1 <= n - 2 && ctx->D_k[k + 1] <= edge) ++k;
+      bucket[b] = static_cast<unsigned short>(k);
+    }
+  }
+  std::vector<float> df(n);
+  for (int k = 0; k < n; ++k) df[k] = static_cast<float>(ctx->D_k[k]);
+  // device layout: coef[n-1] (32-byte aligned) | D[n] | Df[n] | bucket[nb]
   const size_t coef_bytes = sizeof(Coef4) * (n - 1);
   const size_t d_bytes = sizeof(double) * n;
   const size_t df_bytes = sizeof(float) * n;
-  const size_t total = coef_bytes + d_bytes + df_bytes;
+  const size_t b_bytes = sizeof(unsigned short) * nb;
+  const size_t total = coef_bytes + d_bytes + df_bytes + b_bytes;
   if ((rc = check_cuda(cudaMalloc(&ctx->d_table, total), "cudaMalloc(table)"))) { delete ctx; return rc; }
   if ((rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&ctx->d_counters), sizeof(DevCounters)),
                        "cudaMalloc(counters)"))) {
@@ -180,9 +197,8 @@ int cc_create(cc_ctx** out, const cc_cosmology* cosmo, int device) {
   std::vector<unsigned char> host(total);
   std::memcpy(host.data(), ctx->coef.data(), coef_bytes);
   std::memcpy(host.data() + coef_bytes, ctx->D_k.data(), d_bytes);
-  std::vector<float> df(n);
-  for (int k = 0; k < n; ++k) df[k] = static_cast<float>(ctx->D_k[k]);
   std::memcpy(host.data() + coef_bytes + d_bytes, df.data(), df_bytes);
+  std::memcpy(host.data() + coef_bytes + d_bytes + df_bytes, bucket.data(), b_bytes);
   rc = check_cuda(cudaMemcpy(ctx->d_table, host.data(), total, cudaMemcpyHostToDevice), "cudaMemcpy(table)");
   if (!rc) rc = check_cuda(cudaMemset(ctx->d_counters, 0, sizeof(DevCounters)), "cudaMemset(counters)");
   if (rc) { cc_destroy(ctx); return rc; }
@@ -191,10 +207,11 @@ int cc_create(cc_ctx** out, const cc_cosmology* cosmo, int device) {
   t.coef = reinterpret_cast<const Coef4*>(base);
   t.D = reinterpret_cast<const double*>(base + coef_bytes);
   t.Df = reinterpret_cast<const float*>(base + coef_bytes + d_bytes);
+  t.bucket = reinterpret_cast<const unsigned short*>(base + coef_bytes + d_bytes + df_bytes);
   t.n = n;
-  int steps = 0;
-  if (n - 2 >= 1) { steps = 1; while (steps * 2 <= n - 2) steps *= 2; }
-  t.search_steps = steps;
+  t.n_buckets = nb;
+  t.log2_D0 = static_cast<float>(l2lo);
+  t.inv_bucket_width = static_cast<float>(1.0 / width);
   t.a0 = ctx->a_k[0];
   t.D0 = ctx->D_k[0];
   t.Dtop = ctx->D_k[n - 1];

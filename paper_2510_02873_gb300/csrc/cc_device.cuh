@@ -1,27 +1,40 @@
-// cc_device.cuh -- FP64 device arithmetic of the collapse-time path.
+// cc_device.cuh -- device arithmetic of the collapse-time path.
 //
 // Per point (arXiv:2510.02873, Sec. 3): eigenvalues of the symmetric 3x3
 // Hessian (closed-form trigonometric solve, sorted descending), the
-// third-order LPT collapse condition solved as a cubic, and the natural cubic
-// spline a(D) of the inverse growth function. Control flow is predicated
-// where the paper asks for masked execution (Sec. 4.1); the only real branch
-// is the rare near-degenerate eigenvalue pair.
+// third-order LPT collapse condition solved for the growth factor at
+// collapse, and the natural cubic spline a(D) of the inverse growth function.
+//
+// GB300 executes FP64 at 1/64 of the FP32 rate (2 FP64 lanes per clock per
+// SM), so a warp-wide FP64 instruction holds an SM sub-partition's FP64 unit
+// for ~64 cycles while ~63 other instructions can issue. The FP64 routines
+// below are therefore written to minimise FP64 instructions: every
+// approximation (eigenvalue seeds, the cubic's root, interval search, the
+// reciprocals of derivatives) is computed in FP32, and FP64 is spent only on
+// the quantities that set the final accuracy (matrix invariants, Newton
+// corrections, the cubic coefficients, the spline polynomial). Tests on signs,
+// ranges and the running maximum compare FP64 bit patterns as integers
+// (monotone for non-negative doubles), which costs no FP64 instruction.
+// Control flow is predicated (Sec. 4.1); the only branches are the rare
+// near-degenerate eigenvalue pair and the EdS range below the table.
 #pragma once
 
 #include "cc_internal.h"
 
 namespace cc {
 
-constexpr double kSqrt3 = 1.7320508075688772935;
-// 1 + r below this: l1 and l2 nearly coincide and acos(r) loses accuracy in
-// the pair; they are re-solved by deflation (1 + r ~ 4.5 theta^2, eigenvalue
-// error ~ 0.2 eps p / theta, so 1e-8 keeps it below ~1e-12 p).
-constexpr double kPairTau = 1e-8;
+constexpr float kSqrt3f = 1.7320508075688772935f;
+// 1 + r (FP32) below this: l1 and l2 are too close for a Newton step from the
+// FP32 trigonometric seed to converge quadratically; the pair is re-solved by
+// deflation in FP64 instead (about 3e-4 of isotropic Gaussian points).
+constexpr float kPairTauF = 1e-4f;
 
-// Re-solve l1 >= l2 when they are nearly equal: l3 (isolated, accurate from
-// the trigonometric solve) gives an eigenvector v3 as the largest cross
-// product of two rows of A - l3 I; A restricted to the plane orthogonal to v3
-// is a 2x2 symmetric matrix whose eigenvalues follow without cancellation.
+__device__ __forceinline__ long long bits(double x) { return __double_as_longlong(x); }
+
+// Re-solve l1 >= l2 when they are nearly equal: l3 (isolated) gives an
+// eigenvector v3 as the largest cross product of two rows of A - l3 I; A
+// restricted to the plane orthogonal to v3 is a 2x2 symmetric matrix whose
+// eigenvalues follow without cancellation (mean +- hypot(half difference, off-diagonal)).
 __device__ __noinline__ void refine_top_pair(double xx, double yy, double zz, double xy, double xz,
                                              double yz, double l3, double& l1, double& l2) {
   const double r0x = xx - l3, r0y = xy, r0z = xz;
@@ -36,11 +49,10 @@ __device__ __noinline__ void refine_top_pair(double xx, double yy, double zz, do
   double vx = ax, vy = ay, vz = az, nv = na;
   if (nb > nv) { vx = bx; vy = by; vz = bz; nv = nb; }
   if (nc > nv) { vx = cx; vy = cy; vz = cz; nv = nc; }
-  if (!(nv > 0.0)) return;  // l3 not isolated either: all equal, keep the trigonometric values
+  if (!(nv > 0.0)) return;  // l3 not isolated either: all equal, keep the incoming values
   const double iv = rsqrt(nv);
   vx *= iv; vy *= iv; vz *= iv;
-  // u orthogonal to v, then w = v x u
-  double ux, uy, uz;
+  double ux, uy, uz;  // u orthogonal to v, then w = v x u
   if (fabs(vx) > fabs(vy)) {
     const double iu = rsqrt(vx * vx + vz * vz);
     ux = -vz * iu; uy = 0.0; uz = vx * iu;
@@ -64,85 +76,42 @@ __device__ __noinline__ void refine_top_pair(double xx, double yy, double zz, do
   l2 = mean - rad;
 }
 
-// Eigenvalues l1 >= l2 >= l3 of [[xx,xy,xz],[xy,yy,yz],[xz,yz,zz]] by the
-// trigonometric solution of the characteristic cubic (Smith 1961):
-//   q = tr/3, p^2 = (|A - qI|_F^2)/6, r = det(A - qI) / (2 p^3),
-//   phi = acos(r)/3, l1 = q + 2p cos(phi), l3 = q + 2p cos(phi + 2pi/3),
-//   l2 = q + 2p cos(phi - 2pi/3);
-// the two shifted cosines come from one sincos by the angle-sum identity.
-// Returns true when the near-degenerate top pair was re-solved.
-__device__ __forceinline__ bool eigen_sym3(double xx, double yy, double zz, double xy, double xz,
-                                           double yz, double& l1, double& l2, double& l3) {
-  const double q = (xx + yy + zz) * (1.0 / 3.0);
-  const double a = xx - q, b = yy - q, c = zz - q;
-  const double p2 = (a * a + b * b + c * c + 2.0 * (xy * xy + xz * xz + yz * yz)) * (1.0 / 6.0);
-  const double p = sqrt(p2);
-  const double det = a * (b * c - yz * yz) - xy * (xy * c - yz * xz) + xz * (xy * yz - b * xz);
-  double r = (p2 > 0.0) ? det / (2.0 * p2 * p) : 0.0;
-  r = fmin(1.0, fmax(-1.0, r));
-  const double phi = acos(r) * (1.0 / 3.0);
-  double s, co;
-  sincos(phi, &s, &co);
-  l1 = fma(2.0 * p, co, q);
-  l2 = fma(p, fma(kSqrt3, s, -co), q);   // q + 2p cos(phi - 2pi/3)
-  l3 = fma(-p, fma(kSqrt3, s, co), q);   // q + 2p cos(phi + 2pi/3)
-  const bool pair = (1.0 + r) < kPairTau && p2 > 0.0;
-  if (pair) refine_top_pair(xx, yy, zz, xy, xz, yz, l3, l1, l2);
-  return pair;
-}
-
-// Collapse growth factor (Sec. 3, Classic: third-order LPT stretch of the
-// axis with the largest eigenvalue). With u = 1/D the condition A_1(D) = 0
-// becomes the monic cubic
-//   P(u) = u^3 - l1 u^2 + c2 u + c3,  c2 = -3/7 l2 l3,
-//   c3 = l1 (l2 l3 / 9 - 5/21 (l2^2 + l3^2)).
-// For l1 > 0 the collapse root is unique (A_1 is strictly decreasing on D > 0),
-// so D_c = 1/u* with u* the largest real root of P: closed form (Cardano when
-// one root is real, trigonometric when three are), then Newton polish.
-__device__ __forceinline__ double collapse_u_fp64(double l1, double l2, double l3) {
-  const double b = -l1;
-  const double c = (-3.0 / 7.0) * (l2 * l3);
-  const double d = l1 * ((l2 * l3) * (1.0 / 9.0) - (5.0 / 21.0) * (l2 * l2 + l3 * l3));
-  const double b3 = b * (1.0 / 3.0);
-  const double pp = c - b * b3;                                  // c - b^2/3
-  const double qq = b3 * (2.0 * b3 * b3 - c) + d;                 // 2b^3/27 - bc/3 + d
-  const double disc = 0.25 * qq * qq + pp * pp * pp * (1.0 / 27.0);
-  double t;
-  if (disc > 0.0) {
-    const double A = cbrt(0.5 * fabs(qq) + sqrt(disc));
-    const double C = (qq > 0.0) ? -A : A;
-    t = (C != 0.0) ? C - pp / (3.0 * C) : 0.0;
+// Largest real root of the monic cubic u^3 + b u^2 + c u + d (FP32 closed
+// form): Cardano's formula when one root is real, the trigonometric form when
+// three are.
+__device__ __forceinline__ float cubic_largest_root_f32(float b, float c, float d) {
+  const float b3 = b * (1.0f / 3.0f);
+  const float pp = c - b * b3;
+  const float qq = b3 * (2.0f * b3 * b3 - c) + d;
+  const float disc = 0.25f * qq * qq + pp * pp * pp * (1.0f / 27.0f);
+  float t;
+  if (disc > 0.0f) {
+    const float A = cbrtf(0.5f * fabsf(qq) + sqrtf(disc));
+    const float C = (qq > 0.0f) ? -A : A;
+    t = (C != 0.0f) ? C - pp / (3.0f * C) : 0.0f;
   } else {
-    const double m = sqrt(-pp * (1.0 / 3.0));
-    double arg = (m > 0.0) ? (-0.5 * qq) / (m * m * m) : 0.0;
-    arg = fmin(1.0, fmax(-1.0, arg));
-    t = 2.0 * m * cos(acos(arg) * (1.0 / 3.0));
+    const float m = sqrtf(-pp * (1.0f / 3.0f));
+    float arg = (m > 0.0f) ? (-0.5f * qq) / (m * m * m) : 0.0f;
+    arg = fminf(1.0f, fmaxf(-1.0f, arg));
+    t = 2.0f * m * cosf(acosf(arg) * (1.0f / 3.0f));
   }
-  double u = t - b3;
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const double P = fma(fma(u + b, u, c), u, d);
-    const double dP = fma(fma(3.0, u, 2.0 * b), u, c);
-    u = (dP != 0.0) ? u - P / dP : u;
-  }
-  return u;
+  return t - b3;
 }
 
-// a(D) from the natural spline; interval k = largest with D_k <= D (clamped),
-// found by a branch-free binary search; below the first knot a = a0 D / D0.
-__device__ __forceinline__ double a_of_D_fp64(const double* __restrict__ Dk,
-                                              const Coef4* __restrict__ coef,
-                                              const DevTable& tab, double D, bool& eds) {
-  int k = 0;
-  for (int step = tab.search_steps; step > 0; step >>= 1) {
-    const int j = k + step;
-    k = (j <= tab.n - 2 && Dk[j] <= D) ? j : k;
-  }
-  const double t = D - Dk[k];
-  const Coef4 cf = coef[k];
-  const double a_spl = fma(fma(fma(cf.c3, t, cf.c2), t, cf.c1), t, cf.c0);
-  eds = D < tab.D0;
-  return eds ? tab.eds_slope * D : a_spl;
+// Interval of the a(D) spline holding D (FP32 search on FP32 knots): a bucket
+// of the uniform grid in log2 D gives a first interval, two predicated steps
+// finish. Near a knot the FP32 decision may pick the neighbouring interval;
+// the spline is C2 there, so the value changes only by |jump of c3| |t|^3,
+// far below FP64 rounding.
+__device__ __forceinline__ int spline_interval(const float* __restrict__ Dkf,
+                                               const unsigned short* __restrict__ bucket,
+                                               const DevTable& tab, float Df) {
+  float fb = (__log2f(Df) - tab.log2_D0) * tab.inv_bucket_width;
+  fb = fminf(fmaxf(fb, 0.0f), static_cast<float>(tab.n_buckets - 1));
+  int k = bucket[static_cast<int>(fb)];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) k += (k < tab.n - 2 && Dkf[k + 1] <= Df) ? 1 : 0;
+  return k;
 }
 
 struct PointResult {
@@ -150,22 +119,105 @@ struct PointResult {
   bool collapsed, eds, refined;
 };
 
-// Full per-point collapse value F = 1/a_c (or 0 for no collapse).
-__device__ __forceinline__ PointResult collapse_point_fp64(double xx, double yy, double zz, double xy,
-                                                           double xz, double yz,
-                                                           const double* __restrict__ Dk,
-                                                           const Coef4* __restrict__ coef,
-                                                           const DevTable& tab) {
+// FP64 collapse value of one point, F = 1/a_c (0 when there is no collapse).
+//   eigenvalues: invariants of M = A - qI in FP64 (q = tr/3, s6 = |M|_F^2 = 6 p^2,
+//     det M); l1 = q + x with x the largest root of x^3 - 3 p^2 x - det M = 0,
+//     seeded by the FP32 trigonometric solution and corrected by two FP64
+//     Newton steps (FP32 derivative at each iterate); l2 l3 and l2^2 + l3^2
+//     from the invariants
+//     (l2 + l3 = 2q - x, l2 l3 = q (q - x) + x^2 - 3 p^2);
+//   collapse: A_1(D) = 1 - l1 D + c2 D^2 + c3 D^3, root seeded in FP32 from the
+//     FP64 coefficients rounded to FP32 (closed form in u = 1/D, two FP32
+//     Newton steps) and corrected by one FP64 Newton step;
+//   spline: interval from the FP32 search, FP64 Horner; F by one FP64 Newton
+//     step of the reciprocal from the FP32 reciprocal.
+__device__ __forceinline__ PointResult collapse_point_fp64(
+    double xx, double yy, double zz, double xy, double xz, double yz, const double* __restrict__ Dk,
+    const Coef4* __restrict__ coef, const float* __restrict__ Dkf,
+    const unsigned short* __restrict__ bucket, const DevTable& tab) {
   PointResult res;
-  double l1, l2, l3;
-  res.refined = eigen_sym3(xx, yy, zz, xy, xz, yz, l1, l2, l3);
-  const double u = collapse_u_fp64(l1, l2, l3);
-  const double Dc = 1.0 / u;
-  res.collapsed = (l1 > 0.0) && (u > 0.0) && (Dc <= tab.Dtop);
-  bool eds;
-  const double a = a_of_D_fp64(Dk, coef, tab, res.collapsed ? Dc : tab.Dtop, eds);
-  res.eds = eds && res.collapsed;
-  res.F = res.collapsed ? 1.0 / a : 0.0;
+  // ---- invariants (FP64)
+  const double q = (xx + yy + zz) * (1.0 / 3.0);
+  const double a = xx - q, b = yy - q, c = zz - q;
+  const double diag = fma(c, c, fma(b, b, a * a));
+  const double off = fma(yz, yz, fma(xz, xz, xy * xy));
+  const double s6 = fma(2.0, off, diag);  // 6 p^2
+  const double p2x3 = 0.5 * s6;           // 3 p^2
+  const double det = fma(xz, fma(xy, yz, -b * xz), fma(a, fma(b, c, -yz * yz), -xy * fma(xy, c, -yz * xz)));
+  // ---- FP32 trigonometric seed
+  const float p2f = static_cast<float>(s6) * (1.0f / 6.0f);
+  const float detf = static_cast<float>(det);
+  const float pf = sqrtf(p2f);
+  float rf = (p2f > 0.0f) ? detf / (2.0f * p2f * pf) : 0.0f;
+  rf = fminf(1.0f, fmaxf(-1.0f, rf));
+  float sn, cs;
+  sincosf(acosf(rf) * (1.0f / 3.0f), &sn, &cs);
+  const float x1f = 2.0f * pf * cs;                   // l1 - q
+  const float x3f = -pf * fmaf(kSqrt3f, sn, cs);      // l3 - q
+  // ---- FP64 Newton on g(x) = x (x^2 - 3p^2) - det; each step takes its
+  // derivative 3 (x^2 - p^2) in FP32 at the current iterate
+  double x = static_cast<double>(x1f);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const float xf = (it == 0) ? x1f : static_cast<float>(x);
+    const float gpf = 3.0f * (xf * xf - p2f);
+    const double yg = static_cast<double>((gpf != 0.0f) ? 1.0f / gpf : 0.0f);
+    const double g = fma(x, x * x - p2x3, -det);
+    x = fma(-g, yg, x);
+  }
+  res.refined = (1.0f + rf) < kPairTauF && p2f > 0.0f;
+  if (res.refined) {
+    // l1 ~ l2: refine the isolated l3 by Newton (FP64 derivative), then deflate
+    double x3 = static_cast<double>(x3f);
+#pragma unroll
+    for (int it = 0; it < 3; ++it) {
+      const double x32 = x3 * x3;
+      x3 -= fma(x3, x32 - p2x3, -det) / (3.0 * x32 - p2x3);
+    }
+    double l1r = q + x, l2r = 0.0;
+    refine_top_pair(xx, yy, zz, xy, xz, yz, q + x3, l1r, l2r);
+    x = l1r - q;
+  }
+  // ---- collapse condition coefficients (FP64)
+  const double lam1 = q + x;
+  const double Pp = fma(q, q - x, fma(x, x, -p2x3));  // l2 l3
+  const double S = fma(2.0, q, -x);                    // l2 + l3
+  const double Q2 = fma(-2.0, Pp, S * S);              // l2^2 + l3^2
+  const double c2 = (-3.0 / 7.0) * Pp;
+  const double c3 = lam1 * fma(-5.0 / 21.0, Q2, Pp * (1.0 / 9.0));
+  // ---- FP32 root seed from the FP64 coefficients rounded to FP32: largest
+  // root of u^3 - l1 u^2 + c2 u + c3 (u = 1/D), polished on A_1(D) in FP32
+  const float l1f = static_cast<float>(lam1);
+  const float c2f = static_cast<float>(c2);
+  const float c3f = static_cast<float>(c3);
+  const float uf = cubic_largest_root_f32(-l1f, c2f, c3f);
+  float Df = 1.0f / uf;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const float Af = fmaf(fmaf(fmaf(c3f, Df, c2f), Df, -l1f), Df, 1.0f);
+    const float dAf = fmaf(fmaf(3.0f * c3f, Df, 2.0f * c2f), Df, -l1f);
+    Df -= Af / dAf;
+  }
+  const float dAf = fmaf(fmaf(3.0f * c3f, Df, 2.0f * c2f), Df, -l1f);
+  // ---- one FP64 Newton step on A_1
+  double D = static_cast<double>(Df);
+  const double A1 = fma(fma(fma(c3, D, c2), D, -lam1), D, 1.0);
+  D = fma(-A1, static_cast<double>(1.0f / dAf), D);
+  // ---- collapse test on bit patterns: l1 > 0, 0 < D <= D_top
+  const long long bD = bits(D);
+  res.collapsed = bits(lam1) > 0 && bD > 0 && bD <= bits(tab.Dtop);
+  const double Dc = res.collapsed ? D : tab.Dtop;
+  // ---- a(D): FP32 interval search, FP64 Horner
+  const int k = spline_interval(Dkf, bucket, tab, static_cast<float>(Dc));
+  const Coef4 cf = coef[k];
+  const double t = Dc - Dk[k];
+  double av = fma(fma(fma(cf.c3, t, cf.c2), t, cf.c1), t, cf.c0);
+  res.eds = res.collapsed && bits(Dc) < bits(tab.D0);
+  if (res.eds) av = tab.eds_slope * Dc;
+  // ---- F = 1/a: FP32 reciprocal + one FP64 Newton step
+  const double y0 = static_cast<double>(1.0f / static_cast<float>(av));
+  const double F = fma(y0, fma(-av, y0, 1.0), y0);
+  res.F = res.collapsed ? F : 0.0;
   return res;
 }
 

@@ -41,14 +41,23 @@ collapse_fp64_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride
   extern __shared__ Coef4 smem_tab[];
   const Coef4* coef = tab.coef;
   const double* Dk = tab.D;
+  const float* Dkf = tab.Df;
+  const unsigned short* bucket = tab.bucket;
   if constexpr (kSmem) {
-    Coef4* s_coef = smem_tab;
-    double* s_D = reinterpret_cast<double*>(smem_tab + (tab.n - 1));
-    for (int i = threadIdx.x; i < tab.n - 1; i += blockDim.x) s_coef[i] = tab.coef[i];
-    for (int i = threadIdx.x; i < tab.n; i += blockDim.x) s_D[i] = tab.D[i];
+    // the table image (coef | D | Df | bucket) is contiguous: copy it in 16-byte words
+    const int words = static_cast<int>(tab.bytes() / 16);
+    const uint4* src = reinterpret_cast<const uint4*>(tab.coef);
+    uint4* dst = reinterpret_cast<uint4*>(smem_tab);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+    const size_t tail = tab.bytes() & 15;
+    if (threadIdx.x < tail)
+      reinterpret_cast<unsigned char*>(dst + words)[threadIdx.x] =
+          reinterpret_cast<const unsigned char*>(src + words)[threadIdx.x];
     __syncthreads();
-    coef = s_coef;
-    Dk = s_D;
+    coef = smem_tab;
+    Dk = reinterpret_cast<const double*>(smem_tab + (tab.n - 1));
+    Dkf = reinterpret_cast<const float*>(Dk + tab.n);
+    bucket = reinterpret_cast<const unsigned short*>(Dkf + tab.n);
   }
   unsigned n_eval = 0, n_coll = 0, n_eds = 0, n_ref = 0;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -67,11 +76,11 @@ collapse_fp64_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride
         const double xx = ld(h), yy = ld(h + plane_stride), zz = ld(h + 2 * plane_stride);
         const double xy = ld(h + 3 * plane_stride), xz = ld(h + 4 * plane_stride);
         const double yz = ld(h + 5 * plane_stride);
-        const PointResult res = collapse_point_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, tab);
+        const PointResult res = collapse_point_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
         n_coll += res.collapsed;
         n_eds += res.eds;
         n_ref += res.refined;
-        if (res.F > Fm) {
+        if (bits(res.F) > bits(Fm)) {  // both >= 0: integer order == value order
           Fm = res.F;
           im = scale_idx0 + r;
         }
@@ -95,7 +104,7 @@ __global__ void reset_max_kernel(double* __restrict__ F_max, int32_t* __restrict
 template <typename T, bool kSmem>
 int launch_typed(const LaunchArgs& a, const DevTable& tab) {
   auto kern = collapse_fp64_kernel<T, kSmem>;
-  const size_t smem = kSmem ? (sizeof(Coef4) * (tab.n - 1) + sizeof(double) * tab.n) : 0;
+  const size_t smem = kSmem ? ((tab.bytes() + 15) / 16) * 16 : 0;
   static thread_local int occ_cache[2] = {0, 0};
   int& occ = occ_cache[kSmem ? 1 : 0];
   if (kSmem && smem > 48 * 1024) {
@@ -124,8 +133,7 @@ int launch_typed(const LaunchArgs& a, const DevTable& tab) {
 }  // namespace
 
 int launch_fp64(const LaunchArgs& a, const DevTable& tab) {
-  const size_t table_bytes = sizeof(Coef4) * (tab.n - 1) + sizeof(double) * tab.n;
-  const bool smem = table_bytes <= static_cast<size_t>(kSmemTableMaxBytes);
+  const bool smem = tab.bytes() <= static_cast<size_t>(kSmemTableMaxBytes);
   if (a.dtype == CC_F64)
     return smem ? launch_typed<double, true>(a, tab) : launch_typed<double, false>(a, tab);
   return smem ? launch_typed<float, true>(a, tab) : launch_typed<float, false>(a, tab);

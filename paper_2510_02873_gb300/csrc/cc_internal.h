@@ -13,7 +13,8 @@ namespace cc {
 
 constexpr int kMaxKnots = 4096;
 constexpr int kThreads = 256;            // threads per block of the collapse kernels
-constexpr int kSmemTableMaxBytes = 48 * 1024;
+constexpr int kSmemTableMaxBytes = 64 * 1024;
+constexpr int kBucketsPerKnot = 4;  // log2-D buckets per knot (bucket finer than knot spacing)
 
 // Device-side counters; same layout as cc_stats.
 struct DevCounters {
@@ -36,13 +37,20 @@ struct alignas(32) Coef4 {
 // Inverse growth spline on the device: knots D_k (n) and per-interval
 // polynomial coefficients a = c0 + c1 t + c2 t^2 + c3 t^3, t = D - D_k (n - 1).
 struct DevTable {
-  const double* D;      // n knots
-  const Coef4* coef;    // n - 1 intervals
-  const float* Df;      // FP32 copy of the knots (mixed mode interval search)
+  const Coef4* coef;              // n - 1 intervals
+  const double* D;                // n knots
+  const float* Df;                // FP32 copy of the knots (interval search)
+  const unsigned short* bucket;   // n_buckets: largest k with D_k <= bucket's lower edge
   int n;
-  int search_steps;     // largest power of two <= n - 2 (branch-free search start)
-  double a0, D0, Dtop;  // first scale factor, first and last knot
-  double eds_slope;     // a0 / D0
+  int n_buckets;                  // uniform buckets in log2 D over [D_0, D_top]
+  float log2_D0, inv_bucket_width;
+  double a0, D0, Dtop;            // first scale factor, first and last knot
+  double eds_slope;               // a0 / D0
+  // bytes of the table image (coef | D | Df | bucket), staged in shared memory
+  __host__ __device__ size_t bytes() const {
+    return sizeof(Coef4) * (n - 1) + sizeof(double) * n + sizeof(float) * n +
+           sizeof(unsigned short) * n_buckets;
+  }
 };
 
 // host tables (cc_tables.cpp)
@@ -79,7 +87,7 @@ struct cc_ctx {
   int num_sms = 0;
   cc_cosmology cosmo{};
   std::vector<double> a_k, D_k, coef;
-  void* d_table = nullptr;  // D[n] | coef[4(n-1)] | Df[n]
+  void* d_table = nullptr;  // coef[n-1] | D[n] | Df[n] | bucket[n_buckets]
   cc::DevCounters* d_counters = nullptr;
   cc::DevTable tab{};
   // staging of cc_collapse_multi_host (allocated on first use)

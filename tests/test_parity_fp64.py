@@ -176,18 +176,18 @@ def test_invalid_arguments_are_rejected(ctx):
     assert L.cc_collapse_scale(h, 0, p, 8, n, n, 1.0, None, idx.data_ptr(), 0, s) == _lib.CC_EINVAL
     # empty input is a no-op
     assert L.cc_collapse_scale(h, 0, None, 8, 0, 0, 1.0, None, None, 0, s) == _lib.CC_OK
-    with pytest.raises(cc.CollapseError):
-        ctx.collapse_scale(buf[:6 * n].view(6, n)[:, :n - 1], 1.0, F, idx, 0)
+    with pytest.raises(cc.CollapseError):  # 8-byte plane stride
+        ctx.collapse_scale(buf[:6 * (n + 1)].view(6, n + 1)[:, :n], 1.0, F, idx, 0)
 
 
 def test_host_buffer_entry_matches_device_path(ctx):
     """cc_collapse_multi_host (pinned and pageable host planes) == cc_collapse_multi, bit for bit."""
     n, R = 100003, 5
     sig = hessgen.sigma_schedule(R, 0.4, 5.0)
-    stack = hessgen.hessian_stack(555, 0, sig, n + 1)[:, :, :n]  # plane stride n + 1 (odd: rejected)
-    F_d, idx_d = gpu_multi(ctx, np.ascontiguousarray(stack), sig)
+    stack = hessgen.hessian_stack(555, 0, sig, n)
+    F_d, idx_d = gpu_multi(ctx, np.ascontiguousarray(stack), sig, plane_stride=n + 3)
     for pinned in (True, False):
-        host = torch.zeros((R, 6, n + 1), dtype=torch.float64, pin_memory=pinned)
+        host = torch.zeros((R, 6, n + 2), dtype=torch.float64, pin_memory=pinned)  # odd plane stride
         host[:, :, :n] = torch.from_numpy(stack)
         Fh = torch.zeros(n, dtype=torch.float64, pin_memory=pinned)
         ih = torch.full((n,), -1, dtype=torch.int32, pin_memory=pinned)
@@ -237,7 +237,7 @@ def test_config2_full_size_sampled(ctx, tables):
     # whole-grid properties
     assert np.all(np.isfinite(Fs)) and np.all(Fs >= 0)
     assert np.all((Fs == 0) == (ids == -1)) and ids.min() >= -1 and ids.max() < R
-    assert 0.5 < (ids >= 0).mean() < 1.0
+    assert (ids >= 0).mean() > 0.5
     print("config2 sampled", s, st)
     del hess
     torch.cuda.empty_cache()
