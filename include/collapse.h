@@ -148,6 +148,30 @@ CC_API int cc_collapse_multi_host(cc_ctx *ctx, cc_mode mode, const void *hess_ho
                            const double *sigma, int32_t R, double *F_max_host, int32_t *idx_host,
                            int32_t scale_idx0, void *stream);
 
+/* No counterpart in the paper. A variant of cc_collapse_multi for callers that
+ * cannot allocate device memory (code under CUDA stream capture, code whose
+ * device memory is owned by another framework's allocator, or loops that cannot
+ * take cudaMalloc's implicit synchronisation). It needs no context and makes no
+ * allocation of any kind: the spline table for `cosmo` and the launch counters
+ * live in a file-scope static device array of 53.5 KB that every GPU loading
+ * the library holds until exit. Inputs and outputs are the caller's device
+ * buffers, as for cc_collapse_multi (same layout rules and results).
+ *   cosmo: host; n_knots must be <= 1024, larger tables return CC_EINVAL.
+ *   mode: CC_MODE_FP64 only (others return CC_ENOTSUP).
+ *   stats: host, may be NULL; when given, receives this call's counters and
+ *          the call synchronises `stream`.
+ * All calls on a device share the array and it keeps the last call's contents:
+ * the counters are cleared at the start of each call, and the table is copied
+ * in again when the cosmology changes. Calls that overlap on the GPU (other
+ * streams, or another cosmology in flight) race on it. The first call on each
+ * device looks up the array's address and uploads the table: make it before
+ * any stream capture begins. */
+CC_API int cc_collapse_multi_noalloc(const cc_cosmology *cosmo, cc_mode mode, const void *hess,
+                              int32_t dtype, int64_t n, int64_t plane_stride,
+                              int64_t radius_stride, const double *sigma, int32_t R,
+                              double *F_max, int32_t *idx, int32_t scale_idx0, cc_stats *stats,
+                              void *stream);
+
 /* Counters since the last reset (synchronises `stream`). */
 CC_API int cc_get_stats(cc_ctx *ctx, cc_stats *out, void *stream);
 CC_API int cc_reset_stats(cc_ctx *ctx, void *stream);

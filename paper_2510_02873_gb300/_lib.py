@@ -14,7 +14,7 @@ MODES = {"fp64": 0, "mixed": 1, "surrogate": 2, "tabulated": 3}
 # every symbol the public header declares
 EXPORTS = (
     "cc_create", "cc_destroy", "cc_build_growth_table", "cc_get_growth_table", "cc_reset_max", "cc_collapse_scale",
-    "cc_collapse_multi", "cc_collapse_multi_host", "cc_get_stats", "cc_reset_stats", "cc_strerror",
+    "cc_collapse_multi", "cc_collapse_multi_host", "cc_collapse_multi_noalloc", "cc_get_stats", "cc_reset_stats", "cc_strerror",
     "cc_last_error_message", "cc_version",
 )
 
@@ -72,6 +72,8 @@ def load() -> ctypes.CDLL:
         L.cc_collapse_multi.argtypes = [vp, ctypes.c_int, vp, i32, i64, i64, i64,
                                         ctypes.POINTER(d), i32, vp, vp, i32, vp]
         L.cc_collapse_multi_host.argtypes = L.cc_collapse_multi.argtypes
+        L.cc_collapse_multi_noalloc.argtypes = [ctypes.POINTER(CcCosmology), ctypes.c_int, vp, i32, i64, i64, i64,
+                                                ctypes.POINTER(d), i32, vp, vp, i32, ctypes.POINTER(CcStats), vp]
         L.cc_get_stats.argtypes = [vp, ctypes.POINTER(CcStats), vp]
         L.cc_reset_stats.argtypes = [vp, vp]
         L.cc_strerror.argtypes = [ctypes.c_int]
@@ -80,7 +82,7 @@ def load() -> ctypes.CDLL:
         L.cc_last_error_message.restype = ctypes.c_char_p
         L.cc_version.argtypes = []
         for name in ("cc_build_growth_table", "cc_get_growth_table", "cc_reset_max", "cc_collapse_scale",
-                     "cc_collapse_multi", "cc_collapse_multi_host",
+                     "cc_collapse_multi", "cc_collapse_multi_host", "cc_collapse_multi_noalloc",
                      "cc_get_stats", "cc_reset_stats", "cc_version"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L

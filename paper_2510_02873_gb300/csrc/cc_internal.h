@@ -57,6 +57,9 @@ struct DevTable {
 int build_growth_table(const cc_cosmology& c, std::vector<double>& a_k, std::vector<double>& D_k);
 int build_natural_spline(const std::vector<double>& x, const std::vector<double>& y,
                          std::vector<double>& coef);
+// the same, into caller-provided arrays (no allocation); work holds 6 n doubles
+int growth_table_into(const cc_cosmology& c, double* a_k, double* D_k);
+int natural_spline_into(int n, const double* x, const double* y, double* coef, double* work);
 
 // error reporting (cc_api.cu)
 int set_error(int code, const std::string& msg);

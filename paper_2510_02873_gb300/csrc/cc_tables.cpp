@@ -62,14 +62,12 @@ void advance(const Background& bg, double x0, double x1, double y[2]) {
 
 }  // namespace
 
-int build_growth_table(const cc_cosmology& c, std::vector<double>& a_k, std::vector<double>& D_k) {
+int growth_table_into(const cc_cosmology& c, double* a_k, double* D_k) {
   const int n = c.n_knots;
   if (n < 2 || n > kMaxKnots || !(c.a_min > kAStart) || !(c.a_max > c.a_min) ||
       !std::isfinite(c.omega_m) || !std::isfinite(c.omega_l) || !(c.omega_m > 0.0))
     return CC_EINVAL;
   Background bg{c.omega_m, 1.0 - c.omega_m - c.omega_l, c.omega_l};
-  a_k.resize(n);
-  D_k.resize(n);
   const double xlo = std::log(c.a_min), xhi = std::log(c.a_max);
   double y[2] = {kAStart, kAStart};
   double x = std::log(kAStart);
@@ -89,16 +87,28 @@ int build_growth_table(const cc_cosmology& c, std::vector<double>& a_k, std::vec
   return CC_OK;
 }
 
+int build_growth_table(const cc_cosmology& c, std::vector<double>& a_k, std::vector<double>& D_k) {
+  if (c.n_knots < 2 || c.n_knots > kMaxKnots) return CC_EINVAL;
+  a_k.resize(c.n_knots);
+  D_k.resize(c.n_knots);
+  return growth_table_into(c, a_k.data(), D_k.data());
+}
+
 // Natural cubic spline y(x) through (x_k, y_k): solve for the knot slopes'
 // second derivatives s_k (s_0 = s_{n-1} = 0) of the tridiagonal system
 //   (x_k - x_{k-1}) s_{k-1} + 2 (x_{k+1} - x_{k-1}) s_k + (x_{k+1} - x_k) s_{k+1}
 //       = 6 (slope_k - slope_{k-1}),
 // then expand interval k as y_k + b t + c t^2 + d t^3, t = x - x_k.
-int build_natural_spline(const std::vector<double>& x, const std::vector<double>& y,
-                         std::vector<double>& coef /* 4 per interval */) {
-  const int n = static_cast<int>(x.size());
+int natural_spline_into(int n, const double* x, const double* y, double* coef, double* work) {
   if (n < 2) return CC_EINVAL;
-  std::vector<double> h(n - 1), slope(n - 1), s(n, 0.0);
+  // work: h, slope (n - 1 each), s (n), diag, upper, rhs (n - 2 each)
+  double* h = work;
+  double* slope = h + (n - 1);
+  double* s = slope + (n - 1);
+  double* diag = s + n;
+  double* upper = diag + (n - 2 > 0 ? n - 2 : 0);
+  double* rhs = upper + (n - 2 > 0 ? n - 2 : 0);
+  for (int k = 0; k < n; ++k) s[k] = 0.0;
   for (int k = 0; k + 1 < n; ++k) {
     h[k] = x[k + 1] - x[k];
     if (!(h[k] > 0.0)) return CC_EINVAL;
@@ -106,7 +116,6 @@ int build_natural_spline(const std::vector<double>& x, const std::vector<double>
   }
   if (n > 2) {
     const int m = n - 2;  // unknowns s_1 .. s_{n-2}
-    std::vector<double> diag(m), upper(m), rhs(m);
     for (int i = 0; i < m; ++i) {
       diag[i] = 2.0 * (h[i] + h[i + 1]);
       upper[i] = h[i + 1];
@@ -121,7 +130,6 @@ int build_natural_spline(const std::vector<double>& x, const std::vector<double>
     s[m] = rhs[m - 1] / diag[m - 1];
     for (int i = m - 2; i >= 0; --i) s[i + 1] = (rhs[i] - upper[i] * s[i + 2]) / diag[i];
   }
-  coef.resize(4 * (n - 1));
   for (int k = 0; k + 1 < n; ++k) {
     coef[4 * k + 0] = y[k];
     coef[4 * k + 1] = slope[k] - h[k] * (2.0 * s[k] + s[k + 1]) / 6.0;
@@ -129,6 +137,15 @@ int build_natural_spline(const std::vector<double>& x, const std::vector<double>
     coef[4 * k + 3] = (s[k + 1] - s[k]) / (6.0 * h[k]);
   }
   return CC_OK;
+}
+
+int build_natural_spline(const std::vector<double>& x, const std::vector<double>& y,
+                         std::vector<double>& coef /* 4 per interval */) {
+  const int n = static_cast<int>(x.size());
+  if (n < 2) return CC_EINVAL;
+  std::vector<double> work(6 * static_cast<size_t>(n));
+  coef.resize(4 * static_cast<size_t>(n - 1));
+  return natural_spline_into(n, x.data(), y.data(), coef.data(), work.data());
 }
 
 }  // namespace cc
