@@ -38,10 +38,10 @@ WORKLOAD = "collapse 256^3 grid x 25 radii, FP64 SoA Hessian planes (20.1 GB res
 # by the evaluations of the captured launch (profiles/collapse_fp64_kernel_*.md).
 # None until a capture of the current kernel exists.
 FP64_FLOPS_PER_EVAL = 81.0   # profiles/collapse_fp64_kernel_128cube_x4.md
-# DRAM traffic of the same capture, split into per-evaluation (planes) and
-# per-point (F_max/idx read + write) parts to scale it to the full launch.
-DRAM_BYTES_PER_EVAL = 48.4
-DRAM_BYTES_PER_POINT = 24.8
+FP64_FLOPS_PER_EVAL_MIXED = 16.1  # profiles/collapse_kernel_mixed_256cube_x4.md
+# DRAM bytes (read + write) of one full launch of the default workload, from
+# an ncu capture of that launch (profiles/collapse_kernel_fp64_256cube_x25_dram.md).
+TRAFFIC_BYTES_DEFAULT = 20.80e9
 # FP64 FMA rate of one GB300 SM: 1.25 TFLOP/s nominal at 2070 MHz over 152 SMs
 # = 3.97 flop/clk/SM, i.e. 2 DFMA per clock per SM (confirmed by a DFMA-chain probe).
 FP64_FLOP_PER_CLK_PER_SM = 4.0
@@ -57,9 +57,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-variants", action="store_true")
     # smaller problems for profiler captures only (the benchmark workload is the default)
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--radii", type=int, default=N_RADII)
+    ap.add_argument("--mode", choices=["fp64", "mixed"], default="fp64")
     return ap.parse_args()
 
 
@@ -169,6 +171,152 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- mixed variant
+MIXED_GRID, MIXED_RADII = 512, 30
+
+
+def run_mixed_variant(ctx, dev, stream, reps: int = 3) -> dict:
+    """Mixed precision (FP32 planes, FP64 only where it sets accuracy) on a
+    512^3 x 30 grid (96.6 GB of FP32 planes), timed like the main workload and
+    compared with the FP64 kernel on the same planes (which agrees with the
+    FP64 oracle to ~1e-13)."""
+    import torch
+
+    import hessgen
+    import hessgen.device as hdev
+
+    n, R = MIXED_GRID ** 3, MIXED_RADII
+    sig = hessgen.sigma_schedule(R, S_LO, S_HI)
+    hess = torch.empty((R, 6, n), dtype=torch.float32, device=dev)
+    for r in range(R):
+        hdev.fill(hess[r], SEED + 1, 0, r, sig[r])
+    out = {}
+    F = {}
+    for mode in ("fp64", "mixed"):
+        Fm = torch.empty(n, dtype=torch.float64, device=dev)
+        im = torch.empty(n, dtype=torch.int32, device=dev)
+        ctx.reset_max(Fm, im)
+        ctx.collapse_multi(hess, sig, Fm, im, mode=mode)  # warm-up
+        times = []
+        ctx.reset_stats()
+        for _ in range(reps):
+            ctx.reset_max(Fm, im)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.collapse_multi(hess, sig, Fm, im, mode=mode)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        st = ctx.stats()
+        F[mode] = (Fm, im)
+        out[mode] = {"kernel_ms": statistics.mean(times), "evals_per_s": n * R / (statistics.mean(times) * 1e-3),
+                     "fp64_branch_fraction": st["fp64_branch"] / st["evaluations"]}
+    Fr, ir = F["fp64"]
+    Fx, ix = F["mixed"]
+    nz = Fr > 0
+    rel = torch.where(nz, (Fx - Fr).abs() / torch.where(nz, Fr, torch.ones_like(Fr)), (Fx - Fr).abs())
+    edge = ((Fr > 0) & (Fr < 1.0 + 1.2e-4)) | ((Fx > 0) & (Fx < 1.0 + 1.2e-4))
+    rel_ok = rel[~edge]
+    del hess
+    torch.cuda.empty_cache()
+    return {
+        "workload": f"{MIXED_GRID}^3 grid x {MIXED_RADII} radii, FP32 SoA planes (96.6 GB resident)",
+        "evals_per_s": out["mixed"]["evals_per_s"], "kernel_ms": out["mixed"]["kernel_ms"],
+        "fp64_kernel_same_planes_evals_per_s": out["fp64"]["evals_per_s"],
+        "speedup_vs_fp64_kernel": out["fp64"]["kernel_ms"] / out["mixed"]["kernel_ms"],
+        "max_rel_diff_vs_fp64": float(rel_ok.max()), "rms_rel_diff_vs_fp64": float(rel_ok.pow(2).mean().sqrt()),
+        "edge_points_excluded": int(edge.sum()),
+        "argmax_diff_fraction": float((ix != ir).double().mean()),
+        "fp64_branch_fraction": out["mixed"]["fp64_branch_fraction"],
+        "bound_tol": 3e-5,
+    }
+
+
+# ----------------------------------------------------------------------------- batched variant
+BATCH_SEED, BATCH_N = 2514, 48
+BATCH_GRIDS = (64, 96, 128, 192, 256, 384)
+
+
+def run_batch_variant(ctx, dev, stream, reps: int = 3) -> dict:
+    """48 realizations, grids drawn from {64..384}^3 and 8..40 radii (seeded),
+    FP32 planes (240.5 GB resident), mixed precision: one persistent launch
+    replayed from a CUDA graph with autotuned tiles, against one
+    cc_collapse_multi launch per realization on the same data."""
+    import numpy as np
+    import torch
+
+    import hessgen
+    import hessgen.device as hdev
+    import paper_2510_02873_gb300 as cc
+
+    rng = np.random.default_rng(BATCH_SEED)
+    grids = rng.choice(BATCH_GRIDS, BATCH_N)
+    radii = rng.integers(8, 41, BATCH_N)
+    items = []
+    for k, (g, R) in enumerate(zip(grids, radii)):
+        n, R = int(g) ** 3, int(R)
+        sig = hessgen.sigma_schedule(R, S_LO, S_HI)
+        hess = torch.empty((R, 6, n), dtype=torch.float32, device=dev)
+        for r in range(R):
+            hdev.fill(hess[r], BATCH_SEED, k, r, sig[r])
+        items.append((hess, sig, torch.zeros(n, dtype=torch.float64, device=dev),
+                      torch.full((n,), -1, dtype=torch.int32, device=dev)))
+    evals = int(sum(h.shape[0] * h.shape[2] for h, *_ in items))
+
+    def reset():
+        for _, _, F, idx in items:
+            F.zero_()
+            idx.fill_(-1)
+
+    batch = cc.Batch(ctx, items, mode="mixed")
+    t0 = time.perf_counter()
+    batch.autotune(None, stream)
+    tune_s = time.perf_counter() - t0
+    blk, tiles = batch.config()
+    reset()
+    side = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(side):
+        batch.run_graph(side)  # capture + first replay
+        side.synchronize()
+        graph_ms = []
+        for _ in range(reps):
+            reset()
+            side.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(side)
+            batch.run_graph(side)
+            e1.record(side)
+            side.synchronize()
+            graph_ms.append(e0.elapsed_time(e1))
+    F_batch = [F.clone() for _, _, F, _ in items]
+    # baseline: one fused launch per realization
+    loop_ms = []
+    for _ in range(reps):
+        reset()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for hess, sig, F, idx in items:
+            ctx.collapse_multi(hess, sig, F, idx, mode="mixed")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        loop_ms.append(e0.elapsed_time(e1))
+    same = all(torch.equal(a, F) for a, (_, _, F, _) in zip(F_batch, items))
+    batch.close()
+    del items, F_batch
+    torch.cuda.empty_cache()
+    g, l = statistics.mean(graph_ms), statistics.mean(loop_ms)
+    return {
+        "workload": f"{BATCH_N} realizations, grids {{64..384}}^3, 8..40 radii (seed {BATCH_SEED}), "
+                    f"{evals} evaluations, FP32 planes ({evals * 24 / 1e9:.1f} GB resident), mixed precision",
+        "evals_per_s": evals / (g * 1e-3), "graph_replay_ms": g,
+        "per_realization_launches_ms": l, "speedup_vs_per_realization": l / g,
+        "results_identical_to_per_realization": bool(same),
+        "autotune_s": tune_s, "threads_per_block": blk,
+        "tile_points_by_grid": {int(n): t for n, t in sorted(set((int(gg) ** 3, t) for gg, t in zip(grids, tiles)))},
+    }
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -197,7 +345,8 @@ def main():
     R = args.radii
     sig = hessgen.sigma_schedule(R, S_LO, S_HI)
     ctx = cc.Context(**COSMO, device=local)
-    hess = torch.empty((R, 6, n), dtype=torch.float64, device=dev)
+    plane_dtype = torch.float64 if args.mode == "fp64" else torch.float32
+    hess = torch.empty((R, 6, n), dtype=plane_dtype, device=dev)
     for r in range(R):
         hdev.fill(hess[r], SEED, rank, r, sig[r])  # realization = rank: independent problem per GPU
     F = torch.empty(n, dtype=torch.float64, device=dev)
@@ -208,7 +357,7 @@ def main():
         ctx.reset_max(F, idx)
         if ev is not None:
             ev[0].record(stream)
-        ctx.collapse_multi(hess, sig, F, idx)
+        ctx.collapse_multi(hess, sig, F, idx, mode=args.mode)
         if ev is not None:
             ev[1].record(stream)
 
@@ -249,17 +398,18 @@ def main():
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     clk_mhz = clk.get("sm_max_mhz") or 2070.0
     peak_tflops = FP64_FLOP_PER_CLK_PER_SM * sm_count * clk_mhz * 1e6 / 1e12
-    achieved = (FP64_FLOPS_PER_EVAL * evals_launch / kern_avg_s / 1e12) if FP64_FLOPS_PER_EVAL else None
+    fpe = FP64_FLOPS_PER_EVAL if args.mode == "fp64" else FP64_FLOPS_PER_EVAL_MIXED
+    achieved = fpe * evals_launch / kern_avg_s / 1e12
     roofline = {
-        "bound": "alu", "kernel": "collapse_fp64_kernel", "unit": "TFLOP/s",
+        "bound": "alu", "kernel": f"collapse_kernel ({args.mode})", "unit": "TFLOP/s",
         "achieved": achieved, "peak": peak_tflops,
         "frac": (achieved / peak_tflops) if achieved else None,
         "peak_basis": f"FP64 {FP64_FLOP_PER_CLK_PER_SM:g} flop/clk/SM x {sm_count} SMs x {clk_mhz:.0f} MHz (max SM clock)",
-        "flops_per_eval": FP64_FLOPS_PER_EVAL,
+        "flops_per_eval": fpe,
         "evals_per_s_kernel": evals_launch / kern_avg_s,
         "kernel_ms": statistics.mean(kernel_ms),
-        "traffic": (DRAM_BYTES_PER_EVAL * evals_launch + DRAM_BYTES_PER_POINT * n) if DRAM_BYTES_PER_EVAL else None,
-        "traffic_basis": "ncu dram bytes of a 128^3 x 4 capture, scaled per evaluation and per point",
+        "traffic": TRAFFIC_BYTES_DEFAULT if ((args.grid, R) == (GRID, N_RADII) and args.mode == "fp64") else None,
+        "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full launch",
         "algorithmic_bytes": 48.0 * evals_launch + 12.0 * 2 * n,
     }
     if clk.get("sm_mhz"):
@@ -270,7 +420,7 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if (args.grid, R) == (GRID, N_RADII) else f"profiling case {args.grid}^3 x {R}", "points": n, "radii": R, "mode": "fp64",
+        "config": {"workload": WORKLOAD if (args.grid, R) == (GRID, N_RADII) else f"profiling case {args.grid}^3 x {R}", "points": n, "radii": R, "mode": args.mode,
                    "per_gpu": "one independent realization per GPU",
                    "l2": f"inputs {48 * n * R / 1e9:.1f} GB per step vs 129 MB L2 (no flush needed)"},
         "roofline": roofline,
@@ -280,7 +430,7 @@ def main():
     }
 
     # end to end through the host-buffer entry point (H2D of every radius inside the timed region)
-    if not args.no_e2e and rank == 0:
+    if not args.no_e2e and rank == 0 and args.mode == "fp64":
         host = torch.empty((R, 6, n), dtype=torch.float64, pin_memory=True)
         for r in range(R):
             host[r].copy_(hess[r], non_blocking=False)
@@ -307,6 +457,12 @@ def main():
         F_check = F.cpu()
         assert torch.equal(Fh, F_check), "e2e result differs from the device-resident run"
         result["gpu_launches"] += R * args.steps
+    if rank == 0 and not args.no_variants and (args.grid, R) == (GRID, N_RADII) and args.mode == "fp64":
+        if "hess" in locals():
+            del hess
+        torch.cuda.empty_cache()
+        result["variants"] = {"mixed": run_mixed_variant(ctx, dev, stream)}
+        result["variants"]["batched"] = run_batch_variant(ctx, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and (args.grid, R) == (GRID, N_RADII):
         result["cpu_baseline"] = cpu_oracle_rate(args.cpu_seconds)
     if rank == 0:

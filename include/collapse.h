@@ -172,6 +172,54 @@ CC_API int cc_collapse_multi_noalloc(const cc_cosmology *cosmo, cc_mode mode, co
                               double *F_max, int32_t *idx, int32_t scale_idx0, cc_stats *stats,
                               void *stream);
 
+/* ---- batches of independent realizations (one persistent launch) ----
+ * Many realizations of uneven grid sizes and radius counts (e.g. a set of
+ * simulation boxes) are evaluated by ONE persistent kernel: its CTAs take
+ * tiles of points from a device work counter until every tile of every
+ * realization is done, each tile running all radii of its realization with
+ * the running maximum in registers (the per-point work of Sec. 4.1). */
+typedef struct {
+  const void *hess;       /* device planes of this realization (layout as cc_collapse_multi) */
+  int32_t dtype;          /* CC_F64 or CC_F32 */
+  int64_t n;              /* points */
+  int64_t plane_stride;   /* elements between component planes (16-byte aligned planes) */
+  int64_t radius_stride;  /* elements between radii */
+  int32_t R;              /* radii, 1..256 */
+  const double *sigma;    /* host, R values > 0 (copied at cc_batch_create) */
+  double *F_max;          /* device, n entries, updated in place */
+  int32_t *idx;           /* device, n entries, updated in place */
+  int32_t scale_idx0;     /* index of this realization's first radius */
+} cc_batch_item;
+
+typedef struct cc_batch cc_batch;
+
+/* Validate the items and build a plan: the item table, per-radius parameters
+ * and a work counter are copied to device memory owned by the plan (allocated
+ * here). The device buffers the items point to must outlive the plan. */
+CC_API int cc_batch_create(cc_ctx *ctx, cc_mode mode, const cc_batch_item *items, int32_t nitems,
+                           cc_batch **out);
+
+/* Autotuner: per size class (realizations grouped by ceil(log2 n)) picks the
+ * points per tile, and for the whole batch the threads per block, by timing
+ * candidate launches on the class's own realizations (this runs the kernel and
+ * therefore updates their F_max/idx; reset them afterwards). With cache_path
+ * non-NULL, choices are read from / appended to that text file, keyed by GPU
+ * name, mode and class. Synchronises `stream`. */
+CC_API int cc_batch_autotune(cc_batch *b, const char *cache_path, void *stream);
+
+/* One persistent launch over all items on `stream` (work-counter reset + kernel). */
+CC_API int cc_batch_run(cc_batch *b, void *stream);
+
+/* The same launch through a CUDA graph that the plan captures on first use
+ * (on `stream`, which must not be capturing) and replays afterwards. */
+CC_API int cc_batch_run_graph(cc_batch *b, void *stream);
+
+/* Chosen shape: threads per block, and points per tile for each item. */
+CC_API int cc_batch_get_config(const cc_batch *b, int32_t *threads_per_block, int32_t *tile_points,
+                               int32_t nitems);
+
+CC_API void cc_batch_destroy(cc_batch *b);
+
 /* Counters since the last reset (synchronises `stream`). */
 CC_API int cc_get_stats(cc_ctx *ctx, cc_stats *out, void *stream);
 CC_API int cc_reset_stats(cc_ctx *ctx, void *stream);

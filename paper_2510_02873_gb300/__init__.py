@@ -17,7 +17,7 @@ from ._lib import CC_F32, CC_F64, MODES, CcCosmology, CcStats, CollapseError  # 
 
 __all__ = [
     "Context", "cc_create", "cc_destroy", "cc_reset_max", "cc_collapse_scale", "cc_collapse_multi",
-    "cc_collapse_multi_host",
+    "cc_collapse_multi_host", "Batch",
     "cc_get_stats", "cc_reset_stats", "cc_get_growth_table", "cc_build_growth_table", "cc_version", "CollapseError", "build",
 ]
 
@@ -159,6 +159,63 @@ def cc_reset_stats(ctx, stream=None) -> None:
 
 def cc_version() -> int:
     return _lib.load().cc_version()
+
+
+class Batch:
+    """A plan for many realizations in one persistent launch (cc_batch_*).
+
+    items: list of (hess (R, 6, n) CUDA tensor, sigma (R,), F_max (n,) float64
+    CUDA tensor, idx (n,) int32 CUDA tensor[, scale_idx0]). The tensors must
+    outlive the plan."""
+
+    def __init__(self, ctx: "Context", items, mode="mixed"):
+        L = _lib.load()
+        self._keep = []
+        arr = (_lib.CcBatchItem * len(items))()
+        for k, it in enumerate(items):
+            hess, sigma, F_max, idx = it[:4]
+            scale0 = it[4] if len(it) > 4 else 0
+            if hess.dim() != 3 or hess.shape[1] != 6 or hess.stride(2) != 1 or not hess.is_cuda:
+                raise ValueError("hess must be a CUDA (R, 6, n) tensor with unit stride along points")
+            R, _, n = hess.shape
+            _check_outputs(F_max, idx, n)
+            sig = (ctypes.c_double * R)(*[float(s) for s in sigma])
+            self._keep.append(sig)
+            arr[k] = _lib.CcBatchItem(hess.data_ptr(), _dtype_code(hess), n, hess.stride(1), hess.stride(0), R,
+                                      ctypes.cast(sig, ctypes.POINTER(ctypes.c_double)), F_max.data_ptr(),
+                                      idx.data_ptr(), int(scale0))
+        self._h = ctypes.c_void_p()
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        _lib.check(L.cc_batch_create(ctx.handle, m, arr, len(items), ctypes.byref(self._h)), "cc_batch_create")
+        self.nitems = len(items)
+
+    def autotune(self, cache_path=None, stream=None):
+        path = cache_path.encode() if cache_path else None
+        _lib.check(_lib.load().cc_batch_autotune(self._h, path, _stream_ptr(stream)), "cc_batch_autotune")
+
+    def run(self, stream=None):
+        _lib.check(_lib.load().cc_batch_run(self._h, _stream_ptr(stream)), "cc_batch_run")
+
+    def run_graph(self, stream=None):
+        _lib.check(_lib.load().cc_batch_run_graph(self._h, _stream_ptr(stream)), "cc_batch_run_graph")
+
+    def config(self):
+        blk = ctypes.c_int32()
+        tiles = (ctypes.c_int32 * self.nitems)()
+        _lib.check(_lib.load().cc_batch_get_config(self._h, ctypes.byref(blk), tiles, self.nitems),
+                   "cc_batch_get_config")
+        return int(blk.value), list(tiles)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.load().cc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ convenience

@@ -15,7 +15,8 @@ MODES = {"fp64": 0, "mixed": 1, "surrogate": 2, "tabulated": 3}
 EXPORTS = (
     "cc_create", "cc_destroy", "cc_build_growth_table", "cc_get_growth_table", "cc_reset_max", "cc_collapse_scale",
     "cc_collapse_multi", "cc_collapse_multi_host", "cc_collapse_multi_noalloc", "cc_get_stats", "cc_reset_stats", "cc_strerror",
-    "cc_last_error_message", "cc_version",
+    "cc_last_error_message", "cc_version", "cc_batch_create", "cc_batch_autotune", "cc_batch_run",
+    "cc_batch_run_graph", "cc_batch_get_config", "cc_batch_destroy",
 )
 
 
@@ -32,6 +33,13 @@ class CcStats(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "reserved"}
+
+
+class CcBatchItem(ctypes.Structure):
+    _fields_ = [("hess", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("plane_stride", ctypes.c_int64), ("radius_stride", ctypes.c_int64), ("R", ctypes.c_int32),
+                ("sigma", ctypes.POINTER(ctypes.c_double)), ("F_max", ctypes.c_void_p),
+                ("idx", ctypes.c_void_p), ("scale_idx0", ctypes.c_int32)]
 
 
 class CollapseError(RuntimeError):
@@ -75,6 +83,13 @@ def load() -> ctypes.CDLL:
         L.cc_collapse_multi_noalloc.argtypes = [ctypes.POINTER(CcCosmology), ctypes.c_int, vp, i32, i64, i64, i64,
                                                 ctypes.POINTER(d), i32, vp, vp, i32, ctypes.POINTER(CcStats), vp]
         L.cc_get_stats.argtypes = [vp, ctypes.POINTER(CcStats), vp]
+        L.cc_batch_create.argtypes = [vp, ctypes.c_int, ctypes.POINTER(CcBatchItem), i32, ctypes.POINTER(vp)]
+        L.cc_batch_autotune.argtypes = [vp, ctypes.c_char_p, vp]
+        L.cc_batch_run.argtypes = [vp, vp]
+        L.cc_batch_run_graph.argtypes = [vp, vp]
+        L.cc_batch_get_config.argtypes = [vp, ctypes.POINTER(i32), vp, i32]
+        L.cc_batch_destroy.argtypes = [vp]
+        L.cc_batch_destroy.restype = None
         L.cc_reset_stats.argtypes = [vp, vp]
         L.cc_strerror.argtypes = [ctypes.c_int]
         L.cc_strerror.restype = ctypes.c_char_p
@@ -83,7 +98,8 @@ def load() -> ctypes.CDLL:
         L.cc_version.argtypes = []
         for name in ("cc_build_growth_table", "cc_get_growth_table", "cc_reset_max", "cc_collapse_scale",
                      "cc_collapse_multi", "cc_collapse_multi_host", "cc_collapse_multi_noalloc",
-                     "cc_get_stats", "cc_reset_stats", "cc_version"):
+                     "cc_get_stats", "cc_reset_stats", "cc_version", "cc_batch_create", "cc_batch_autotune",
+                     "cc_batch_run", "cc_batch_run_graph", "cc_batch_get_config"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L

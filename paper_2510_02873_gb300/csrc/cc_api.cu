@@ -84,6 +84,7 @@ int run_collapse(cc_ctx* ctx, cc_mode mode, const void* hess, int32_t dtype, int
     case CC_MODE_FP64:
       return launch_fp64(a, ctx->tab);
     case CC_MODE_MIXED:
+      return launch_mixed(a, ctx->tab, sigma);
     case CC_MODE_SURROGATE:
     case CC_MODE_TABULATED:
       return set_error(CC_ENOTSUP, "mode not available in this build");

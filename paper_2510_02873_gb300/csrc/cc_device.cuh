@@ -35,7 +35,7 @@ __device__ __forceinline__ long long bits(double x) { return __double_as_longlon
 // eigenvector v3 as the largest cross product of two rows of A - l3 I; A
 // restricted to the plane orthogonal to v3 is a 2x2 symmetric matrix whose
 // eigenvalues follow without cancellation (mean +- hypot(half difference, off-diagonal)).
-__device__ __noinline__ void refine_top_pair(double xx, double yy, double zz, double xy, double xz,
+static __device__ __noinline__ void refine_top_pair(double xx, double yy, double zz, double xy, double xz,
                                              double yz, double l3, double& l1, double& l2) {
   const double r0x = xx - l3, r0y = xy, r0z = xz;
   const double r1x = xy, r1y = yy - l3, r1z = yz;
@@ -218,6 +218,114 @@ __device__ __forceinline__ PointResult collapse_point_fp64(
   const double y0 = static_cast<double>(1.0f / static_cast<float>(av));
   const double F = fma(y0, fma(-av, y0, 1.0), y0);
   res.F = res.collapsed ? F : 0.0;
+  return res;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision (CC_MODE_MIXED): FP32 bulk, FP64 only for (i) points whose
+// eigenvalues are (nearly) degenerate, (ii) the collapse-condition root polish
+// and (iii) the a(D) spline, as the mixed path is specified. Target: F within
+// 3e-5 of the FP64 oracle.
+//
+// The FP32 eigenvalue l1 = q + x carries an absolute error of about
+// eps32 p^3 / ((x1 - x2)(x1 - x3)) (the FP32 residual of the characteristic
+// cubic over its slope), and D_c is relatively as sensitive to l1 as to the
+// other coefficients (c3 is proportional to l1). Points where that estimate
+// divided by |l1| exceeds kMixedEstTau get one FP64 Newton step on
+// det(A - l I), evaluated from the FP32 entries widened to FP64 (products of
+// two FP32 numbers are exact in FP64). Points with 1 + r < kPairTauF (l1 ~ l2)
+// or l1 - l3 below 1e-4 s (all three close; s = rms of tr H at this radius)
+// take the whole FP64 path.
+constexpr float kMixedEstTau = 3e-6f;
+constexpr float kMixedEstCoef = 2.4e-7f;  // ~4 eps32: rounding of det and of the cubic residual
+
+struct MixedResult {
+  double F;
+  bool collapsed, eds, refined, fp64;
+};
+
+__device__ __forceinline__ MixedResult collapse_point_mixed(
+    float xx, float yy, float zz, float xy, float xz, float yz, float tri_thr,
+    const double* __restrict__ Dk, const Coef4* __restrict__ coef, const float* __restrict__ Dkf,
+    const unsigned short* __restrict__ bucket, const DevTable& tab) {
+  MixedResult res;
+  res.refined = false;
+  res.fp64 = false;
+  // ---- FP32 invariants and trigonometric eigenvalues
+  const float q = (xx + yy + zz) * (1.0f / 3.0f);
+  const float a = xx - q, b = yy - q, c = zz - q;
+  const float s6 = fmaf(2.0f, fmaf(yz, yz, fmaf(xz, xz, xy * xy)), fmaf(c, c, fmaf(b, b, a * a)));
+  const float p2 = s6 * (1.0f / 6.0f), p2x3 = 0.5f * s6;
+  const float det = fmaf(xz, fmaf(xy, yz, -b * xz), fmaf(a, fmaf(b, c, -yz * yz), -xy * fmaf(xy, c, -yz * xz)));
+  const float pf = sqrtf(p2);
+  float rf = (p2 > 0.0f) ? det / (2.0f * p2 * pf) : 0.0f;
+  rf = fminf(1.0f, fmaxf(-1.0f, rf));
+  float sn, cs;
+  sincosf(acosf(rf) * (1.0f / 3.0f), &sn, &cs);
+  float x = 2.0f * pf * cs;
+  const float x2 = pf * fmaf(kSqrt3f, sn, -cs);
+  const float x3 = -pf * fmaf(kSqrt3f, sn, cs);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {  // FP32 Newton on x (x^2 - 3p^2) - det
+    const float gp = 3.0f * (x * x - p2);
+    x = (gp != 0.0f) ? x - fmaf(x, x * x - p2x3, -det) / gp : x;
+  }
+  const bool full = ((1.0f + rf) < kPairTauF && p2 > 0.0f) || (x - x3) < tri_thr;
+  if (full) {
+    const PointResult r64 = collapse_point_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
+    res.F = r64.F;
+    res.collapsed = r64.collapsed;
+    res.eds = r64.eds;
+    res.refined = r64.refined;
+    res.fp64 = true;
+    return res;
+  }
+  const float lam1f = q + x;
+  double lam1 = static_cast<double>(lam1f);
+  const float est = kMixedEstCoef * p2 * pf / fmaxf((x - x2) * (x - x3) * fabsf(lam1f), 1e-30f);
+  if (est > kMixedEstTau) {
+    // one FP64 Newton step on g(l) = det(A - l I); g'(l) = -3 (x^2 - p^2) from FP32
+    const double dxx = static_cast<double>(xx) - lam1, dyy = static_cast<double>(yy) - lam1;
+    const double dzz = static_cast<double>(zz) - lam1;
+    const double dxy = xy, dxz = xz, dyz = yz;
+    const double g = fma(dxx, fma(dyy, dzz, -dyz * dyz),
+                         fma(-dxy, fma(dxy, dzz, -dyz * dxz), dxz * fma(dxy, dyz, -dyy * dxz)));
+    const float gpf = 3.0f * (x * x - p2);
+    lam1 = fma(g, static_cast<double>(1.0f / gpf), lam1);
+    x = static_cast<float>(lam1 - static_cast<double>(q));
+    res.fp64 = true;
+  }
+  // ---- FP32 collapse-condition coefficients
+  const float Pp = fmaf(q, q - x, fmaf(x, x, -p2x3));  // l2 l3
+  const float S = fmaf(2.0f, q, -x);                   // l2 + l3
+  const float Q2 = fmaf(-2.0f, Pp, S * S);             // l2^2 + l3^2
+  const float l1f = static_cast<float>(lam1);
+  const float c2f = (-3.0f / 7.0f) * Pp;
+  const float c3f = l1f * fmaf(-5.0f / 21.0f, Q2, Pp * (1.0f / 9.0f));
+  const float uf = cubic_largest_root_f32(-l1f, c2f, c3f);
+  float Df = 1.0f / uf;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const float Af = fmaf(fmaf(fmaf(c3f, Df, c2f), Df, -l1f), Df, 1.0f);
+    const float dAf = fmaf(fmaf(3.0f * c3f, Df, 2.0f * c2f), Df, -l1f);
+    Df -= Af / dAf;
+  }
+  const float dAf = fmaf(fmaf(3.0f * c3f, Df, 2.0f * c2f), Df, -l1f);
+  // ---- FP64 root polish: one Newton step on A_1 with the FP32 coefficients
+  double D = static_cast<double>(Df);
+  const double A1 = fma(fma(fma(static_cast<double>(c3f), D, static_cast<double>(c2f)), D, -lam1), D, 1.0);
+  D = fma(-A1, static_cast<double>(1.0f / dAf), D);
+  const long long bD = bits(D);
+  res.collapsed = lam1f > 0.0f && bD > 0 && bD <= bits(tab.Dtop);
+  const double Dc = res.collapsed ? D : tab.Dtop;
+  // ---- FP64 spline (interval from the FP32 root)
+  const int k = spline_interval(Dkf, bucket, tab, res.collapsed ? Df : static_cast<float>(tab.Dtop));
+  const Coef4 cf = coef[k];
+  const double t = Dc - Dk[k];
+  double av = fma(fma(fma(cf.c3, t, cf.c2), t, cf.c1), t, cf.c0);
+  res.eds = res.collapsed && bits(Dc) < bits(tab.D0);
+  if (res.eds) av = tab.eds_slope * Dc;
+  res.F = res.collapsed ? static_cast<double>(1.0f / static_cast<float>(av)) : 0.0;
   return res;
 }
 

@@ -65,7 +65,13 @@ int natural_spline_into(int n, const double* x, const double* y, double* coef, d
 int set_error(int code, const std::string& msg);
 int check_cuda(cudaError_t e, const char* what);
 
-// kernel launchers (cc_fp64.cu)
+// per-radius parameters of one launch (kernel-parameter space)
+constexpr int kMaxRadiiPerLaunch = 256;
+struct RadiusParams {
+  float tri_thr[kMaxRadiiPerLaunch];  // MIXED: 1e-4 s(R), the all-three-close threshold
+};
+
+// kernel launchers (cc_kernels.cu)
 struct LaunchArgs {
   const void* hess;
   int dtype;
@@ -81,6 +87,7 @@ struct LaunchArgs {
   int num_sms;
 };
 int launch_fp64(const LaunchArgs& a, const DevTable& tab);
+int launch_mixed(const LaunchArgs& a, const DevTable& tab, const double* sigma);
 int launch_reset_max(double* F_max, int32_t* idx, int64_t n, cudaStream_t stream, int num_sms);
 
 }  // namespace cc

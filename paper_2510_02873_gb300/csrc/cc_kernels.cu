@@ -1,5 +1,5 @@
-// cc_fp64.cu -- the plain FP64 collapse kernel (arXiv:2510.02873, Sec. 4.1,
-// "Classic" kernel) and the device-array initialisation kernel.
+// cc_kernels.cu -- the collapse kernels (arXiv:2510.02873, Sec. 4.1, "Classic"
+// kernel) in FP64 and mixed precision, and the device-array initialisation kernel.
 //
 // One thread per grid point (Sec. 4.1: "assigning the computation at each grid
 // point to an individual GPU-thread"), structure-of-arrays planes so that
@@ -18,26 +18,35 @@ __device__ __forceinline__ double ld(const T* p) {
   return static_cast<double>(__ldg(p));
 }
 
+template <typename T>
+__device__ __forceinline__ float ldf(const T* p) {
+  return static_cast<float>(__ldg(p));
+}
+
 __device__ __forceinline__ void add_counters(DevCounters* cnt, unsigned evals, unsigned coll,
-                                             unsigned eds, unsigned refined) {
+                                             unsigned eds, unsigned refined, unsigned fp64) {
   evals = __reduce_add_sync(0xffffffffu, evals);
   coll = __reduce_add_sync(0xffffffffu, coll);
   eds = __reduce_add_sync(0xffffffffu, eds);
   refined = __reduce_add_sync(0xffffffffu, refined);
+  fp64 = __reduce_add_sync(0xffffffffu, fp64);
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(&cnt->evaluations, static_cast<unsigned long long>(evals));
     if (coll) atomicAdd(&cnt->collapsed, static_cast<unsigned long long>(coll));
     if (eds) atomicAdd(&cnt->eds_branch, static_cast<unsigned long long>(eds));
     if (refined) atomicAdd(&cnt->refined, static_cast<unsigned long long>(refined));
+    if (fp64) atomicAdd(&cnt->fp64_branch, static_cast<unsigned long long>(fp64));
   }
 }
 
-template <typename T, bool kSmem>
+// One thread per point (grid-stride), all R radii of the launch in registers.
+// kMixed selects collapse_point_mixed (FP32 bulk) over collapse_point_fp64.
+template <typename T, bool kSmem, bool kMixed>
 __global__ void __launch_bounds__(kThreads)
-collapse_fp64_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
-                     int64_t radius_stride, int R, int32_t scale_idx0, DevTable tab,
-                     double* __restrict__ F_max, int32_t* __restrict__ idx,
-                     DevCounters* __restrict__ cnt) {
+collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
+                int64_t radius_stride, int R, int32_t scale_idx0, DevTable tab, RadiusParams rp,
+                double* __restrict__ F_max, int32_t* __restrict__ idx,
+                DevCounters* __restrict__ cnt) {
   extern __shared__ Coef4 smem_tab[];
   const Coef4* coef = tab.coef;
   const double* Dk = tab.D;
@@ -59,7 +68,7 @@ collapse_fp64_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride
     Dkf = reinterpret_cast<const float*>(Dk + tab.n);
     bucket = reinterpret_cast<const unsigned short*>(Dkf + tab.n);
   }
-  unsigned n_eval = 0, n_coll = 0, n_eds = 0, n_ref = 0;
+  unsigned n_eval = 0, n_coll = 0, n_eds = 0, n_ref = 0, n_fp64 = 0;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   // whole warps stay in the loop together so the warp-level counter reduction
   // at the end sees all 32 lanes
@@ -73,15 +82,30 @@ collapse_fp64_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride
       const T* base = hess + p;
       for (int r = 0; r < R; ++r) {
         const T* h = base + static_cast<int64_t>(r) * radius_stride;
-        const double xx = ld(h), yy = ld(h + plane_stride), zz = ld(h + 2 * plane_stride);
-        const double xy = ld(h + 3 * plane_stride), xz = ld(h + 4 * plane_stride);
-        const double yz = ld(h + 5 * plane_stride);
-        const PointResult res = collapse_point_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
-        n_coll += res.collapsed;
-        n_eds += res.eds;
-        n_ref += res.refined;
-        if (bits(res.F) > bits(Fm)) {  // both >= 0: integer order == value order
-          Fm = res.F;
+        double F;
+        if constexpr (kMixed) {
+          const float xx = ldf(h), yy = ldf(h + plane_stride), zz = ldf(h + 2 * plane_stride);
+          const float xy = ldf(h + 3 * plane_stride), xz = ldf(h + 4 * plane_stride);
+          const float yz = ldf(h + 5 * plane_stride);
+          const MixedResult res =
+              collapse_point_mixed(xx, yy, zz, xy, xz, yz, rp.tri_thr[r], Dk, coef, Dkf, bucket, tab);
+          n_coll += res.collapsed;
+          n_eds += res.eds;
+          n_ref += res.refined;
+          n_fp64 += res.fp64;
+          F = res.F;
+        } else {
+          const double xx = ld(h), yy = ld(h + plane_stride), zz = ld(h + 2 * plane_stride);
+          const double xy = ld(h + 3 * plane_stride), xz = ld(h + 4 * plane_stride);
+          const double yz = ld(h + 5 * plane_stride);
+          const PointResult res = collapse_point_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
+          n_coll += res.collapsed;
+          n_eds += res.eds;
+          n_ref += res.refined;
+          F = res.F;
+        }
+        if (bits(F) > bits(Fm)) {  // both >= 0: integer order == value order
+          Fm = F;
           im = scale_idx0 + r;
         }
       }
@@ -90,7 +114,7 @@ collapse_fp64_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride
       n_eval += R;
     }
   }
-  add_counters(cnt, n_eval, n_coll, n_eds, n_ref);
+  add_counters(cnt, n_eval, n_coll, n_eds, n_ref, n_fp64);
 }
 
 __global__ void reset_max_kernel(double* __restrict__ F_max, int32_t* __restrict__ idx, int64_t n) {
@@ -101,12 +125,11 @@ __global__ void reset_max_kernel(double* __restrict__ F_max, int32_t* __restrict
   }
 }
 
-template <typename T, bool kSmem>
-int launch_typed(const LaunchArgs& a, const DevTable& tab) {
-  auto kern = collapse_fp64_kernel<T, kSmem>;
+template <typename T, bool kSmem, bool kMixed>
+int launch_typed(const LaunchArgs& a, const DevTable& tab, const RadiusParams& rp) {
+  auto kern = collapse_kernel<T, kSmem, kMixed>;
   const size_t smem = kSmem ? ((tab.bytes() + 15) / 16) * 16 : 0;
-  static thread_local int occ_cache[2] = {0, 0};
-  int& occ = occ_cache[kSmem ? 1 : 0];
+  static thread_local int occ = 0;
   if (kSmem && smem > 48 * 1024) {
     if (int rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  static_cast<int>(smem)),
@@ -125,18 +148,38 @@ int launch_typed(const LaunchArgs& a, const DevTable& tab) {
   const int64_t cap = static_cast<int64_t>(a.num_sms) * occ;
   const int grid = static_cast<int>(need < cap ? need : cap);
   kern<<<grid, kThreads, smem, a.stream>>>(static_cast<const T*>(a.hess), a.n, a.plane_stride,
-                                           a.radius_stride, a.R, a.scale_idx0, tab, a.F_max, a.idx,
-                                           a.counters);
-  return check_cuda(cudaGetLastError(), "collapse_fp64_kernel launch");
+                                           a.radius_stride, a.R, a.scale_idx0, tab, rp, a.F_max,
+                                           a.idx, a.counters);
+  return check_cuda(cudaGetLastError(), "collapse_kernel launch");
+}
+
+template <bool kMixed>
+int launch_mode(const LaunchArgs& a, const DevTable& tab, const RadiusParams& rp) {
+  const bool smem = tab.bytes() <= static_cast<size_t>(kSmemTableMaxBytes);
+  if (a.dtype == CC_F64)
+    return smem ? launch_typed<double, true, kMixed>(a, tab, rp) : launch_typed<double, false, kMixed>(a, tab, rp);
+  return smem ? launch_typed<float, true, kMixed>(a, tab, rp) : launch_typed<float, false, kMixed>(a, tab, rp);
 }
 
 }  // namespace
 
 int launch_fp64(const LaunchArgs& a, const DevTable& tab) {
-  const bool smem = tab.bytes() <= static_cast<size_t>(kSmemTableMaxBytes);
-  if (a.dtype == CC_F64)
-    return smem ? launch_typed<double, true>(a, tab) : launch_typed<double, false>(a, tab);
-  return smem ? launch_typed<float, true>(a, tab) : launch_typed<float, false>(a, tab);
+  return launch_mode<false>(a, tab, RadiusParams{});
+}
+
+int launch_mixed(const LaunchArgs& a, const DevTable& tab, const double* sigma) {
+  // at most kMaxRadiiPerLaunch radii per launch (their thresholds ride in the
+  // kernel parameters); longer radius lists run as consecutive launches
+  for (int r0 = 0; r0 < a.R; r0 += kMaxRadiiPerLaunch) {
+    LaunchArgs c = a;
+    c.R = (a.R - r0 < kMaxRadiiPerLaunch) ? a.R - r0 : kMaxRadiiPerLaunch;
+    c.hess = static_cast<const unsigned char*>(a.hess) + static_cast<size_t>(r0) * a.radius_stride * a.dtype;
+    c.scale_idx0 = a.scale_idx0 + r0;
+    RadiusParams rp;
+    for (int r = 0; r < c.R; ++r) rp.tri_thr[r] = static_cast<float>(1e-4 * sigma[r0 + r]);
+    if (int rc = launch_mode<true>(c, tab, rp)) return rc;
+  }
+  return CC_OK;
 }
 
 int launch_reset_max(double* F_max, int32_t* idx, int64_t n, cudaStream_t stream, int num_sms) {
