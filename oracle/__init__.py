@@ -25,8 +25,10 @@ FLAG_EDGE = 4
 FLAG_SIGN0 = 8
 FLAG_EDS = 16
 FLAG_AXIS23 = 32
+FLAG_HULL_OUT = 64
+FLAG_HULL_EDGE = 128
 # flags whose points sit on a discontinuity of F (either branch is a valid answer)
-FLAGS_AMBIGUOUS = FLAG_EDGE | FLAG_SIGN0
+FLAGS_AMBIGUOUS = FLAG_EDGE | FLAG_SIGN0 | FLAG_HULL_EDGE
 
 _lock = threading.Lock()
 _lib = None
@@ -49,6 +51,13 @@ def build(force: bool = False) -> str:
 class _Tables(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("a", ctypes.POINTER(ctypes.c_double)),
                 ("D", ctypes.POINTER(ctypes.c_double)), ("M", ctypes.POINTER(ctypes.c_double))]
+
+
+class _Tab(ctypes.Structure):
+    _fields_ = [("nd", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("dg", ctypes.POINTER(ctypes.c_double)), ("xg", ctypes.POINTER(ctypes.c_double)),
+                ("yg", ctypes.POINTER(ctypes.c_double)), ("val", ctypes.POINTER(ctypes.c_double)),
+                ("M", ctypes.POINTER(ctypes.c_double))]
 
 
 def lib():
@@ -83,6 +92,15 @@ def lib():
                                             ctypes.c_int32, vp, i]
             L.or_collapse_scale_f32.argtypes = L.or_collapse_scale.argtypes
             L.or_F_points.argtypes = [ctypes.POINTER(_Tables), vp, i64, i64, vp, vp, i]
+            L.or_cubic_largest_root.argtypes = [d, d, d]
+            L.or_cubic_largest_root.restype = d
+            L.or_tab_node_value.argtypes = [d, d, d]
+            L.or_tab_node_value.restype = d
+            L.or_tab_init.argtypes = [ctypes.POINTER(_Tab), i, vp, i, vp, i, vp, vp]
+            L.or_tab_free.argtypes = [ctypes.POINTER(_Tab)]
+            L.or_tab_query.argtypes = [ctypes.POINTER(_Tab), d, d, d]
+            L.or_tab_query.restype = d
+            L.or_F_tab_points.argtypes = [ctypes.POINTER(_Tables), ctypes.POINTER(_Tab), vp, i64, i64, vp, vp, i]
             _lib = L
     return _lib
 
@@ -238,3 +256,57 @@ class Tables:
         for r in range(R):
             flags_or |= self.collapse_scale(hess_stack[r], F_max, idx, r, nthreads)
         return F_max, idx, flags_or
+
+
+# ---------------------------------------------------------------- tabulated collapse
+def cubic_largest_root(b, c, d) -> float:
+    return lib().or_cubic_largest_root(float(b), float(c), float(d))
+
+
+def tab_node_value(delta, x, y) -> float:
+    return lib().or_tab_node_value(float(delta), float(x), float(y))
+
+
+def tab_node_values(dg, xg, yg) -> np.ndarray:
+    """u = 1/D_c at every node, layout [ix][iy][k] (flattened like the library's)."""
+    L = lib()
+    out = np.empty((len(xg), len(yg), len(dg)))
+    for i, x in enumerate(xg):
+        for j, y in enumerate(yg):
+            for k, dd in enumerate(dg):
+                out[i, j, k] = L.or_tab_node_value(float(dd), float(x), float(y))
+    return out
+
+
+class Tab:
+    """Table of u = 1/D_c over (delta, x, y) with natural splines along delta."""
+
+    def __init__(self, dg, xg, yg, val):
+        self.dg, self.xg, self.yg = _f64(dg), _f64(xg), _f64(yg)
+        val = _f64(val).reshape(len(self.xg), len(self.yg), len(self.dg))
+        self.val = val
+        self._t = _Tab()
+        rc = lib().or_tab_init(ctypes.byref(self._t), len(self.dg), _p(self.dg), len(self.xg), _p(self.xg),
+                               len(self.yg), _p(self.yg), _p(np.ascontiguousarray(val)))
+        if rc:
+            raise ValueError(f"or_tab_init failed: {rc}")
+
+    def __del__(self):
+        try:
+            lib().or_tab_free(ctypes.byref(self._t))
+        except Exception:
+            pass
+
+    def query(self, delta, x, y) -> np.ndarray:
+        L = lib()
+        return np.array([L.or_tab_query(ctypes.byref(self._t), float(a), float(b), float(c))
+                         for a, b, c in zip(np.atleast_1d(delta), np.atleast_1d(x), np.atleast_1d(y))])
+
+    def F_points(self, tables: "Tables", hess: np.ndarray, nthreads: int = 0):
+        hess = _f64(hess)
+        n = hess.shape[1]
+        F = np.empty(n)
+        flags = np.empty(n, dtype=np.int32)
+        lib().or_F_tab_points(ctypes.byref(tables._t), ctypes.byref(self._t), _p(hess), n, n, _p(F), _p(flags),
+                              nthreads)
+        return F, flags

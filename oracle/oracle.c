@@ -447,3 +447,135 @@ void or_F_points(const or_tables *t, const double *hess, int64_t n, int64_t plan
     if (flags) flags[p] = f;
   }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Tabulated collapse (Sec. 3: collapse times precomputed on a grid of
+ * delta = sum l_i, x = l1 - l2, y = l2 - l3 with eigenvalues sorted
+ * descending, a cubic spline along delta and bilinear interpolation in x and
+ * y; Sec. 4.2: the mixed spline/bilinear scheme). The tabulated quantity is
+ * read as u = 1/D_c (see oracle.h).                                          */
+
+double or_cubic_largest_root(double b, double c, double d) {
+  /* all real roots lie in [-B, B] (Cauchy bound); P is increasing right of its
+   * last critical point and left of its first one */
+  double B = 1.0 + fmax(fabs(b), fmax(fabs(c), fabs(d)));
+  double lo = -B, hi = B;
+  double disc = b * b - 3.0 * c; /* critical points of P: 3u^2 + 2bu + c = 0 */
+  if (disc > 0.0) {
+    double s = sqrt(disc);
+    double e1 = (-b - s) / 3.0, e2 = (-b + s) / 3.0; /* local max, local min */
+    double Pe2 = ((e2 + b) * e2 + c) * e2 + d;
+    if (Pe2 <= 0.0) lo = e2; else hi = e1;
+  }
+  for (int it = 0; it < 400; ++it) {
+    double mid = lo + 0.5 * (hi - lo);
+    if (mid <= lo || mid >= hi) break;
+    double P = ((mid + b) * mid + c) * mid + d;
+    if (P < 0.0) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+double or_tab_node_value(double delta, double x, double y) {
+  double l2 = (delta - x + y) / 3.0;
+  double l[3] = {l2 + x, l2, l2 - y};
+  double c[4];
+  or_axis_coeffs(l, 0, c); /* A_1 = 1 + c1 D + c2 D^2 + c3 D^3 -> u^3 + c1 u^2 + c2 u + c3 */
+  return or_cubic_largest_root(c[1], c[2], c[3]);
+}
+
+void or_tab_free(or_tab *t) {
+  free(t->dg); free(t->xg); free(t->yg); free(t->val); free(t->M);
+  memset(t, 0, sizeof(*t));
+}
+
+int or_tab_init(or_tab *t, int nd, const double *dg, int nx, const double *xg, int ny, const double *yg,
+                const double *val) {
+  memset(t, 0, sizeof(*t));
+  if (nd < 2 || nx < 2 || ny < 2) return -1;
+  t->nd = nd; t->nx = nx; t->ny = ny;
+  size_t nv = (size_t)nx * ny * nd;
+  t->dg = malloc(sizeof(double) * nd);
+  t->xg = malloc(sizeof(double) * nx);
+  t->yg = malloc(sizeof(double) * ny);
+  t->val = malloc(sizeof(double) * nv);
+  t->M = malloc(sizeof(double) * nv);
+  if (!t->dg || !t->xg || !t->yg || !t->val || !t->M) { or_tab_free(t); return -3; }
+  memcpy(t->dg, dg, sizeof(double) * nd);
+  memcpy(t->xg, xg, sizeof(double) * nx);
+  memcpy(t->yg, yg, sizeof(double) * ny);
+  memcpy(t->val, val, sizeof(double) * nv);
+  for (int i = 0; i + 1 < nx; ++i) if (!(xg[i + 1] > xg[i])) { or_tab_free(t); return -2; }
+  for (int i = 0; i + 1 < ny; ++i) if (!(yg[i + 1] > yg[i])) { or_tab_free(t); return -2; }
+  for (size_t s = 0; s < (size_t)nx * ny; ++s) {
+    int rc = or_spline_build(nd, dg, t->val + s * nd, 0.0, 0.0, t->M + s * nd);
+    if (rc) { or_tab_free(t); return rc; }
+  }
+  return 0;
+}
+
+double or_tab_query(const or_tab *t, double delta, double x, double y) {
+  int ix = or_find_interval(t->nx, t->xg, x), iy = or_find_interval(t->ny, t->yg, y);
+  double z[4]; /* corners (ix, iy), (ix+1, iy), (ix, iy+1), (ix+1, iy+1) */
+  for (int c = 0; c < 4; ++c) {
+    size_t s = (size_t)(ix + (c & 1)) * t->ny + (iy + (c >> 1));
+    z[c] = or_spline_eval(t->nd, t->dg, t->val + s * t->nd, t->M + s * t->nd, delta);
+  }
+  double xg2[2] = {t->xg[ix], t->xg[ix + 1]}, yg2[2] = {t->yg[iy], t->yg[iy + 1]};
+  double zz[4] = {z[0], z[2], z[1], z[3]}; /* or_bilinear layout z[ix*ny + iy] */
+  return or_bilinear(2, xg2, 2, yg2, zz, x, y);
+}
+
+static int or_near(double v, double edge) {
+  return fabs(v - edge) <= 1e-12 * fmax(1.0, fabs(edge));
+}
+
+double or_F_tab_point(const or_tables *t, const or_tab *tab, const double h[6], int *flags) {
+  double l[3];
+  or_eigen_jacobi(h, l);
+  int f = 0;
+  double lmax = fmax(fabs(l[0]), fmax(fabs(l[1]), fabs(l[2])));
+  if (fabs(l[0]) <= 1e-9 * lmax) f |= OR_FLAG_SIGN0;
+  double F = 0.0;
+  if (l[0] > 0.0) {
+    double delta = l[0] + l[1] + l[2], x = l[0] - l[1], y = l[1] - l[2];
+    double D_top = t->D[t->n - 1];
+    int inside = delta >= tab->dg[0] && delta <= tab->dg[tab->nd - 1] && x <= tab->xg[tab->nx - 1] &&
+                 y <= tab->yg[tab->ny - 1] && x >= tab->xg[0] && y >= tab->yg[0];
+    if (or_near(delta, tab->dg[0]) || or_near(delta, tab->dg[tab->nd - 1]) ||
+        or_near(x, tab->xg[tab->nx - 1]) || or_near(y, tab->yg[tab->ny - 1]))
+      f |= OR_FLAG_HULL_EDGE;
+    double Dc = 0.0;
+    if (inside) {
+      double u = or_tab_query(tab, delta, x, y);
+      if (u > 0.0) {
+        Dc = 1.0 / u;
+        if (fabs(Dc - D_top) <= 1e-9 * D_top) f |= OR_FLAG_EDGE;
+        if (Dc > D_top) Dc = 0.0;
+      }
+    } else {
+      f |= OR_FLAG_HULL_OUT;
+      Dc = or_collapse_D(l, D_top, &f);
+    }
+    if (Dc > 0.0) {
+      f |= OR_FLAG_COLLAPSED;
+      F = 1.0 / or_a_of_D(t, Dc, &f);
+    }
+  }
+  if (flags) *flags |= f;
+  return F;
+}
+
+void or_F_tab_points(const or_tables *t, const or_tab *tab, const double *hess, int64_t n, int64_t plane_stride,
+                     double *F, int32_t *flags, int nthreads) {
+  int nt = or_threads(nthreads);
+  (void)nt;
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nt)
+  for (int64_t p = 0; p < n; ++p) {
+    double h[6];
+    for (int c = 0; c < 6; ++c) h[c] = hess[c * plane_stride + p];
+    int f = 0;
+    F[p] = or_F_tab_point(t, tab, h, &f);
+    if (flags) flags[p] = f;
+  }
+}

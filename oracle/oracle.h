@@ -60,6 +60,8 @@ extern "C" {
 #define OR_FLAG_SIGN0       8  /* |lambda1| <= 1e-9 * max|lambda|: lambda1>0 test ambiguous */
 #define OR_FLAG_EDS        16  /* D_c below the first knot: EdS limit used             */
 #define OR_FLAG_AXIS23     32  /* A_2 or A_3 crosses zero before A_1 does (diagnostic) */
+#define OR_FLAG_HULL_OUT   64  /* tabulated: outside the table, R-LPT used instead        */
+#define OR_FLAG_HULL_EDGE 128  /* tabulated: within 1e-12 of the table's hull (either side valid) */
 
 /* ---- linear growth factor (Sec. 3, Sec. 4.2) ---- */
 int or_growth_table(double omega_m, double omega_l, int n_knots, double a_min, double a_max,
@@ -109,6 +111,30 @@ void or_collapse_scale_f32(const or_tables *t, const float *hess, int64_t n, int
 /* F of each point (no max), with flags. */
 void or_F_points(const or_tables *t, const double *hess, int64_t n, int64_t plane_stride,
                  double *F, int32_t *flags, int nthreads);
+
+/* ---- tabulated collapse (Sec. 3 "Tabulated" option; Sec. 4.2 spline x bilinear) ----
+ * Reading: the table holds u = 1/D_c, the largest real root of the monic
+ * cubic u^3 - l1 u^2 + c2 u + c3 (finite everywhere, ~linear in (delta, x, y)),
+ * on non-uniform axes delta (nd), x = l1 - l2 (nx), y = l2 - l3 (ny);
+ * val[(ix * ny + iy) * nd + k]. A query splines delta (natural cubic) at the
+ * four (x, y) corners of its cell and blends them bilinearly. Outside the
+ * table the R-LPT root is used. */
+double or_cubic_largest_root(double b, double c, double d); /* of u^3 + b u^2 + c u + d */
+double or_tab_node_value(double delta, double x, double y);  /* u at a node, eigenvalues from (delta, x, y) */
+
+typedef struct {
+  int nd, nx, ny;
+  double *dg, *xg, *yg;  /* axes */
+  double *val, *M;       /* values and natural-spline second derivatives along delta */
+} or_tab;
+
+int  or_tab_init(or_tab *t, int nd, const double *dg, int nx, const double *xg, int ny, const double *yg,
+                 const double *val);
+void or_tab_free(or_tab *t);
+double or_tab_query(const or_tab *t, double delta, double x, double y);
+double or_F_tab_point(const or_tables *t, const or_tab *tab, const double h[6], int *flags);
+void or_F_tab_points(const or_tables *t, const or_tab *tab, const double *hess, int64_t n, int64_t plane_stride,
+                     double *F, int32_t *flags, int nthreads);
 
 #ifdef __cplusplus
 }

@@ -386,3 +386,71 @@ def test_collapse_condition_is_monotone_for_sorted_eigenvalues():
     # the D^2 coefficient is positive only when l2 l3 < 0
     c2 = np.array([oracle.axis_coeffs(l, 0)[2] for l in lam[:4000]])
     assert np.all((c2 > 0) == (lam[:4000, 1] * lam[:4000, 2] < 0))
+
+
+# ------------------------------------------------------------------- tabulated
+def test_cubic_largest_root_matches_numpy():
+    rng = _rng(13)
+    for _ in range(500):
+        b, c, d = rng.normal(size=3) * rng.lognormal(0, 1.5, size=3)
+        r = np.roots([1.0, b, c, d])
+        real = r[np.abs(r.imag) <= 1e-9 * np.maximum(1, np.abs(r))].real
+        want = real.max()
+        assert abs(oracle.cubic_largest_root(b, c, d) - want) <= 1e-9 * max(1.0, abs(want))
+    # three real roots, a double root, a triple root
+    assert abs(oracle.cubic_largest_root(-6, 11, -6) - 3.0) < 1e-14
+    assert abs(oracle.cubic_largest_root(-4, 5, -2) - 2.0) < 1e-14          # (u-1)^2 (u-2)
+    assert abs(oracle.cubic_largest_root(-3, 3, -1) - 1.0) < 1e-5           # (u-1)^3
+
+
+def test_table_node_value_is_inverse_collapse_growth():
+    rng = _rng(14)
+    for _ in range(200):
+        lam = np.sort(rng.normal(size=3) * 3)[::-1].copy()
+        if lam[0] <= 0:
+            continue
+        Dc, _ = oracle.collapse_D(lam, 1e9)
+        u = oracle.tab_node_value(lam.sum(), lam[0] - lam[1], lam[1] - lam[2])
+        assert abs(u * Dc - 1.0) <= 1e-12
+
+
+def test_table_query_exact_on_linear_times_bilinear():
+    """A natural spline is exact on data linear in delta and bilinear
+    interpolation on bilinear data, so the spline x bilinear query reproduces
+    (a + b delta)(c + e x)(g + k y) everywhere in the table, and node values at nodes."""
+    rng = _rng(15)
+    dg = np.sort(rng.uniform(-20, 30, 40))
+    xg = np.sort(np.concatenate([[0.0], rng.uniform(0, 10, 15)]))
+    yg = np.sort(np.concatenate([[0.0], rng.uniform(0, 8, 12)]))
+    f = lambda d, x, y: (0.4 + 0.3 * d) * (1.5 - 0.2 * x) * (0.7 + 0.9 * y)
+    val = f(dg[None, None, :], xg[:, None, None], yg[None, :, None])
+    tab = oracle.Tab(dg, xg, yg, val)
+    d = rng.uniform(dg[0], dg[-1], 300)
+    x = rng.uniform(xg[0], xg[-1], 300)
+    y = rng.uniform(yg[0], yg[-1], 300)
+    np.testing.assert_allclose(tab.query(d, x, y), f(d, x, y), rtol=1e-11, atol=1e-11)
+    i, j, k = 3, 5, 7
+    assert abs(tab.query([dg[k]], [xg[i]], [yg[j]])[0] - val[i, j, k]) <= 1e-12 * abs(val[i, j, k])
+
+
+def test_tabulated_F_close_to_classic_and_exact_outside(oracle_tables):
+    dg = np.linspace(-10, 12, 128)
+    xg = np.linspace(0, 8, 64)
+    yg = np.linspace(0, 8, 64)
+    tab = oracle.Tab(dg, xg, yg, oracle.tab_node_values(dg, xg, yg))
+    h = hessgen.hessian_planes(808, 0, 0, 3.0, 20000)
+    F_tab, fl = tab.F_points(oracle_tables, h)
+    F_cls, _ = oracle_tables.F_points(h)
+    inside = (fl & oracle.FLAG_HULL_OUT) == 0
+    both = (F_tab > 0) & (F_cls > 0)
+    rel = np.abs(F_tab - F_cls)[both] / F_cls[both]
+    # interpolation error only: small in the bulk, larger where u = 1/D_c is small
+    assert np.median(rel) < 2e-4 and np.quantile(rel, 0.99) < 1e-2
+    assert (F_cls[inside] > 0).mean() > 0.3
+    # larger contrasts leave the table: those points take the R-LPT root exactly
+    h8 = hessgen.hessian_planes(809, 0, 0, 8.0, 5000)
+    F_tab8, fl8 = tab.F_points(oracle_tables, h8)
+    F_cls8, _ = oracle_tables.F_points(h8)
+    out = (fl8 & oracle.FLAG_HULL_OUT) != 0
+    assert out.sum() > 100
+    np.testing.assert_array_equal(F_tab8[out], F_cls8[out])
