@@ -172,6 +172,44 @@ CC_API int cc_collapse_multi_noalloc(const cc_cosmology *cosmo, cc_mode mode, co
                               double *F_max, int32_t *idx, int32_t scale_idx0, cc_stats *stats,
                               void *stream);
 
+/* ---- tabulated collapse and the interpolation routines (Sec. 3, 4.2, 4.3) ----
+ * The "Tabulated" option precomputes collapse times on a grid of
+ * delta = l1 + l2 + l3, x = l1 - l2, y = l2 - l3 and interpolates with a cubic
+ * spline along delta and bilinear interpolation in x and y (Sec. 3, Sec. 4.2).
+ * The tabulated quantity here is u = 1/D_c (the inverse growth factor at
+ * collapse: finite everywhere, nearly linear in (delta, x, y)).
+ *   dgrid (nd, 4..256), xgrid (nx, 2..256), ygrid (ny, 2..256): host, strictly
+ *   increasing, x and y axes starting at >= 0;
+ *   values: host, nx * ny * nd, values[(ix * ny + iy) * nd + k] = u(d_k, x_ix, y_iy). */
+
+/* Copy a table to the context and build its natural splines along delta on the
+ * device (the paper rebuilds them at every smoothing radius, Sec. 4.2). Later
+ * CC_MODE_TABULATED launches use it; points outside [d_0, d_last] x [0, x_last]
+ * x [0, y_last] fall back to the R-LPT root. Device memory for the table is
+ * allocated on first use and kept by the context. Calls on one context are
+ * stream-ordered: do not replace a table that launches on another stream still read. */
+CC_API int cc_set_table(cc_ctx *ctx, const double *dgrid, int32_t nd, const double *xgrid, int32_t nx,
+                        const double *ygrid, int32_t ny, const double *values, void *stream);
+
+/* Helper for building a table without an external collapse model: u = 1/D_c of
+ * the R-LPT condition at every node, computed on the device; values (host) receives
+ * nx * ny * nd entries in the layout above. Synchronises `stream`. */
+CC_API int cc_table_nodes_rlpt(cc_ctx *ctx, const double *dgrid, int32_t nd, const double *xgrid, int32_t nx,
+                               const double *ygrid, int32_t ny, double *values, void *stream);
+
+/* The table interpolation routine on its own (the paper's spline x bilinear
+ * toy, Sec. 4.3): out[i] = u(d[i], x[i], y[i]) for m device queries; outside the
+ * axes the edge cells extrapolate. */
+CC_API int cc_table_query(cc_ctx *ctx, const double *d, const double *x, const double *y, int64_t m,
+                          double *out, void *stream);
+
+/* The cubic-spline routine on its own (the paper's y(x) toy, Sec. 4.3): a
+ * natural cubic spline through n host knots (2 <= n <= 4096, strictly
+ * increasing xk) built on the device, evaluated at m device queries q into out
+ * (device); outside the knots the end intervals extrapolate. */
+CC_API int cc_spline_eval(cc_ctx *ctx, const double *xk, const double *yk, int32_t n, const double *q,
+                          int64_t m, double *out, void *stream);
+
 /* ---- batches of independent realizations (one persistent launch) ----
  * Many realizations of uneven grid sizes and radius counts (e.g. a set of
  * simulation boxes) are evaluated by ONE persistent kernel: its CTAs take

@@ -96,10 +96,15 @@ def lib():
             L.or_cubic_largest_root.restype = d
             L.or_tab_node_value.argtypes = [d, d, d]
             L.or_tab_node_value.restype = d
+            L.or_tab_node_values.argtypes = [i, vp, i, vp, i, vp, vp]
             L.or_tab_init.argtypes = [ctypes.POINTER(_Tab), i, vp, i, vp, i, vp, vp]
             L.or_tab_free.argtypes = [ctypes.POINTER(_Tab)]
             L.or_tab_query.argtypes = [ctypes.POINTER(_Tab), d, d, d]
             L.or_tab_query.restype = d
+            L.or_mlp_forward.argtypes = [vp, vp]
+            L.or_mlp_forward.restype = d
+            L.or_mlp_loss_grad.argtypes = [vp, vp, vp, i, vp]
+            L.or_mlp_loss_grad.restype = d
             L.or_F_tab_points.argtypes = [ctypes.POINTER(_Tables), ctypes.POINTER(_Tab), vp, i64, i64, vp, vp, i]
             _lib = L
     return _lib
@@ -269,12 +274,9 @@ def tab_node_value(delta, x, y) -> float:
 
 def tab_node_values(dg, xg, yg) -> np.ndarray:
     """u = 1/D_c at every node, layout [ix][iy][k] (flattened like the library's)."""
-    L = lib()
+    dg, xg, yg = _f64(dg), _f64(xg), _f64(yg)
     out = np.empty((len(xg), len(yg), len(dg)))
-    for i, x in enumerate(xg):
-        for j, y in enumerate(yg):
-            for k, dd in enumerate(dg):
-                out[i, j, k] = L.or_tab_node_value(float(dd), float(x), float(y))
+    lib().or_tab_node_values(len(dg), _p(dg), len(xg), _p(xg), len(yg), _p(yg), _p(out))
     return out
 
 
@@ -310,3 +312,22 @@ class Tab:
         lib().or_F_tab_points(ctypes.byref(tables._t), ctypes.byref(self._t), _p(hess), n, n, _p(F), _p(flags),
                               nthreads)
         return F, flags
+
+
+# ---------------------------------------------------------------- MLP surrogate reference
+MLP_H = 64
+MLP_NPARAM = 3 * 64 + 64 + 64 * 64 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def mlp_forward(params, z) -> np.ndarray:
+    params = _f64(params)
+    z = np.atleast_2d(_f64(z))
+    L = lib()
+    return np.array([L.or_mlp_forward(_p(params), _p(np.ascontiguousarray(row))) for row in z])
+
+
+def mlp_loss_grad(params, z, t):
+    params, z, t = _f64(params), np.ascontiguousarray(_f64(z).reshape(-1, 3)), _f64(t)
+    grad = np.empty(MLP_NPARAM)
+    loss = lib().or_mlp_loss_grad(_p(params), _p(z), _p(t), len(t), _p(grad))
+    return loss, grad

@@ -579,3 +579,111 @@ void or_F_tab_points(const or_tables *t, const or_tab *tab, const double *hess, 
     if (flags) flags[p] = f;
   }
 }
+
+void or_tab_node_values(int nd, const double *dg, int nx, const double *xg, int ny, const double *yg,
+                        double *out) {
+#pragma omp parallel for schedule(static)
+  for (int ix = 0; ix < nx; ++ix)
+    for (int iy = 0; iy < ny; ++iy)
+      for (int k = 0; k < nd; ++k)
+        out[((size_t)ix * ny + iy) * nd + k] = or_tab_node_value(dg[k], xg[ix], yg[iy]);
+}
+
+/* ------------------------------------------------------------------------- */
+/* MLP surrogate reference (FP64, plain loops). No counterpart in the paper. */
+
+static double or_silu(double v) { return v / (1.0 + exp(-v)); }
+static double or_dsilu(double v) {
+  double s = 1.0 / (1.0 + exp(-v));
+  return s * (1.0 + v * (1.0 - s));
+}
+
+typedef struct {
+  const double *W1, *b1, *W2, *b2, *W3, *b3, *W4, *b4;
+} or_mlp_view;
+
+static or_mlp_view or_mlp_split(const double *p) {
+  or_mlp_view v;
+  v.W1 = p; p += 3 * OR_MLP_H;
+  v.b1 = p; p += OR_MLP_H;
+  v.W2 = p; p += OR_MLP_H * OR_MLP_H;
+  v.b2 = p; p += OR_MLP_H;
+  v.W3 = p; p += OR_MLP_H * OR_MLP_H;
+  v.b3 = p; p += OR_MLP_H;
+  v.W4 = p; p += OR_MLP_H;
+  v.b4 = p;
+  return v;
+}
+
+/* forward pass keeping pre-activations u1..u3 and activations a1..a3 */
+static double or_mlp_fwd(const or_mlp_view *m, const double z[3], double *u1, double *a1, double *u2, double *a2,
+                         double *u3, double *a3) {
+  for (int j = 0; j < OR_MLP_H; ++j) {
+    double s = m->b1[j];
+    for (int i = 0; i < 3; ++i) s += z[i] * m->W1[i * OR_MLP_H + j];
+    u1[j] = s; a1[j] = or_silu(s);
+  }
+  for (int j = 0; j < OR_MLP_H; ++j) {
+    double s = m->b2[j];
+    for (int i = 0; i < OR_MLP_H; ++i) s += a1[i] * m->W2[i * OR_MLP_H + j];
+    u2[j] = s; a2[j] = or_silu(s);
+  }
+  for (int j = 0; j < OR_MLP_H; ++j) {
+    double s = m->b3[j];
+    for (int i = 0; i < OR_MLP_H; ++i) s += a2[i] * m->W3[i * OR_MLP_H + j];
+    u3[j] = s; a3[j] = or_silu(s);
+  }
+  double f = m->b4[0];
+  for (int i = 0; i < OR_MLP_H; ++i) f += a3[i] * m->W4[i];
+  return f;
+}
+
+double or_mlp_forward(const double *params, const double z[3]) {
+  or_mlp_view m = or_mlp_split(params);
+  double u1[OR_MLP_H], a1[OR_MLP_H], u2[OR_MLP_H], a2[OR_MLP_H], u3[OR_MLP_H], a3[OR_MLP_H];
+  return or_mlp_fwd(&m, z, u1, a1, u2, a2, u3, a3);
+}
+
+double or_mlp_loss_grad(const double *params, const double *z, const double *t, int n, double *grad) {
+  or_mlp_view m = or_mlp_split(params);
+  memset(grad, 0, sizeof(double) * OR_MLP_NPARAM);
+  double *gW1 = grad, *gb1 = gW1 + 3 * OR_MLP_H, *gW2 = gb1 + OR_MLP_H, *gb2 = gW2 + OR_MLP_H * OR_MLP_H;
+  double *gW3 = gb2 + OR_MLP_H, *gb3 = gW3 + OR_MLP_H * OR_MLP_H, *gW4 = gb3 + OR_MLP_H, *gb4 = gW4 + OR_MLP_H;
+  double loss = 0.0;
+  for (int s = 0; s < n; ++s) {
+    double u1[OR_MLP_H], a1[OR_MLP_H], u2[OR_MLP_H], a2[OR_MLP_H], u3[OR_MLP_H], a3[OR_MLP_H];
+    const double *zs = z + 3 * s;
+    double f = or_mlp_fwd(&m, zs, u1, a1, u2, a2, u3, a3);
+    double r = f - t[s];
+    loss += r * r;
+    double df = 2.0 * r / n;
+    double d3[OR_MLP_H], d2[OR_MLP_H], d1[OR_MLP_H];
+    gb4[0] += df;
+    for (int i = 0; i < OR_MLP_H; ++i) {
+      gW4[i] += a3[i] * df;
+      d3[i] = df * m.W4[i] * or_dsilu(u3[i]);
+    }
+    for (int j = 0; j < OR_MLP_H; ++j) gb3[j] += d3[j];
+    for (int i = 0; i < OR_MLP_H; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < OR_MLP_H; ++j) {
+        gW3[i * OR_MLP_H + j] += a2[i] * d3[j];
+        acc += m.W3[i * OR_MLP_H + j] * d3[j];
+      }
+      d2[i] = acc * or_dsilu(u2[i]);
+    }
+    for (int j = 0; j < OR_MLP_H; ++j) gb2[j] += d2[j];
+    for (int i = 0; i < OR_MLP_H; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < OR_MLP_H; ++j) {
+        gW2[i * OR_MLP_H + j] += a1[i] * d2[j];
+        acc += m.W2[i * OR_MLP_H + j] * d2[j];
+      }
+      d1[i] = acc * or_dsilu(u1[i]);
+    }
+    for (int j = 0; j < OR_MLP_H; ++j) gb1[j] += d1[j];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < OR_MLP_H; ++j) gW1[i * OR_MLP_H + j] += zs[i] * d1[j];
+  }
+  return loss / n;
+}

@@ -121,6 +121,8 @@ void or_F_points(const or_tables *t, const double *hess, int64_t n, int64_t plan
  * table the R-LPT root is used. */
 double or_cubic_largest_root(double b, double c, double d); /* of u^3 + b u^2 + c u + d */
 double or_tab_node_value(double delta, double x, double y);  /* u at a node, eigenvalues from (delta, x, y) */
+void or_tab_node_values(int nd, const double *dg, int nx, const double *xg, int ny, const double *yg,
+                        double *out); /* every node, layout [ix][iy][k] */
 
 typedef struct {
   int nd, nx, ny;
@@ -135,6 +137,17 @@ double or_tab_query(const or_tab *t, double delta, double x, double y);
 double or_F_tab_point(const or_tables *t, const or_tab *tab, const double h[6], int *flags);
 void or_F_tab_points(const or_tables *t, const or_tab *tab, const double *hess, int64_t n, int64_t plane_stride,
                      double *F, int32_t *flags, int nthreads);
+
+/* ---- learned surrogate: MLP 3-64-64-64-1 with SiLU, FP64 (gradient reference) ----
+ * f(z) = W4 . s(W3 s(W2 s(W1 z + b1) + b2) + b3) + b4, s(v) = v / (1 + exp(-v)),
+ * z = (l1, l2, l3) / sigma, f ~ log(D_c sigma). Parameters flattened as
+ * W1[3][64], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[64], b4
+ * (W[in][out]). Loss = mean (f(z_i) - t_i)^2. No counterpart in the paper:
+ * this checks the GPU training kernels. */
+#define OR_MLP_H 64
+#define OR_MLP_NPARAM (3 * 64 + 64 + 64 * 64 + 64 + 64 * 64 + 64 + 64 + 1)
+double or_mlp_forward(const double *params, const double z[3]);
+double or_mlp_loss_grad(const double *params, const double *z, const double *t, int n, double *grad);
 
 #ifdef __cplusplus
 }

@@ -263,6 +263,35 @@ class Context:
     def collapse_multi_host(self, hess, sigma, F_max, idx, scale_idx0=0, mode="fp64", stream=None):
         cc_collapse_multi_host(self._h, mode, hess, sigma, F_max, idx, scale_idx0, stream)
 
+    # ---- tabulated collapse and interpolation routines
+    def set_table(self, dgrid, xgrid, ygrid, values, stream=None):
+        """values: (nx, ny, nd) array of u = 1/D_c at the nodes (host)."""
+        dg, xg, yg = (np.ascontiguousarray(a, dtype=np.float64) for a in (dgrid, xgrid, ygrid))
+        v = np.ascontiguousarray(values, dtype=np.float64).reshape(len(xg), len(yg), len(dg))
+        _lib.check(_lib.load().cc_set_table(self._h, dg.ctypes.data, len(dg), xg.ctypes.data, len(xg),
+                                            yg.ctypes.data, len(yg), v.ctypes.data, _stream_ptr(stream)),
+                   "cc_set_table")
+
+    def table_nodes_rlpt(self, dgrid, xgrid, ygrid, stream=None) -> np.ndarray:
+        dg, xg, yg = (np.ascontiguousarray(a, dtype=np.float64) for a in (dgrid, xgrid, ygrid))
+        out = np.empty((len(xg), len(yg), len(dg)))
+        _lib.check(_lib.load().cc_table_nodes_rlpt(self._h, dg.ctypes.data, len(dg), xg.ctypes.data, len(xg),
+                                                   yg.ctypes.data, len(yg), out.ctypes.data, _stream_ptr(stream)),
+                   "cc_table_nodes_rlpt")
+        return out
+
+    def table_query(self, d, x, y, out, stream=None):
+        """d, x, y, out: float64 CUDA tensors of equal length."""
+        m = d.numel()
+        _lib.check(_lib.load().cc_table_query(self._h, d.data_ptr(), x.data_ptr(), y.data_ptr(), m,
+                                              out.data_ptr(), _stream_ptr(stream)), "cc_table_query")
+
+    def spline_eval(self, xk, yk, q, out, stream=None):
+        """xk, yk: host knots; q, out: float64 CUDA tensors."""
+        xk, yk = (np.ascontiguousarray(a, dtype=np.float64) for a in (xk, yk))
+        _lib.check(_lib.load().cc_spline_eval(self._h, xk.ctypes.data, yk.ctypes.data, len(xk), q.data_ptr(),
+                                              q.numel(), out.data_ptr(), _stream_ptr(stream)), "cc_spline_eval")
+
     def stats(self, stream=None) -> dict:
         return cc_get_stats(self._h, stream)
 

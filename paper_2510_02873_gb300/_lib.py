@@ -16,7 +16,8 @@ EXPORTS = (
     "cc_create", "cc_destroy", "cc_build_growth_table", "cc_get_growth_table", "cc_reset_max", "cc_collapse_scale",
     "cc_collapse_multi", "cc_collapse_multi_host", "cc_collapse_multi_noalloc", "cc_get_stats", "cc_reset_stats", "cc_strerror",
     "cc_last_error_message", "cc_version", "cc_batch_create", "cc_batch_autotune", "cc_batch_run",
-    "cc_batch_run_graph", "cc_batch_get_config", "cc_batch_destroy",
+    "cc_batch_run_graph", "cc_batch_get_config", "cc_batch_destroy", "cc_set_table", "cc_table_nodes_rlpt",
+    "cc_table_query", "cc_spline_eval",
 )
 
 
@@ -90,6 +91,10 @@ def load() -> ctypes.CDLL:
         L.cc_batch_get_config.argtypes = [vp, ctypes.POINTER(i32), vp, i32]
         L.cc_batch_destroy.argtypes = [vp]
         L.cc_batch_destroy.restype = None
+        L.cc_set_table.argtypes = [vp, vp, i32, vp, i32, vp, i32, vp, vp]
+        L.cc_table_nodes_rlpt.argtypes = [vp, vp, i32, vp, i32, vp, i32, vp, vp]
+        L.cc_table_query.argtypes = [vp, vp, vp, vp, i64, vp, vp]
+        L.cc_spline_eval.argtypes = [vp, vp, vp, i32, vp, i64, vp, vp]
         L.cc_reset_stats.argtypes = [vp, vp]
         L.cc_strerror.argtypes = [ctypes.c_int]
         L.cc_strerror.restype = ctypes.c_char_p
@@ -99,7 +104,8 @@ def load() -> ctypes.CDLL:
         for name in ("cc_build_growth_table", "cc_get_growth_table", "cc_reset_max", "cc_collapse_scale",
                      "cc_collapse_multi", "cc_collapse_multi_host", "cc_collapse_multi_noalloc",
                      "cc_get_stats", "cc_reset_stats", "cc_version", "cc_batch_create", "cc_batch_autotune",
-                     "cc_batch_run", "cc_batch_run_graph", "cc_batch_get_config"):
+                     "cc_batch_run", "cc_batch_run_graph", "cc_batch_get_config", "cc_set_table",
+                     "cc_table_nodes_rlpt", "cc_table_query", "cc_spline_eval"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L

@@ -85,8 +85,9 @@ int run_collapse(cc_ctx* ctx, cc_mode mode, const void* hess, int32_t dtype, int
       return launch_fp64(a, ctx->tab);
     case CC_MODE_MIXED:
       return launch_mixed(a, ctx->tab, sigma);
-    case CC_MODE_SURROGATE:
     case CC_MODE_TABULATED:
+      return launch_tab_checked(ctx, a);
+    case CC_MODE_SURROGATE:
       return set_error(CC_ENOTSUP, "mode not available in this build");
   }
   return set_error(CC_EINVAL, "unknown mode");
@@ -237,6 +238,10 @@ void cc_destroy(cc_ctx* ctx) {
   if (ctx->d_F) cudaFree(ctx->d_F);
   if (ctx->d_idx) cudaFree(ctx->d_idx);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->d_tab_axes) cudaFree(ctx->d_tab_axes);
+  if (ctx->d_tab_coef) cudaFree(ctx->d_tab_coef);
+  if (ctx->d_tab_work) cudaFree(ctx->d_tab_work);
+  if (ctx->d_spl) cudaFree(ctx->d_spl);
   if (cur >= 0 && cur != ctx->device) cudaSetDevice(cur);
   delete ctx;
 }

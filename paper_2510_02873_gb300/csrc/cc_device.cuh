@@ -119,23 +119,18 @@ struct PointResult {
   bool collapsed, eds, refined;
 };
 
-// FP64 collapse value of one point, F = 1/a_c (0 when there is no collapse).
-//   eigenvalues: invariants of M = A - qI in FP64 (q = tr/3, s6 = |M|_F^2 = 6 p^2,
-//     det M); l1 = q + x with x the largest root of x^3 - 3 p^2 x - det M = 0,
-//     seeded by the FP32 trigonometric solution and corrected by two FP64
-//     Newton steps (FP32 derivative at each iterate); l2 l3 and l2^2 + l3^2
-//     from the invariants
-//     (l2 + l3 = 2q - x, l2 l3 = q (q - x) + x^2 - 3 p^2);
-//   collapse: A_1(D) = 1 - l1 D + c2 D^2 + c3 D^3, root seeded in FP32 from the
-//     FP64 coefficients rounded to FP32 (closed form in u = 1/D, two FP32
-//     Newton steps) and corrected by one FP64 Newton step;
-//   spline: interval from the FP32 search, FP64 Horner; F by one FP64 Newton
-//     step of the reciprocal from the FP32 reciprocal.
-__device__ __forceinline__ PointResult collapse_point_fp64(
-    double xx, double yy, double zz, double xy, double xz, double yz, const double* __restrict__ Dk,
-    const Coef4* __restrict__ coef, const float* __restrict__ Dkf,
-    const unsigned short* __restrict__ bucket, const DevTable& tab) {
-  PointResult res;
+struct EigenTop {
+  double q, x, p2x3, det;  // tr/3, l1 - q, 3 p^2, det(A - qI)
+  float p2f;
+  bool refined;            // l1 ~ l2 re-solved by deflation
+};
+
+// Largest eigenvalue l1 = q + x of the symmetric matrix in FP64 (FP32 trigonometric
+// seed, two FP64 Newton steps on the depressed characteristic cubic, deflation
+// when l1 ~ l2) together with the invariants the collapse condition needs.
+__device__ __forceinline__ EigenTop eigen_top_fp64(double xx, double yy, double zz, double xy, double xz,
+                                                   double yz) {
+  EigenTop e;
   // ---- invariants (FP64)
   const double q = (xx + yy + zz) * (1.0 / 3.0);
   const double a = xx - q, b = yy - q, c = zz - q;
@@ -165,8 +160,8 @@ __device__ __forceinline__ PointResult collapse_point_fp64(
     const double g = fma(x, x * x - p2x3, -det);
     x = fma(-g, yg, x);
   }
-  res.refined = (1.0f + rf) < kPairTauF && p2f > 0.0f;
-  if (res.refined) {
+  e.refined = (1.0f + rf) < kPairTauF && p2f > 0.0f;
+  if (e.refined) {
     // l1 ~ l2: refine the isolated l3 by Newton (FP64 derivative), then deflate
     double x3 = static_cast<double>(x3f);
 #pragma unroll
@@ -178,10 +173,18 @@ __device__ __forceinline__ PointResult collapse_point_fp64(
     refine_top_pair(xx, yy, zz, xy, xz, yz, q + x3, l1r, l2r);
     x = l1r - q;
   }
-  // ---- collapse condition coefficients (FP64)
-  const double lam1 = q + x;
-  const double Pp = fma(q, q - x, fma(x, x, -p2x3));  // l2 l3
-  const double S = fma(2.0, q, -x);                    // l2 + l3
+  e.q = q;
+  e.x = x;
+  e.p2x3 = p2x3;
+  e.det = det;
+  e.p2f = p2f;
+  return e;
+}
+
+// Growth factor at collapse from l1, l2 l3 and l2 + l3 (R-LPT): the FP64
+// coefficients of A_1(D) = 1 - l1 D + c2 D^2 + c3 D^3, an FP32 seed from them
+// (closed form in u = 1/D and two FP32 Newton steps) and one FP64 Newton step.
+__device__ __forceinline__ double rlpt_root_fp64(double lam1, double Pp, double S) {
   const double Q2 = fma(-2.0, Pp, S * S);              // l2^2 + l3^2
   const double c2 = (-3.0 / 7.0) * Pp;
   const double c3 = lam1 * fma(-5.0 / 21.0, Q2, Pp * (1.0 / 9.0));
@@ -203,6 +206,34 @@ __device__ __forceinline__ PointResult collapse_point_fp64(
   double D = static_cast<double>(Df);
   const double A1 = fma(fma(fma(c3, D, c2), D, -lam1), D, 1.0);
   D = fma(-A1, static_cast<double>(1.0f / dAf), D);
+  return D;
+}
+
+// FP64 collapse value of one point, F = 1/a_c (0 when there is no collapse).
+//   eigenvalues: invariants of M = A - qI in FP64 (q = tr/3, s6 = |M|_F^2 = 6 p^2,
+//     det M); l1 = q + x with x the largest root of x^3 - 3 p^2 x - det M = 0,
+//     seeded by the FP32 trigonometric solution and corrected by two FP64
+//     Newton steps (FP32 derivative at each iterate); l2 l3 and l2^2 + l3^2
+//     from the invariants
+//     (l2 + l3 = 2q - x, l2 l3 = q (q - x) + x^2 - 3 p^2);
+//   collapse: A_1(D) = 1 - l1 D + c2 D^2 + c3 D^3, root seeded in FP32 from the
+//     FP64 coefficients rounded to FP32 (closed form in u = 1/D, two FP32
+//     Newton steps) and corrected by one FP64 Newton step;
+//   spline: interval from the FP32 search, FP64 Horner; F by one FP64 Newton
+//     step of the reciprocal from the FP32 reciprocal.
+__device__ __forceinline__ PointResult collapse_point_fp64(
+    double xx, double yy, double zz, double xy, double xz, double yz, const double* __restrict__ Dk,
+    const Coef4* __restrict__ coef, const float* __restrict__ Dkf,
+    const unsigned short* __restrict__ bucket, const DevTable& tab) {
+  PointResult res;
+  const EigenTop e = eigen_top_fp64(xx, yy, zz, xy, xz, yz);
+  res.refined = e.refined;
+  const double q = e.q, x = e.x, p2x3 = e.p2x3;
+  // ---- collapse condition coefficients (FP64) and root
+  const double lam1 = q + x;
+  const double Pp = fma(q, q - x, fma(x, x, -p2x3));  // l2 l3
+  const double S = fma(2.0, q, -x);                    // l2 + l3
+  const double D = rlpt_root_fp64(lam1, Pp, S);
   // ---- collapse test on bit patterns: l1 > 0, 0 < D <= D_top
   const long long bD = bits(D);
   res.collapsed = bits(lam1) > 0 && bD > 0 && bD <= bits(tab.Dtop);
@@ -244,13 +275,18 @@ struct MixedResult {
   bool collapsed, eds, refined, fp64;
 };
 
-__device__ __forceinline__ MixedResult collapse_point_mixed(
-    float xx, float yy, float zz, float xy, float xz, float yz, float tri_thr,
-    const double* __restrict__ Dk, const Coef4* __restrict__ coef, const float* __restrict__ Dkf,
-    const unsigned short* __restrict__ bucket, const DevTable& tab) {
-  MixedResult res;
-  res.refined = false;
-  res.fp64 = false;
+// FP32 eigenvalue stage of the mixed path (shared with the surrogate path).
+struct MixedEigen {
+  float q, x, x2, x3, p2x3, lam1f;  // x = l1 - q (x2, x3: FP32 seeds of l2 - q, l3 - q)
+  double lam1;                      // l1, refined in FP64 when flagged
+  bool full;                        // take the whole FP64 path instead
+  bool fp64;                        // the FP64 eigenvalue refinement ran
+};
+
+__device__ __forceinline__ MixedEigen mixed_eigen(float xx, float yy, float zz, float xy, float xz, float yz,
+                                                  float tri_thr) {
+  MixedEigen m;
+  m.fp64 = false;
   // ---- FP32 invariants and trigonometric eigenvalues
   const float q = (xx + yy + zz) * (1.0f / 3.0f);
   const float a = xx - q, b = yy - q, c = zz - q;
@@ -270,20 +306,11 @@ __device__ __forceinline__ MixedResult collapse_point_mixed(
     const float gp = 3.0f * (x * x - p2);
     x = (gp != 0.0f) ? x - fmaf(x, x * x - p2x3, -det) / gp : x;
   }
-  const bool full = ((1.0f + rf) < kPairTauF && p2 > 0.0f) || (x - x3) < tri_thr;
-  if (full) {
-    const PointResult r64 = collapse_point_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
-    res.F = r64.F;
-    res.collapsed = r64.collapsed;
-    res.eds = r64.eds;
-    res.refined = r64.refined;
-    res.fp64 = true;
-    return res;
-  }
+  m.full = ((1.0f + rf) < kPairTauF && p2 > 0.0f) || (x - x3) < tri_thr;
   const float lam1f = q + x;
   double lam1 = static_cast<double>(lam1f);
   const float est = kMixedEstCoef * p2 * pf / fmaxf((x - x2) * (x - x3) * fabsf(lam1f), 1e-30f);
-  if (est > kMixedEstTau) {
+  if (!m.full && est > kMixedEstTau) {
     // one FP64 Newton step on g(l) = det(A - l I); g'(l) = -3 (x^2 - p^2) from FP32
     const double dxx = static_cast<double>(xx) - lam1, dyy = static_cast<double>(yy) - lam1;
     const double dzz = static_cast<double>(zz) - lam1;
@@ -293,39 +320,206 @@ __device__ __forceinline__ MixedResult collapse_point_mixed(
     const float gpf = 3.0f * (x * x - p2);
     lam1 = fma(g, static_cast<double>(1.0f / gpf), lam1);
     x = static_cast<float>(lam1 - static_cast<double>(q));
-    res.fp64 = true;
+    m.fp64 = true;
   }
-  // ---- FP32 collapse-condition coefficients
-  const float Pp = fmaf(q, q - x, fmaf(x, x, -p2x3));  // l2 l3
-  const float S = fmaf(2.0f, q, -x);                   // l2 + l3
-  const float Q2 = fmaf(-2.0f, Pp, S * S);             // l2^2 + l3^2
-  const float l1f = static_cast<float>(lam1);
-  const float c2f = (-3.0f / 7.0f) * Pp;
-  const float c3f = l1f * fmaf(-5.0f / 21.0f, Q2, Pp * (1.0f / 9.0f));
-  const float uf = cubic_largest_root_f32(-l1f, c2f, c3f);
-  float Df = 1.0f / uf;
+  m.q = q;
+  m.x = x;
+  m.x2 = x2;
+  m.x3 = x3;
+  m.p2x3 = p2x3;
+  m.lam1f = lam1f;
+  m.lam1 = lam1;
+  return m;
+}
+
+// FP32 collapse-condition coefficients of the mixed path
+struct MixedCoef {
+  float l1f, c2f, c3f;
+};
+
+__device__ __forceinline__ MixedCoef mixed_coef(const MixedEigen& m) {
+  const float q = m.q, x = m.x;
+  const float Pp = fmaf(q, q - x, fmaf(x, x, -m.p2x3));  // l2 l3
+  const float S = fmaf(2.0f, q, -x);                     // l2 + l3
+  const float Q2 = fmaf(-2.0f, Pp, S * S);               // l2^2 + l3^2
+  MixedCoef k;
+  k.l1f = static_cast<float>(m.lam1);
+  k.c2f = (-3.0f / 7.0f) * Pp;
+  k.c3f = k.l1f * fmaf(-5.0f / 21.0f, Q2, Pp * (1.0f / 9.0f));
+  return k;
+}
+
+// FP32 Newton steps on A_1(D) = 1 - l1 D + c2 D^2 + c3 D^3 from Df
+template <int kSteps>
+__device__ __forceinline__ float newton_f32(const MixedCoef& k, float Df) {
 #pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const float Af = fmaf(fmaf(fmaf(c3f, Df, c2f), Df, -l1f), Df, 1.0f);
-    const float dAf = fmaf(fmaf(3.0f * c3f, Df, 2.0f * c2f), Df, -l1f);
+  for (int it = 0; it < kSteps; ++it) {
+    const float Af = fmaf(fmaf(fmaf(k.c3f, Df, k.c2f), Df, -k.l1f), Df, 1.0f);
+    const float dAf = fmaf(fmaf(3.0f * k.c3f, Df, 2.0f * k.c2f), Df, -k.l1f);
     Df -= Af / dAf;
   }
-  const float dAf = fmaf(fmaf(3.0f * c3f, Df, 2.0f * c2f), Df, -l1f);
-  // ---- FP64 root polish: one Newton step on A_1 with the FP32 coefficients
+  return Df;
+}
+
+// From an FP32 root Df: one FP64 Newton step (the root polish), the FP64
+// a(D) spline and F.
+__device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const MixedCoef& k, float Df,
+                                                    const double* __restrict__ Dk, const Coef4* __restrict__ coef,
+                                                    const float* __restrict__ Dkf,
+                                                    const unsigned short* __restrict__ bucket, const DevTable& tab) {
+  MixedResult res;
+  res.refined = false;
+  res.fp64 = m.fp64;
+  const float dAf = fmaf(fmaf(3.0f * k.c3f, Df, 2.0f * k.c2f), Df, -k.l1f);
   double D = static_cast<double>(Df);
-  const double A1 = fma(fma(fma(static_cast<double>(c3f), D, static_cast<double>(c2f)), D, -lam1), D, 1.0);
+  const double A1 = fma(fma(fma(static_cast<double>(k.c3f), D, static_cast<double>(k.c2f)), D, -m.lam1), D, 1.0);
   D = fma(-A1, static_cast<double>(1.0f / dAf), D);
   const long long bD = bits(D);
-  res.collapsed = lam1f > 0.0f && bD > 0 && bD <= bits(tab.Dtop);
+  res.collapsed = m.lam1f > 0.0f && bD > 0 && bD <= bits(tab.Dtop);
   const double Dc = res.collapsed ? D : tab.Dtop;
-  // ---- FP64 spline (interval from the FP32 root)
-  const int k = spline_interval(Dkf, bucket, tab, res.collapsed ? Df : static_cast<float>(tab.Dtop));
-  const Coef4 cf = coef[k];
-  const double t = Dc - Dk[k];
+  const int kk = spline_interval(Dkf, bucket, tab, res.collapsed ? Df : static_cast<float>(tab.Dtop));
+  const Coef4 cf = coef[kk];
+  const double t = Dc - Dk[kk];
   double av = fma(fma(fma(cf.c3, t, cf.c2), t, cf.c1), t, cf.c0);
   res.eds = res.collapsed && bits(Dc) < bits(tab.D0);
   if (res.eds) av = tab.eds_slope * Dc;
   res.F = res.collapsed ? static_cast<double>(1.0f / static_cast<float>(av)) : 0.0;
+  return res;
+}
+
+__device__ __forceinline__ MixedResult full_fp64(float xx, float yy, float zz, float xy, float xz, float yz,
+                                                 const double* __restrict__ Dk, const Coef4* __restrict__ coef,
+                                                 const float* __restrict__ Dkf,
+                                                 const unsigned short* __restrict__ bucket, const DevTable& tab) {
+  const PointResult r64 = collapse_point_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
+  MixedResult res;
+  res.F = r64.F;
+  res.collapsed = r64.collapsed;
+  res.eds = r64.eds;
+  res.refined = r64.refined;
+  res.fp64 = true;
+  return res;
+}
+
+__device__ __forceinline__ MixedResult collapse_point_mixed(
+    float xx, float yy, float zz, float xy, float xz, float yz, float tri_thr,
+    const double* __restrict__ Dk, const Coef4* __restrict__ coef, const float* __restrict__ Dkf,
+    const unsigned short* __restrict__ bucket, const DevTable& tab) {
+  const MixedEigen m = mixed_eigen(xx, yy, zz, xy, xz, yz, tri_thr);
+  if (m.full) return full_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
+  const MixedCoef k = mixed_coef(m);
+  // FP32 closed-form root of u^3 - l1 u^2 + c2 u + c3 (u = 1/D), two FP32 Newton steps on A_1
+  const float uf = cubic_largest_root_f32(-k.l1f, k.c2f, k.c3f);
+  const float Df = newton_f32<2>(k, 1.0f / uf);
+  return mixed_finish(m, k, Df, Dk, coef, Dkf, bucket, tab);
+}
+
+// ---------------------------------------------------------------------------
+// Tabulated collapse (Sec. 3 "Tabulated" option; Sec. 4.2: cubic spline along
+// delta at the four (x, y) corners of the cell, bilinear blend). The table holds
+// u = 1/D_c; outside it the R-LPT root is used.
+
+__device__ __forceinline__ double horner(const Coef4& c, double t) {
+  return fma(fma(fma(c.c3, t, c.c2), t, c.c1), t, c.c0);
+}
+
+// u(delta, x, y) from the table; ax is the axes image (shared memory), x, y >= 0.
+// Cells in x and y are found on FP64 bit patterns (exact: bilinear interpolation
+// is only continuous across cell edges); the delta interval by an FP32 search
+// (the spline is C2 across its knots).
+__device__ __forceinline__ double tab_interp(const TabDev& td, const double* __restrict__ ax,
+                                             const Coef4* __restrict__ tcoef, double delta, double x, double y) {
+  const double* dg = ax;
+  const double* xg = dg + td.nd;
+  const double* yg = xg + td.nx;
+  const double* ihx = yg + td.ny;
+  const double* ihy = ihx + (td.nx - 1);
+  const float* dgf = reinterpret_cast<const float*>(ihy + (td.ny - 1));
+  const long long bx = bits(x), by = bits(y);
+  int ix = 0, iy = 0, kd = 0;
+  for (int step = td.x_steps; step > 0; step >>= 1) {
+    const int j = ix + step;
+    ix = (j <= td.nx - 2 && bits(xg[j]) <= bx) ? j : ix;
+  }
+  for (int step = td.y_steps; step > 0; step >>= 1) {
+    const int j = iy + step;
+    iy = (j <= td.ny - 2 && bits(yg[j]) <= by) ? j : iy;
+  }
+  const float df = static_cast<float>(delta);
+  for (int step = td.d_steps; step > 0; step >>= 1) {
+    const int j = kd + step;
+    kd = (j <= td.nd - 2 && dgf[j] <= df) ? j : kd;
+  }
+  const double t = delta - dg[kd];
+  const size_t nseg = static_cast<size_t>(td.nd - 1);
+  const size_t s00 = (static_cast<size_t>(ix) * td.ny + iy) * nseg + kd;
+  const size_t sx = static_cast<size_t>(td.ny) * nseg;
+  const double z00 = horner(tcoef[s00], t);
+  const double z10 = horner(tcoef[s00 + sx], t);
+  const double z01 = horner(tcoef[s00 + nseg], t);
+  const double z11 = horner(tcoef[s00 + sx + nseg], t);
+  const double tx = (x - xg[ix]) * ihx[ix];
+  const double ty = (y - yg[iy]) * ihy[iy];
+  const double z0 = fma(tx, z10 - z00, z00);
+  const double z1 = fma(tx, z11 - z01, z01);
+  return fma(ty, z1 - z0, z0);
+}
+
+struct TabResult {
+  double F;
+  bool collapsed, eds, refined, outside;
+};
+
+__device__ __forceinline__ TabResult collapse_point_tab(
+    double xx, double yy, double zz, double xy, double xz, double yz, const double* __restrict__ Dk,
+    const Coef4* __restrict__ coef, const float* __restrict__ Dkf, const unsigned short* __restrict__ bucket,
+    const DevTable& tab, const TabDev& td, const double* __restrict__ ax, const Coef4* __restrict__ tcoef) {
+  TabResult res;
+  const EigenTop e = eigen_top_fp64(xx, yy, zz, xy, xz, yz);
+  res.refined = e.refined;
+  const double q = e.q, x = e.x, p2x3 = e.p2x3;
+  const double lam1 = q + x;
+  const double Pp = fma(q, q - x, fma(x, x, -p2x3));  // l2 l3
+  const double S = fma(2.0, q, -x);                    // l2 + l3
+  // y = l2 - l3 from (l2 + l3)^2 - 4 l2 l3; near l2 = l3 that difference
+  // cancels, so the pair is re-solved by deflation around the isolated l1
+  const double D2 = fma(S, S, -4.0 * Pp);
+  double l2, l3;
+  if (D2 < 1e-10 * p2x3) {
+    l2 = 0.5 * S;
+    l3 = 0.5 * S;
+    refine_top_pair(xx, yy, zz, xy, xz, yz, lam1, l2, l3);
+    res.refined = true;
+  } else {
+    const double yv = sqrt(D2);
+    l2 = 0.5 * (S + yv);
+    l3 = 0.5 * (S - yv);
+  }
+  double yv = l2 - l3, xv = lam1 - l2;
+  yv = bits(yv) > 0 ? yv : 0.0;
+  xv = bits(xv) > 0 ? xv : 0.0;
+  const double delta = xx + yy + zz;
+  res.outside = !(delta >= td.d_lo && delta <= td.d_hi && bits(xv) <= bits(td.x_hi) && bits(yv) <= bits(td.y_hi));
+  double D;
+  bool root = true;
+  if (!res.outside) {
+    const double u = tab_interp(td, ax, tcoef, delta, xv, yv);
+    const double r0 = static_cast<double>(1.0f / static_cast<float>(u));
+    D = fma(r0, fma(-u, r0, 1.0), r0);  // 1/u: FP32 reciprocal + one FP64 Newton step
+    root = bits(u) > 0;
+  } else {
+    D = rlpt_root_fp64(lam1, Pp, S);
+  }
+  const long long bD = bits(D);
+  res.collapsed = bits(lam1) > 0 && root && bD > 0 && bD <= bits(tab.Dtop);
+  const double Dc = res.collapsed ? D : tab.Dtop;
+  const int k = spline_interval(Dkf, bucket, tab, static_cast<float>(Dc));
+  double av = horner(coef[k], Dc - Dk[k]);
+  res.eds = res.collapsed && bits(Dc) < bits(tab.D0);
+  if (res.eds) av = tab.eds_slope * Dc;
+  const double y0 = static_cast<double>(1.0f / static_cast<float>(av));
+  const double F = fma(y0, fma(-av, y0, 1.0), y0);
+  res.F = res.collapsed ? F : 0.0;
   return res;
 }
 

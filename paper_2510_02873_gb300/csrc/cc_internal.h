@@ -53,6 +53,22 @@ struct DevTable {
   }
 };
 
+// Tabulated collapse: table of u = 1/D_c over (delta, x = l1 - l2, y = l2 - l3),
+// natural cubic splines along delta (per-interval coefficients, built on the
+// device), bilinear in (x, y).
+constexpr int kTabMaxD = 256;
+constexpr int kTabMaxXY = 256;
+struct TabDev {
+  const double* axes;  // image: dg[nd] | xg[nx] | yg[ny] | 1/hx[nx-1] | 1/hy[ny-1] | dgf (float)[nd]
+  const Coef4* coef;   // [(ix * ny + iy) * (nd - 1) + k]
+  int nd, nx, ny;
+  int d_steps, x_steps, y_steps;  // largest power of two <= n - 2 (branch-free searches)
+  double d_lo, d_hi, x_hi, y_hi;
+  __host__ __device__ size_t axes_bytes() const {
+    return sizeof(double) * (nd + nx + ny + (nx - 1) + (ny - 1)) + sizeof(float) * nd;
+  }
+};
+
 // host tables (cc_tables.cpp)
 int build_growth_table(const cc_cosmology& c, std::vector<double>& a_k, std::vector<double>& D_k);
 int build_natural_spline(const std::vector<double>& x, const std::vector<double>& y,
@@ -88,9 +104,15 @@ struct LaunchArgs {
 };
 int launch_fp64(const LaunchArgs& a, const DevTable& tab);
 int launch_mixed(const LaunchArgs& a, const DevTable& tab, const double* sigma);
+int launch_tab(const LaunchArgs& a, const DevTable& tab, const TabDev& td);
 int launch_reset_max(double* F_max, int32_t* idx, int64_t n, cudaStream_t stream, int num_sms);
 
 }  // namespace cc
+
+struct cc_ctx;
+namespace cc {
+int launch_tab_checked(cc_ctx* ctx, const LaunchArgs& a);  // cc_tab.cu
+}
 
 struct cc_ctx {
   int device = -1;
@@ -109,4 +131,16 @@ struct cc_ctx {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_consumed[2] = {nullptr, nullptr};
+  // tabulated mode (cc_set_table)
+  bool tab_valid = false;
+  void* d_tab_axes = nullptr;
+  size_t tab_axes_cap = 0;
+  cc::Coef4* d_tab_coef = nullptr;
+  size_t tab_coef_cap = 0;
+  double* d_tab_work = nullptr;  // node values and tridiagonal scratch
+  size_t tab_work_cap = 0;
+  cc::TabDev tabdev{};
+  // interpolation toy (cc_spline_eval)
+  void* d_spl = nullptr;
+  size_t spl_cap = 0;
 };

@@ -39,13 +39,17 @@ __device__ __forceinline__ void add_counters(DevCounters* cnt, unsigned evals, u
   }
 }
 
+constexpr int kModeFP64 = 0, kModeMixed = 1, kModeTab = 2;
+
 // One thread per point (grid-stride), all R radii of the launch in registers.
-// kMixed selects collapse_point_mixed (FP32 bulk) over collapse_point_fp64.
-template <typename T, bool kSmem, bool kMixed>
+// kMode selects collapse_point_fp64, collapse_point_mixed (FP32 bulk) or
+// collapse_point_tab (tabulated 1/D_c; its axes follow the spline table in
+// shared memory).
+template <typename T, bool kSmem, int kMode>
 __global__ void __launch_bounds__(kThreads)
 collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
                 int64_t radius_stride, int R, int32_t scale_idx0, DevTable tab, RadiusParams rp,
-                double* __restrict__ F_max, int32_t* __restrict__ idx,
+                TabDev td, double* __restrict__ F_max, int32_t* __restrict__ idx,
                 DevCounters* __restrict__ cnt) {
   extern __shared__ Coef4 smem_tab[];
   const Coef4* coef = tab.coef;
@@ -68,6 +72,15 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
     Dkf = reinterpret_cast<const float*>(Dk + tab.n);
     bucket = reinterpret_cast<const unsigned short*>(Dkf + tab.n);
   }
+  const double* tax = nullptr;
+  if constexpr (kMode == kModeTab) {
+    // axes image after the spline image (16-byte aligned offset)
+    double* dst = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(smem_tab) + ((tab.bytes() + 15) / 16) * 16);
+    const int nwords = static_cast<int>((td.axes_bytes() + 7) / 8);
+    for (int i = threadIdx.x; i < nwords; i += blockDim.x) dst[i] = td.axes[i];
+    __syncthreads();
+    tax = dst;
+  }
   unsigned n_eval = 0, n_coll = 0, n_eds = 0, n_ref = 0, n_fp64 = 0;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   // whole warps stay in the loop together so the warp-level counter reduction
@@ -83,7 +96,7 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
       for (int r = 0; r < R; ++r) {
         const T* h = base + static_cast<int64_t>(r) * radius_stride;
         double F;
-        if constexpr (kMixed) {
+        if constexpr (kMode == kModeMixed) {
           const float xx = ldf(h), yy = ldf(h + plane_stride), zz = ldf(h + 2 * plane_stride);
           const float xy = ldf(h + 3 * plane_stride), xz = ldf(h + 4 * plane_stride);
           const float yz = ldf(h + 5 * plane_stride);
@@ -93,6 +106,16 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
           n_eds += res.eds;
           n_ref += res.refined;
           n_fp64 += res.fp64;
+          F = res.F;
+        } else if constexpr (kMode == kModeTab) {
+          const double xx = ld(h), yy = ld(h + plane_stride), zz = ld(h + 2 * plane_stride);
+          const double xy = ld(h + 3 * plane_stride), xz = ld(h + 4 * plane_stride);
+          const double yz = ld(h + 5 * plane_stride);
+          const TabResult res = collapse_point_tab(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab, td, tax, td.coef);
+          n_coll += res.collapsed;
+          n_eds += res.eds;
+          n_ref += res.refined;
+          n_fp64 += res.outside;
           F = res.F;
         } else {
           const double xx = ld(h), yy = ld(h + plane_stride), zz = ld(h + 2 * plane_stride);
@@ -125,10 +148,11 @@ __global__ void reset_max_kernel(double* __restrict__ F_max, int32_t* __restrict
   }
 }
 
-template <typename T, bool kSmem, bool kMixed>
-int launch_typed(const LaunchArgs& a, const DevTable& tab, const RadiusParams& rp) {
-  auto kern = collapse_kernel<T, kSmem, kMixed>;
-  const size_t smem = kSmem ? ((tab.bytes() + 15) / 16) * 16 : 0;
+template <typename T, bool kSmem, int kMode>
+int launch_typed(const LaunchArgs& a, const DevTable& tab, const RadiusParams& rp, const TabDev& td) {
+  auto kern = collapse_kernel<T, kSmem, kMode>;
+  size_t smem = kSmem ? ((tab.bytes() + 15) / 16) * 16 : 0;
+  if (kMode == kModeTab) smem = ((tab.bytes() + 15) / 16) * 16 + ((td.axes_bytes() + 15) / 16) * 16;
   static thread_local int occ = 0;
   if (kSmem && smem > 48 * 1024) {
     if (int rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -148,23 +172,31 @@ int launch_typed(const LaunchArgs& a, const DevTable& tab, const RadiusParams& r
   const int64_t cap = static_cast<int64_t>(a.num_sms) * occ;
   const int grid = static_cast<int>(need < cap ? need : cap);
   kern<<<grid, kThreads, smem, a.stream>>>(static_cast<const T*>(a.hess), a.n, a.plane_stride,
-                                           a.radius_stride, a.R, a.scale_idx0, tab, rp, a.F_max,
+                                           a.radius_stride, a.R, a.scale_idx0, tab, rp, td, a.F_max,
                                            a.idx, a.counters);
   return check_cuda(cudaGetLastError(), "collapse_kernel launch");
 }
 
-template <bool kMixed>
-int launch_mode(const LaunchArgs& a, const DevTable& tab, const RadiusParams& rp) {
+template <int kMode>
+int launch_mode(const LaunchArgs& a, const DevTable& tab, const RadiusParams& rp, const TabDev& td) {
   const bool smem = tab.bytes() <= static_cast<size_t>(kSmemTableMaxBytes);
+  if (kMode == kModeTab) {  // the tabulated kernel always stages both images
+    if (a.dtype == CC_F64) return launch_typed<double, true, kMode>(a, tab, rp, td);
+    return launch_typed<float, true, kMode>(a, tab, rp, td);
+  }
   if (a.dtype == CC_F64)
-    return smem ? launch_typed<double, true, kMixed>(a, tab, rp) : launch_typed<double, false, kMixed>(a, tab, rp);
-  return smem ? launch_typed<float, true, kMixed>(a, tab, rp) : launch_typed<float, false, kMixed>(a, tab, rp);
+    return smem ? launch_typed<double, true, kMode>(a, tab, rp, td) : launch_typed<double, false, kMode>(a, tab, rp, td);
+  return smem ? launch_typed<float, true, kMode>(a, tab, rp, td) : launch_typed<float, false, kMode>(a, tab, rp, td);
 }
 
 }  // namespace
 
 int launch_fp64(const LaunchArgs& a, const DevTable& tab) {
-  return launch_mode<false>(a, tab, RadiusParams{});
+  return launch_mode<kModeFP64>(a, tab, RadiusParams{}, TabDev{});
+}
+
+int launch_tab(const LaunchArgs& a, const DevTable& tab, const TabDev& td) {
+  return launch_mode<kModeTab>(a, tab, RadiusParams{}, td);
 }
 
 int launch_mixed(const LaunchArgs& a, const DevTable& tab, const double* sigma) {
@@ -177,7 +209,7 @@ int launch_mixed(const LaunchArgs& a, const DevTable& tab, const double* sigma) 
     c.scale_idx0 = a.scale_idx0 + r0;
     RadiusParams rp;
     for (int r = 0; r < c.R; ++r) rp.tri_thr[r] = static_cast<float>(1e-4 * sigma[r0 + r]);
-    if (int rc = launch_mode<true>(c, tab, rp)) return rc;
+    if (int rc = launch_mode<kModeMixed>(c, tab, rp, TabDev{})) return rc;
   }
   return CC_OK;
 }

@@ -454,3 +454,29 @@ def test_tabulated_F_close_to_classic_and_exact_outside(oracle_tables):
     out = (fl8 & oracle.FLAG_HULL_OUT) != 0
     assert out.sum() > 100
     np.testing.assert_array_equal(F_tab8[out], F_cls8[out])
+
+
+# ------------------------------------------------------------------- MLP reference
+def test_mlp_gradient_matches_finite_differences():
+    """The FP64 MLP reference's analytic gradient (used to check the GPU
+    training kernels) agrees with central finite differences of its loss."""
+    rng = _rng(16)
+    params = rng.normal(size=oracle.MLP_NPARAM) * 0.2
+    z = rng.normal(size=(7, 3))
+    t = rng.normal(size=7)
+    loss, grad = oracle.mlp_loss_grad(params, z, t)
+    for k in list(rng.choice(oracle.MLP_NPARAM, 40, replace=False)) + [0, oracle.MLP_NPARAM - 1]:
+        e = np.zeros_like(params)
+        e[k] = 1e-6
+        lp, _ = oracle.mlp_loss_grad(params + e, z, t)
+        lm, _ = oracle.mlp_loss_grad(params - e, z, t)
+        fd = (lp - lm) / 2e-6
+        assert abs(fd - grad[k]) <= 1e-6 * max(1.0, abs(fd))
+    # forward is the plain composition (SiLU = v sigmoid(v))
+    silu = lambda v: v / (1 + np.exp(-v))
+    W1 = params[:192].reshape(3, 64); b1 = params[192:256]
+    W2 = params[256:4352].reshape(64, 64); b2 = params[4352:4416]
+    W3 = params[4416:8512].reshape(64, 64); b3 = params[8512:8576]
+    W4 = params[8576:8640]; b4 = params[8640]
+    ref = silu(silu(silu(z @ W1 + b1) @ W2 + b2) @ W3 + b3) @ W4 + b4
+    np.testing.assert_allclose(oracle.mlp_forward(params, z), ref, rtol=1e-13, atol=1e-13)

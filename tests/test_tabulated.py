@@ -1,0 +1,181 @@
+"""GPU parity of the tabulated mode and of the interpolation routines against the oracle."""
+import numpy as np
+import pytest
+
+import hessgen
+import oracle
+from parity import REL_TOL_FP64, compare_max, rel_err, running_max
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def table_axes(nd=128, nxy=64, d_max=40.0, xy_max=40.0):
+    """Non-uniform axes, denser near zero (the paper samples delta non-uniformly)."""
+    t = np.linspace(-1.0, 1.0, nd)
+    dg = d_max * np.sinh(2.5 * t) / np.sinh(2.5)
+    s = np.linspace(0.0, 1.0, nxy)
+    xg = xy_max * (0.3 * s + 0.7 * s ** 2)
+    return dg, xg, xg.copy()
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2510_02873_gb300 as cc
+    c = cc.Context(0.3, 0.7, 512, 1e-3, 1.0, device=0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def tables():
+    return oracle.Tables(0.3, 0.7, 512, 1e-3, 1.0)
+
+
+@pytest.fixture(scope="module")
+def table(ctx):
+    dg, xg, yg = table_axes()
+    val = oracle.tab_node_values(dg, xg, yg)
+    ctx.set_table(dg, xg, yg, val)
+    return oracle.Tab(dg, xg, yg, val), (dg, xg, yg, val)
+
+
+def oracle_tab_per_radius(tables, tab, stack):
+    Fs, fl = [], []
+    for r in range(stack.shape[0]):
+        F, f = tab.F_points(tables, stack[r].astype(np.float64))
+        Fs.append(F)
+        fl.append(f)
+    return np.stack(Fs), np.stack(fl)
+
+
+def run_tab(ctx, stack, sig, plane_stride=None):
+    R, _, n = stack.shape
+    ps = n if plane_stride is None else plane_stride
+    buf = torch.zeros((R, 6, ps), dtype=torch.float64, device="cuda")
+    buf[:, :, :n] = torch.from_numpy(stack).cuda()
+    F = torch.empty(n, dtype=torch.float64, device="cuda")
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    ctx.reset_max(F, idx)
+    ctx.reset_stats()
+    ctx.collapse_multi(buf[:, :, :n], sig, F, idx, mode="tabulated")
+    torch.cuda.synchronize()
+    return F.cpu().numpy(), idx.cpu().numpy(), ctx.stats()
+
+
+def test_tabulated_32cube_x8(ctx, tables, table):
+    tab, _ = table
+    n, R = 32 ** 3, 8
+    sig = hessgen.sigma_schedule(R, 0.3, 16.0)  # the largest radii leave the +-40 table
+    stack = hessgen.hessian_stack(2515, 0, sig, n)
+    F_all, fl = oracle_tab_per_radius(tables, tab, stack)
+    F, idx, st = run_tab(ctx, stack, sig)
+    s = compare_max(F, idx, F_all, fl)
+    outside = int(((fl & oracle.FLAG_HULL_OUT) != 0).sum())
+    assert outside > 0  # the fallback is exercised
+    print("tabulated 32^3 x 8", s, "outside", outside, st)
+
+
+@pytest.mark.parametrize("n", [1, 33, 4097, 200003])
+def test_tabulated_ragged(ctx, tables, table, n):
+    tab, _ = table
+    stack = hessgen.hessian_stack(4000 + n, 0, [3.0], n)
+    F_all, fl = oracle_tab_per_radius(tables, tab, stack)
+    F, idx, _ = run_tab(ctx, stack, [3.0], plane_stride=n + (n % 2))
+    compare_max(F, idx, F_all, fl)
+
+
+def test_tabulated_degenerate_spectra(ctx, tables, table):
+    tab, _ = table
+    rng = np.random.default_rng(21)
+    spectra = []
+    for s in (0.5, 3.0):
+        spectra += [[s, s, s], [s, 0, 0], [s, 0.2 * s, 0.2 * s], [s, -s, -s], [0.05 * s, -s, -s]]
+        for eps in (1e-3, 1e-6, 1e-9, 1e-12):
+            spectra += [[s, s * (1 - eps), -0.4 * s], [s, 0.2 * s, 0.2 * s * (1 - eps)]]
+    Ms = np.array([(lambda Q: Q @ np.diag(l) @ Q.T)(np.linalg.qr(rng.normal(size=(3, 3)))[0]) for l in spectra])
+    planes = np.stack([Ms[:, 0, 0], Ms[:, 1, 1], Ms[:, 2, 2], Ms[:, 0, 1], Ms[:, 0, 2], Ms[:, 1, 2]])
+    stack = planes[None]
+    F_all, fl = oracle_tab_per_radius(tables, tab, stack)
+    n = stack.shape[2]
+    F, idx, _ = run_tab(ctx, stack, [1.0], plane_stride=n + (n % 2))
+    compare_max(F, idx, F_all, fl)
+
+
+def test_tabulated_close_to_classic(ctx, table):
+    """Same planes through the table and through the R-LPT root: they differ by
+    interpolation error only."""
+    n = 100000
+    stack = hessgen.hessian_stack(99, 0, [2.0], n)
+    F_t, _, st = run_tab(ctx, stack, [2.0])
+    d = torch.from_numpy(stack).cuda()
+    F = torch.empty(n, dtype=torch.float64, device="cuda")
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    ctx.reset_max(F, idx)
+    ctx.collapse_multi(d, [2.0], F, idx, mode="fp64")
+    F_c = F.cpu().numpy()
+    both = (F_t > 0) & (F_c > 0)
+    rel = np.abs(F_t - F_c)[both] / F_c[both]
+    # interpolation error of a 128 x 64 x 64 table spanning +-40: ~2e-4 typical
+    assert np.median(rel) < 1e-3 and np.quantile(rel, 0.99) < 2e-2
+
+
+def test_device_table_nodes_match_oracle(ctx, table):
+    _, (dg, xg, yg, val) = table
+    got = ctx.table_nodes_rlpt(dg, xg, yg)
+    err = np.abs(got - val) / np.maximum(np.abs(val), 1e-3)
+    assert np.quantile(err, 0.999) < 1e-13 and err.max() < 1e-7
+
+
+def test_table_query_toy(ctx, table):
+    """The spline x bilinear routine on its own (the paper's 64 x 64 grid with a
+    128-knot spline per node), against the oracle's query."""
+    tab, (dg, xg, yg, val) = table
+    rng = np.random.default_rng(3)
+    m = 20000
+    q = [rng.uniform(dg[0], dg[-1], m), rng.uniform(0, xg[-1], m), rng.uniform(0, yg[-1], m)]
+    qd = [torch.from_numpy(a).cuda() for a in q]
+    out = torch.empty(m, dtype=torch.float64, device="cuda")
+    ctx.table_query(*qd, out)
+    torch.cuda.synchronize()
+    ref = tab.query(*q)
+    assert np.all(rel_err(out.cpu().numpy(), ref) <= 1e-12 * np.maximum(1.0, 1.0 / np.maximum(np.abs(ref), 1e-300)))
+
+
+def test_spline_toy_x_squared(ctx):
+    """The paper's spline toy: y = x^2 on 512 random knots, random queries;
+    GPU vs the oracle's natural spline to rounding, and the residual vs x^2."""
+    rng = np.random.default_rng(4)
+    xk = np.sort(rng.uniform(0.0, 1.0, 512))
+    yk = xk ** 2
+    m = 100000
+    q = rng.uniform(xk[0], xk[-1], m)
+    qd = torch.from_numpy(q).cuda()
+    out = torch.empty(m, dtype=torch.float64, device="cuda")
+    ctx.spline_eval(xk, yk, qd, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    M = oracle.spline_build(xk, yk)
+    sample = rng.choice(m, 3000, replace=False)
+    ref = oracle.spline_eval(xk, yk, M, q[sample])
+    assert np.all(np.abs(got[sample] - ref) <= 1e-14 * np.maximum(1.0, np.abs(ref)) + 1e-15)
+    resid = np.abs(got - q ** 2) / q ** 2
+    assert np.median(resid) < 1e-6
+
+
+def test_tabulated_needs_a_table():
+    import paper_2510_02873_gb300 as cc
+    with cc.Context() as c:
+        n = 64
+        d = torch.zeros((1, 6, n), dtype=torch.float64, device="cuda")
+        F = torch.zeros(n, dtype=torch.float64, device="cuda")
+        idx = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        with pytest.raises(cc.CollapseError):
+            c.collapse_multi(d, [1.0], F, idx, mode="tabulated")
+        with pytest.raises(cc.CollapseError):  # bad axes
+            c.set_table([0, 1, 1, 2], [0, 1], [0, 1], np.zeros((2, 2, 4)))
