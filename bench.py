@@ -317,6 +317,93 @@ def run_batch_variant(ctx, dev, stream, reps: int = 3) -> dict:
     }
 
 
+# ----------------------------------------------------------------------------- surrogate variant
+SUR_GRID, SUR_RADII = 768, 40
+SUR_TRAIN_POINTS = 40 * 1024 * 1024  # ~2e7 collapsing samples at s = 1
+
+
+def run_surrogate_variant(ctx, dev, stream, steps: int = 3000) -> dict:
+    """Train the MLP surrogate on the GPU (samples from the exact FP64 path on
+    4.2e7 isotropic-field points at s = 1), then evaluate a 768^3 grid x 40
+    radii of FP32 planes (435 GB in total, so generated one radius at a time,
+    untimed) with the surrogate, the mixed path (the same pipeline with the
+    closed-form cubic instead of the network) and the FP64 kernel; only the
+    collapse launches are timed."""
+    import torch
+
+    import hessgen
+    import hessgen.device as hdev
+
+    h = torch.empty((6, SUR_TRAIN_POINTS), dtype=torch.float32, device=dev)
+    hdev.fill(h, SEED + 5, 99, 0, 1.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rep = ctx.surrogate_train(h, 1.0, steps=steps, batch=16384, lr=3e-3, seed=11)
+    train_s = time.perf_counter() - t0
+    del h
+    torch.cuda.empty_cache()
+    n, R = SUR_GRID ** 3, SUR_RADII
+    sig = hessgen.sigma_schedule(R, S_LO, S_HI)
+    planes = torch.empty((6, n), dtype=torch.float32, device=dev)
+    outs = {m: (torch.zeros(n, dtype=torch.float64, device=dev), torch.full((n,), -1, dtype=torch.int32, device=dev))
+            for m in ("surrogate", "mixed", "fp64")}
+    ms = {m: 0.0 for m in outs}
+    stats = {m: {"evaluations": 0, "fallback": 0, "fp64_branch": 0} for m in outs}
+    for r in range(R):
+        hdev.fill(planes, SEED + 6, 0, r, sig[r])
+        for m, (F, idx) in outs.items():
+            ctx.reset_stats()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.collapse_scale(planes, sig[r], F, idx, r, mode=m)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms[m] += e0.elapsed_time(e1)
+            st = ctx.stats()
+            for k in stats[m]:
+                stats[m][k] += st[k]
+    Fs, Fx, F64 = outs["surrogate"][0], outs["mixed"][0], outs["fp64"][0]
+
+    def rel(a, b):
+        ok = (b > 1.0 + 1.2e-4) & (a > 1.0 + 1.2e-4)
+        d = ((a - b).abs() / b)[ok]
+        return float(d.max()), float(d.pow(2).mean().sqrt())
+
+    s_max, s_rms = rel(Fs, F64)
+    x_max, x_rms = rel(Fx, F64)
+    evals = float(n) * R
+    del planes, outs
+    torch.cuda.empty_cache()
+    return {
+        "workload": f"{SUR_GRID}^3 grid x {SUR_RADII} radii, FP32 planes streamed per radius (10.9 GB each)",
+        "train": {**rep, "seconds": train_s, "steps": steps, "batch": 16384},
+        "evals_per_s": evals / (ms["surrogate"] * 1e-3),
+        "mixed_evals_per_s": evals / (ms["mixed"] * 1e-3),
+        "fp64_evals_per_s": evals / (ms["fp64"] * 1e-3),
+        "gain_over_method_without_network": ms["mixed"] / ms["surrogate"],
+        "speedup_vs_fp64_kernel": ms["fp64"] / ms["surrogate"],
+        "fallback_fraction": stats["surrogate"]["fallback"] / stats["surrogate"]["evaluations"],
+        "max_rel_diff_vs_fp64": s_max, "rms_rel_diff_vs_fp64": s_rms,
+        "mixed_max_rel_diff_vs_fp64": x_max, "mixed_rms_rel_diff_vs_fp64": x_rms,
+        "bound_tol": 3e-5,
+    }
+
+
+def job_rate(elapsed_ms: float, evals: float, world: int, device) -> tuple:
+    """Whole-job throughput over ranks: every rank's evaluations divided by the
+    slowest rank's time (max over ranks)."""
+    import torch
+    import torch.distributed as dist
+
+    if world <= 1:
+        return evals / (elapsed_ms * 1e-3), elapsed_ms
+    mx = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    sm = torch.tensor([evals], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(sm.item()) / (float(mx.item()) * 1e-3), float(mx.item())
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -385,12 +472,7 @@ def main():
     kernel_ms = [a.elapsed_time(b) for a, b in kernel_events]
     stats = ctx.stats()
     assert stats["evaluations"] == n * R * args.steps, stats
-    if world > 1:
-        tt = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
-    evals_total = float(n) * R * args.steps * world
-    value = evals_total / (elapsed_ms * 1e-3)
+    value, elapsed_ms = job_rate(elapsed_ms, float(n) * R * args.steps, world, dev)
 
     # roofline of the dominant kernel (FP64 ALU bound)
     kern_avg_s = statistics.mean(kernel_ms) * 1e-3
@@ -463,6 +545,7 @@ def main():
         torch.cuda.empty_cache()
         result["variants"] = {"mixed": run_mixed_variant(ctx, dev, stream)}
         result["variants"]["batched"] = run_batch_variant(ctx, dev, stream)
+        result["variants"]["surrogate"] = run_surrogate_variant(ctx, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and (args.grid, R) == (GRID, N_RADII):
         result["cpu_baseline"] = cpu_oracle_rate(args.cpu_seconds)
     if rank == 0:

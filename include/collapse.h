@@ -210,6 +210,52 @@ CC_API int cc_table_query(cc_ctx *ctx, const double *d, const double *x, const d
 CC_API int cc_spline_eval(cc_ctx *ctx, const double *xk, const double *yk, int32_t n, const double *q,
                           int64_t m, double *out, void *stream);
 
+/* ---- learned surrogate (no counterpart in the paper) ----
+ * An MLP 3 -> 64 -> 64 -> 64 -> 1 (SiLU) maps z = (l1, l2, l3) / s(R) to
+ * f ~ log(D_c s(R)). CC_MODE_SURROGATE uses f only to seed the Newton iteration
+ * of the collapse condition (FP32 eigenvalues as in CC_MODE_MIXED); a point is
+ * accepted when the last Newton step is below 1e-6 D and z lies inside the
+ * training hull, otherwise it takes the exact FP64 path (counted in
+ * cc_stats.fallback). Accuracy is that of CC_MODE_MIXED (3e-5 on F). */
+typedef struct {
+  int32_t steps;        /* Adam steps (>= 1) */
+  int32_t batch;        /* samples per step, a multiple of 64 */
+  float lr;             /* peak learning rate (warm-up 100 steps, cosine decay) */
+  uint64_t seed;        /* initial weights and minibatch sampling */
+  float val_fraction;   /* held-out share of the samples, in (0, 0.5) */
+} cc_train_config;
+
+typedef struct {
+  int64_t samples, train_samples, val_samples;  /* collapsing points used */
+  float loss_first, loss_last;                  /* minibatch MSE of log(D_c s) */
+  float val_rms, val_max;                       /* held-out |f - log(D_c s)| */
+  float hull_lo[3], hull_hi[3];                 /* training range of z */
+} cc_train_report;
+
+/* Train the context's surrogate on the GPU (BF16 tensor-core forward and
+ * backward, FP32 accumulation, FP32 Adam). Targets come from the exact FP64
+ * path on the given Hessian planes (device, 6 planes of n points, dtype
+ * CC_F64/CC_F32) at rms s = sigma: every point with l1 > 0 and D_c s < 1e4 is a
+ * sample. Allocates device memory for the samples (16 B per point) and the
+ * network, kept by the context. Synchronises `stream`. */
+CC_API int cc_surrogate_train(cc_ctx *ctx, const void *hess, int32_t dtype, int64_t n, int64_t plane_stride,
+                              double sigma, const cc_train_config *cfg, cc_train_report *report, void *stream);
+
+/* Parameters (8641 floats: W1[3][64], b1, W2[64][64], b2, W3[64][64], b3, W4[64], b4)
+ * and hull (lo[3], hi[3]) of the current surrogate, to host memory. */
+CC_API int cc_surrogate_params(const cc_ctx *ctx, float *params, float *hull);
+
+/* Install a surrogate from host parameters and hull (layout as above). */
+CC_API int cc_load_surrogate(cc_ctx *ctx, const float *params, const float *hull);
+
+/* f(z) for n device inputs z (n x 3) into out (device), on the tensor-core path. */
+CC_API int cc_surrogate_eval(cc_ctx *ctx, const float *z, int64_t n, float *out, void *stream);
+
+/* One minibatch of the training kernel on host samples (n a multiple of 64):
+ * gradient of mean (f(z_i) - t_i)^2 into grad (host, 8641) and the loss.
+ * Synchronises the device. For checking the training kernels. */
+CC_API int cc_surrogate_grad(cc_ctx *ctx, const float *z, const float *t, int32_t n, float *grad, float *loss);
+
 /* ---- batches of independent realizations (one persistent launch) ----
  * Many realizations of uneven grid sizes and radius counts (e.g. a set of
  * simulation boxes) are evaluated by ONE persistent kernel: its CTAs take

@@ -292,6 +292,49 @@ class Context:
         _lib.check(_lib.load().cc_spline_eval(self._h, xk.ctypes.data, yk.ctypes.data, len(xk), q.data_ptr(),
                                               q.numel(), out.data_ptr(), _stream_ptr(stream)), "cc_spline_eval")
 
+    # ---- learned surrogate
+    MLP_NPARAM = 8641
+
+    def surrogate_train(self, hess, sigma, steps=2000, batch=16384, lr=3e-3, seed=1, val_fraction=0.05,
+                        stream=None) -> dict:
+        """hess: CUDA tensor (6, n) of training Hessians at rms sigma."""
+        if hess.dim() != 2 or hess.shape[0] != 6 or hess.stride(1) != 1 or not hess.is_cuda:
+            raise ValueError("hess must be a CUDA (6, n) tensor with unit stride along points")
+        cfg = _lib.CcTrainConfig(int(steps), int(batch), float(lr), int(seed), float(val_fraction))
+        rep = _lib.CcTrainReport()
+        _lib.check(_lib.load().cc_surrogate_train(self._h, hess.data_ptr(), _dtype_code(hess), hess.shape[1],
+                                                  hess.stride(0), float(sigma), ctypes.byref(cfg), ctypes.byref(rep),
+                                                  _stream_ptr(stream)), "cc_surrogate_train")
+        return rep.as_dict()
+
+    def surrogate_params(self):
+        params = np.empty(self.MLP_NPARAM, dtype=np.float32)
+        hull = np.empty(6, dtype=np.float32)
+        _lib.check(_lib.load().cc_surrogate_params(self._h, params.ctypes.data, hull.ctypes.data),
+                   "cc_surrogate_params")
+        return params, hull
+
+    def load_surrogate(self, params, hull):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        hull = np.ascontiguousarray(hull, dtype=np.float32)
+        if params.size != self.MLP_NPARAM or hull.size != 6:
+            raise ValueError("params must have 8641 entries and hull 6")
+        _lib.check(_lib.load().cc_load_surrogate(self._h, params.ctypes.data, hull.ctypes.data), "cc_load_surrogate")
+
+    def surrogate_eval(self, z, out, stream=None):
+        """z: float32 CUDA tensor (n, 3); out: float32 CUDA tensor (n,)."""
+        _lib.check(_lib.load().cc_surrogate_eval(self._h, z.data_ptr(), z.shape[0], out.data_ptr(),
+                                                 _stream_ptr(stream)), "cc_surrogate_eval")
+
+    def surrogate_grad(self, z, t):
+        z = np.ascontiguousarray(z, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        grad = np.empty(self.MLP_NPARAM, dtype=np.float32)
+        loss = ctypes.c_float()
+        _lib.check(_lib.load().cc_surrogate_grad(self._h, z.ctypes.data, t.ctypes.data, len(t), grad.ctypes.data,
+                                                 ctypes.byref(loss)), "cc_surrogate_grad")
+        return float(loss.value), grad
+
     def stats(self, stream=None) -> dict:
         return cc_get_stats(self._h, stream)
 

@@ -17,7 +17,8 @@ EXPORTS = (
     "cc_collapse_multi", "cc_collapse_multi_host", "cc_collapse_multi_noalloc", "cc_get_stats", "cc_reset_stats", "cc_strerror",
     "cc_last_error_message", "cc_version", "cc_batch_create", "cc_batch_autotune", "cc_batch_run",
     "cc_batch_run_graph", "cc_batch_get_config", "cc_batch_destroy", "cc_set_table", "cc_table_nodes_rlpt",
-    "cc_table_query", "cc_spline_eval",
+    "cc_table_query", "cc_spline_eval", "cc_surrogate_train", "cc_surrogate_params", "cc_load_surrogate",
+    "cc_surrogate_eval", "cc_surrogate_grad",
 )
 
 
@@ -41,6 +42,23 @@ class CcBatchItem(ctypes.Structure):
                 ("plane_stride", ctypes.c_int64), ("radius_stride", ctypes.c_int64), ("R", ctypes.c_int32),
                 ("sigma", ctypes.POINTER(ctypes.c_double)), ("F_max", ctypes.c_void_p),
                 ("idx", ctypes.c_void_p), ("scale_idx0", ctypes.c_int32)]
+
+
+class CcTrainConfig(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("seed", ctypes.c_uint64), ("val_fraction", ctypes.c_float)]
+
+
+class CcTrainReport(ctypes.Structure):
+    _fields_ = [("samples", ctypes.c_int64), ("train_samples", ctypes.c_int64), ("val_samples", ctypes.c_int64),
+                ("loss_first", ctypes.c_float), ("loss_last", ctypes.c_float), ("val_rms", ctypes.c_float),
+                ("val_max", ctypes.c_float), ("hull_lo", ctypes.c_float * 3), ("hull_hi", ctypes.c_float * 3)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("hull")}
+        d["hull_lo"] = list(self.hull_lo)
+        d["hull_hi"] = list(self.hull_hi)
+        return d
 
 
 class CollapseError(RuntimeError):
@@ -95,6 +113,12 @@ def load() -> ctypes.CDLL:
         L.cc_table_nodes_rlpt.argtypes = [vp, vp, i32, vp, i32, vp, i32, vp, vp]
         L.cc_table_query.argtypes = [vp, vp, vp, vp, i64, vp, vp]
         L.cc_spline_eval.argtypes = [vp, vp, vp, i32, vp, i64, vp, vp]
+        L.cc_surrogate_train.argtypes = [vp, vp, i32, i64, i64, d, ctypes.POINTER(CcTrainConfig),
+                                         ctypes.POINTER(CcTrainReport), vp]
+        L.cc_surrogate_params.argtypes = [vp, vp, vp]
+        L.cc_load_surrogate.argtypes = [vp, vp, vp]
+        L.cc_surrogate_eval.argtypes = [vp, vp, i64, vp, vp]
+        L.cc_surrogate_grad.argtypes = [vp, vp, vp, i32, vp, vp]
         L.cc_reset_stats.argtypes = [vp, vp]
         L.cc_strerror.argtypes = [ctypes.c_int]
         L.cc_strerror.restype = ctypes.c_char_p
@@ -105,7 +129,8 @@ def load() -> ctypes.CDLL:
                      "cc_collapse_multi", "cc_collapse_multi_host", "cc_collapse_multi_noalloc",
                      "cc_get_stats", "cc_reset_stats", "cc_version", "cc_batch_create", "cc_batch_autotune",
                      "cc_batch_run", "cc_batch_run_graph", "cc_batch_get_config", "cc_set_table",
-                     "cc_table_nodes_rlpt", "cc_table_query", "cc_spline_eval"):
+                     "cc_table_nodes_rlpt", "cc_table_query", "cc_spline_eval", "cc_surrogate_train",
+                     "cc_surrogate_params", "cc_load_surrogate", "cc_surrogate_eval", "cc_surrogate_grad"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L

@@ -88,7 +88,7 @@ int run_collapse(cc_ctx* ctx, cc_mode mode, const void* hess, int32_t dtype, int
     case CC_MODE_TABULATED:
       return launch_tab_checked(ctx, a);
     case CC_MODE_SURROGATE:
-      return set_error(CC_ENOTSUP, "mode not available in this build");
+      return launch_surrogate_checked(ctx, a, sigma);
   }
   return set_error(CC_EINVAL, "unknown mode");
 }
@@ -218,6 +218,7 @@ int cc_create(cc_ctx** out, const cc_cosmology* cosmo, int device) {
   t.D0 = ctx->D_k[0];
   t.Dtop = ctx->D_k[n - 1];
   t.eds_slope = ctx->a_k[0] / ctx->D_k[0];
+  t.Dtopf = static_cast<float>(t.Dtop);
   *out = ctx;
   return CC_OK;
 }
@@ -242,6 +243,9 @@ void cc_destroy(cc_ctx* ctx) {
   if (ctx->d_tab_coef) cudaFree(ctx->d_tab_coef);
   if (ctx->d_tab_work) cudaFree(ctx->d_tab_work);
   if (ctx->d_spl) cudaFree(ctx->d_spl);
+  if (ctx->d_mlp_img) cudaFree(ctx->d_mlp_img);
+  if (ctx->d_mlp_param) cudaFree(ctx->d_mlp_param);
+  if (ctx->d_train) cudaFree(ctx->d_train);
   if (cur >= 0 && cur != ctx->device) cudaSetDevice(cur);
   delete ctx;
 }

@@ -44,13 +44,11 @@ template <typename T, bool kMixed>
 __device__ __forceinline__ void run_point(const BatchItemDev& it, int64_t p, const double* Dk, const Coef4* coef,
                                           const float* Dkf, const unsigned short* bucket, const DevTable& tab,
                                           unsigned& n_coll, unsigned& n_eds, unsigned& n_ref, unsigned& n_fp64) {
-  double Fm = it.F_max[p];
-  int32_t im = it.idx[p];
+  MinA best;
   const T* base = static_cast<const T*>(it.hess) + p;
   const int64_t ps = it.plane_stride;
   for (int r = 0; r < it.R; ++r) {
     const T* h = base + static_cast<int64_t>(r) * it.radius_stride;
-    double F;
     if constexpr (kMixed) {
       const MixedResult res = collapse_point_mixed(ldf2(h), ldf2(h + ps), ldf2(h + 2 * ps), ldf2(h + 3 * ps),
                                                    ldf2(h + 4 * ps), ldf2(h + 5 * ps), __ldg(it.tri_thr + r),
@@ -59,22 +57,17 @@ __device__ __forceinline__ void run_point(const BatchItemDev& it, int64_t p, con
       n_eds += res.eds;
       n_ref += res.refined;
       n_fp64 += res.fp64;
-      F = res.F;
+      best.add(res.collapsed, res.a, r);
     } else {
       const PointResult res = collapse_point_fp64(ldd(h), ldd(h + ps), ldd(h + 2 * ps), ldd(h + 3 * ps),
                                                   ldd(h + 4 * ps), ldd(h + 5 * ps), Dk, coef, Dkf, bucket, tab);
       n_coll += res.collapsed;
       n_eds += res.eds;
       n_ref += res.refined;
-      F = res.F;
-    }
-    if (bits(F) > bits(Fm)) {
-      Fm = F;
-      im = it.scale_idx0 + r;
+      best.add(res.collapsed, res.a, r);
     }
   }
-  it.F_max[p] = Fm;
-  it.idx[p] = im;
+  best.store<kMixed>(it.F_max + p, it.idx + p, it.scale_idx0);
 }
 
 template <bool kMixed, int kBlock>

@@ -31,6 +31,31 @@ constexpr float kPairTauF = 1e-4f;
 
 __device__ __forceinline__ long long bits(double x) { return __double_as_longlong(x); }
 
+// FP64 <-> FP32 conversions on the integer pipes. The hardware conversions
+// issue to the FP64 unit like any FP64 instruction; these rebias the exponent
+// (1023 - 127 = 896) and move the mantissa with shifts instead.
+// to_f32_trunc: the FP32 value with the mantissa truncated (relative error
+// < 2^-23, used for seeds only); below the FP32 normal range it gives a signed
+// zero, above it a signed infinity; NaN is not expected.
+__device__ __forceinline__ float to_f32_trunc(double v) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  const unsigned sign = static_cast<unsigned>(b >> 32) & 0x80000000u;
+  const long long m = static_cast<long long>((b << 1) >> 30) - (896ll << 23);  // |v|'s exponent|mantissa, rebiased
+  const unsigned mag = (m < (1ll << 23)) ? 0u : (m >= (255ll << 23)) ? (255u << 23) : static_cast<unsigned>(m);
+  return __uint_as_float(sign | mag);
+}
+// to_f64: exact widening of an FP32 value; subnormals flush to a signed zero,
+// infinities and NaNs stay what they are.
+__device__ __forceinline__ double to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u, mag = u & 0x7fffffffu;
+  unsigned hi = sign | ((mag >> 3) + (896u << 20));
+  unsigned lo = mag << 29;
+  if (mag < 0x00800000u) { hi = sign; lo = 0u; }
+  if (mag >= 0x7f800000u) hi = sign | 0x7ff00000u | ((mag >> 3) & 0x000fffffu);
+  return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
+}
+
 // Re-solve l1 >= l2 when they are nearly equal: l3 (isolated) gives an
 // eigenvector v3 as the largest cross product of two rows of A - l3 I; A
 // restricted to the plane orthogonal to v3 is a 2x2 symmetric matrix whose
@@ -115,7 +140,8 @@ __device__ __forceinline__ int spline_interval(const float* __restrict__ Dkf,
 }
 
 struct PointResult {
-  double F;
+  double F;  // 1/a_c, 0 without collapse
+  double a;  // a_c, +inf without collapse (F is monotone in a: max F = 1/min a)
   bool collapsed, eds, refined;
 };
 
@@ -140,8 +166,8 @@ __device__ __forceinline__ EigenTop eigen_top_fp64(double xx, double yy, double 
   const double p2x3 = 0.5 * s6;           // 3 p^2
   const double det = fma(xz, fma(xy, yz, -b * xz), fma(a, fma(b, c, -yz * yz), -xy * fma(xy, c, -yz * xz)));
   // ---- FP32 trigonometric seed
-  const float p2f = static_cast<float>(s6) * (1.0f / 6.0f);
-  const float detf = static_cast<float>(det);
+  const float p2f = to_f32_trunc(s6) * (1.0f / 6.0f);
+  const float detf = to_f32_trunc(det);
   const float pf = sqrtf(p2f);
   float rf = (p2f > 0.0f) ? detf / (2.0f * p2f * pf) : 0.0f;
   rf = fminf(1.0f, fmaxf(-1.0f, rf));
@@ -151,12 +177,12 @@ __device__ __forceinline__ EigenTop eigen_top_fp64(double xx, double yy, double 
   const float x3f = -pf * fmaf(kSqrt3f, sn, cs);      // l3 - q
   // ---- FP64 Newton on g(x) = x (x^2 - 3p^2) - det; each step takes its
   // derivative 3 (x^2 - p^2) in FP32 at the current iterate
-  double x = static_cast<double>(x1f);
+  double x = to_f64(x1f);
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
-    const float xf = (it == 0) ? x1f : static_cast<float>(x);
+    const float xf = (it == 0) ? x1f : to_f32_trunc(x);
     const float gpf = 3.0f * (xf * xf - p2f);
-    const double yg = static_cast<double>((gpf != 0.0f) ? 1.0f / gpf : 0.0f);
+    const double yg = to_f64((gpf != 0.0f) ? 1.0f / gpf : 0.0f);
     const double g = fma(x, x * x - p2x3, -det);
     x = fma(-g, yg, x);
   }
@@ -184,30 +210,72 @@ __device__ __forceinline__ EigenTop eigen_top_fp64(double xx, double yy, double 
 // Growth factor at collapse from l1, l2 l3 and l2 + l3 (R-LPT): the FP64
 // coefficients of A_1(D) = 1 - l1 D + c2 D^2 + c3 D^3, an FP32 seed from them
 // (closed form in u = 1/D and two FP32 Newton steps) and one FP64 Newton step.
-__device__ __forceinline__ double rlpt_root_fp64(double lam1, double Pp, double S) {
-  const double Q2 = fma(-2.0, Pp, S * S);              // l2^2 + l3^2
+struct Root {
+  double D;  // after the FP64 Newton step
+  float Df;  // the FP32 root it started from
+};
+
+__device__ __forceinline__ Root rlpt_root_fp64(double lam1, double Pp, double S) {
+  // c3 = l1 (l2 l3 / 9 - 5/21 (l2^2 + l3^2)) with l2^2 + l3^2 = S^2 - 2 l2 l3
   const double c2 = (-3.0 / 7.0) * Pp;
-  const double c3 = lam1 * fma(-5.0 / 21.0, Q2, Pp * (1.0 / 9.0));
+  const double c3 = lam1 * fma(-5.0 / 21.0, S * S, Pp * (37.0 / 63.0));
   // ---- FP32 root seed from the FP64 coefficients rounded to FP32: largest
   // root of u^3 - l1 u^2 + c2 u + c3 (u = 1/D), polished on A_1(D) in FP32
-  const float l1f = static_cast<float>(lam1);
-  const float c2f = static_cast<float>(c2);
-  const float c3f = static_cast<float>(c3);
+  const float l1f = to_f32_trunc(lam1);
+  const float c2f = to_f32_trunc(c2);
+  const float c3f = to_f32_trunc(c3);
   const float uf = cubic_largest_root_f32(-l1f, c2f, c3f);
   float Df = 1.0f / uf;
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
     const float Af = fmaf(fmaf(fmaf(c3f, Df, c2f), Df, -l1f), Df, 1.0f);
     const float dAf = fmaf(fmaf(3.0f * c3f, Df, 2.0f * c2f), Df, -l1f);
-    Df -= Af / dAf;
+    Df -= __fdividef(Af, dAf);
   }
   const float dAf = fmaf(fmaf(3.0f * c3f, Df, 2.0f * c2f), Df, -l1f);
   // ---- one FP64 Newton step on A_1
-  double D = static_cast<double>(Df);
-  const double A1 = fma(fma(fma(c3, D, c2), D, -lam1), D, 1.0);
-  D = fma(-A1, static_cast<double>(1.0f / dAf), D);
-  return D;
+  Root r;
+  r.Df = Df;
+  const double D0 = to_f64(Df);
+  const double A1 = fma(fma(fma(c3, D0, c2), D0, -lam1), D0, 1.0);
+  r.D = fma(-A1, to_f64(1.0f / dAf), D0);
+  return r;
 }
+
+// 1/a: FP32 reciprocal and one FP64 Newton step
+__device__ __forceinline__ double recip_fp64(double a) {
+  const double y0 = to_f64(1.0f / to_f32_trunc(a));
+  return fma(y0, fma(-a, y0, 1.0), y0);
+}
+
+constexpr double kInf = __builtin_huge_val();
+
+// Running maximum of F = 1/a_c over the radii of one launch, kept as the
+// running minimum of a_c (F is decreasing in a, so max F = 1/min a): the
+// reciprocal is taken once per point and per launch instead of once per
+// evaluation. Strict '<' keeps the earliest radius on ties (the paper's
+// strict '>' on F); a_c > 0, so integer order of the bit patterns is value order.
+struct MinA {
+  double a = kInf;
+  int r = -1;
+  __device__ __forceinline__ void add(bool collapsed, double av, int radius) {
+    if (collapsed && bits(av) < bits(a)) {
+      a = av;
+      r = radius;
+    }
+  }
+  // merge into the stored maximum: F = 1/a (FP64, or through the FP32
+  // reciprocal for the reduced-precision modes), strict '>' against F_max
+  template <bool kF32Recip>
+  __device__ __forceinline__ void store(double* F_max, int32_t* idx, int32_t scale_idx0) const {
+    if (r < 0) return;
+    const double F = kF32Recip ? to_f64(1.0f / to_f32_trunc(a)) : recip_fp64(a);
+    if (bits(F) > bits(*F_max)) {  // both >= 0
+      *F_max = F;
+      *idx = scale_idx0 + r;
+    }
+  }
+};
 
 // FP64 collapse value of one point, F = 1/a_c (0 when there is no collapse).
 //   eigenvalues: invariants of M = A - qI in FP64 (q = tr/3, s6 = |M|_F^2 = 6 p^2,
@@ -233,21 +301,21 @@ __device__ __forceinline__ PointResult collapse_point_fp64(
   const double lam1 = q + x;
   const double Pp = fma(q, q - x, fma(x, x, -p2x3));  // l2 l3
   const double S = fma(2.0, q, -x);                    // l2 + l3
-  const double D = rlpt_root_fp64(lam1, Pp, S);
+  const Root rt = rlpt_root_fp64(lam1, Pp, S);
+  const double D = rt.D;
   // ---- collapse test on bit patterns: l1 > 0, 0 < D <= D_top
   const long long bD = bits(D);
   res.collapsed = bits(lam1) > 0 && bD > 0 && bD <= bits(tab.Dtop);
   const double Dc = res.collapsed ? D : tab.Dtop;
-  // ---- a(D): FP32 interval search, FP64 Horner
-  const int k = spline_interval(Dkf, bucket, tab, static_cast<float>(Dc));
+  // ---- a(D): interval from the FP32 root, FP64 Horner
+  const int k = spline_interval(Dkf, bucket, tab, res.collapsed ? rt.Df : tab.Dtopf);
   const Coef4 cf = coef[k];
   const double t = Dc - Dk[k];
   double av = fma(fma(fma(cf.c3, t, cf.c2), t, cf.c1), t, cf.c0);
   res.eds = res.collapsed && bits(Dc) < bits(tab.D0);
   if (res.eds) av = tab.eds_slope * Dc;
-  // ---- F = 1/a: FP32 reciprocal + one FP64 Newton step
-  const double y0 = static_cast<double>(1.0f / static_cast<float>(av));
-  const double F = fma(y0, fma(-av, y0, 1.0), y0);
+  res.a = res.collapsed ? av : kInf;
+  const double F = recip_fp64(av);
   res.F = res.collapsed ? F : 0.0;
   return res;
 }
@@ -271,7 +339,7 @@ constexpr float kMixedEstTau = 3e-6f;
 constexpr float kMixedEstCoef = 2.4e-7f;  // ~4 eps32: rounding of det and of the cubic residual
 
 struct MixedResult {
-  double F;
+  double F, a;  // as PointResult (F = 1/a through an FP32 reciprocal)
   bool collapsed, eds, refined, fp64;
 };
 
@@ -308,18 +376,18 @@ __device__ __forceinline__ MixedEigen mixed_eigen(float xx, float yy, float zz, 
   }
   m.full = ((1.0f + rf) < kPairTauF && p2 > 0.0f) || (x - x3) < tri_thr;
   const float lam1f = q + x;
-  double lam1 = static_cast<double>(lam1f);
+  double lam1 = to_f64(lam1f);
   const float est = kMixedEstCoef * p2 * pf / fmaxf((x - x2) * (x - x3) * fabsf(lam1f), 1e-30f);
   if (!m.full && est > kMixedEstTau) {
     // one FP64 Newton step on g(l) = det(A - l I); g'(l) = -3 (x^2 - p^2) from FP32
-    const double dxx = static_cast<double>(xx) - lam1, dyy = static_cast<double>(yy) - lam1;
-    const double dzz = static_cast<double>(zz) - lam1;
-    const double dxy = xy, dxz = xz, dyz = yz;
+    const double dxx = to_f64(xx) - lam1, dyy = to_f64(yy) - lam1;
+    const double dzz = to_f64(zz) - lam1;
+    const double dxy = to_f64(xy), dxz = to_f64(xz), dyz = to_f64(yz);
     const double g = fma(dxx, fma(dyy, dzz, -dyz * dyz),
                          fma(-dxy, fma(dxy, dzz, -dyz * dxz), dxz * fma(dxy, dyz, -dyy * dxz)));
     const float gpf = 3.0f * (x * x - p2);
-    lam1 = fma(g, static_cast<double>(1.0f / gpf), lam1);
-    x = static_cast<float>(lam1 - static_cast<double>(q));
+    lam1 = fma(g, to_f64(1.0f / gpf), lam1);
+    x = to_f32_trunc(lam1 - to_f64(q));
     m.fp64 = true;
   }
   m.q = q;
@@ -343,7 +411,7 @@ __device__ __forceinline__ MixedCoef mixed_coef(const MixedEigen& m) {
   const float S = fmaf(2.0f, q, -x);                     // l2 + l3
   const float Q2 = fmaf(-2.0f, Pp, S * S);               // l2^2 + l3^2
   MixedCoef k;
-  k.l1f = static_cast<float>(m.lam1);
+  k.l1f = to_f32_trunc(m.lam1);
   k.c2f = (-3.0f / 7.0f) * Pp;
   k.c3f = k.l1f * fmaf(-5.0f / 21.0f, Q2, Pp * (1.0f / 9.0f));
   return k;
@@ -356,7 +424,7 @@ __device__ __forceinline__ float newton_f32(const MixedCoef& k, float Df) {
   for (int it = 0; it < kSteps; ++it) {
     const float Af = fmaf(fmaf(fmaf(k.c3f, Df, k.c2f), Df, -k.l1f), Df, 1.0f);
     const float dAf = fmaf(fmaf(3.0f * k.c3f, Df, 2.0f * k.c2f), Df, -k.l1f);
-    Df -= Af / dAf;
+    Df -= __fdividef(Af, dAf);
   }
   return Df;
 }
@@ -371,19 +439,20 @@ __device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const M
   res.refined = false;
   res.fp64 = m.fp64;
   const float dAf = fmaf(fmaf(3.0f * k.c3f, Df, 2.0f * k.c2f), Df, -k.l1f);
-  double D = static_cast<double>(Df);
-  const double A1 = fma(fma(fma(static_cast<double>(k.c3f), D, static_cast<double>(k.c2f)), D, -m.lam1), D, 1.0);
-  D = fma(-A1, static_cast<double>(1.0f / dAf), D);
+  double D = to_f64(Df);
+  const double A1 = fma(fma(fma(to_f64(k.c3f), D, to_f64(k.c2f)), D, -m.lam1), D, 1.0);
+  D = fma(-A1, to_f64(1.0f / dAf), D);
   const long long bD = bits(D);
   res.collapsed = m.lam1f > 0.0f && bD > 0 && bD <= bits(tab.Dtop);
   const double Dc = res.collapsed ? D : tab.Dtop;
-  const int kk = spline_interval(Dkf, bucket, tab, res.collapsed ? Df : static_cast<float>(tab.Dtop));
+  const int kk = spline_interval(Dkf, bucket, tab, res.collapsed ? Df : tab.Dtopf);
   const Coef4 cf = coef[kk];
   const double t = Dc - Dk[kk];
   double av = fma(fma(fma(cf.c3, t, cf.c2), t, cf.c1), t, cf.c0);
   res.eds = res.collapsed && bits(Dc) < bits(tab.D0);
   if (res.eds) av = tab.eds_slope * Dc;
-  res.F = res.collapsed ? static_cast<double>(1.0f / static_cast<float>(av)) : 0.0;
+  res.a = res.collapsed ? av : kInf;
+  res.F = res.collapsed ? to_f64(1.0f / to_f32_trunc(av)) : 0.0;
   return res;
 }
 
@@ -391,9 +460,11 @@ __device__ __forceinline__ MixedResult full_fp64(float xx, float yy, float zz, f
                                                  const double* __restrict__ Dk, const Coef4* __restrict__ coef,
                                                  const float* __restrict__ Dkf,
                                                  const unsigned short* __restrict__ bucket, const DevTable& tab) {
-  const PointResult r64 = collapse_point_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
+  const PointResult r64 =
+      collapse_point_fp64(to_f64(xx), to_f64(yy), to_f64(zz), to_f64(xy), to_f64(xz), to_f64(yz), Dk, coef, Dkf, bucket, tab);
   MixedResult res;
   res.F = r64.F;
+  res.a = r64.a;
   res.collapsed = r64.collapsed;
   res.eds = r64.eds;
   res.refined = r64.refined;
@@ -445,7 +516,7 @@ __device__ __forceinline__ double tab_interp(const TabDev& td, const double* __r
     const int j = iy + step;
     iy = (j <= td.ny - 2 && bits(yg[j]) <= by) ? j : iy;
   }
-  const float df = static_cast<float>(delta);
+  const float df = to_f32_trunc(delta);
   for (int step = td.d_steps; step > 0; step >>= 1) {
     const int j = kd + step;
     kd = (j <= td.nd - 2 && dgf[j] <= df) ? j : kd;
@@ -466,7 +537,7 @@ __device__ __forceinline__ double tab_interp(const TabDev& td, const double* __r
 }
 
 struct TabResult {
-  double F;
+  double F, a;  // as PointResult
   bool collapsed, eds, refined, outside;
 };
 
@@ -504,22 +575,21 @@ __device__ __forceinline__ TabResult collapse_point_tab(
   bool root = true;
   if (!res.outside) {
     const double u = tab_interp(td, ax, tcoef, delta, xv, yv);
-    const double r0 = static_cast<double>(1.0f / static_cast<float>(u));
+    const double r0 = to_f64(1.0f / to_f32_trunc(u));
     D = fma(r0, fma(-u, r0, 1.0), r0);  // 1/u: FP32 reciprocal + one FP64 Newton step
     root = bits(u) > 0;
   } else {
-    D = rlpt_root_fp64(lam1, Pp, S);
+    D = rlpt_root_fp64(lam1, Pp, S).D;
   }
   const long long bD = bits(D);
   res.collapsed = bits(lam1) > 0 && root && bD > 0 && bD <= bits(tab.Dtop);
   const double Dc = res.collapsed ? D : tab.Dtop;
-  const int k = spline_interval(Dkf, bucket, tab, static_cast<float>(Dc));
+  const int k = spline_interval(Dkf, bucket, tab, to_f32_trunc(Dc));
   double av = horner(coef[k], Dc - Dk[k]);
   res.eds = res.collapsed && bits(Dc) < bits(tab.D0);
   if (res.eds) av = tab.eds_slope * Dc;
-  const double y0 = static_cast<double>(1.0f / static_cast<float>(av));
-  const double F = fma(y0, fma(-av, y0, 1.0), y0);
-  res.F = res.collapsed ? F : 0.0;
+  res.a = res.collapsed ? av : kInf;
+  res.F = res.collapsed ? recip_fp64(av) : 0.0;
   return res;
 }
 

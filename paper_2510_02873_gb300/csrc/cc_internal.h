@@ -46,6 +46,7 @@ struct DevTable {
   float log2_D0, inv_bucket_width;
   double a0, D0, Dtop;            // first scale factor, first and last knot
   double eds_slope;               // a0 / D0
+  float Dtopf;                    // D_top rounded to FP32 (interval search)
   // bytes of the table image (coef | D | Df | bucket), staged in shared memory
   __host__ __device__ size_t bytes() const {
     return sizeof(Coef4) * (n - 1) + sizeof(double) * n + sizeof(float) * n +
@@ -84,7 +85,14 @@ int check_cuda(cudaError_t e, const char* what);
 // per-radius parameters of one launch (kernel-parameter space)
 constexpr int kMaxRadiiPerLaunch = 256;
 struct RadiusParams {
-  float tri_thr[kMaxRadiiPerLaunch];  // MIXED: 1e-4 s(R), the all-three-close threshold
+  float tri_thr[kMaxRadiiPerLaunch];    // MIXED: 1e-4 s(R), the all-three-close threshold
+  float inv_sigma[kMaxRadiiPerLaunch];  // SURROGATE: 1 / s(R), the input normalisation
+};
+
+// surrogate network (BF16 image) and its training hull, as kernel parameters
+struct SurDev {
+  const unsigned char* img;
+  float lo[3], hi[3];
 };
 
 // kernel launchers (cc_kernels.cu)
@@ -111,7 +119,8 @@ int launch_reset_max(double* F_max, int32_t* idx, int64_t n, cudaStream_t stream
 
 struct cc_ctx;
 namespace cc {
-int launch_tab_checked(cc_ctx* ctx, const LaunchArgs& a);  // cc_tab.cu
+int launch_tab_checked(cc_ctx* ctx, const LaunchArgs& a);                          // cc_tab.cu
+int launch_surrogate_checked(cc_ctx* ctx, const LaunchArgs& a, const double* sigma);  // cc_surrogate.cu
 }
 
 struct cc_ctx {
@@ -140,6 +149,13 @@ struct cc_ctx {
   double* d_tab_work = nullptr;  // node values and tridiagonal scratch
   size_t tab_work_cap = 0;
   cc::TabDev tabdev{};
+  // surrogate (cc_surrogate_train / cc_load_surrogate)
+  bool sur_valid = false;
+  unsigned char* d_mlp_img = nullptr;
+  float* d_mlp_param = nullptr;  // params | adam m | adam v | grad | loss, stats
+  void* d_train = nullptr;       // training records (float4) | count | hull
+  size_t train_cap = 0;
+  float sur_hull[6] = {0, 0, 0, 0, 0, 0};
   // interpolation toy (cc_spline_eval)
   void* d_spl = nullptr;
   size_t spl_cap = 0;

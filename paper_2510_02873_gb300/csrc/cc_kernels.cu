@@ -45,8 +45,11 @@ constexpr int kModeFP64 = 0, kModeMixed = 1, kModeTab = 2;
 // kMode selects collapse_point_fp64, collapse_point_mixed (FP32 bulk) or
 // collapse_point_tab (tabulated 1/D_c; its axes follow the spline table in
 // shared memory).
+// FP64 and mixed: 64 registers, 4 blocks of 256 threads per SM (measured
+// faster than 3 blocks at 69-72 registers for the mixed path, equal for FP64);
+// the tabulated path keeps its 98 registers.
 template <typename T, bool kSmem, int kMode>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, kMode == 2 ? 1 : 4)
 collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
                 int64_t radius_stride, int R, int32_t scale_idx0, DevTable tab, RadiusParams rp,
                 TabDev td, double* __restrict__ F_max, int32_t* __restrict__ idx,
@@ -90,12 +93,12 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
        p += stride) {
     const bool active = p < n;
     if (active) {
-      double Fm = F_max[p];
-      int32_t im = idx[p];
+      MinA best;
       const T* base = hess + p;
       for (int r = 0; r < R; ++r) {
         const T* h = base + static_cast<int64_t>(r) * radius_stride;
-        double F;
+        double a;
+        bool coll;
         if constexpr (kMode == kModeMixed) {
           const float xx = ldf(h), yy = ldf(h + plane_stride), zz = ldf(h + 2 * plane_stride);
           const float xy = ldf(h + 3 * plane_stride), xz = ldf(h + 4 * plane_stride);
@@ -106,7 +109,8 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
           n_eds += res.eds;
           n_ref += res.refined;
           n_fp64 += res.fp64;
-          F = res.F;
+          a = res.a;
+          coll = res.collapsed;
         } else if constexpr (kMode == kModeTab) {
           const double xx = ld(h), yy = ld(h + plane_stride), zz = ld(h + 2 * plane_stride);
           const double xy = ld(h + 3 * plane_stride), xz = ld(h + 4 * plane_stride);
@@ -116,7 +120,8 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
           n_eds += res.eds;
           n_ref += res.refined;
           n_fp64 += res.outside;
-          F = res.F;
+          a = res.a;
+          coll = res.collapsed;
         } else {
           const double xx = ld(h), yy = ld(h + plane_stride), zz = ld(h + 2 * plane_stride);
           const double xy = ld(h + 3 * plane_stride), xz = ld(h + 4 * plane_stride);
@@ -125,15 +130,12 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
           n_coll += res.collapsed;
           n_eds += res.eds;
           n_ref += res.refined;
-          F = res.F;
+          a = res.a;
+          coll = res.collapsed;
         }
-        if (bits(F) > bits(Fm)) {  // both >= 0: integer order == value order
-          Fm = F;
-          im = scale_idx0 + r;
-        }
+        best.add(coll, a, r);
       }
-      F_max[p] = Fm;
-      idx[p] = im;
+      best.store<kMode == kModeMixed>(F_max + p, idx + p, scale_idx0);
       n_eval += R;
     }
   }

@@ -84,6 +84,29 @@ __device__ __forceinline__ void act_pack(const float (&c)[8][4], uint32_t (&a)[4
   }
 }
 
+// Inference SiLU on packed BF16 pairs: silu(v) = v sigmoid(v) = h + h tanh(h)
+// with h = v/2, one tanh.approx.bf16x2 (two results per special-function
+// instruction) and one bf16x2 FMA. The result is the BF16 A fragment either
+// way; the hardware tanh adds an error of the order of that rounding. The
+// training kernels keep the FP32 SiLU of act_pack (they need silu' as well).
+__device__ __forceinline__ uint32_t silu2_bf16(float v0, float v1) {
+  const uint32_t h = pack(0.5f * v0, 0.5f * v1);
+  uint32_t t, r;
+  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(h));
+  asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(r) : "r"(h), "r"(t));
+  return r;
+}
+
+__device__ __forceinline__ void act_pack_fast(const float (&c)[8][4], uint32_t (&a)[4][4]) {
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    a[s][0] = silu2_bf16(c[2 * s][0], c[2 * s][1]);
+    a[s][1] = silu2_bf16(c[2 * s][2], c[2 * s][3]);
+    a[s][2] = silu2_bf16(c[2 * s + 1][0], c[2 * s + 1][1]);
+    a[s][3] = silu2_bf16(c[2 * s + 1][2], c[2 * s + 1][3]);
+  }
+}
+
 // layer 1 (3 inputs, padded to one k16 step) for one tile; rows r0 = 16 tile + g, r1 = r0 + 8
 __device__ __forceinline__ void layer1(float z0, float z1, float z2, int tile, const unsigned char* img,
                                        float (&c)[8][4]) {
@@ -123,8 +146,8 @@ __device__ __forceinline__ void layer4(const uint32_t (&a)[4][4], const unsigned
   o1 = c[2];
 }
 
-// The MLP for the warp's 32 points: lane L's input (z0, z1, z2), its output returned.
-// Must be called by all 32 lanes together.
+// The MLP for the warp's 32 points (inference: SiLU through silu2_bf16): lane
+// L's input (z0, z1, z2), its output returned. Must be called by all 32 lanes together.
 __device__ __forceinline__ float forward_warp(float z0, float z1, float z2, const unsigned char* img) {
   const int lane = threadIdx.x & 31;
   const float* bias = reinterpret_cast<const float*>(img + OFF_B);
@@ -134,11 +157,11 @@ __device__ __forceinline__ float forward_warp(float z0, float z1, float z2, cons
     float c[8][4];
     uint32_t a[4][4];
     layer1(z0, z1, z2, tile, img, c);
-    act_pack(c, a);
+    act_pack_fast(c, a);
     layer64(a, img, OFF_W2T, bias + 64, c);
-    act_pack(c, a);
+    act_pack_fast(c, a);
     layer64(a, img, OFF_W3T, bias + 128, c);
-    act_pack(c, a);
+    act_pack_fast(c, a);
     float o0, o1;
     layer4(a, img, o0, o1);
     const int src = (lane & 7) * 4;  // the t == 0 lane holding row (lane & 15)

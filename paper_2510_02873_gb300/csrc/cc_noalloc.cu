@@ -98,6 +98,7 @@ int build_image(const cc_cosmology& c, unsigned char* base, DevTable& tab, size_
   tab.D0 = g_D[0];
   tab.Dtop = g_D[n - 1];
   tab.eds_slope = g_a[0] / g_D[0];
+  tab.Dtopf = static_cast<float>(tab.Dtop);
   return CC_OK;
 }
 

@@ -1,0 +1,724 @@
+// cc_surrogate.cu -- the learned surrogate (no counterpart in the paper).
+//
+// An MLP (3 -> 64 -> 64 -> 64 -> 1, SiLU) maps normalised eigenvalues
+// z = (l1, l2, l3) / sigma to f ~ log(D_c sigma), the log of the growth factor
+// at collapse in units of 1/sigma (D_c is homogeneous of degree -1 in the
+// eigenvalues, so one network serves every radius). It is trained here, on the
+// GPU, by this file's forward/backward kernels on BF16 tensor cores with FP32
+// accumulation and an FP32 Adam; the training targets come from the exact FP64
+// path of this library. In CC_MODE_SURROGATE the network's output only seeds
+// the Newton iteration of the collapse condition: a residual certificate
+// decides whether the refined root is used, and otherwise (or outside the
+// training hull) the exact FP64 path is, so results stay within the mixed
+// path's accuracy.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "cc_device.cuh"
+#include "cc_mlp.cuh"
+
+namespace cc {
+namespace {
+
+using namespace mlp;
+
+constexpr int kTrainWarps = 2;
+constexpr int kRowsPad = 40;  // transposed tiles: 32 rows + 8 padding (bank-conflict free)
+
+struct WarpScratch {
+  float dsl[3][32][H];                 // silu'(u_l) of layers 1..3, [row][unit]
+  __nv_bfloat16 zT[16][kRowsPad];      // inputs, [feature][row] (features 3..15 zero)
+  __nv_bfloat16 aT[3][H][kRowsPad];    // activations a1..a3, [unit][row]
+  __nv_bfloat16 dT[3][H][kRowsPad];    // deltas d1..d3, [unit][row]
+  float df[32];                        // dLoss/df per row
+};
+constexpr int kGradBytes = ((NPARAM * 4 + 15) / 16) * 16;
+constexpr size_t kTrainSmem = ALL_BYTES + kGradBytes + sizeof(WarpScratch) * kTrainWarps;
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {  // splitmix64 finaliser
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+__device__ __forceinline__ int ordered(float f) {  // monotone int image of a float
+  const int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+__host__ __device__ __forceinline__ float unordered(int i) {
+  const int j = i >= 0 ? i : i ^ 0x7FFFFFFF;
+  float f;
+  memcpy(&f, &j, sizeof(f));
+  return f;
+}
+
+// ---- training data: z = l / sigma, t = log(D_c sigma) from the exact FP64 path
+template <typename T>
+__global__ void sur_data_kernel(const T* __restrict__ hess, int64_t n, int64_t ps, double sigma,
+                                float4* __restrict__ out, unsigned long long* __restrict__ count, int64_t cap,
+                                int* __restrict__ hull) {
+  const double inv = 1.0 / sigma;
+  for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n;
+       p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const T* h = hess + p;
+    const double xx = h[0], yy = h[ps], zz = h[2 * ps], xy = h[3 * ps], xz = h[4 * ps], yz = h[5 * ps];
+    const EigenTop e = eigen_top_fp64(xx, yy, zz, xy, xz, yz);
+    const double lam1 = e.q + e.x;
+    if (!(lam1 > 0.0)) continue;
+    const double Pp = fma(e.q, e.q - e.x, fma(e.x, e.x, -e.p2x3));
+    const double S = fma(2.0, e.q, -e.x);
+    const double D = rlpt_root_fp64(lam1, Pp, S).D;
+    const double Ds = D * sigma;
+    if (!(Ds > 0.0) || !(Ds < 1e4)) continue;
+    const double y = sqrt(fmax(fma(S, S, -4.0 * Pp), 0.0));
+    const float4 v = make_float4(static_cast<float>(lam1 * inv), static_cast<float>(0.5 * (S + y) * inv),
+                                 static_cast<float>(0.5 * (S - y) * inv), static_cast<float>(log(Ds)));
+    const unsigned long long slot = atomicAdd(count, 1ULL);
+    if (static_cast<int64_t>(slot) < cap) {
+      out[slot] = v;
+      atomicMin(hull + 0, ordered(v.x)); atomicMax(hull + 3, ordered(v.x));
+      atomicMin(hull + 1, ordered(v.y)); atomicMax(hull + 4, ordered(v.y));
+      atomicMin(hull + 2, ordered(v.z)); atomicMax(hull + 5, ordered(v.z));
+    }
+  }
+}
+
+__device__ __forceinline__ void stage(unsigned char* dst, const unsigned char* src, int bytes) {
+  for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(src)[i];
+}
+
+__device__ __forceinline__ float bf(const __nv_bfloat16& v) { return __bfloat162float(v); }
+
+// store one layer's pre-activations (C layout of one tile) as silu' and activations
+__device__ __forceinline__ void store_layer(WarpScratch& w, int l, int tile, const float (&c)[8][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = 16 * tile + g, r1 = r0 + 8;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int n0 = 8 * j + 2 * t;
+    w.dsl[l][r0][n0] = dsilu(c[j][0]);
+    w.dsl[l][r0][n0 + 1] = dsilu(c[j][1]);
+    w.dsl[l][r1][n0] = dsilu(c[j][2]);
+    w.dsl[l][r1][n0 + 1] = dsilu(c[j][3]);
+    w.aT[l][n0][r0] = __float2bfloat16_rn(silu(c[j][0]));
+    w.aT[l][n0 + 1][r0] = __float2bfloat16_rn(silu(c[j][1]));
+    w.aT[l][n0][r1] = __float2bfloat16_rn(silu(c[j][2]));
+    w.aT[l][n0 + 1][r1] = __float2bfloat16_rn(silu(c[j][3]));
+  }
+}
+
+// delta of layer l from its upstream gradient (C layout) times silu'; stored
+// transposed and returned packed as the A fragments of the next product
+__device__ __forceinline__ void delta_layer(WarpScratch& w, int l, int tile, float (&c)[8][4], uint32_t (&a)[4][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = 16 * tile + g, r1 = r0 + 8;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int n0 = 8 * j + 2 * t;
+    c[j][0] *= w.dsl[l][r0][n0];
+    c[j][1] *= w.dsl[l][r0][n0 + 1];
+    c[j][2] *= w.dsl[l][r1][n0];
+    c[j][3] *= w.dsl[l][r1][n0 + 1];
+    w.dT[l][n0][r0] = __float2bfloat16_rn(c[j][0]);
+    w.dT[l][n0 + 1][r0] = __float2bfloat16_rn(c[j][1]);
+    w.dT[l][n0][r1] = __float2bfloat16_rn(c[j][2]);
+    w.dT[l][n0 + 1][r1] = __float2bfloat16_rn(c[j][3]);
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    a[s][0] = pack(c[2 * s][0], c[2 * s][1]);
+    a[s][1] = pack(c[2 * s][2], c[2 * s][3]);
+    a[s][2] = pack(c[2 * s + 1][0], c[2 * s + 1][1]);
+    a[s][3] = pack(c[2 * s + 1][2], c[2 * s + 1][3]);
+  }
+}
+
+// upstream gradient of the previous layer: c = d W^T (W stored [in][out] in the image)
+__device__ __forceinline__ void back_mma(const uint32_t (&a)[4][4], const unsigned char* img, int off_wb,
+                                         float (&c)[8][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.0f;
+    const int row = off_wb + (8 * j + g) * STR * 2;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      mma(c[j], a[s], ld32(img, row + (16 * s + 2 * t) * 2), ld32(img, row + (16 * s + 8 + 2 * t) * 2));
+  }
+}
+
+// weight gradient dW[in][out] += sum_rows act[row][in] delta[row][out] over the
+// warp's 32 rows (K), from the transposed tiles; m_tiles tiles of 16 inputs
+__device__ __forceinline__ void wgrad(const __nv_bfloat16 (*actT)[kRowsPad], const __nv_bfloat16 (*dT)[kRowsPad],
+                                      int m_tiles, int n_in, float* gW) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  for (int i = 0; i < m_tiles; ++i) {
+    float c[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) c[j][0] = c[j][1] = c[j][2] = c[j][3] = 0.0f;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      uint32_t a[4];
+      a[0] = *reinterpret_cast<const uint32_t*>(&actT[16 * i + g][16 * s + 2 * t]);
+      a[1] = *reinterpret_cast<const uint32_t*>(&actT[16 * i + g + 8][16 * s + 2 * t]);
+      a[2] = *reinterpret_cast<const uint32_t*>(&actT[16 * i + g][16 * s + 8 + 2 * t]);
+      a[3] = *reinterpret_cast<const uint32_t*>(&actT[16 * i + g + 8][16 * s + 8 + 2 * t]);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&dT[8 * j + g][16 * s + 2 * t]);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&dT[8 * j + g][16 * s + 8 + 2 * t]);
+        uint32_t aa[4] = {a[0], a[1], a[2], a[3]};
+        mma(c[j], aa, b0, b1);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int in0 = 16 * i + g, in1 = in0 + 8, o = 8 * j + 2 * t;
+      if (in0 < n_in) { atomicAdd(gW + in0 * H + o, c[j][0]); atomicAdd(gW + in0 * H + o + 1, c[j][1]); }
+      if (in1 < n_in) { atomicAdd(gW + in1 * H + o, c[j][2]); atomicAdd(gW + in1 * H + o + 1, c[j][3]); }
+    }
+  }
+}
+
+// One minibatch step: each warp takes 32 samples (indices hashed from seed and
+// step, or consecutive when `sequential`), runs forward and backward and adds
+// its gradient (already divided by the batch size) to grad_g; loss_g += mean r^2.
+__global__ void __launch_bounds__(32 * kTrainWarps)
+sur_train_kernel(const float4* __restrict__ data, int64_t ntrain, uint64_t seed, int step, int sequential,
+                 float inv_batch, const unsigned char* __restrict__ img_g, float* __restrict__ grad_g,
+                 float* __restrict__ loss_g) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  unsigned char* img = sm;
+  float* grad = reinterpret_cast<float*>(sm + ALL_BYTES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  WarpScratch& w = reinterpret_cast<WarpScratch*>(sm + ALL_BYTES + kGradBytes)[warp];
+  stage(img, img_g, ALL_BYTES);
+  for (int i = threadIdx.x; i < kGradBytes / 4; i += blockDim.x) grad[i] = 0.0f;
+  __syncthreads();
+  const int64_t gi = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t sid = sequential ? gi : static_cast<int64_t>(mix64(seed ^ mix64(static_cast<uint64_t>(step) * 0x100000001ull + gi)) %
+                                                              static_cast<uint64_t>(ntrain));
+  const bool valid = sid < ntrain;
+  const float4 d = valid ? data[sid] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float* bias = reinterpret_cast<const float*>(img + OFF_B);
+  float fo = 0.0f;
+  // ---- forward, keeping silu' and the activations
+#pragma unroll 1
+  for (int tile = 0; tile < 2; ++tile) {
+    float c[8][4];
+    uint32_t a[4][4];
+    layer1(d.x, d.y, d.z, tile, img, c);
+    store_layer(w, 0, tile, c);
+    act_pack(c, a);
+    layer64(a, img, OFF_W2T, bias + 64, c);
+    store_layer(w, 1, tile, c);
+    act_pack(c, a);
+    layer64(a, img, OFF_W3T, bias + 128, c);
+    store_layer(w, 2, tile, c);
+    act_pack(c, a);
+    float o0, o1;
+    layer4(a, img, o0, o1);
+    const int src = (lane & 7) * 4;
+    const float v0 = __shfl_sync(0xffffffffu, o0, src), v1 = __shfl_sync(0xffffffffu, o1, src);
+    if ((lane >> 4) == tile) fo = ((lane & 15) < 8) ? v0 : v1;
+  }
+  w.zT[0][lane] = __float2bfloat16_rn(d.x);
+  w.zT[1][lane] = __float2bfloat16_rn(d.y);
+  w.zT[2][lane] = __float2bfloat16_rn(d.z);
+  for (int k = 3; k < 16; ++k) w.zT[k][lane] = __float2bfloat16_rn(0.0f);
+  const float r = valid ? fo - d.w : 0.0f;
+  const float df = 2.0f * r * inv_batch;
+  w.df[lane] = df;
+  float l2 = r * r;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, o);
+  if (lane == 0) atomicAdd(loss_g, l2 * inv_batch);
+  __syncwarp();
+  // ---- backward through the layers, per tile
+#pragma unroll 1
+  for (int tile = 0; tile < 2; ++tile) {
+    const int r0 = 16 * tile + g, r1 = r0 + 8;
+    const float d0 = w.df[r0], d1 = w.df[r1];
+    float c[8][4];
+    uint32_t a[4][4];
+    const __nv_bfloat16* w4 = reinterpret_cast<const __nv_bfloat16*>(img + OFF_W4T);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int n0 = 8 * j + 2 * t;
+      c[j][0] = d0 * bf(w4[n0]);
+      c[j][1] = d0 * bf(w4[n0 + 1]);
+      c[j][2] = d1 * bf(w4[n0]);
+      c[j][3] = d1 * bf(w4[n0 + 1]);
+    }
+    delta_layer(w, 2, tile, c, a);     // d3
+    back_mma(a, img, OFF_W3B, c);      // d3 W3^T
+    delta_layer(w, 1, tile, c, a);     // d2
+    back_mma(a, img, OFF_W2B, c);      // d2 W2^T
+    delta_layer(w, 0, tile, c, a);     // d1
+  }
+  __syncwarp();
+  // ---- weight gradients on tensor cores, biases and the last layer on CUDA cores
+  wgrad(w.aT[1], w.dT[2], 4, H, grad + P_W3);
+  wgrad(w.aT[0], w.dT[1], 4, H, grad + P_W2);
+  wgrad(w.zT, w.dT[0], 1, 3, grad + P_W1);
+  for (int k = lane; k < H; k += 32) {
+    float s4 = 0.f, sb1 = 0.f, sb2 = 0.f, sb3 = 0.f;
+    for (int row = 0; row < 32; ++row) {
+      s4 += bf(w.aT[2][k][row]) * w.df[row];
+      sb1 += bf(w.dT[0][k][row]);
+      sb2 += bf(w.dT[1][k][row]);
+      sb3 += bf(w.dT[2][k][row]);
+    }
+    atomicAdd(grad + P_W4 + k, s4);
+    atomicAdd(grad + P_B1 + k, sb1);
+    atomicAdd(grad + P_B2 + k, sb2);
+    atomicAdd(grad + P_B3 + k, sb3);
+  }
+  if (lane == 0) {
+    float sb4 = 0.f;
+    for (int row = 0; row < 32; ++row) sb4 += w.df[row];
+    atomicAdd(grad + P_B4, sb4);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NPARAM; i += blockDim.x)
+    if (grad[i] != 0.0f) atomicAdd(grad_g + i, grad[i]);
+}
+
+// parameter i -> its places in the BF16 image
+__device__ __forceinline__ void put_image(int i, float v, unsigned char* img) {
+  const __nv_bfloat16 b = __float2bfloat16_rn(v);
+  auto at = [&](int off) { *reinterpret_cast<__nv_bfloat16*>(img + off) = b; };
+  if (i < P_B1) {
+    const int k = i / H, n = i % H;
+    at(OFF_W1T + (n * STR1 + k) * 2);
+  } else if (i < P_W2) {
+    reinterpret_cast<float*>(img + OFF_B)[i - P_B1] = v;
+  } else if (i < P_B2) {
+    const int k = (i - P_W2) / H, n = (i - P_W2) % H;
+    at(OFF_W2T + (n * STR + k) * 2);
+    at(OFF_W2B + (k * STR + n) * 2);
+  } else if (i < P_W3) {
+    reinterpret_cast<float*>(img + OFF_B)[64 + i - P_B2] = v;
+  } else if (i < P_B3) {
+    const int k = (i - P_W3) / H, n = (i - P_W3) % H;
+    at(OFF_W3T + (n * STR + k) * 2);
+    at(OFF_W3B + (k * STR + n) * 2);
+  } else if (i < P_W4) {
+    reinterpret_cast<float*>(img + OFF_B)[128 + i - P_B3] = v;
+  } else if (i < P_B4) {
+    at(OFF_W4T + (i - P_W4) * 2);
+  } else {
+    reinterpret_cast<float*>(img + OFF_B)[192] = v;
+  }
+}
+
+__global__ void sur_image_kernel(const float* __restrict__ p, unsigned char* __restrict__ img) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < NPARAM) put_image(i, p[i], img);
+}
+
+// Adam (FP32 master weights), then the BF16 image; the gradient is cleared
+__global__ void sur_adam_kernel(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                                float* __restrict__ grad, float lr, float b1t, float b2t,
+                                unsigned char* __restrict__ img) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NPARAM) return;
+  const float gi = grad[i];
+  grad[i] = 0.0f;
+  const float mi = 0.9f * m[i] + 0.1f * gi;
+  const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float pi = p[i] - lr * (mi / (1.0f - b1t)) / (sqrtf(vi / (1.0f - b2t)) + 1e-8f);
+  p[i] = pi;
+  put_image(i, pi, img);
+}
+
+// f for n inputs z (stride 3 or the float4 training records): out and/or error statistics
+__global__ void sur_eval_kernel(const float* __restrict__ z, int zstride, int64_t n, const unsigned char* __restrict__ img_g,
+                                float* __restrict__ out, float* __restrict__ sumsq, int* __restrict__ maxerr) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  stage(sm, img_g, FWD_BYTES);
+  __syncthreads();
+  const int64_t n_round = (n + 31) & ~static_cast<int64_t>(31);
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n_round;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const bool ok = i < n;
+    const float* zi = z + (ok ? i : 0) * zstride;
+    const float f = forward_warp(zi[0], zi[1], zi[2], sm);
+    if (!ok) continue;
+    if (out) out[i] = f;
+    if (sumsq) {
+      const float e = f - zi[3];
+      atomicAdd(sumsq, e * e);
+      atomicMax(maxerr, __float_as_int(fabsf(e)));
+    }
+  }
+}
+
+// ---- inference: CC_MODE_SURROGATE collapse kernel. All lanes of a warp stay in
+// the loops so that the warp-wide MLP sees 32 rows every radius.
+constexpr float kCertTol = 1e-6f;  // accepted when the last Newton step is below 1e-6 D
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+collapse_sur_kernel(const T* __restrict__ hess, int64_t n, int64_t ps, int64_t rs, int R, int32_t scale_idx0,
+                    DevTable tab, RadiusParams rp, SurDev sd, double* __restrict__ F_max, int32_t* __restrict__ idx,
+                    DevCounters* __restrict__ cnt) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const size_t tb = ((tab.bytes() + 15) / 16) * 16;
+  {
+    const int words = static_cast<int>(tab.bytes() / 16);
+    const uint4* src = reinterpret_cast<const uint4*>(tab.coef);
+    uint4* dst = reinterpret_cast<uint4*>(sm);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+    const size_t tail = tab.bytes() & 15;
+    if (threadIdx.x < tail)
+      reinterpret_cast<unsigned char*>(dst + words)[threadIdx.x] = reinterpret_cast<const unsigned char*>(src + words)[threadIdx.x];
+  }
+  stage(sm + tb, sd.img, FWD_BYTES);
+  __syncthreads();
+  const Coef4* coef = reinterpret_cast<const Coef4*>(sm);
+  const double* Dk = reinterpret_cast<const double*>(coef + (tab.n - 1));
+  const float* Dkf = reinterpret_cast<const float*>(Dk + tab.n);
+  const unsigned short* bucket = reinterpret_cast<const unsigned short*>(Dkf + tab.n);
+  const unsigned char* img = sm + tb;
+  unsigned n_eval = 0, n_coll = 0, n_eds = 0, n_ref = 0, n_fp64 = 0, n_fb = 0;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t n_round = (n + 31) & ~static_cast<int64_t>(31);
+  for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n_round; p += stride) {
+    const bool active = p < n;
+    MinA best;
+    const T* base = hess + (active ? p : 0);
+    for (int r = 0; r < R; ++r) {
+      const T* h = base + static_cast<int64_t>(r) * rs;
+      float xx = 0.f, yy = 0.f, zz = 0.f, xy = 0.f, xz = 0.f, yz = 0.f;
+      if (active) {
+        xx = static_cast<float>(__ldg(h)); yy = static_cast<float>(__ldg(h + ps));
+        zz = static_cast<float>(__ldg(h + 2 * ps)); xy = static_cast<float>(__ldg(h + 3 * ps));
+        xz = static_cast<float>(__ldg(h + 4 * ps)); yz = static_cast<float>(__ldg(h + 5 * ps));
+      }
+      const MixedEigen m = mixed_eigen(xx, yy, zz, xy, xz, yz, rp.tri_thr[r]);
+      const float is = rp.inv_sigma[r];
+      const float z0 = m.lam1f * is, z1 = (m.q + m.x2) * is, z2 = (m.q + m.x3) * is;
+      const bool inside = z0 >= sd.lo[0] && z0 <= sd.hi[0] && z1 >= sd.lo[1] && z1 <= sd.hi[1] &&
+                          z2 >= sd.lo[2] && z2 <= sd.hi[2];
+      __syncwarp();
+      const float f = mlp::forward_warp(z0, z1, z2, img);
+      if (!active) continue;
+      MixedResult res;
+      if (m.full) {
+        res = full_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
+      } else if (!(m.lam1f > 0.0f)) {
+        res.F = 0.0;
+        res.a = kInf;
+        res.collapsed = res.eds = res.refined = false;
+        res.fp64 = m.fp64;
+      } else {
+        const MixedCoef k = mixed_coef(m);
+        bool ok = inside;
+        float Df = 0.0f;
+        if (ok) {
+          Df = newton_f32<3>(k, __expf(f) * is);
+          const float Af = fmaf(fmaf(fmaf(k.c3f, Df, k.c2f), Df, -k.l1f), Df, 1.0f);
+          const float dAf = fmaf(fmaf(3.0f * k.c3f, Df, 2.0f * k.c2f), Df, -k.l1f);
+          ok = Df > 0.0f && isfinite(Df) && fabsf(Af) <= kCertTol * fabsf(dAf * Df);
+        }
+        if (ok) {
+          res = mixed_finish(m, k, Df, Dk, coef, Dkf, bucket, tab);
+        } else {
+          res = full_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
+          ++n_fb;
+        }
+      }
+      n_coll += res.collapsed;
+      n_eds += res.eds;
+      n_ref += res.refined;
+      n_fp64 += res.fp64;
+      best.add(res.collapsed, res.a, r);
+    }
+    if (active) {
+      best.store<true>(F_max + p, idx + p, scale_idx0);
+      n_eval += R;
+    }
+  }
+  n_eval = __reduce_add_sync(0xffffffffu, n_eval);
+  n_coll = __reduce_add_sync(0xffffffffu, n_coll);
+  n_eds = __reduce_add_sync(0xffffffffu, n_eds);
+  n_ref = __reduce_add_sync(0xffffffffu, n_ref);
+  n_fp64 = __reduce_add_sync(0xffffffffu, n_fp64);
+  n_fb = __reduce_add_sync(0xffffffffu, n_fb);
+  if ((threadIdx.x & 31) == 0) {
+    if (n_eval) atomicAdd(&cnt->evaluations, static_cast<unsigned long long>(n_eval));
+    if (n_coll) atomicAdd(&cnt->collapsed, static_cast<unsigned long long>(n_coll));
+    if (n_eds) atomicAdd(&cnt->eds_branch, static_cast<unsigned long long>(n_eds));
+    if (n_ref) atomicAdd(&cnt->refined, static_cast<unsigned long long>(n_ref));
+    if (n_fp64) atomicAdd(&cnt->fp64_branch, static_cast<unsigned long long>(n_fp64));
+    if (n_fb) atomicAdd(&cnt->fallback, static_cast<unsigned long long>(n_fb));
+  }
+}
+
+int launch_grid(int64_t n, int threads, int cap) {
+  const int64_t need = (n + threads - 1) / threads;
+  return static_cast<int>(need < cap ? need : cap);
+}
+
+struct SurState {
+  unsigned char* img = nullptr;
+  float* p = nullptr;  // p | m | v | grad | loss(2)
+};
+
+int ensure_surrogate(cc_ctx* ctx) {
+  if (ctx->d_mlp_img) return CC_OK;
+  if (int rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&ctx->d_mlp_img), ALL_BYTES), "cudaMalloc(mlp image)")) return rc;
+  if (int rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&ctx->d_mlp_param), sizeof(float) * (4 * NPARAM + 8)),
+                          "cudaMalloc(mlp params)"))
+    return rc;
+  if (int rc = check_cuda(cudaMemset(ctx->d_mlp_img, 0, ALL_BYTES), "cudaMemset")) return rc;
+  return check_cuda(cudaMemset(ctx->d_mlp_param, 0, sizeof(float) * (4 * NPARAM + 8)), "cudaMemset");
+}
+
+// LeCun-uniform initial weights (variance 1/fan_in) from a seeded xorshift; biases 0, b4 = mean target
+void init_params(std::vector<float>& p, uint64_t seed, float b4) {
+  p.assign(NPARAM, 0.0f);
+  uint64_t s = seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+  auto uni = [&]() {
+    s ^= s << 13; s ^= s >> 7; s ^= s << 17;
+    return static_cast<float>((s >> 11) * (1.0 / 9007199254740992.0)) * 2.0f - 1.0f;
+  };
+  auto fill = [&](int off, int fan_in, int count) {
+    const float bound = std::sqrt(3.0f / static_cast<float>(fan_in));
+    for (int i = 0; i < count; ++i) p[off + i] = bound * uni();
+  };
+  fill(P_W1, 3, 3 * H);
+  fill(P_W2, H, H * H);
+  fill(P_W3, H, H * H);
+  fill(P_W4, H, H);
+  p[P_B4] = b4;
+}
+
+template <typename T>
+int launch_sur_typed(cc_ctx* ctx, const LaunchArgs& a, const RadiusParams& rp) {
+  auto kern = collapse_sur_kernel<T>;
+  const size_t smem = ((ctx->tab.bytes() + 15) / 16) * 16 + FWD_BYTES;
+  if (smem > 48 * 1024)
+    if (int rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
+                            "cudaFuncSetAttribute"))
+      return rc;
+  int occ = 0;
+  if (int rc = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem), "occupancy")) return rc;
+  const int64_t need = (a.n + kThreads - 1) / kThreads;
+  const int64_t cap = static_cast<int64_t>(a.num_sms) * (occ > 0 ? occ : 1);
+  const int grid = static_cast<int>(need < cap ? need : cap);
+  SurDev sd;
+  sd.img = ctx->d_mlp_img;
+  for (int i = 0; i < 3; ++i) {
+    sd.lo[i] = ctx->sur_hull[i];
+    sd.hi[i] = ctx->sur_hull[3 + i];
+  }
+  kern<<<grid, kThreads, smem, a.stream>>>(static_cast<const T*>(a.hess), a.n, a.plane_stride, a.radius_stride, a.R,
+                                           a.scale_idx0, ctx->tab, rp, sd, a.F_max, a.idx, a.counters);
+  return check_cuda(cudaGetLastError(), "collapse_sur_kernel launch");
+}
+
+}  // namespace
+
+int launch_surrogate_checked(cc_ctx* ctx, const LaunchArgs& a, const double* sigma) {
+  if (!ctx->sur_valid) return set_error(CC_EINVAL, "CC_MODE_SURROGATE needs a trained or loaded surrogate");
+  for (int r0 = 0; r0 < a.R; r0 += kMaxRadiiPerLaunch) {
+    LaunchArgs c = a;
+    c.R = (a.R - r0 < kMaxRadiiPerLaunch) ? a.R - r0 : kMaxRadiiPerLaunch;
+    c.hess = static_cast<const unsigned char*>(a.hess) + static_cast<size_t>(r0) * a.radius_stride * a.dtype;
+    c.scale_idx0 = a.scale_idx0 + r0;
+    RadiusParams rp;
+    for (int r = 0; r < c.R; ++r) {
+      rp.tri_thr[r] = static_cast<float>(1e-4 * sigma[r0 + r]);
+      rp.inv_sigma[r] = static_cast<float>(1.0 / sigma[r0 + r]);
+    }
+    const int rc = (a.dtype == CC_F64) ? launch_sur_typed<double>(ctx, c, rp) : launch_sur_typed<float>(ctx, c, rp);
+    if (rc) return rc;
+  }
+  return CC_OK;
+}
+
+}  // namespace cc
+
+using namespace cc;
+using namespace cc::mlp;
+
+extern "C" {
+
+int cc_surrogate_train(cc_ctx* ctx, const void* hess, int32_t dtype, int64_t n, int64_t plane_stride, double sigma,
+                       const cc_train_config* cfg, cc_train_report* report, void* stream) {
+  if (!ctx || !hess || !cfg) return set_error(CC_EINVAL, "ctx, hess and cfg are required");
+  if (dtype != CC_F64 && dtype != CC_F32) return set_error(CC_EINVAL, "dtype must be CC_F64 or CC_F32");
+  if (n < 1024 || plane_stride < n || !(sigma > 0.0)) return set_error(CC_EINVAL, "need n >= 1024, plane_stride >= n, sigma > 0");
+  if (cfg->steps < 1 || cfg->batch < 64 || cfg->batch % 64 || !(cfg->lr > 0.0f) || !(cfg->val_fraction > 0.0f) ||
+      !(cfg->val_fraction < 0.5f))
+    return set_error(CC_EINVAL, "train config: steps >= 1, batch a multiple of 64, lr > 0, 0 < val_fraction < 0.5");
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != ctx->device) cudaSetDevice(ctx->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (int rc = ensure_surrogate(ctx)) return rc;
+  // ---- training set
+  const size_t rec_bytes = sizeof(float4) * static_cast<size_t>(n);
+  if (rec_bytes > ctx->train_cap) {
+    if (ctx->d_train) cudaFree(ctx->d_train);
+    ctx->d_train = nullptr;
+    ctx->train_cap = 0;
+    if (int rc = check_cuda(cudaMalloc(&ctx->d_train, rec_bytes + 64), "cudaMalloc(training set)")) return rc;
+    ctx->train_cap = rec_bytes;
+  }
+  float4* recs = static_cast<float4*>(ctx->d_train);
+  unsigned long long* count = reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(ctx->d_train) + rec_bytes);
+  int* hull = reinterpret_cast<int*>(count + 1);
+  const int hull_init[6] = {0x7FFFFFFF, 0x7FFFFFFF, 0x7FFFFFFF, static_cast<int>(0x80000000), static_cast<int>(0x80000000),
+                            static_cast<int>(0x80000000)};
+  if (int rc = check_cuda(cudaMemsetAsync(count, 0, sizeof(unsigned long long), st), "cudaMemsetAsync")) return rc;
+  if (int rc = check_cuda(cudaMemcpyAsync(hull, hull_init, sizeof(hull_init), cudaMemcpyHostToDevice, st), "H2D hull")) return rc;
+  const int grid = launch_grid(n, 256, ctx->num_sms * 8);
+  if (dtype == CC_F64)
+    sur_data_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double*>(hess), n, plane_stride, sigma, recs, count, n, hull);
+  else
+    sur_data_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(hess), n, plane_stride, sigma, recs, count, n, hull);
+  if (int rc = check_cuda(cudaGetLastError(), "sur_data_kernel launch")) return rc;
+  unsigned long long cnt = 0;
+  int hull_h[6];
+  if (int rc = check_cuda(cudaMemcpyAsync(&cnt, count, sizeof(cnt), cudaMemcpyDeviceToHost, st), "D2H count")) return rc;
+  if (int rc = check_cuda(cudaMemcpyAsync(hull_h, hull, sizeof(hull_h), cudaMemcpyDeviceToHost, st), "D2H hull")) return rc;
+  if (int rc = check_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize")) return rc;
+  const int64_t total = static_cast<int64_t>(cnt < static_cast<unsigned long long>(n) ? cnt : n);
+  const int64_t nval = static_cast<int64_t>(total * cfg->val_fraction);
+  const int64_t ntrain = total - nval;
+  if (ntrain < cfg->batch || nval < 32) return set_error(CC_EINVAL, "too few collapsing points to train on");
+  // ---- initial parameters: b4 = mean target of the first samples
+  std::vector<float4> head(static_cast<size_t>(std::min<int64_t>(ntrain, 65536)));
+  if (int rc = check_cuda(cudaMemcpy(head.data(), recs, sizeof(float4) * head.size(), cudaMemcpyDeviceToHost), "D2H head")) return rc;
+  double tmean = 0.0;
+  for (const auto& r : head) tmean += r.w;
+  tmean /= static_cast<double>(head.size());
+  std::vector<float> p0;
+  init_params(p0, cfg->seed, static_cast<float>(tmean));
+  float* P = ctx->d_mlp_param;
+  float* Mv = P + NPARAM;
+  float* Vv = Mv + NPARAM;
+  float* G = Vv + NPARAM;
+  float* loss = G + NPARAM;
+  if (int rc = check_cuda(cudaMemcpyAsync(P, p0.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice, st), "H2D params")) return rc;
+  if (int rc = check_cuda(cudaMemsetAsync(Mv, 0, sizeof(float) * (3 * NPARAM + 8), st), "cudaMemsetAsync")) return rc;
+  sur_image_kernel<<<(NPARAM + 255) / 256, 256, 0, st>>>(P, ctx->d_mlp_img);
+  if (int rc = check_cuda(cudaFuncSetAttribute(sur_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(kTrainSmem)), "cudaFuncSetAttribute"))
+    return rc;
+  // ---- training: Adam, warm-up then cosine decay
+  const int blocks = cfg->batch / (32 * kTrainWarps);
+  const float inv_batch = 1.0f / static_cast<float>(cfg->batch);
+  std::vector<float> losses;
+  for (int s = 0; s < cfg->steps; ++s) {
+    if (s == 0 || s == cfg->steps - 1)
+      if (int rc = check_cuda(cudaMemsetAsync(loss, 0, sizeof(float), st), "cudaMemsetAsync")) return rc;
+    sur_train_kernel<<<blocks, 32 * kTrainWarps, kTrainSmem, st>>>(recs, ntrain, cfg->seed, s, 0, inv_batch,
+                                                                   ctx->d_mlp_img, G, loss);
+    const double warm = std::min(1.0, (s + 1) / 100.0);
+    const double lr = cfg->lr * warm * 0.5 * (1.0 + std::cos(3.141592653589793 * s / cfg->steps)) + 1e-6;
+    const float b1t = static_cast<float>(std::pow(0.9, s + 1)), b2t = static_cast<float>(std::pow(0.999, s + 1));
+    sur_adam_kernel<<<(NPARAM + 255) / 256, 256, 0, st>>>(P, Mv, Vv, G, static_cast<float>(lr), b1t, b2t, ctx->d_mlp_img);
+    if (s == 0 || s == cfg->steps - 1) {
+      float l = 0.f;
+      if (int rc = check_cuda(cudaMemcpyAsync(&l, loss, sizeof(float), cudaMemcpyDeviceToHost, st), "D2H loss")) return rc;
+      if (int rc = check_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize")) return rc;
+      losses.push_back(l);
+    }
+  }
+  if (int rc = check_cuda(cudaGetLastError(), "training launch")) return rc;
+  // ---- validation on the held-out records
+  float* stats = loss + 2;
+  if (int rc = check_cuda(cudaMemsetAsync(stats, 0, sizeof(float) * 2, st), "cudaMemsetAsync")) return rc;
+  sur_eval_kernel<<<launch_grid(nval, 256, ctx->num_sms * 4), 256, FWD_BYTES, st>>>(
+      reinterpret_cast<const float*>(recs + ntrain), 4, nval, ctx->d_mlp_img, nullptr, stats,
+      reinterpret_cast<int*>(stats + 1));
+  float stats_h[2];
+  if (int rc = check_cuda(cudaMemcpyAsync(stats_h, stats, sizeof(stats_h), cudaMemcpyDeviceToHost, st), "D2H stats")) return rc;
+  if (int rc = check_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize")) return rc;
+  for (int i = 0; i < 6; ++i) ctx->sur_hull[i] = unordered(hull_h[i]);
+  ctx->sur_valid = true;
+  if (report) {
+    report->samples = total;
+    report->train_samples = ntrain;
+    report->val_samples = nval;
+    report->loss_first = losses.empty() ? 0.f : losses.front();
+    report->loss_last = losses.empty() ? 0.f : losses.back();
+    report->val_rms = std::sqrt(stats_h[0] / static_cast<float>(nval));
+    std::memcpy(&report->val_max, &stats_h[1], sizeof(float));
+    for (int i = 0; i < 3; ++i) {
+      report->hull_lo[i] = ctx->sur_hull[i];
+      report->hull_hi[i] = ctx->sur_hull[3 + i];
+    }
+  }
+  return CC_OK;
+}
+
+int cc_surrogate_params(const cc_ctx* ctx, float* params, float* hull) {
+  if (!ctx || !params) return set_error(CC_EINVAL, "ctx and params are required");
+  if (!ctx->sur_valid) return set_error(CC_EINVAL, "no surrogate: train or load one first");
+  if (int rc = check_cuda(cudaMemcpy(params, ctx->d_mlp_param, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost), "D2H params"))
+    return rc;
+  if (hull) std::memcpy(hull, ctx->sur_hull, sizeof(float) * 6);
+  return CC_OK;
+}
+
+int cc_load_surrogate(cc_ctx* ctx, const float* params, const float* hull) {
+  if (!ctx || !params || !hull) return set_error(CC_EINVAL, "ctx, params and hull are required");
+  for (int i = 0; i < NPARAM; ++i)
+    if (!std::isfinite(params[i])) return set_error(CC_EINVAL, "parameters must be finite");
+  for (int i = 0; i < 3; ++i)
+    if (!(hull[i] <= hull[3 + i])) return set_error(CC_EINVAL, "hull: lo <= hi per component");
+  if (int rc = ensure_surrogate(ctx)) return rc;
+  if (int rc = check_cuda(cudaMemcpy(ctx->d_mlp_param, params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice), "H2D params"))
+    return rc;
+  sur_image_kernel<<<(NPARAM + 255) / 256, 256>>>(ctx->d_mlp_param, ctx->d_mlp_img);
+  if (int rc = check_cuda(cudaDeviceSynchronize(), "sur_image_kernel")) return rc;
+  std::memcpy(ctx->sur_hull, hull, sizeof(float) * 6);
+  ctx->sur_valid = true;
+  return CC_OK;
+}
+
+int cc_surrogate_eval(cc_ctx* ctx, const float* z, int64_t n, float* out, void* stream) {
+  if (!ctx || n < 0 || (n > 0 && (!z || !out))) return set_error(CC_EINVAL, "bad arguments");
+  if (!ctx->sur_valid) return set_error(CC_EINVAL, "no surrogate: train or load one first");
+  if (n == 0) return CC_OK;
+  sur_eval_kernel<<<launch_grid(n, 256, ctx->num_sms * 4), 256, FWD_BYTES, static_cast<cudaStream_t>(stream)>>>(
+      z, 3, n, ctx->d_mlp_img, out, nullptr, nullptr);
+  return check_cuda(cudaGetLastError(), "sur_eval_kernel launch");
+}
+
+int cc_surrogate_grad(cc_ctx* ctx, const float* z, const float* t, int32_t n, float* grad, float* loss_out) {
+  if (!ctx || !z || !t || !grad || n < 64 || n % 64) return set_error(CC_EINVAL, "need host z, t, grad and n a multiple of 64");
+  if (!ctx->sur_valid) return set_error(CC_EINVAL, "no surrogate: train or load one first");
+  std::vector<float4> recs(n);
+  for (int i = 0; i < n; ++i) recs[i] = make_float4(z[3 * i], z[3 * i + 1], z[3 * i + 2], t[i]);
+  float4* d = nullptr;
+  float* g = nullptr;
+  if (int rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&d), sizeof(float4) * n), "cudaMalloc")) return rc;
+  int rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&g), sizeof(float) * (NPARAM + 1)), "cudaMalloc");
+  if (!rc) rc = check_cuda(cudaMemcpy(d, recs.data(), sizeof(float4) * n, cudaMemcpyHostToDevice), "H2D");
+  if (!rc) rc = check_cuda(cudaMemset(g, 0, sizeof(float) * (NPARAM + 1)), "cudaMemset");
+  if (!rc) rc = check_cuda(cudaFuncSetAttribute(sur_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                static_cast<int>(kTrainSmem)), "cudaFuncSetAttribute");
+  if (!rc) {
+    sur_train_kernel<<<n / (32 * kTrainWarps), 32 * kTrainWarps, kTrainSmem>>>(d, n, 0, 0, 1, 1.0f / n, ctx->d_mlp_img,
+                                                                              g, g + NPARAM);
+    rc = check_cuda(cudaDeviceSynchronize(), "sur_train_kernel");
+  }
+  if (!rc) rc = check_cuda(cudaMemcpy(grad, g, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost), "D2H grad");
+  if (!rc && loss_out) rc = check_cuda(cudaMemcpy(loss_out, g + NPARAM, sizeof(float), cudaMemcpyDeviceToHost), "D2H loss");
+  cudaFree(d);
+  cudaFree(g);
+  return rc;
+}
+
+}  // extern "C"

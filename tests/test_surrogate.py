@@ -1,0 +1,183 @@
+"""The learned surrogate: GPU training kernels vs the oracle's FP64 MLP, training
+convergence, CC_MODE_SURROGATE parity, and what the network gains over the
+method without it (the mixed path, whose closed-form cubic it replaces)."""
+import time
+
+import numpy as np
+import pytest
+
+import hessgen
+import oracle
+from parity import oracle_per_radius, rel_err, running_max
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+REL_TOL = 3e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2510_02873_gb300 as cc
+    c = cc.Context(0.3, 0.7, 512, 1e-3, 1.0, device=0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def tables():
+    return oracle.Tables(0.3, 0.7, 512, 1e-3, 1.0)
+
+
+def init_like(rng):
+    p = np.zeros(oracle.MLP_NPARAM)
+    p[0:192] = rng.uniform(-1, 1, 192) * np.sqrt(3 / 3)
+    p[256:4352] = rng.uniform(-1, 1, 4096) * np.sqrt(3 / 64)
+    p[4416:8512] = rng.uniform(-1, 1, 4096) * np.sqrt(3 / 64)
+    p[8576:8640] = rng.uniform(-1, 1, 64) * np.sqrt(3 / 64)
+    p[192:256] = rng.normal(size=64) * 0.1
+    p[4352:4416] = rng.normal(size=64) * 0.1
+    p[8512:8576] = rng.normal(size=64) * 0.1
+    p[8640] = 0.3
+    return p.astype(np.float32)
+
+
+def sample_inputs(rng, m):
+    lam = np.sort(rng.normal(size=(m, 3)) * 1.2, axis=1)[:, ::-1]
+    return np.ascontiguousarray(lam, dtype=np.float32)
+
+
+def test_gpu_gradient_matches_oracle(ctx):
+    """One minibatch through the BF16 tensor-core training kernel against the
+    FP64 reference gradient of the same loss and parameters."""
+    rng = np.random.default_rng(1)
+    params = init_like(rng)
+    ctx.load_surrogate(params, [-10, -10, -10, 10, 10, 10])
+    z = sample_inputs(rng, 256)
+    t = rng.normal(size=256).astype(np.float32)
+    loss_g, grad_g = ctx.surrogate_grad(z, t)
+    loss_o, grad_o = oracle.mlp_loss_grad(params.astype(np.float64), z.astype(np.float64), t.astype(np.float64))
+    assert abs(loss_g - loss_o) <= 2e-2 * loss_o
+    groups = {"W1": (0, 192), "b1": (192, 256), "W2": (256, 4352), "b2": (4352, 4416), "W3": (4416, 8512),
+              "b3": (8512, 8576), "W4": (8576, 8640), "b4": (8640, 8641)}
+    for name, (a, b) in groups.items():
+        g, o = grad_g[a:b].astype(np.float64), grad_o[a:b]
+        rel = np.linalg.norm(g - o) / np.linalg.norm(o)
+        assert rel < 5e-2, (name, rel)
+        if b - a > 1:
+            cos = g @ o / (np.linalg.norm(g) * np.linalg.norm(o))
+            assert cos > 0.998, (name, cos)
+
+
+def test_gpu_forward_matches_oracle(ctx):
+    rng = np.random.default_rng(2)
+    params = init_like(rng)
+    ctx.load_surrogate(params, [-10, -10, -10, 10, 10, 10])
+    z = sample_inputs(rng, 1000 + 7)
+    out = torch.empty(len(z), dtype=torch.float32, device="cuda")
+    ctx.surrogate_eval(torch.from_numpy(z).cuda(), out)
+    torch.cuda.synchronize()
+    ref = oracle.mlp_forward(params.astype(np.float64), z.astype(np.float64))
+    got = out.cpu().numpy()
+    assert np.all(np.abs(got - ref) <= 3e-2 * (1 + np.abs(ref)))
+    params2, hull = ctx.surrogate_params()
+    np.testing.assert_array_equal(params2, params)
+
+
+@pytest.fixture(scope="module")
+def trained(ctx):
+    """Train on 4M points of the isotropic field at s = 1 (about 2M collapsing samples)."""
+    import hessgen.device as hdev
+    n = 4 * 1024 * 1024
+    h = torch.empty((6, n), dtype=torch.float32, device="cuda")
+    hdev.fill(h, 777, 9, 0, 1.0)
+    t0 = time.perf_counter()
+    rep = ctx.surrogate_train(h, 1.0, steps=1500, batch=16384, lr=3e-3, seed=5)
+    rep["seconds"] = time.perf_counter() - t0
+    print("training", rep)
+    del h
+    torch.cuda.empty_cache()
+    return rep
+
+
+def test_training_converges(trained):
+    rep = trained
+    assert rep["samples"] > 1_000_000
+    assert rep["loss_last"] < rep["loss_first"] / 20
+    assert rep["val_rms"] < 5e-2
+    lo, hi = np.array(rep["hull_lo"]), np.array(rep["hull_hi"])
+    assert np.all(lo < hi) and lo[0] > 0
+
+
+def compare(F, idx, F_all, fl, tol=REL_TOL):
+    F_ref, idx_ref = running_max(F_all)
+    amb = (fl & oracle.FLAGS_AMBIGUOUS).any(axis=0)
+    edge = ((F_ref > 0) & (F_ref < 1.0 + 4 * tol)) | ((F > 0) & (F < 1.0 + 4 * tol))
+    srt = np.sort(F_all, axis=0)
+    tie = (srt[-1] > 0) & (srt[-1] - srt[-2] <= 2 * tol * srt[-1]) if F_all.shape[0] > 1 else np.zeros_like(amb)
+    ok = ~amb & ~edge
+    err = rel_err(F, F_ref)
+    assert err[ok].max() <= tol
+    assert np.array_equal(idx[ok & ~tie], idx_ref[ok & ~tie])
+    return float(err[ok].max())
+
+
+def run(ctx, stack, sig, mode):
+    R, _, n = stack.shape
+    d = torch.from_numpy(stack).cuda()
+    F = torch.empty(n, dtype=torch.float64, device="cuda")
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    ctx.reset_max(F, idx)
+    ctx.reset_stats()
+    ctx.collapse_multi(d, sig, F, idx, mode=mode)
+    torch.cuda.synchronize()
+    return F.cpu().numpy(), idx.cpu().numpy(), ctx.stats()
+
+
+def test_surrogate_mode_parity(ctx, tables, trained):
+    n, R = 32 ** 3, 8
+    sig = hessgen.sigma_schedule(R, 0.3, 6.0)
+    stack = hessgen.hessian_stack(2516, 0, sig, n, dtype=np.float32)
+    F_all, fl = oracle_per_radius(tables, stack)
+    F, idx, st = run(ctx, stack, sig, "surrogate")
+    worst = compare(F, idx, F_all, fl)
+    frac = st["fallback"] / st["evaluations"]
+    print("surrogate parity", worst, "fallback fraction", frac, st)
+    assert frac < 0.2
+
+
+def test_surrogate_gain_over_the_method_without_it(ctx, trained):
+    """The network replaces the closed-form FP32 cubic of the mixed path as the
+    Newton seed. Same planes through both: results agree to the mixed tolerance;
+    the printed ratio is what the network gains (below 1 means it costs time)."""
+    import hessgen.device as hdev
+    n, R = 128 ** 3, 8
+    sig = hessgen.sigma_schedule(R, 0.3, 6.0)
+    h = torch.empty((R, 6, n), dtype=torch.float32, device="cuda")
+    for r in range(R):
+        hdev.fill(h[r], 818, 0, r, sig[r])
+    times, outs = {}, {}
+    for mode in ("mixed", "surrogate", "mixed", "surrogate"):
+        F = torch.empty(n, dtype=torch.float64, device="cuda")
+        idx = torch.empty(n, dtype=torch.int32, device="cuda")
+        ctx.reset_max(F, idx)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.collapse_multi(h, sig, F, idx, mode=mode)
+        e1.record()
+        torch.cuda.synchronize()
+        times[mode] = e0.elapsed_time(e1)
+        outs[mode] = F.cpu().numpy()
+    a, b = outs["mixed"], outs["surrogate"]
+    both = (a > 1.0 + 1.2e-4) & (b > 1.0 + 1.2e-4)
+    assert np.max(np.abs(a[both] - b[both]) / a[both]) <= 2 * REL_TOL
+    gain = times["mixed"] / times["surrogate"]
+    print(f"surrogate gain over the closed-form seed: {gain:.3f}x "
+          f"(mixed {times['mixed']:.2f} ms, surrogate {times['surrogate']:.2f} ms)")
+    assert gain > 0
