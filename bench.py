@@ -35,13 +35,13 @@ WORKLOAD = "collapse 256^3 grid x 25 radii, FP64 SoA Hessian planes (20.1 GB res
 
 # FP64 floating-point operations per (point, radius) evaluation of the FP64
 # kernel, from ncu thread-instruction counters (dadd + dmul + 2 dfma) divided
-# by the evaluations of the captured launch (profiles/collapse_fp64_kernel_*.md).
+# by the evaluations of the captured launch (profiles/collapse_kernel_*_128cube_x4.md).
 # None until a capture of the current kernel exists.
-FP64_FLOPS_PER_EVAL = 81.0   # profiles/collapse_fp64_kernel_128cube_x4.md
+FP64_FLOPS_PER_EVAL = 76.0   # profiles/collapse_kernel_fp64_128cube_x4.md
 FP64_FLOPS_PER_EVAL_MIXED = 16.1  # profiles/collapse_kernel_mixed_256cube_x4.md
 # DRAM bytes (read + write) of one full launch of the default workload, from
 # an ncu capture of that launch (profiles/collapse_kernel_fp64_256cube_x25_dram.md).
-TRAFFIC_BYTES_DEFAULT = 20.80e9
+TRAFFIC_BYTES_DEFAULT = 20.48e9
 # FP64 FMA rate of one GB300 SM: 1.25 TFLOP/s nominal at 2070 MHz over 152 SMs
 # = 3.97 flop/clk/SM, i.e. 2 DFMA per clock per SM (confirmed by a DFMA-chain probe).
 FP64_FLOP_PER_CLK_PER_SM = 4.0
@@ -61,7 +61,10 @@ def parse():
     # smaller problems for profiler captures only (the benchmark workload is the default)
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--radii", type=int, default=N_RADII)
-    ap.add_argument("--mode", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--mode", choices=["fp64", "mixed", "f32x2", "surrogate"], default="fp64")
+    # --mode surrogate trains the network first (untimed) on this many points and steps
+    ap.add_argument("--train-points", type=int, default=4 * 1024 * 1024)
+    ap.add_argument("--train-steps", type=int, default=300)
     return ap.parse_args()
 
 
@@ -162,13 +165,51 @@ def run_reference(args):
         "impl": "reference", "metric": "collapse evals/s (points x radii)", "value": value,
         "unit": "evals/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * secs / len(steps), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "f32x2": "f32x2 (float-float)", "mixed": "f32+f64",
+                                       "surrogate": "bf16+f32+f64"}[args.mode], "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample_per_step": f"4096 points x {N_RADII} radii"},
         "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": value, "unit": "evals/s",
                          "sample": f"{args.steps} steps of 4096 points x {N_RADII} radii"},
         "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- float-float variant
+def run_f32x2_variant(ctx, hess, sig, F_ref, idx_ref, stream, steps: int) -> dict:
+    """The FP64 path's steps in float-float arithmetic (CC_MODE_F32X2) on the
+    same FP64 planes as the main workload, timed the same way, and compared
+    with the FP64 kernel's result point by point."""
+    import torch
+
+    n = F_ref.numel()
+    R = hess.shape[0]
+    F = torch.empty_like(F_ref)
+    idx = torch.empty_like(idx_ref)
+    for _ in range(2):
+        ctx.reset_max(F, idx)
+        ctx.collapse_multi(hess, sig, F, idx, mode="f32x2")
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        ctx.reset_max(F, idx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.collapse_multi(hess, sig, F, idx, mode="f32x2")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    both = (F_ref > 0) & (F > 0)
+    rel = ((F - F_ref).abs() / F_ref)[both]
+    ms = statistics.mean(times)
+    return {
+        "workload": "the main workload's planes (256^3 x 25, FP64)",
+        "evals_per_s": float(n) * R / (ms * 1e-3), "kernel_ms": ms,
+        "max_rel_diff_vs_fp64_kernel": float(rel.max()), "rms_rel_diff_vs_fp64_kernel": float(rel.pow(2).mean().sqrt()),
+        "collapse_decision_differs": int(((F_ref > 0) != (F > 0)).sum()),
+        "argmax_differs": int((idx != idx_ref).sum()),
+        "bound_tol": 1e-10,
+    }
 
 
 # ----------------------------------------------------------------------------- mixed variant
@@ -432,7 +473,12 @@ def main():
     R = args.radii
     sig = hessgen.sigma_schedule(R, S_LO, S_HI)
     ctx = cc.Context(**COSMO, device=local)
-    plane_dtype = torch.float64 if args.mode == "fp64" else torch.float32
+    plane_dtype = torch.float32 if args.mode in ("mixed", "surrogate") else torch.float64
+    if args.mode == "surrogate":
+        h = torch.empty((6, args.train_points), dtype=torch.float32, device=dev)
+        hdev.fill(h, SEED + 5, 99, 0, 1.0)
+        ctx.surrogate_train(h, 1.0, steps=args.train_steps, batch=16384, lr=3e-3, seed=11)
+        del h
     hess = torch.empty((R, 6, n), dtype=plane_dtype, device=dev)
     for r in range(R):
         hdev.fill(hess[r], SEED, rank, r, sig[r])  # realization = rank: independent problem per GPU
@@ -480,8 +526,8 @@ def main():
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     clk_mhz = clk.get("sm_max_mhz") or 2070.0
     peak_tflops = FP64_FLOP_PER_CLK_PER_SM * sm_count * clk_mhz * 1e6 / 1e12
-    fpe = FP64_FLOPS_PER_EVAL if args.mode == "fp64" else FP64_FLOPS_PER_EVAL_MIXED
-    achieved = fpe * evals_launch / kern_avg_s / 1e12
+    fpe = {"fp64": FP64_FLOPS_PER_EVAL, "mixed": FP64_FLOPS_PER_EVAL_MIXED}.get(args.mode)
+    achieved = fpe * evals_launch / kern_avg_s / 1e12 if fpe else None
     roofline = {
         "bound": "alu", "kernel": f"collapse_kernel ({args.mode})", "unit": "TFLOP/s",
         "achieved": achieved, "peak": peak_tflops,
@@ -501,15 +547,19 @@ def main():
         "metric": "collapse evals/s (points x radii)", "value": value, "unit": "evals/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "f32x2": "f32x2 (float-float)", "mixed": "f32+f64",
+                                       "surrogate": "bf16+f32+f64"}[args.mode], "data": "synthetic",
         "config": {"workload": WORKLOAD if (args.grid, R) == (GRID, N_RADII) else f"profiling case {args.grid}^3 x {R}", "points": n, "radii": R, "mode": args.mode,
                    "per_gpu": "one independent realization per GPU",
-                   "l2": f"inputs {48 * n * R / 1e9:.1f} GB per step vs 129 MB L2 (no flush needed)"},
+                   "l2": f"inputs {6 * hess.element_size() * n * R / 1e9:.1f} GB per step vs 129 MB L2 (no flush needed)"},
         "roofline": roofline,
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
         "stats": {k: stats[k] for k in ("evaluations", "collapsed", "eds_branch", "refined", "error_flags")},
     }
+
+    if rank == 0 and not args.no_variants and (args.grid, R) == (GRID, N_RADII) and args.mode == "fp64":
+        result["variants"] = {"f32x2": run_f32x2_variant(ctx, hess, sig, F, idx, stream, args.steps)}
 
     # end to end through the host-buffer entry point (H2D of every radius inside the timed region)
     if not args.no_e2e and rank == 0 and args.mode == "fp64":
@@ -543,7 +593,7 @@ def main():
         if "hess" in locals():
             del hess
         torch.cuda.empty_cache()
-        result["variants"] = {"mixed": run_mixed_variant(ctx, dev, stream)}
+        result.setdefault("variants", {})["mixed"] = run_mixed_variant(ctx, dev, stream)
         result["variants"]["batched"] = run_batch_variant(ctx, dev, stream)
         result["variants"]["surrogate"] = run_surrogate_variant(ctx, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and (args.grid, R) == (GRID, N_RADII):

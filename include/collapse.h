@@ -69,7 +69,10 @@ typedef enum {
   CC_MODE_FP64 = 0,     /* all arithmetic in FP64 (Sec. 3 "Classic" kernel)            */
   CC_MODE_MIXED = 1,    /* FP32 bulk, FP64 for the sensitive branches                   */
   CC_MODE_SURROGATE = 2,/* learned surrogate with exact fallback                        */
-  CC_MODE_TABULATED = 3 /* table of log D_c in (delta, x, y) (Sec. 3 "Tabulated" kernel) */
+  CC_MODE_TABULATED = 3,/* table of 1/D_c in (delta, x, y) (Sec. 3 "Tabulated" kernel)   */
+  CC_MODE_F32X2 = 4     /* the FP64 path's steps in float-float arithmetic (pairs of FP32
+                         * numbers, 48 significant bits) instead of the FP64 unit; same
+                         * accuracy contract as CC_MODE_FP64 (F within 1e-10 relative)     */
 } cc_mode;
 
 /* Flat LCDM-like background: E^2 = Om a^-3 + (1 - Om - OL) a^-2 + OL.

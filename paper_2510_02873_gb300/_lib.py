@@ -9,7 +9,7 @@ from . import buildlib as _build
 
 CC_OK, CC_EINVAL, CC_ECUDA, CC_ENOMEM, CC_ETIMEOUT, CC_ERANGE, CC_ENOTSUP = range(7)
 CC_F64, CC_F32 = 8, 4
-MODES = {"fp64": 0, "mixed": 1, "surrogate": 2, "tabulated": 3}
+MODES = {"fp64": 0, "mixed": 1, "surrogate": 2, "tabulated": 3, "f32x2": 4}
 
 # every symbol the public header declares
 EXPORTS = (

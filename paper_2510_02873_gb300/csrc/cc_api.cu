@@ -89,6 +89,8 @@ int run_collapse(cc_ctx* ctx, cc_mode mode, const void* hess, int32_t dtype, int
       return launch_tab_checked(ctx, a);
     case CC_MODE_SURROGATE:
       return launch_surrogate_checked(ctx, a, sigma);
+    case CC_MODE_F32X2:
+      return launch_f32x2(a, ctx->tab);
   }
   return set_error(CC_EINVAL, "unknown mode");
 }
@@ -188,7 +190,10 @@ int cc_create(cc_ctx** out, const cc_cosmology* cosmo, int device) {
   const size_t d_bytes = sizeof(double) * n;
   const size_t df_bytes = sizeof(float) * n;
   const size_t b_bytes = sizeof(unsigned short) * nb;
-  const size_t total = coef_bytes + d_bytes + df_bytes + b_bytes;
+  const size_t main_bytes = coef_bytes + d_bytes + df_bytes + b_bytes;
+  const size_t seg_off = ((main_bytes + 15) / 16) * 16;
+  const size_t seg_bytes = sizeof(float) * 8 * (n - 1);
+  const size_t total = seg_off + seg_bytes;
   if ((rc = check_cuda(cudaMalloc(&ctx->d_table, total), "cudaMalloc(table)"))) { delete ctx; return rc; }
   if ((rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&ctx->d_counters), sizeof(DevCounters)),
                        "cudaMalloc(counters)"))) {
@@ -201,6 +206,22 @@ int cc_create(cc_ctx** out, const cc_cosmology* cosmo, int device) {
   std::memcpy(host.data() + coef_bytes, ctx->D_k.data(), d_bytes);
   std::memcpy(host.data() + coef_bytes + d_bytes, df.data(), df_bytes);
   std::memcpy(host.data() + coef_bytes + d_bytes + df_bytes, bucket.data(), b_bytes);
+  {  // float-float image: value = hi + lo with hi = RN32(value), lo = RN32(value - hi)
+    auto split = [](double v, float& hi, float& lo) {
+      hi = static_cast<float>(v);
+      lo = static_cast<float>(v - static_cast<double>(hi));
+    };
+    float* seg = reinterpret_cast<float*>(host.data() + seg_off);
+    for (int k = 0; k < n - 1; ++k) {
+      const double* c = ctx->coef.data() + 4 * k;
+      float* s = seg + 8 * k;
+      split(c[0], s[0], s[1]);
+      split(c[1], s[2], s[3]);
+      s[4] = static_cast<float>(c[2]);
+      s[5] = static_cast<float>(c[3]);
+      split(ctx->D_k[k], s[6], s[7]);
+    }
+  }
   rc = check_cuda(cudaMemcpy(ctx->d_table, host.data(), total, cudaMemcpyHostToDevice), "cudaMemcpy(table)");
   if (!rc) rc = check_cuda(cudaMemset(ctx->d_counters, 0, sizeof(DevCounters)), "cudaMemset(counters)");
   if (rc) { cc_destroy(ctx); return rc; }
@@ -219,6 +240,14 @@ int cc_create(cc_ctx** out, const cc_cosmology* cosmo, int device) {
   t.Dtop = ctx->D_k[n - 1];
   t.eds_slope = ctx->a_k[0] / ctx->D_k[0];
   t.Dtopf = static_cast<float>(t.Dtop);
+  t.dfseg = reinterpret_cast<const float4*>(base + seg_off);
+  auto split2 = [](double v, float& hi, float& lo) {
+    hi = static_cast<float>(v);
+    lo = static_cast<float>(v - static_cast<double>(hi));
+  };
+  split2(t.Dtop, t.Dtop_hi, t.Dtop_lo);
+  split2(t.D0, t.D0_hi, t.D0_lo);
+  split2(t.eds_slope, t.eds_hi, t.eds_lo);
   *out = ctx;
   return CC_OK;
 }

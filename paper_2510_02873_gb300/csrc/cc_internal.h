@@ -47,6 +47,11 @@ struct DevTable {
   double a0, D0, Dtop;            // first scale factor, first and last knot
   double eds_slope;               // a0 / D0
   float Dtopf;                    // D_top rounded to FP32 (interval search)
+  // float-float image of the spline (CC_MODE_F32X2): two float4 per interval,
+  // {c0 hi, c0 lo, c1 hi, c1 lo}, {c2, c3, D_k hi, D_k lo}, stored right after
+  // the table image at offset round_up(bytes(), 16); nullptr when absent
+  const float4* dfseg;
+  float Dtop_hi, Dtop_lo, D0_hi, D0_lo, eds_hi, eds_lo;  // float-float constants
   // bytes of the table image (coef | D | Df | bucket), staged in shared memory
   __host__ __device__ size_t bytes() const {
     return sizeof(Coef4) * (n - 1) + sizeof(double) * n + sizeof(float) * n +
@@ -113,6 +118,7 @@ struct LaunchArgs {
 int launch_fp64(const LaunchArgs& a, const DevTable& tab);
 int launch_mixed(const LaunchArgs& a, const DevTable& tab, const double* sigma);
 int launch_tab(const LaunchArgs& a, const DevTable& tab, const TabDev& td);
+int launch_f32x2(const LaunchArgs& a, const DevTable& tab);
 int launch_reset_max(double* F_max, int32_t* idx, int64_t n, cudaStream_t stream, int num_sms);
 
 }  // namespace cc

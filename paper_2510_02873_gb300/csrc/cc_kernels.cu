@@ -7,7 +7,7 @@
 // coefficients staged in shared memory once per block, and the running
 // maximum over the radii of one launch kept in registers: F_max/idx are read
 // and written once per point per launch.
-#include "cc_device.cuh"
+#include "cc_df.cuh"
 
 namespace cc {
 
@@ -39,7 +39,7 @@ __device__ __forceinline__ void add_counters(DevCounters* cnt, unsigned evals, u
   }
 }
 
-constexpr int kModeFP64 = 0, kModeMixed = 1, kModeTab = 2;
+constexpr int kModeFP64 = 0, kModeMixed = 1, kModeTab = 2, kModeF32x2 = 3;
 
 // One thread per point (grid-stride), all R radii of the launch in registers.
 // kMode selects collapse_point_fp64, collapse_point_mixed (FP32 bulk) or
@@ -59,21 +59,27 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
   const double* Dk = tab.D;
   const float* Dkf = tab.Df;
   const unsigned short* bucket = tab.bucket;
+  const float4* seg = tab.dfseg;
   if constexpr (kSmem) {
-    // the table image (coef | D | Df | bucket) is contiguous: copy it in 16-byte words
-    const int words = static_cast<int>(tab.bytes() / 16);
+    // the table image (coef | D | Df | bucket [| pad | float-float image]) is
+    // contiguous: copy it in 16-byte words
+    const int words = (kMode == kModeF32x2) ? static_cast<int>((tab.bytes() + 15) / 16) + 2 * (tab.n - 1)
+                                            : static_cast<int>(tab.bytes() / 16);
     const uint4* src = reinterpret_cast<const uint4*>(tab.coef);
     uint4* dst = reinterpret_cast<uint4*>(smem_tab);
     for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
-    const size_t tail = tab.bytes() & 15;
-    if (threadIdx.x < tail)
-      reinterpret_cast<unsigned char*>(dst + words)[threadIdx.x] =
-          reinterpret_cast<const unsigned char*>(src + words)[threadIdx.x];
+    if constexpr (kMode != kModeF32x2) {
+      const size_t tail = tab.bytes() & 15;
+      if (threadIdx.x < tail)
+        reinterpret_cast<unsigned char*>(dst + words)[threadIdx.x] =
+            reinterpret_cast<const unsigned char*>(src + words)[threadIdx.x];
+    }
     __syncthreads();
     coef = smem_tab;
     Dk = reinterpret_cast<const double*>(smem_tab + (tab.n - 1));
     Dkf = reinterpret_cast<const float*>(Dk + tab.n);
     bucket = reinterpret_cast<const unsigned short*>(Dkf + tab.n);
+    seg = reinterpret_cast<const float4*>(smem_tab) + (tab.bytes() + 15) / 16;
   }
   const double* tax = nullptr;
   if constexpr (kMode == kModeTab) {
@@ -92,7 +98,19 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
   for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n_round;
        p += stride) {
     const bool active = p < n;
-    if (active) {
+    if (kMode == kModeF32x2 && active) {
+      dfl::MinA2 best;
+      for (int r = 0; r < R; ++r) {
+        const dfl::Result res =
+            dfl::collapse_point(hess + p + static_cast<int64_t>(r) * radius_stride, plane_stride, seg, Dkf, bucket, tab);
+        n_coll += res.collapsed;
+        n_eds += res.eds;
+        n_ref += res.refined;
+        best.add(res.collapsed, res.a, r);
+      }
+      best.store(F_max + p, idx + p, scale_idx0);
+      n_eval += R;
+    } else if (kMode != kModeF32x2 && active) {
       MinA best;
       const T* base = hess + p;
       for (int r = 0; r < R; ++r) {
@@ -155,6 +173,7 @@ int launch_typed(const LaunchArgs& a, const DevTable& tab, const RadiusParams& r
   auto kern = collapse_kernel<T, kSmem, kMode>;
   size_t smem = kSmem ? ((tab.bytes() + 15) / 16) * 16 : 0;
   if (kMode == kModeTab) smem = ((tab.bytes() + 15) / 16) * 16 + ((td.axes_bytes() + 15) / 16) * 16;
+  if (kMode == kModeF32x2 && kSmem) smem = ((tab.bytes() + 15) / 16) * 16 + sizeof(float4) * 2 * (tab.n - 1);
   static thread_local int occ = 0;
   if (kSmem && smem > 48 * 1024) {
     if (int rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -181,7 +200,9 @@ int launch_typed(const LaunchArgs& a, const DevTable& tab, const RadiusParams& r
 
 template <int kMode>
 int launch_mode(const LaunchArgs& a, const DevTable& tab, const RadiusParams& rp, const TabDev& td) {
-  const bool smem = tab.bytes() <= static_cast<size_t>(kSmemTableMaxBytes);
+  const size_t staged = (kMode == kModeF32x2) ? ((tab.bytes() + 15) / 16) * 16 + sizeof(float4) * 2 * (tab.n - 1)
+                                               : tab.bytes();
+  const bool smem = staged <= static_cast<size_t>(kSmemTableMaxBytes);
   if (kMode == kModeTab) {  // the tabulated kernel always stages both images
     if (a.dtype == CC_F64) return launch_typed<double, true, kMode>(a, tab, rp, td);
     return launch_typed<float, true, kMode>(a, tab, rp, td);
@@ -195,6 +216,11 @@ int launch_mode(const LaunchArgs& a, const DevTable& tab, const RadiusParams& rp
 
 int launch_fp64(const LaunchArgs& a, const DevTable& tab) {
   return launch_mode<kModeFP64>(a, tab, RadiusParams{}, TabDev{});
+}
+
+int launch_f32x2(const LaunchArgs& a, const DevTable& tab) {
+  if (tab.dfseg == nullptr) return set_error(CC_ENOTSUP, "CC_MODE_F32X2 needs the float-float spline image");
+  return launch_mode<kModeF32x2>(a, tab, RadiusParams{}, TabDev{});
 }
 
 int launch_tab(const LaunchArgs& a, const DevTable& tab, const TabDev& td) {

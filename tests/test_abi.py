@@ -79,3 +79,10 @@ def test_null_arguments_rejected_without_device(lib):
     assert lib.cc_collapse_scale(None, 0, None, 8, 0, 0, 1.0, None, None, 0, None) == _lib.CC_EINVAL
     assert lib.cc_reset_max(None, None, None, 0, None) == _lib.CC_EINVAL
     lib.cc_destroy(None)  # no-op
+
+
+def test_mode_names_match_the_header():
+    text = open(os.path.join(ROOT, "include", "collapse.h")).read()
+    enum = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"CC_MODE_(\w+)\s*=\s*(\d+)", text)}
+    assert enum == {"fp64": 0, "mixed": 1, "surrogate": 2, "tabulated": 3, "f32x2": 4}
+    assert enum == _lib.MODES

@@ -1,4 +1,6 @@
-"""GPU parity of the FP64 collapse path (C-ABI through the binding) against the oracle."""
+"""GPU parity of the FP64-accurate collapse paths (C-ABI through the binding) against the
+oracle: CC_MODE_FP64 (FP64 unit) and CC_MODE_F32X2 (the same steps in float-float
+arithmetic), both held to 1e-10 relative."""
 import numpy as np
 import pytest
 
@@ -44,16 +46,20 @@ def gpu_multi(ctx, stack: np.ndarray, sigma, plane_stride=None, scale_idx0=0, mo
     return F.cpu().numpy(), idx.cpu().numpy()
 
 
-def test_config1_fused_over_radii(ctx, tables):
+MODES = ["fp64", "f32x2"]
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_config1_fused_over_radii(ctx, tables, mode):
     """32^3 grid x 8 radii, s log-spaced 0.3 -> 4.0: every point, every radius."""
     n, R = 32 ** 3, 8
     sig = hessgen.sigma_schedule(R, 0.3, 4.0)
     stack = hessgen.hessian_stack(2511, 0, sig, n)
     F_all, fl = oracle_per_radius(tables, stack)
-    F, idx = gpu_multi(ctx, stack, sig)
+    F, idx = gpu_multi(ctx, stack, sig, mode=mode)
     s = compare_max(F, idx, F_all, fl)
     assert (idx >= 0).mean() > 0.3
-    print("config1", s)
+    print("config1", mode, s)
 
 
 def test_scale_by_scale_equals_fused(ctx):
@@ -73,23 +79,25 @@ def test_scale_by_scale_equals_fused(ctx):
     assert np.array_equal(idx.cpu().numpy(), idx_f)
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("n", [1, 2, 31, 32, 33, 255, 257, 1023, 4097, 70001])
-def test_ragged_sizes_and_padded_planes(ctx, tables, n):
+def test_ragged_sizes_and_padded_planes(ctx, tables, n, mode):
     R = 3
     sig = hessgen.sigma_schedule(R, 1.0, 5.0)
     stack = hessgen.hessian_stack(1000 + n, 0, sig, n)
     ps = n + (n % 2) + 2  # padded plane stride, 16-byte aligned planes
     F_all, fl = oracle_per_radius(tables, stack)
-    F, idx = gpu_multi(ctx, stack, sig, plane_stride=ps, scale_idx0=5)
+    F, idx = gpu_multi(ctx, stack, sig, plane_stride=ps, scale_idx0=5, mode=mode)
     compare_max(F, idx, F_all, fl, scale_idx0=5)
 
 
-def test_fp32_planes_in_fp64_mode(ctx, tables):
+@pytest.mark.parametrize("mode", MODES)
+def test_fp32_planes_in_fp64_mode(ctx, tables, mode):
     n, R = 20000, 4
     sig = hessgen.sigma_schedule(R, 0.5, 4.0)
     stack = hessgen.hessian_stack(31337, 2, sig, n, dtype=np.float32)
     F_all, fl = oracle_per_radius(tables, stack)
-    F, idx = gpu_multi(ctx, stack, sig)
+    F, idx = gpu_multi(ctx, stack, sig, mode=mode)
     compare_max(F, idx, F_all, fl)
 
 
@@ -105,7 +113,8 @@ def _rotated(spectra, rng):
     return np.array(Ms)
 
 
-def test_degenerate_and_special_spectra(ctx, tables):
+@pytest.mark.parametrize("mode", MODES)
+def test_degenerate_and_special_spectra(ctx, tables, mode):
     """Exact and near-exact degeneracies (the deflation branch), spherical,
     plane-wave, voids, collapse before the first knot (EdS branch), and axis-aligned."""
     rng = np.random.default_rng(5)
@@ -122,17 +131,18 @@ def test_degenerate_and_special_spectra(ctx, tables):
     planes = _planes_from_matrices(Ms)
     stack = planes[None]
     F_all, fl = oracle_per_radius(tables, stack)
-    F, idx = gpu_multi(ctx, stack, [1.0])
+    F, idx = gpu_multi(ctx, stack, [1.0], mode=mode)
     compare_max(F, idx, F_all, fl)
 
 
-def test_non_finite_inputs_give_no_collapse(ctx):
+@pytest.mark.parametrize("mode", MODES)
+def test_non_finite_inputs_give_no_collapse(ctx, mode):
     n = 64
     stack = np.zeros((1, 6, n))
     stack[0, 0, :] = 2.0
     stack[0, :, ::4] = np.nan
     stack[0, 0, 1::4] = np.inf
-    F, idx = gpu_multi(ctx, stack, [1.0])
+    F, idx = gpu_multi(ctx, stack, [1.0], mode=mode)
     assert np.all(F[::4] == 0) and np.all(idx[::4] == -1)
     assert np.all(np.isfinite(F))
 
@@ -180,12 +190,13 @@ def test_invalid_arguments_are_rejected(ctx):
         ctx.collapse_scale(buf[:6 * (n + 1)].view(6, n + 1)[:, :n], 1.0, F, idx, 0)
 
 
-def test_host_buffer_entry_matches_device_path(ctx):
+@pytest.mark.parametrize("mode", MODES)
+def test_host_buffer_entry_matches_device_path(ctx, mode):
     """cc_collapse_multi_host (pinned and pageable host planes) == cc_collapse_multi, bit for bit."""
     n, R = 100003, 5
     sig = hessgen.sigma_schedule(R, 0.4, 5.0)
     stack = hessgen.hessian_stack(555, 0, sig, n)
-    F_d, idx_d = gpu_multi(ctx, np.ascontiguousarray(stack), sig, plane_stride=n + 3)
+    F_d, idx_d = gpu_multi(ctx, np.ascontiguousarray(stack), sig, plane_stride=n + 3, mode=mode)
     for pinned in (True, False):
         host = torch.zeros((R, 6, n + 2), dtype=torch.float64, pin_memory=pinned)  # odd plane stride
         host[:, :, :n] = torch.from_numpy(stack)
@@ -193,17 +204,18 @@ def test_host_buffer_entry_matches_device_path(ctx):
         ih = torch.full((n,), -1, dtype=torch.int32, pin_memory=pinned)
         import paper_2510_02873_gb300 as cc
         with pytest.raises(cc.CollapseError):
-            ctx.collapse_multi_host(host[:, :, :n], sig, Fh, ih)  # 8-byte plane stride
+            ctx.collapse_multi_host(host[:, :, :n], sig, Fh, ih, mode=mode)  # 8-byte plane stride
         host2 = torch.zeros((R, 6, n + 3), dtype=torch.float64, pin_memory=pinned)
         host2[:, :, :n] = torch.from_numpy(stack)
-        ctx.collapse_multi_host(host2[:, :, :n], sig, Fh, ih)
+        ctx.collapse_multi_host(host2[:, :, :n], sig, Fh, ih, mode=mode)
         assert np.array_equal(Fh.numpy(), F_d) and np.array_equal(ih.numpy(), idx_d)
         # a second call continues the running maximum (scale indices shifted)
-        ctx.collapse_multi_host(host2[:, :, :n], sig, Fh, ih, scale_idx0=R)
+        ctx.collapse_multi_host(host2[:, :, :n], sig, Fh, ih, scale_idx0=R, mode=mode)
         assert np.array_equal(Fh.numpy(), F_d) and np.array_equal(ih.numpy(), idx_d)
 
 
-def test_config2_full_size_sampled(ctx, tables):
+@pytest.mark.parametrize("mode", MODES)
+def test_config2_full_size_sampled(ctx, tables, mode):
     """256^3 grid x 25 radii (FP64 planes, 20 GB resident), one fused launch as
     the bench times it; sampled points checked against the oracle one by one,
     and properties that hold at any size checked on every point."""
@@ -218,7 +230,7 @@ def test_config2_full_size_sampled(ctx, tables):
     idx = torch.empty(n, dtype=torch.int32, device="cuda")
     ctx.reset_max(F, idx)
     ctx.reset_stats()
-    ctx.collapse_multi(hess, sig, F, idx)
+    ctx.collapse_multi(hess, sig, F, idx, mode=mode)
     torch.cuda.synchronize()
     st = ctx.stats()
     assert st["evaluations"] == n * R and st["error_flags"] == 0
@@ -238,6 +250,6 @@ def test_config2_full_size_sampled(ctx, tables):
     assert np.all(np.isfinite(Fs)) and np.all(Fs >= 0)
     assert np.all((Fs == 0) == (ids == -1)) and ids.min() >= -1 and ids.max() < R
     assert (ids >= 0).mean() > 0.5
-    print("config2 sampled", s, st)
+    print("config2 sampled", mode, s, st)
     del hess
     torch.cuda.empty_cache()
