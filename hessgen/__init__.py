@@ -136,3 +136,21 @@ def hessian_stack(seed: int, realization: int, sigmas, n_points: int, dtype=np.f
     """(R, 6, n_points) planes for every radius."""
     return np.stack([hessian_planes(seed, realization, r, float(s), n_points, dtype)
                      for r, s in enumerate(sigmas)])
+
+
+def hessian_stack_correlated(seed: int, realization: int, sigmas, n_points: int, rho: float,
+                             dtype=np.float64) -> np.ndarray:
+    """(R, 6, n_points) planes with correlated radii: a unit-rms field
+    G_0 = N_0, G_r = rho G_{r-1} + sqrt(1 - rho^2) N_r (N_r the radius-r draw at
+    s = 1), planes_r = s_r G_r. Smoothing the same field at neighbouring radii
+    correlates its Hessians; this AR(1) chain stands in for that."""
+    points = np.arange(n_points, dtype=np.int64)
+    crho = math.sqrt(1.0 - rho * rho)
+    out = np.empty((len(sigmas), 6, n_points), dtype=dtype)
+    G = None
+    for r, s in enumerate(sigmas):
+        N = hessian_points(seed, realization, r, 1.0, points)
+        G = N if G is None else rho * G + crho * N
+        out[r] = (float(s) * G).astype(dtype)
+    return out
+

@@ -45,6 +45,11 @@ def _load():
                                   ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
                                   ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
             L.hg_fill.restype = ctypes.c_int
+            L.hg_fill_correlated.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                             ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+            L.hg_fill_correlated.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -62,3 +67,26 @@ def fill(planes, seed: int, realization: int, radius: int, s: float, point_offse
                          planes.data_ptr(), planes.stride(0), dtype, ctypes.c_void_p(st.cuda_stream))
     if rc:
         raise RuntimeError(f"hg_fill failed with status {rc}")
+
+
+def fill_correlated(planes, state, seed: int, realization: int, radius: int, s: float, rho: float,
+                    first: bool, stream=None) -> None:
+    """Correlated-radius fill (same definition as hessgen.hessian_stack_correlated):
+    state is a CUDA float64 (6, n) tensor carried from radius to radius."""
+    import math
+
+    import torch
+    assert planes.is_cuda and planes.dim() == 2 and planes.shape[0] == 6 and planes.stride(1) == 1
+    assert state.is_cuda and state.dtype == torch.float64 and state.is_contiguous()
+    assert state.shape == (6, planes.shape[1])
+    dtype = 8 if planes.dtype == torch.float64 else 4 if planes.dtype == torch.float32 else None
+    if dtype is None:
+        raise TypeError("planes must be float64 or float32")
+    st = torch.cuda.current_stream() if stream is None else stream
+    rc = _load().hg_fill_correlated(seed, realization, radius, float(s), C1, C2, float(rho),
+                                    math.sqrt(1.0 - rho * rho), planes.shape[1], planes.data_ptr(),
+                                    planes.stride(0), dtype, state.data_ptr(), int(bool(first)),
+                                    ctypes.c_void_p(st.cuda_stream))
+    if rc:
+        raise RuntimeError(f"hg_fill_correlated failed with status {rc}")
+

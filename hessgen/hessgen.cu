@@ -8,6 +8,9 @@
 // The mixing uses explicitly rounded products and sums (no FMA contraction) so
 // it matches the host version operation by operation; only the Box-Muller
 // log/sin/cos of the two math libraries may differ in the last bits.
+// Correlated radii (hg_fill_correlated): a unit-rms field G_r per radius,
+// G_0 = N_0, G_r = rho G_{r-1} + sqrt(1 - rho^2) N_r (an AR(1) chain over the
+// radii, kept in an FP64 state buffer), planes = s_r G_r.
 // This file holds none of the collapse-time arithmetic.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -31,10 +34,11 @@ __device__ __forceinline__ void philox10(uint32_t c[4], uint32_t k0, uint32_t k1
   }
 }
 
-template <typename T>
+template <typename T, bool kCorr>
 __global__ void fill_kernel(uint64_t seed, uint32_t realization, uint32_t radius, double s, double c1,
                             double c2, int64_t n, int64_t point_offset, T* __restrict__ out,
-                            int64_t plane_stride) {
+                            int64_t plane_stride, double rho, double crho, double* __restrict__ state,
+                            int first) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
     const uint64_t p = static_cast<uint64_t>(point_offset + i);
@@ -64,15 +68,20 @@ __global__ void fill_kernel(uint64_t seed, uint32_t realization, uint32_t radius
       g[2 * j] = __dmul_rn(r, cs);
       g[2 * j + 1] = __dmul_rn(r, sn);
     }
+    double unit[6];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double v = __dmul_rn(s, __dadd_rn(__dmul_rn(c2, g[1 + a]), __dmul_rn(c1, g[0])));
-      out[a * plane_stride + i] = static_cast<T>(v);
-    }
+    for (int a = 0; a < 3; ++a) unit[a] = __dadd_rn(__dmul_rn(c2, g[1 + a]), __dmul_rn(c1, g[0]));
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const double v = __dmul_rn(s, __dmul_rn(c1, g[4 + a]));
-      out[(3 + a) * plane_stride + i] = static_cast<T>(v);
+    for (int a = 0; a < 3; ++a) unit[3 + a] = __dmul_rn(c1, g[4 + a]);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      double v = unit[a];
+      if constexpr (kCorr) {
+        double* st = state + a * n + i;
+        v = first ? v : __dadd_rn(__dmul_rn(rho, *st), __dmul_rn(crho, v));
+        *st = v;
+      }
+      out[a * plane_stride + i] = static_cast<T>(__dmul_rn(s, v));
     }
   }
 }
@@ -94,10 +103,33 @@ extern "C" __attribute__((visibility("default"))) int hg_fill(uint64_t seed, uin
   const int grid = static_cast<int>(need < cap ? need : cap);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (dtype == 8)
-    fill_kernel<double><<<grid, 256, 0, st>>>(seed, realization, radius, s, c1, c2, n, point_offset,
-                                              static_cast<double*>(out), plane_stride);
+    fill_kernel<double, false><<<grid, 256, 0, st>>>(seed, realization, radius, s, c1, c2, n, point_offset,
+                                                     static_cast<double*>(out), plane_stride, 0.0, 0.0, nullptr, 1);
   else
-    fill_kernel<float><<<grid, 256, 0, st>>>(seed, realization, radius, s, c1, c2, n, point_offset,
-                                             static_cast<float*>(out), plane_stride);
+    fill_kernel<float, false><<<grid, 256, 0, st>>>(seed, realization, radius, s, c1, c2, n, point_offset,
+                                                    static_cast<float*>(out), plane_stride, 0.0, 0.0, nullptr, 1);
+  return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+// Correlated radii: state is a device FP64 (6, n) buffer holding G_{r-1}
+// (overwritten with G_r); first != 0 starts the chain (G_0 = N_0).
+extern "C" __attribute__((visibility("default"))) int hg_fill_correlated(
+    uint64_t seed, uint32_t realization, uint32_t radius, double s, double c1, double c2, double rho,
+    double crho, int64_t n, void* out, int64_t plane_stride, int dtype, double* state, int first, void* stream) {
+  if (n <= 0) return 0;
+  if (out == nullptr || state == nullptr || plane_stride < n || (dtype != 8 && dtype != 4)) return 1;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t need = (n + 255) / 256;
+  const int64_t cap = static_cast<int64_t>(sms > 0 ? sms : 1) * 16;
+  const int grid = static_cast<int>(need < cap ? need : cap);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (dtype == 8)
+    fill_kernel<double, true><<<grid, 256, 0, st>>>(seed, realization, radius, s, c1, c2, n, 0,
+                                                    static_cast<double*>(out), plane_stride, rho, crho, state, first);
+  else
+    fill_kernel<float, true><<<grid, 256, 0, st>>>(seed, realization, radius, s, c1, c2, n, 0,
+                                                   static_cast<float*>(out), plane_stride, rho, crho, state, first);
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }

@@ -19,7 +19,11 @@ LIB_PATH = os.path.join(BUILD_DIR, "libcollapse.so")
 INCLUDE = os.path.join(os.path.dirname(PKG_DIR), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-COMMON = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden",
+# -fmad=false: no implicit multiply-add contraction in device code. Every FMA
+# is written out (fma/fmaf), so a device function computes bit-identical
+# results in every kernel it is inlined into (the batched kernel reproduces the
+# per-realization kernel exactly).
+COMMON = ["-std=c++17", "-O3", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-fvisibility=hidden",
           f"-I{INCLUDE}", f"-I{CSRC}"]
 
 

@@ -71,12 +71,12 @@ __device__ __forceinline__ void run_point(const BatchItemDev& it, int64_t p, con
 }
 
 template <bool kMixed, int kBlock>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, 1024 / kBlock)  // 64 registers, like collapse_kernel
 batched_kernel(const BatchItemDev* __restrict__ items, int nitems, int64_t total_tiles,
                unsigned long long* __restrict__ work, DevTable tab, DevCounters* __restrict__ cnt) {
   extern __shared__ Coef4 smem_tab[];
   __shared__ long long s_tile;
-  __shared__ int s_item;
+  __shared__ BatchItemDev s_it;
   {  // table image to shared memory (16-byte words)
     const int words = static_cast<int>(tab.bytes() / 16);
     const uint4* src = reinterpret_cast<const uint4*>(tab.coef);
@@ -101,14 +101,12 @@ batched_kernel(const BatchItemDev* __restrict__ items, int nitems, int64_t total
         if (items[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
       }
       s_tile = t;
-      s_item = lo;
+      if (t < total_tiles) s_it = items[lo];
     }
     __syncthreads();  // also orders the table staging before first use
     const long long t = s_tile;
-    const int i = s_item;
-    __syncthreads();
     if (t >= total_tiles) break;
-    const BatchItemDev it = items[i];
+    const BatchItemDev& it = s_it;  // read from shared memory (keeps registers for the point)
     const int64_t p0 = (t - it.tile_begin) * it.tile_points;
     const int64_t p1 = min(p0 + it.tile_points, it.n);
     for (int64_t p = p0 + threadIdx.x; p < p1; p += kBlock) {
@@ -118,6 +116,7 @@ batched_kernel(const BatchItemDev* __restrict__ items, int nitems, int64_t total
         run_point<double, kMixed>(it, p, Dk, coef, Dkf, bucket, tab, n_coll, n_eds, n_ref, n_fp64);
       n_eval += it.R;
     }
+    __syncthreads();  // every thread is done with s_it before thread 0 takes the next tile
   }
   n_eval = __reduce_add_sync(0xffffffffu, n_eval);
   n_coll = __reduce_add_sync(0xffffffffu, n_coll);

@@ -106,12 +106,12 @@ static __device__ __noinline__ void refine_top_pair(double xx, double yy, double
 // three are.
 __device__ __forceinline__ float cubic_largest_root_f32(float b, float c, float d) {
   const float b3 = b * (1.0f / 3.0f);
-  const float pp = c - b * b3;
-  const float qq = b3 * (2.0f * b3 * b3 - c) + d;
-  const float disc = 0.25f * qq * qq + pp * pp * pp * (1.0f / 27.0f);
+  const float pp = fmaf(-b, b3, c);
+  const float qq = fmaf(b3, fmaf(2.0f * b3, b3, -c), d);
+  const float disc = fmaf(0.25f * qq, qq, pp * pp * pp * (1.0f / 27.0f));
   float t;
   if (disc > 0.0f) {
-    const float A = cbrtf(0.5f * fabsf(qq) + sqrtf(disc));
+    const float A = cbrtf(fmaf(0.5f, fabsf(qq), sqrtf(disc)));
     const float C = (qq > 0.0f) ? -A : A;
     t = (C != 0.0f) ? C - pp / (3.0f * C) : 0.0f;
   } else {
@@ -181,9 +181,9 @@ __device__ __forceinline__ EigenTop eigen_top_fp64(double xx, double yy, double 
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
     const float xf = (it == 0) ? x1f : to_f32_trunc(x);
-    const float gpf = 3.0f * (xf * xf - p2f);
+    const float gpf = 3.0f * fmaf(xf, xf, -p2f);
     const double yg = to_f64((gpf != 0.0f) ? 1.0f / gpf : 0.0f);
-    const double g = fma(x, x * x - p2x3, -det);
+    const double g = fma(x, fma(x, x, -p2x3), -det);
     x = fma(-g, yg, x);
   }
   e.refined = (1.0f + rf) < kPairTauF && p2f > 0.0f;
@@ -193,7 +193,7 @@ __device__ __forceinline__ EigenTop eigen_top_fp64(double xx, double yy, double 
 #pragma unroll
     for (int it = 0; it < 3; ++it) {
       const double x32 = x3 * x3;
-      x3 -= fma(x3, x32 - p2x3, -det) / (3.0 * x32 - p2x3);
+      x3 -= fma(x3, x32 - p2x3, -det) / fma(3.0, x32, -p2x3);
     }
     double l1r = q + x, l2r = 0.0;
     refine_top_pair(xx, yy, zz, xy, xz, yz, q + x3, l1r, l2r);
@@ -371,8 +371,8 @@ __device__ __forceinline__ MixedEigen mixed_eigen(float xx, float yy, float zz, 
   const float x3 = -pf * fmaf(kSqrt3f, sn, cs);
 #pragma unroll
   for (int it = 0; it < 2; ++it) {  // FP32 Newton on x (x^2 - 3p^2) - det
-    const float gp = 3.0f * (x * x - p2);
-    x = (gp != 0.0f) ? x - fmaf(x, x * x - p2x3, -det) / gp : x;
+    const float gp = 3.0f * fmaf(x, x, -p2);
+    x = (gp != 0.0f) ? x - fmaf(x, fmaf(x, x, -p2x3), -det) / gp : x;
   }
   m.full = ((1.0f + rf) < kPairTauF && p2 > 0.0f) || (x - x3) < tri_thr;
   const float lam1f = q + x;
@@ -385,7 +385,7 @@ __device__ __forceinline__ MixedEigen mixed_eigen(float xx, float yy, float zz, 
     const double dxy = to_f64(xy), dxz = to_f64(xz), dyz = to_f64(yz);
     const double g = fma(dxx, fma(dyy, dzz, -dyz * dyz),
                          fma(-dxy, fma(dxy, dzz, -dyz * dxz), dxz * fma(dxy, dyz, -dyy * dxz)));
-    const float gpf = 3.0f * (x * x - p2);
+    const float gpf = 3.0f * fmaf(x, x, -p2);
     lam1 = fma(g, to_f64(1.0f / gpf), lam1);
     x = to_f32_trunc(lam1 - to_f64(q));
     m.fp64 = true;

@@ -46,21 +46,26 @@ __device__ __forceinline__ f2 add(f2 a, f2 b) {
   return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
 __device__ __forceinline__ f2 sub(f2 a, f2 b) { return add(a, neg(b)); }
+// Products are returned unnormalised: {RN(ab), the rest}, |lo| a few ulp(hi)
+// at most. Every sum renormalises (Fast2Sum), and only sums are compared, so
+// the renormalisation a product would need is left to the sum that consumes it.
 __device__ __forceinline__ f2 mul(f2 a, f2 b) {
   const float p = __fmul_rn(a.hi, b.hi);
-  const float e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p)));
-  return fast_two_sum(p, e);
+  return {p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p)))};
 }
 __device__ __forceinline__ f2 mul(f2 a, float b) {
   const float p = __fmul_rn(a.hi, b);
-  const float e = fmaf(a.lo, b, fmaf(a.hi, b, -p));
-  return fast_two_sum(p, e);
+  return {p, fmaf(a.lo, b, fmaf(a.hi, b, -p))};
 }
 __device__ __forceinline__ f2 sqr(f2 a) {
   const float p = __fmul_rn(a.hi, a.hi);
-  const float e = fmaf(2.0f * a.hi, a.lo, fmaf(a.hi, a.hi, -p));
-  return fast_two_sum(p, e);
+  return {p, fmaf(2.0f * a.hi, a.lo, fmaf(a.hi, a.hi, -p))};
 }
+__device__ __forceinline__ f2 two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ f2 norm(f2 a) { return fast_two_sum(a.hi, a.lo); }
 // exact scaling by a power of two
 __device__ __forceinline__ f2 scale(f2 a, float pow2) { return {a.hi * pow2, a.lo * pow2}; }
 // order of two normalised float-float numbers (hi first, then lo)
@@ -97,6 +102,36 @@ constexpr cf2 kM3_7 = make_const(-3.0 / 7.0);
 constexpr cf2 kM5_21 = make_const(-5.0 / 21.0);
 constexpr cf2 k37_63 = make_const(37.0 / 63.0);
 
+// ---- FP32 seeds. Two Newton corrections follow every seed, so 1e-4 relative
+// is enough: the seeds use the special-function unit directly.
+// arccos by the Hastings approximation of Abramowitz & Stegun 4.4.45
+// (|error| <= 5e-5 rad on [0, 1]; acos(-x) = pi - acos(x)).
+__device__ __forceinline__ float acos_seed(float x) {
+  const float ax = fabsf(x);
+  const float p = fmaf(fmaf(fmaf(-0.0187293f, ax, 0.0742610f), ax, -0.2121144f), ax, 1.5707288f) * sqrtf(1.0f - ax);
+  return (x < 0.0f) ? 3.14159265f - p : p;
+}
+// largest real root of u^3 + b u^2 + c u + d (Cardano / trigonometric form, as
+// cubic_largest_root_f32, with the fast seeds)
+__device__ __forceinline__ float cubic_largest_root_seed(float b, float c, float d) {
+  const float b3 = b * (1.0f / 3.0f);
+  const float pp = fmaf(-b, b3, c);
+  const float qq = fmaf(b3, fmaf(2.0f * b3, b3, -c), d);
+  const float disc = fmaf(0.25f * qq, qq, pp * pp * pp * (1.0f / 27.0f));
+  float t;
+  if (disc > 0.0f) {
+    const float A = __powf(fmaf(0.5f, fabsf(qq), sqrtf(disc)), 1.0f / 3.0f);  // cube root, A >= 0
+    const float C = (qq > 0.0f) ? -A : A;
+    t = (C != 0.0f) ? C - __fdividef(pp, 3.0f * C) : 0.0f;
+  } else {
+    const float m = sqrtf(-pp * (1.0f / 3.0f));
+    float arg = (m > 0.0f) ? __fdividef(-0.5f * qq, m * m * m) : 0.0f;
+    arg = fminf(1.0f, fmaxf(-1.0f, arg));
+    t = 2.0f * m * __cosf(acos_seed(arg) * (1.0f / 3.0f));
+  }
+  return t - b3;
+}
+
 struct Result {
   f2 a;  // a_c (meaningful when collapsed)
   bool collapsed, eds, refined;
@@ -122,18 +157,20 @@ __device__ __forceinline__ Result collapse_point(const T* __restrict__ h, int64_
   // ---- FP32 trigonometric seed of x = l1 - q
   const float p2f = p2x3.hi * (1.0f / 3.0f);
   const float pf = sqrtf(p2f);
-  float rf = (p2f > 0.0f) ? det.hi / (2.0f * p2f * pf) : 0.0f;
+  float rf = (p2f > 0.0f) ? __fdividef(det.hi, 2.0f * p2f * pf) : 0.0f;
   rf = fminf(1.0f, fmaxf(-1.0f, rf));
-  float sn, cs;
-  sincosf(acosf(rf) * (1.0f / 3.0f), &sn, &cs);
-  const float x1f = 2.0f * pf * cs;
+  const float x1f = 2.0f * pf * __cosf(acos_seed(rf) * (1.0f / 3.0f));
   // ---- two Newton corrections on x (x^2 - 3p^2) - det (FP32 derivative at each iterate)
-  f2 x = make(x1f);
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const float xf = x.hi;
-    const float gpf = 3.0f * (xf * xf - p2f);
-    const float yg = (gpf != 0.0f) ? 1.0f / gpf : 0.0f;
+  f2 x;
+  {
+    const float gpf = 3.0f * fmaf(x1f, x1f, -p2f);
+    const float yg = (gpf != 0.0f) ? __fdividef(1.0f, gpf) : 0.0f;
+    const f2 g = sub(mul(sub(two_prod(x1f, x1f), p2x3), x1f), det);
+    x = add(make(x1f), mul(g, -yg));
+  }
+  {
+    const float gpf = 3.0f * fmaf(x.hi, x.hi, -p2f);
+    const float yg = (gpf != 0.0f) ? __fdividef(1.0f, gpf) : 0.0f;
     const f2 g = sub(mul(x, sub(sqr(x), p2x3)), det);
     x = add(x, mul(g, -yg));
   }
@@ -154,8 +191,8 @@ __device__ __forceinline__ Result collapse_point(const T* __restrict__ h, int64_
   const f2 c2 = mul(Pp, k(kM3_7));
   const f2 c3 = mul(lam1, add(mul(sqr(S), k(kM5_21)), mul(Pp, k(k37_63))));
   // ---- FP32 root (closed form in u = 1/D, two Newton steps), one float-float Newton correction
-  const float uf = cubic_largest_root_f32(-lam1.hi, c2.hi, c3.hi);
-  float Df = 1.0f / uf;
+  const float uf = cubic_largest_root_seed(-lam1.hi, c2.hi, c3.hi);
+  float Df = __fdividef(1.0f, uf);
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
     const float Af = fmaf(fmaf(fmaf(c3.hi, Df, c2.hi), Df, -lam1.hi), Df, 1.0f);
@@ -164,7 +201,7 @@ __device__ __forceinline__ Result collapse_point(const T* __restrict__ h, int64_
   }
   const float dAf = fmaf(fmaf(3.0f * c3.hi, Df, 2.0f * c2.hi), Df, -lam1.hi);
   const f2 A1 = add(mul(add(mul(add(mul(c3, Df), c2), Df), neg(lam1)), Df), make(1.0f));
-  const f2 D = fast_two_sum(Df, -A1.hi * (1.0f / dAf));  // the correction is ~1e-7 D
+  const f2 D = fast_two_sum(Df, -__fdividef(A1.hi, dAf));  // the correction is ~1e-7 D
   // ---- collapse test: l1 > 0, 0 < D <= D_top
   const f2 Dtop = {tab.Dtop_hi, tab.Dtop_lo};
   res.collapsed = lam1.hi > 0.0f && D.hi > 0.0f && less_equal(D, Dtop);
@@ -177,7 +214,7 @@ __device__ __forceinline__ Result collapse_point(const T* __restrict__ h, int64_
   const f2 v = add(f2{s0.z, s0.w}, mul(t, u));
   res.a = add(f2{s0.x, s0.y}, mul(t, v));
   res.eds = res.collapsed && less(Dc, f2{tab.D0_hi, tab.D0_lo});
-  if (res.eds) res.a = mul(Dc, f2{tab.eds_hi, tab.eds_lo});
+  if (res.eds) res.a = norm(mul(Dc, f2{tab.eds_hi, tab.eds_lo}));
   return res;
 }
 

@@ -55,7 +55,7 @@ __device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint3
 __device__ __forceinline__ float silu(float v) { return __fdividef(v, 1.0f + __expf(-v)); }
 __device__ __forceinline__ float dsilu(float v) {
   const float s = __fdividef(1.0f, 1.0f + __expf(-v));
-  return s * (1.0f + v * (1.0f - s));
+  return s * fmaf(v, 1.0f - s, 1.0f);
 }
 
 // one 16-row tile through a 64 -> 64 layer: c = A W + b (Wt rows = output units)
