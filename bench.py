@@ -45,7 +45,16 @@ TRAFFIC_BYTES_DEFAULT = 20.48e9
 # FP64 FMA rate of one GB300 SM: 1.25 TFLOP/s nominal at 2070 MHz over 152 SMs
 # = 3.97 flop/clk/SM, i.e. 2 DFMA per clock per SM (confirmed by a DFMA-chain probe).
 FP64_FLOP_PER_CLK_PER_SM = 4.0
-HBM_GBS = None  # filled from MEASURED_PEAKS.json when present
+def _measured_hbm_gbs():
+    """HBM copy bandwidth measured on this machine type (MEASURED_PEAKS.json at the repository root)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+HBM_GBS = _measured_hbm_gbs()
 
 
 def parse():
@@ -61,7 +70,7 @@ def parse():
     # smaller problems for profiler captures only (the benchmark workload is the default)
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--radii", type=int, default=N_RADII)
-    ap.add_argument("--mode", choices=["fp64", "mixed", "f32x2", "surrogate"], default="fp64")
+    ap.add_argument("--mode", choices=["fp64", "mixed", "f32x2", "surrogate", "exact_growth"], default="fp64")
     # --mode surrogate trains the network first (untimed) on this many points and steps
     ap.add_argument("--train-points", type=int, default=4 * 1024 * 1024)
     ap.add_argument("--train-steps", type=int, default=300)
@@ -166,7 +175,8 @@ def run_reference(args):
         "unit": "evals/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * secs / len(steps), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp64": "f64", "f32x2": "f32x2 (float-float)", "mixed": "f32+f64",
-                                       "surrogate": "bf16+f32+f64"}[args.mode], "data": "synthetic",
+                                       "surrogate": "bf16+f32+f64", "exact_growth": "f64"}[args.mode],
+        "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample_per_step": f"4096 points x {N_RADII} radii"},
         "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": value, "unit": "evals/s",
                          "sample": f"{args.steps} steps of 4096 points x {N_RADII} radii"},
@@ -210,6 +220,119 @@ def run_f32x2_variant(ctx, hess, sig, F_ref, idx_ref, stream, steps: int) -> dic
         "argmax_differs": int((idx != idx_ref).sum()),
         "bound_tol": 1e-10,
     }
+
+
+# ----------------------------------------------------------------------------- science proxy
+SCI_RHO = 0.9
+SCI_EDGES = [1.0 + 0.25 * k for k in range(41)]  # z_c bins of 0.25 from 0 to 10
+
+
+def run_science_variant(ctx, dev, stream, reps: int = 10) -> dict:
+    """The paper's science check (collapsed points per redshift bin) on a
+    256^3 x 25 FP64 field whose radii are correlated (AR(1) chain, rho = 0.9):
+    FP64 collapse, then the counts per z_c bin on the GPU."""
+    import torch
+
+    import hessgen
+    import hessgen.device as hdev
+
+    n, R = GRID ** 3, N_RADII
+    sig = hessgen.sigma_schedule(R, S_LO, S_HI)
+    hess = torch.empty((R, 6, n), dtype=torch.float64, device=dev)
+    state = torch.empty((6, n), dtype=torch.float64, device=dev)
+    for r in range(R):
+        hdev.fill_correlated(hess[r], state, SEED + 7, 0, r, sig[r], SCI_RHO, first=(r == 0))
+    del state
+    F = torch.empty(n, dtype=torch.float64, device=dev)
+    idx = torch.empty(n, dtype=torch.int32, device=dev)
+    ctx.reset_max(F, idx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.collapse_multi(hess, sig, F, idx, mode="fp64")
+    e1.record(stream)
+    counts = torch.empty(len(SCI_EDGES) + 1, dtype=torch.int64, device=dev)
+    ctx.histogram(F, SCI_EDGES, counts)
+    torch.cuda.synchronize()
+    collapse_ms = e0.elapsed_time(e1)
+    times = []
+    for _ in range(reps):
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        ctx.histogram(F, SCI_EDGES, counts)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        times.append(h0.elapsed_time(h1))
+    c = counts.cpu().tolist()
+    hist_ms = statistics.median(times)
+    del hess
+    torch.cuda.empty_cache()
+    return {
+        "workload": f"{GRID}^3 grid x {R} correlated radii (rho {SCI_RHO}), FP64 planes",
+        "z_edges": [round(e - 1.0, 4) for e in SCI_EDGES],
+        "collapsed_per_z_bin": c[1:-1], "not_collapsed_or_z_below_0": c[0], "z_above_last_edge": c[-1],
+        "collapsed_fraction": float((F > 0).double().mean()),
+        "collapse_kernel_ms": collapse_ms, "evals_per_s": n * R / (collapse_ms * 1e-3),
+        "histogram_kernel_ms": hist_ms,
+        "histogram_roofline": {"bound": "hbm", "unit": "GB/s", "achieved": 8.0 * n / (hist_ms * 1e-3) / 1e9,
+                               "peak": HBM_GBS, "frac": (8.0 * n / (hist_ms * 1e-3) / 1e9 / HBM_GBS) if HBM_GBS else None,
+                               "algorithmic_bytes": 8.0 * n},
+    }
+
+
+# ----------------------------------------------------------------------------- field -> Hessian -> collapse
+FIELD_SPEC = dict(box=2.0 * GRID, amplitude=222.0, index=-1.5, k_cut=1.2)
+FIELD_RADII = (1.0, 12.0)
+
+
+def run_field_variant(ctx, dev, stream, reps: int = 2) -> dict:
+    """One realization kept on the device from white noise to F_max: cuFFT
+    smoothing into the six Hessian planes per radius, then the collapse
+    launch on those planes (256^3 grid, 25 radii). FP64 planes + FP64
+    collapse, and FP32 planes + mixed collapse."""
+    import numpy as np
+    import torch
+
+    import hessgen.device as hdev
+    import paper_2510_02873_gb300 as cc
+
+    n, R = GRID ** 3, N_RADII
+    white = torch.empty(n, dtype=torch.float64, device=dev)
+    hdev.white(white, SEED + 8, 0)
+    field = cc.Field(ctx, white, **FIELD_SPEC)
+    del white
+    radii = np.geomspace(FIELD_RADII[0], FIELD_RADII[1], R)
+    sig = [field.sigma(x) for x in radii]
+    out = {}
+    for label, dt, mode in (("fp64", torch.float64, "fp64"), ("fp32_planes_mixed", torch.float32, "mixed")):
+        planes = torch.empty((6, n), dtype=dt, device=dev)
+        F = torch.empty(n, dtype=torch.float64, device=dev)
+        idx = torch.empty(n, dtype=torch.int32, device=dev)
+        fft_ms, col_ms, tot_ms = [], [], []
+        for rep in range(reps + 1):
+            ctx.reset_max(F, idx)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * R + 1)]
+            ev[0].record(stream)
+            for r in range(R):
+                field.hessian(radii[r], planes)
+                ev[2 * r + 1].record(stream)
+                ctx.collapse_scale(planes, sig[r], F, idx, r, mode=mode)
+                ev[2 * r + 2].record(stream)
+            torch.cuda.synchronize()
+            if rep == 0:
+                continue  # first pass builds the cuFFT plans
+            fft_ms.append(sum(ev[2 * r].elapsed_time(ev[2 * r + 1]) for r in range(R)))
+            col_ms.append(sum(ev[2 * r + 1].elapsed_time(ev[2 * r + 2]) for r in range(R)))
+            tot_ms.append(ev[0].elapsed_time(ev[2 * R]))
+        t = statistics.mean(tot_ms)
+        out[label] = {"evals_per_s": n * R / (t * 1e-3), "ms_per_realization": t,
+                      "hessian_fft_ms": statistics.mean(fft_ms), "collapse_ms": statistics.mean(col_ms),
+                      "collapsed_fraction": float((F > 0).double().mean())}
+        del planes
+    field.close()
+    torch.cuda.empty_cache()
+    return {"workload": f"{GRID}^3 white noise -> P(k) = A k^n exp(-(k/k_c)^2) ({FIELD_SPEC}) -> "
+                        f"{R} Gaussian radii {FIELD_RADII[0]}..{FIELD_RADII[1]} -> Hessian planes -> collapse, all on the device",
+            "sigma_range": [float(sig[-1]), float(sig[0])], **out}
 
 
 # ----------------------------------------------------------------------------- mixed variant
@@ -548,7 +671,8 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp64": "f64", "f32x2": "f32x2 (float-float)", "mixed": "f32+f64",
-                                       "surrogate": "bf16+f32+f64"}[args.mode], "data": "synthetic",
+                                       "surrogate": "bf16+f32+f64", "exact_growth": "f64"}[args.mode],
+        "data": "synthetic",
         "config": {"workload": WORKLOAD if (args.grid, R) == (GRID, N_RADII) else f"profiling case {args.grid}^3 x {R}", "points": n, "radii": R, "mode": args.mode,
                    "per_gpu": "one independent realization per GPU",
                    "l2": f"inputs {6 * hess.element_size() * n * R / 1e9:.1f} GB per step vs 129 MB L2 (no flush needed)"},
@@ -596,6 +720,8 @@ def main():
         result.setdefault("variants", {})["mixed"] = run_mixed_variant(ctx, dev, stream)
         result["variants"]["batched"] = run_batch_variant(ctx, dev, stream)
         result["variants"]["surrogate"] = run_surrogate_variant(ctx, dev, stream)
+        result["variants"]["science_proxy"] = run_science_variant(ctx, dev, stream)
+        result["variants"]["field_to_collapse"] = run_field_variant(ctx, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and (args.grid, R) == (GRID, N_RADII):
         result["cpu_baseline"] = cpu_oracle_rate(args.cpu_seconds)
     if rank == 0:

@@ -154,3 +154,13 @@ def hessian_stack_correlated(seed: int, realization: int, sigmas, n_points: int,
         out[r] = (float(s) * G).astype(dtype)
     return out
 
+
+WHITE_SLOT = 0xFFFFFFFF  # stream slot (radius word of the counter) of the white-noise draws
+
+
+def white_noise(seed: int, realization: int, n_points: int) -> np.ndarray:
+    """n_points unit Gaussians: the first Box-Muller draw of each point's stream
+    in the white-noise slot (input of the field -> Hessian stage)."""
+    u = uniforms(seed, realization, WHITE_SLOT, np.arange(n_points, dtype=np.int64))
+    return np.sqrt(-2.0 * np.log(u[0])) * np.cos((2.0 * math.pi) * u[1])
+

@@ -50,6 +50,9 @@ def _load():
                                              ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
                                              ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
             L.hg_fill_correlated.restype = ctypes.c_int
+            L.hg_white.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64,
+                                   ctypes.c_void_p, ctypes.c_void_p]
+            L.hg_white.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -89,4 +92,16 @@ def fill_correlated(planes, state, seed: int, realization: int, radius: int, s: 
                                     ctypes.c_void_p(st.cuda_stream))
     if rc:
         raise RuntimeError(f"hg_fill_correlated failed with status {rc}")
+
+
+def white(out, seed: int, realization: int, stream=None) -> None:
+    """Fill a contiguous float64 CUDA tensor with unit white noise (hessgen.white_noise)."""
+    import torch
+
+    from . import WHITE_SLOT
+    assert out.is_cuda and out.dtype == torch.float64 and out.is_contiguous()
+    st = torch.cuda.current_stream() if stream is None else stream
+    rc = _load().hg_white(seed, realization, WHITE_SLOT, out.numel(), out.data_ptr(), ctypes.c_void_p(st.cuda_stream))
+    if rc:
+        raise RuntimeError(f"hg_white failed with status {rc}")
 

@@ -86,7 +86,40 @@ __global__ void fill_kernel(uint64_t seed, uint32_t realization, uint32_t radius
   }
 }
 
+// unit white noise: the first Gaussian of the point's draws (counter 4p, the
+// given stream slot as the radius word)
+__global__ void white_kernel(uint64_t seed, uint32_t realization, uint32_t slot, int64_t n, double* __restrict__ out) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint64_t ctr = static_cast<uint64_t>(i) * 4u;
+    uint32_t c[4] = {static_cast<uint32_t>(ctr), static_cast<uint32_t>(ctr >> 32), slot, realization};
+    philox10(c, static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+    double u[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint64_t m = (static_cast<uint64_t>(c[2 * h] & 0xFFFFFu) << 32) | c[2 * h + 1];
+      u[h] = __dmul_rn(__dadd_rn(static_cast<double>(m), 0.5), 0x1p-52);
+    }
+    const double r = __dsqrt_rn(__dmul_rn(-2.0, log(u[0])));
+    out[i] = __dmul_rn(r, cos(__dmul_rn(6.283185307179586, u[1])));
+  }
+}
+
 }  // namespace
+
+extern "C" __attribute__((visibility("default"))) int hg_white(uint64_t seed, uint32_t realization, uint32_t slot,
+                                                              int64_t n, double* out, void* stream) {
+  if (n <= 0) return 0;
+  if (out == nullptr) return 1;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t need = (n + 255) / 256;
+  const int64_t cap = static_cast<int64_t>(sms > 0 ? sms : 1) * 16;
+  white_kernel<<<static_cast<int>(need < cap ? need : cap), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      seed, realization, slot, n, out);
+  return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
 
 extern "C" __attribute__((visibility("default"))) int hg_fill(uint64_t seed, uint32_t realization,
                                                              uint32_t radius, double s, double c1,

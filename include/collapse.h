@@ -70,9 +70,12 @@ typedef enum {
   CC_MODE_MIXED = 1,    /* FP32 bulk, FP64 for the sensitive branches                   */
   CC_MODE_SURROGATE = 2,/* learned surrogate with exact fallback                        */
   CC_MODE_TABULATED = 3,/* table of 1/D_c in (delta, x, y) (Sec. 3 "Tabulated" kernel)   */
-  CC_MODE_F32X2 = 4     /* the FP64 path's steps in float-float arithmetic (pairs of FP32
+  CC_MODE_F32X2 = 4,    /* the FP64 path's steps in float-float arithmetic (pairs of FP32
                          * numbers, 48 significant bits) instead of the FP64 unit; same
                          * accuracy contract as CC_MODE_FP64 (F within 1e-10 relative)     */
+  CC_MODE_EXACT_GROWTH = 5 /* FP64 path with the EdS growth ratios of the collapse condition
+                         * replaced by the second- and third-order growth factors of the
+                         * context's background (D2/D1^2, D3a/D1^3, D3b/D1^3 as splines in D) */
 } cc_mode;
 
 /* Flat LCDM-like background: E^2 = Om a^-3 + (1 - Om - OL) a^-2 + OL.
@@ -306,6 +309,58 @@ CC_API int cc_batch_get_config(const cc_batch *b, int32_t *threads_per_block, in
                                int32_t nitems);
 
 CC_API void cc_batch_destroy(cc_batch *b);
+
+/* Counts of F_max per bin: the number of collapsed points per redshift bin
+ * of the paper's production-run check (Sec. 5.5), with F = 1 + z_c.
+ *   F_max  device, n values >= 0 (as written by the collapse calls; 0 = no collapse)
+ *   edges  host, nbins + 1 values, positive, finite, strictly increasing (1 <= nbins <= 1023)
+ *   counts device, nbins + 2 values, overwritten (asynchronously on `stream`):
+ *          counts[0] = #{F < edges[0]} (every non-collapsed point among them),
+ *          counts[1 + k] = #{edges[k] <= F < edges[k + 1]},
+ *          counts[nbins + 1] = #{F >= edges[nbins]}.
+ * Integer work: exact, independent of the order of the points. Errors:
+ * CC_EINVAL for bad edges, NULL or misaligned (8-byte) pointers. */
+CC_API int cc_histogram(cc_ctx *ctx, const double *F_max, int64_t n, const double *edges, int32_t nbins,
+                        unsigned long long *counts, void *stream);
+
+/* ---- device-resident field -> smoothed Hessian planes ------------------
+ * The FFT stage ahead of the collapse computation (Sec. 3: PINOCCHIO's FFTs
+ * produce the second derivatives of the potential; keeping them on the device
+ * between the FFTs and the collapse kernel is the step the paper plans).
+ * Conventions: an N^3 periodic grid of side `box`, cells in C order (x
+ * slowest, z fastest); wavenumbers k = 2 pi m / box (m the signed DFT
+ * frequency); delta_k = DFT(w) sqrt(P(k)) for unit white noise w, with
+ * P(k) = amplitude k^index exp(-(k / k_cut)^2), Nyquist modes (any |m| = N/2)
+ * and k = 0 zeroed, so var(delta) = mean of P over the k grid; the Hessian at
+ * radius R is H_ij = IDFT[(k_i k_j / k^2) exp(-k^2 R^2 / 2) delta_k] (its trace
+ * is the smoothed density). The transforms are cuFFT's. */
+typedef struct {
+  double box;        /* side of the periodic box (same length unit as R) */
+  double amplitude;  /* A of P(k) = A k^index exp(-(k/k_cut)^2), > 0 */
+  double index;
+  double k_cut;      /* > 0 */
+} cc_spectrum;
+
+typedef struct cc_field cc_field;
+
+/* Colours the unit white noise `white` (device, N^3 doubles, C order,
+ * 16-byte aligned; not modified) into delta_k, kept on the device by the field
+ * (N even, 4 <= N <= 1024). Synchronises `stream` once. */
+CC_API int cc_field_create(cc_ctx *ctx, const double *white, int32_t N, const cc_spectrum *spec, cc_field **out,
+                           void *stream);
+
+/* rms of the density smoothed at radius R, sqrt(mean over the k grid of
+ * P(k) exp(-k^2 R^2)) (the s(R) to pass with the planes); synchronises. */
+CC_API int cc_field_sigma(cc_field *f, double R, double *sigma, void *stream);
+
+/* The six Hessian planes at radius R (components xx yy zz xy xz yz, each N^3
+ * values in C order, plane c at planes + c * plane_stride elements) in FP64
+ * (dtype CC_F64) or FP32 (CC_F32: FP32 inverse transforms of the FP64 k-space
+ * products). plane_stride >= N^3, planes 16-byte aligned. Asynchronous on
+ * `stream`; the first call for a (dtype, plane_stride) pair builds a cuFFT plan. */
+CC_API int cc_field_hessian(cc_field *f, double R, void *planes, int32_t dtype, int64_t plane_stride, void *stream);
+
+CC_API void cc_field_destroy(cc_field *f);
 
 /* Counters since the last reset (synchronises `stream`). */
 CC_API int cc_get_stats(cc_ctx *ctx, cc_stats *out, void *stream);

@@ -60,6 +60,11 @@ class _Tab(ctypes.Structure):
                 ("M", ctypes.POINTER(ctypes.c_double))]
 
 
+class _RatioTables(ctypes.Structure):
+    _fields_ = [("base", _Tables), ("r", ctypes.POINTER(ctypes.c_double) * 3),
+                ("Mr", ctypes.POINTER(ctypes.c_double) * 3)]
+
+
 def lib():
     global _lib
     with _lock:
@@ -106,6 +111,15 @@ def lib():
             L.or_mlp_loss_grad.argtypes = [vp, vp, vp, i, vp]
             L.or_mlp_loss_grad.restype = d
             L.or_F_tab_points.argtypes = [ctypes.POINTER(_Tables), ctypes.POINTER(_Tab), vp, i64, i64, vp, vp, i]
+            L.or_growth_ratios.argtypes = [d, d, i, d, d, vp, vp, vp, vp, vp]
+            L.or_ratio_tables_init.argtypes = [ctypes.POINTER(_RatioTables), d, d, i, d, d]
+            L.or_ratio_tables_free.argtypes = [ctypes.POINTER(_RatioTables)]
+            L.or_ratios_at.argtypes = [ctypes.POINTER(_RatioTables), d, vp]
+            L.or_axis_stretch_exact.argtypes = [ctypes.POINTER(_RatioTables), vp, i, d]
+            L.or_axis_stretch_exact.restype = d
+            L.or_collapse_D_exact.argtypes = [ctypes.POINTER(_RatioTables), vp, ctypes.POINTER(ctypes.c_int)]
+            L.or_collapse_D_exact.restype = d
+            L.or_F_points_exact.argtypes = [ctypes.POINTER(_RatioTables), vp, i64, i64, vp, vp, i]
             _lib = L
     return _lib
 
@@ -331,3 +345,146 @@ def mlp_loss_grad(params, z, t):
     grad = np.empty(MLP_NPARAM)
     loss = lib().or_mlp_loss_grad(_p(params), _p(z), _p(t), len(t), _p(grad))
     return loss, grad
+
+
+def histogram(F, edges) -> np.ndarray:
+    """Counts of F per bin (Sec. 5.5: collapsed points per redshift bin, F = 1 + z_c).
+
+    counts[0] = #{F < e_0} (every non-collapsed point, F = 0, among them),
+    counts[1 + k] = #{e_k <= F < e_(k+1)}, counts[nb + 1] = #{F >= e_nb}:
+    the slot of a value is the number of edges at or below it."""
+    F = np.asarray(F, dtype=np.float64)
+    edges = np.asarray(edges, dtype=np.float64)
+    slot = np.searchsorted(edges, F, side="right")
+    return np.bincount(slot, minlength=len(edges) + 1).astype(np.int64)
+
+
+# ---------------------------------------------------------------------------
+# Field -> smoothed Hessian (the FFT stage ahead of the collapse computation,
+# Sec. 3: the second derivatives of the potential that PINOCCHIO's FFTs
+# produce). Plain numpy FFTs in FP64.
+#
+# Conventions (one reading, the paper prints none): an N^3 periodic grid of
+# side `box`, cells in C order (x slowest, z fastest), wavenumbers
+# k = 2 pi m / box with m the signed DFT frequency; a dimensionless power
+# spectrum P(k) = A k^n exp(-(k / k_cut)^2) applied to unit white noise,
+# delta_k = DFT(w) sqrt(P(k)), so that var(delta) = mean over the k grid of P;
+# Nyquist modes (any |m| = N/2) and k = 0 set to zero; Gaussian smoothing
+# G(kR) = exp(-k^2 R^2 / 2); the Hessian of the potential phi with
+# laplacian(phi) = delta: H_ij(k) = (k_i k_j / k^2) delta_k G(kR), whose trace
+# is the smoothed density.
+HESSIAN_COMPONENTS = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))
+
+
+def _kgrid(N: int, box: float):
+    m = np.fft.fftfreq(N, 1.0 / N)
+    mz = np.arange(N // 2 + 1, dtype=np.float64)
+    two_pi = 2.0 * np.pi / box
+    kx = (two_pi * m)[:, None, None]
+    ky = (two_pi * m)[None, :, None]
+    kz = (two_pi * mz)[None, None, :]
+    nyq = (np.abs(m)[:, None, None] == N // 2) | (np.abs(m)[None, :, None] == N // 2) | (mz[None, None, :] == N // 2)
+    return kx, ky, kz, nyq
+
+
+def spectrum(k, amplitude: float, index: float, k_cut: float):
+    """P(k) = A k^n exp(-(k/k_cut)^2), P(0) = 0."""
+    k = np.asarray(k, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        p = amplitude * np.power(k, index) * np.exp(-(k / k_cut) ** 2)
+    return np.where(k > 0, p, 0.0)
+
+
+def field_delta_k(white, box: float, amplitude: float, index: float, k_cut: float):
+    """delta_k = DFT(w) sqrt(P(k)) on the half-complex grid, Nyquist and k = 0 zeroed."""
+    white = np.asarray(white, dtype=np.float64)
+    N = white.shape[0]
+    kx, ky, kz, nyq = _kgrid(N, box)
+    k = np.sqrt(kx * kx + ky * ky + kz * kz)
+    dk = np.fft.rfftn(white) * np.sqrt(spectrum(k, amplitude, index, k_cut))
+    dk[np.broadcast_to(nyq, dk.shape)] = 0.0
+    return dk
+
+
+def hessian_from_delta_k(dk, N: int, box: float, R: float):
+    """(6, N^3) planes H_ij(x) = IDFT[(k_i k_j / k^2) G(kR) delta_k] in component order xx yy zz xy xz yz."""
+    kx, ky, kz, _ = _kgrid(N, box)
+    kv = (kx, ky, kz)
+    k2 = kx * kx + ky * ky + kz * kz
+    g = np.exp(-0.5 * k2 * R * R)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = np.where(k2 > 0, 1.0 / k2, 0.0)
+    out = np.empty((6, N ** 3))
+    for c, (i, j) in enumerate(HESSIAN_COMPONENTS):
+        out[c] = np.fft.irfftn(dk * (kv[i] * kv[j] * inv * g), s=(N, N, N), axes=(0, 1, 2)).reshape(-1)
+    return out
+
+
+def field_sigma(N: int, box: float, amplitude: float, index: float, k_cut: float, R: float) -> float:
+    """rms of the smoothed density: sqrt(mean over the full k grid of P G^2), Nyquist and k = 0 excluded."""
+    m = np.fft.fftfreq(N, 1.0 / N)
+    two_pi = 2.0 * np.pi / box
+    kx, ky, kz = np.meshgrid(two_pi * m, two_pi * m, two_pi * m, indexing="ij")
+    k = np.sqrt(kx * kx + ky * ky + kz * kz)
+    keep = np.all(np.abs(np.stack(np.meshgrid(m, m, m, indexing="ij"))) != N // 2, axis=0)
+    p = spectrum(k, amplitude, index, k_cut) * np.exp(-(k * R) ** 2)
+    return float(np.sqrt(np.sum(np.where(keep, p, 0.0)) / N ** 3))
+
+
+# ---------------------------------------------------------------- exact-background growth ratios
+EDS_RATIOS = (-3.0 / 7.0, -1.0 / 3.0, 10.0 / 21.0)
+
+
+def growth_ratios(omega_m=0.3, omega_l=0.7, n_knots=512, a_min=1e-3, a_max=1.0):
+    """(a_k, D_k, r2_k, r3a_k, r3b_k): second- and third-order growth ratios at the knots."""
+    out = [np.empty(n_knots) for _ in range(5)]
+    rc = lib().or_growth_ratios(omega_m, omega_l, n_knots, a_min, a_max, *[_p(x) for x in out])
+    if rc:
+        raise ValueError(f"or_growth_ratios failed: {rc}")
+    return tuple(out)
+
+
+class RatioTables:
+    """Tables of the classic path plus natural splines of r2, r3a, r3b in D."""
+
+    def __init__(self, omega_m=0.3, omega_l=0.7, n_knots=512, a_min=1e-3, a_max=1.0):
+        self._t = _RatioTables()
+        rc = lib().or_ratio_tables_init(ctypes.byref(self._t), omega_m, omega_l, n_knots, a_min, a_max)
+        if rc:
+            raise ValueError(f"or_ratio_tables_init failed: {rc}")
+        self.n = n_knots
+
+    def __del__(self):
+        try:
+            lib().or_ratio_tables_free(ctypes.byref(self._t))
+        except Exception:
+            pass
+
+    @property
+    def D_top(self) -> float:
+        return self._t.base.D[self.n - 1]
+
+    def ratios_at(self, D) -> np.ndarray:
+        r = np.empty(3)
+        lib().or_ratios_at(ctypes.byref(self._t), float(D), _p(r))
+        return r
+
+    def axis_stretch(self, lam, axis: int, D: float) -> float:
+        lam = _f64(lam)
+        return lib().or_axis_stretch_exact(ctypes.byref(self._t), _p(lam), axis, float(D))
+
+    def collapse_D(self, lam):
+        lam = _f64(lam)
+        f = ctypes.c_int(0)
+        Dc = lib().or_collapse_D_exact(ctypes.byref(self._t), _p(lam), ctypes.byref(f))
+        return Dc, f.value
+
+    def F_points(self, hess: np.ndarray, nthreads: int = 0):
+        """hess: (6, n) planes (FP64 or FP32, widened exactly). Returns (F, flags)."""
+        hess = np.ascontiguousarray(hess, dtype=np.float64)
+        n = hess.shape[1]
+        F = np.empty(n)
+        fl = np.zeros(n, dtype=np.int32)
+        lib().or_F_points_exact(ctypes.byref(self._t), _p(hess), n, n, _p(F), _p(fl), nthreads)
+        return F, fl
+

@@ -449,6 +449,161 @@ void or_F_points(const or_tables *t, const double *hess, int64_t n, int64_t plan
 }
 
 /* ------------------------------------------------------------------------- */
+/* Exact-background growth ratios (see oracle.h). State y = (D1, D1', D2, D2',
+ * D3a, D3a', D3b, D3b') in the variable a, classical RK4 on the same
+ * geometric steps as the linear growth factor.                              */
+
+static void or_ratio_rhs(const or_cosmo *c, double a, const double y[8], double dy[8]) {
+  double damp = 3.0 / a + or_dlnE_da(c, a);
+  double w = 1.5 * c->om / (a * a * a * a * a * or_E2(c, a));
+  double D1 = y[0], D2 = y[2];
+  double s[4] = {0.0, -w * D1 * D1, -2.0 * w * D1 * D1 * D1, -2.0 * w * (D1 * D2 - D1 * D1 * D1)};
+  for (int o = 0; o < 4; ++o) {
+    dy[2 * o] = y[2 * o + 1];
+    dy[2 * o + 1] = -damp * y[2 * o + 1] + w * y[2 * o] + s[o];
+  }
+}
+
+static void or_ratio_rk4_step(const or_cosmo *c, double a, double h, double y[8]) {
+  double k1[8], k2[8], k3[8], k4[8], t[8];
+  or_ratio_rhs(c, a, y, k1);
+  for (int i = 0; i < 8; ++i) t[i] = y[i] + 0.5 * h * k1[i];
+  or_ratio_rhs(c, a + 0.5 * h, t, k2);
+  for (int i = 0; i < 8; ++i) t[i] = y[i] + 0.5 * h * k2[i];
+  or_ratio_rhs(c, a + 0.5 * h, t, k3);
+  for (int i = 0; i < 8; ++i) t[i] = y[i] + h * k3[i];
+  or_ratio_rhs(c, a + h, t, k4);
+  for (int i = 0; i < 8; ++i) y[i] += h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
+static void or_ratio_integrate(const or_cosmo *c, double a0, double a1, double y[8]) {
+  if (!(a1 > a0)) return;
+  int nsub = (int)ceil(log(a1 / a0) / OR_DLOG_MAX);
+  if (nsub < 1) nsub = 1;
+  double ratio = log(a1 / a0) / nsub;
+  double a = a0;
+  for (int j = 1; j <= nsub; ++j) {
+    double an = (j == nsub) ? a1 : a0 * exp(ratio * j);
+    or_ratio_rk4_step(c, a, an - a, y);
+    a = an;
+  }
+}
+
+int or_growth_ratios(double omega_m, double omega_l, int n_knots, double a_min, double a_max, double *a_k,
+                     double *D_k, double *r2_k, double *r3a_k, double *r3b_k) {
+  int rc = or_growth_table(omega_m, omega_l, n_knots, a_min, a_max, a_k, D_k);
+  if (rc) return rc;
+  or_cosmo c = {omega_m, 1.0 - omega_m - omega_l, omega_l};
+  double a = OR_A_START;
+  double y[8] = {a, 1.0, -3.0 / 7.0 * a * a, -6.0 / 7.0 * a, -1.0 / 3.0 * a * a * a, -a * a,
+                 10.0 / 21.0 * a * a * a, 10.0 / 7.0 * a * a};
+  for (int k = 0; k < n_knots; ++k) {
+    or_ratio_integrate(&c, a, a_k[k], y);
+    a = a_k[k];
+    double D1 = y[0];
+    r2_k[k] = y[2] / (D1 * D1);
+    r3a_k[k] = y[4] / (D1 * D1 * D1);
+    r3b_k[k] = y[6] / (D1 * D1 * D1);
+  }
+  return 0;
+}
+
+int or_ratio_tables_init(or_ratio_tables *t, double omega_m, double omega_l, int n_knots, double a_min,
+                         double a_max) {
+  memset(t, 0, sizeof(*t));
+  int rc = or_tables_init(&t->base, omega_m, omega_l, n_knots, a_min, a_max);
+  if (rc) return rc;
+  for (int o = 0; o < 3; ++o) {
+    t->r[o] = malloc(sizeof(double) * n_knots);
+    t->Mr[o] = malloc(sizeof(double) * n_knots);
+    if (!t->r[o] || !t->Mr[o]) { or_ratio_tables_free(t); return -3; }
+  }
+  double *a_k = malloc(sizeof(double) * n_knots), *D_k = malloc(sizeof(double) * n_knots);
+  if (!a_k || !D_k) { free(a_k); free(D_k); or_ratio_tables_free(t); return -3; }
+  rc = or_growth_ratios(omega_m, omega_l, n_knots, a_min, a_max, a_k, D_k, t->r[0], t->r[1], t->r[2]);
+  free(a_k);
+  free(D_k);
+  for (int o = 0; o < 3 && !rc; ++o) rc = or_spline_build(n_knots, t->base.D, t->r[o], 0.0, 0.0, t->Mr[o]);
+  if (rc) { or_ratio_tables_free(t); return rc; }
+  return 0;
+}
+
+void or_ratio_tables_free(or_ratio_tables *t) {
+  or_tables_free(&t->base);
+  for (int o = 0; o < 3; ++o) {
+    free(t->r[o]);
+    free(t->Mr[o]);
+    t->r[o] = t->Mr[o] = NULL;
+  }
+}
+
+void or_ratios_at(const or_ratio_tables *t, double D, double r[3]) {
+  static const double eds[3] = {-3.0 / 7.0, -1.0 / 3.0, 10.0 / 21.0};
+  for (int o = 0; o < 3; ++o)
+    r[o] = (D < t->base.D[0]) ? eds[o] : or_spline_eval(t->base.n, t->base.D, t->r[o], t->Mr[o], D);
+}
+
+double or_axis_stretch_exact(const or_ratio_tables *t, const double l[3], int axis, double D) {
+  int i = axis, j = (axis + 1) % 3, k = (axis + 2) % 3;
+  double r[3];
+  or_ratios_at(t, D, r);
+  double c3 = -r[1] / 3.0 * l[0] * l[1] * l[2] - r[2] / 2.0 * l[i] * (l[j] * l[j] + l[k] * l[k]);
+  return 1.0 - l[i] * D + r[0] * l[j] * l[k] * D * D + c3 * D * D * D;
+}
+
+/* smallest D in (0, D_top] with A_1(D) <= 0: a grid scan, then bisection */
+double or_collapse_D_exact(const or_ratio_tables *t, const double l[3], int *flags) {
+  int f = 0;
+  double D_top = t->base.D[t->base.n - 1];
+  double lmax = fmax(fabs(l[0]), fmax(fabs(l[1]), fabs(l[2])));
+  if (fabs(l[0]) <= 1e-9 * lmax) f |= OR_FLAG_SIGN0;
+  double Dc = 0.0;
+  if (l[0] > 0.0) {
+    if (fabs(or_axis_stretch_exact(t, l, 0, D_top)) <= OR_EDGE_TOL) f |= OR_FLAG_EDGE;
+    double prev = 0.0;
+    for (int m = 1; m <= 4 * OR_GRID; ++m) {
+      double D = D_top * m / (4 * OR_GRID);
+      if (or_axis_stretch_exact(t, l, 0, D) <= 0.0) {
+        double lo = prev, hi = D;
+        for (int it = 0; it < 400; ++it) {
+          double mid = lo + 0.5 * (hi - lo);
+          if (mid <= lo || mid >= hi) break;
+          if (or_axis_stretch_exact(t, l, 0, mid) > 0.0) lo = mid; else hi = mid;
+        }
+        Dc = hi;
+        break;
+      }
+      prev = D;
+    }
+    if (Dc > 0.0) f |= OR_FLAG_COLLAPSED;
+  }
+  if (flags) *flags |= f;
+  return Dc;
+}
+
+double or_F_point_exact(const or_ratio_tables *t, const double h[6], int *flags) {
+  double l[3];
+  or_eigen_jacobi(h, l);
+  double Dc = or_collapse_D_exact(t, l, flags);
+  if (Dc <= 0.0) return 0.0;
+  return 1.0 / or_a_of_D(&t->base, Dc, flags);
+}
+
+void or_F_points_exact(const or_ratio_tables *t, const double *hess, int64_t n, int64_t plane_stride, double *F,
+                       int32_t *flags, int nthreads) {
+  int nt = or_threads(nthreads);
+  (void)nt;
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nt)
+  for (int64_t p = 0; p < n; ++p) {
+    double h[6];
+    for (int c = 0; c < 6; ++c) h[c] = hess[c * plane_stride + p];
+    int f = 0;
+    F[p] = or_F_point_exact(t, h, &f);
+    if (flags) flags[p] = f;
+  }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Tabulated collapse (Sec. 3: collapse times precomputed on a grid of
  * delta = sum l_i, x = l1 - l2, y = l2 - l3 with eigenvalues sorted
  * descending, a cubic spline along delta and bilinear interpolation in x and

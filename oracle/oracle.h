@@ -112,6 +112,38 @@ void or_collapse_scale_f32(const or_tables *t, const float *hess, int64_t n, int
 void or_F_points(const or_tables *t, const double *hess, int64_t n, int64_t plane_stride,
                  double *F, int32_t *flags, int nthreads);
 
+/* ---- exact-background growth ratios (a reading beyond the paper: the
+ * EdS ratios of the R-LPT condition replaced by the second- and third-order
+ * growth factors of the actual background) ----
+ * With D1 the linear growth factor and w(a) = 3/2 Omega_m a^-5 E^-2, every
+ * order solves f'' + (3/a + E'/E) f' - w f = s(a):
+ *   D2:  s = -w D1^2,  D3a: s = -2 w D1^3,  D3b: s = -2 w (D1 D2 - D1^3),
+ * from EdS initial conditions at a = 1e-5 (D1 = a, D2 = -3/7 a^2,
+ * D3a = -1/3 a^3, D3b = 10/21 a^3), which these sources keep exactly in EdS.
+ * The ratios r2 = D2/D1^2, r3a = D3a/D1^3, r3b = D3b/D1^3 (independent of the
+ * normalisation of D1) enter the stretch as
+ *   A_i = 1 - D l_i + r2 D^2 l_j l_k + D^3 [-r3a/3 l1 l2 l3 - r3b/2 l_i (l_j^2 + l_k^2)],
+ * which is the R-LPT A_i for the EdS values (-3/7, -1/3, 10/21). */
+int or_growth_ratios(double omega_m, double omega_l, int n_knots, double a_min, double a_max, double *a_k,
+                     double *D_k, double *r2_k, double *r3a_k, double *r3b_k);
+
+typedef struct {
+  or_tables base;        /* D(a) and a(D) as in the classic path */
+  double *r[3];          /* r2, r3a, r3b at the knots D_k */
+  double *Mr[3];         /* natural-spline second derivatives of r(D) */
+} or_ratio_tables;
+
+int  or_ratio_tables_init(or_ratio_tables *t, double omega_m, double omega_l, int n_knots, double a_min,
+                          double a_max);
+void or_ratio_tables_free(or_ratio_tables *t);
+/* r2, r3a, r3b at D (natural splines in D over the knots; EdS values below the first knot) */
+void or_ratios_at(const or_ratio_tables *t, double D, double r[3]);
+double or_axis_stretch_exact(const or_ratio_tables *t, const double l[3], int axis, double D);
+double or_collapse_D_exact(const or_ratio_tables *t, const double l[3], int *flags);
+double or_F_point_exact(const or_ratio_tables *t, const double h[6], int *flags);
+void or_F_points_exact(const or_ratio_tables *t, const double *hess, int64_t n, int64_t plane_stride, double *F,
+                       int32_t *flags, int nthreads);
+
 /* ---- tabulated collapse (Sec. 3 "Tabulated" option; Sec. 4.2 spline x bilinear) ----
  * Reading: the table holds u = 1/D_c, the largest real root of the monic
  * cubic u^3 - l1 u^2 + c2 u + c3 (finite everywhere, ~linear in (delta, x, y)),

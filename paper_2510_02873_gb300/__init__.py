@@ -292,6 +292,20 @@ class Context:
         _lib.check(_lib.load().cc_spline_eval(self._h, xk.ctypes.data, yk.ctypes.data, len(xk), q.data_ptr(),
                                               q.numel(), out.data_ptr(), _stream_ptr(stream)), "cc_spline_eval")
 
+    def histogram(self, F_max, edges, counts, stream=None):
+        """Counts of F_max per bin (cc_histogram). F_max: float64 CUDA tensor;
+        edges: host, nbins + 1 increasing positive values; counts: int64 CUDA
+        tensor of nbins + 2 (below, bins..., above), overwritten."""
+        import torch
+        edges = np.ascontiguousarray(edges, dtype=np.float64)
+        if F_max.dtype != torch.float64 or not F_max.is_cuda or not F_max.is_contiguous():
+            raise TypeError("F_max must be a contiguous float64 CUDA tensor")
+        if counts.dtype != torch.int64 or not counts.is_cuda or counts.numel() != len(edges) + 1:
+            raise TypeError("counts must be an int64 CUDA tensor of nbins + 2 entries")
+        _lib.check(_lib.load().cc_histogram(self._h, F_max.data_ptr(), F_max.numel(), edges.ctypes.data,
+                                            len(edges) - 1, counts.data_ptr(), _stream_ptr(stream)),
+                   "cc_histogram")
+
     # ---- learned surrogate
     MLP_NPARAM = 8641
 
@@ -340,3 +354,53 @@ class Context:
 
     def reset_stats(self, stream=None):
         cc_reset_stats(self._h, stream)
+
+
+class Field:
+    """A Gaussian field kept on the device, smoothed into Hessian planes by FFT
+    (cc_field_*). white: contiguous float64 CUDA tensor of N^3 unit white noise
+    (C order over x, y, z); P(k) = amplitude k^index exp(-(k/k_cut)^2) on a box of side `box`."""
+
+    def __init__(self, ctx: "Context", white, box: float, amplitude: float, index: float, k_cut: float, stream=None):
+        import torch
+        if white.dtype != torch.float64 or not white.is_cuda or not white.is_contiguous():
+            raise TypeError("white must be a contiguous float64 CUDA tensor")
+        N = round(white.numel() ** (1.0 / 3.0))
+        if N ** 3 != white.numel():
+            raise ValueError("white must hold N^3 values")
+        self.N = N
+        self._ctx = ctx  # keeps the context alive
+        spec = _lib.CcSpectrum(box, amplitude, index, k_cut)
+        h = ctypes.c_void_p()
+        _lib.check(_lib.load().cc_field_create(ctx._h, white.data_ptr(), N, ctypes.byref(spec), ctypes.byref(h),
+                                               _stream_ptr(stream)), "cc_field_create")
+        self._h = h.value
+
+    def sigma(self, R: float, stream=None) -> float:
+        out = ctypes.c_double()
+        _lib.check(_lib.load().cc_field_sigma(self._h, float(R), ctypes.byref(out), _stream_ptr(stream)),
+                   "cc_field_sigma")
+        return out.value
+
+    def hessian(self, R: float, planes, stream=None) -> None:
+        """planes: CUDA tensor (6, m >= N^3), float64 or float32, unit inner stride."""
+        import torch
+        if planes.dim() != 2 or planes.shape[0] != 6 or planes.stride(1) != 1 or not planes.is_cuda:
+            raise TypeError("planes must be a (6, m) CUDA tensor with unit inner stride")
+        dt = CC_F64 if planes.dtype == torch.float64 else CC_F32 if planes.dtype == torch.float32 else None
+        if dt is None:
+            raise TypeError("planes must be float64 or float32")
+        _lib.check(_lib.load().cc_field_hessian(self._h, float(R), planes.data_ptr(), dt, planes.stride(0),
+                                                _stream_ptr(stream)), "cc_field_hessian")
+
+    def close(self) -> None:
+        if self._h:
+            _lib.load().cc_field_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -9,7 +9,7 @@ from . import buildlib as _build
 
 CC_OK, CC_EINVAL, CC_ECUDA, CC_ENOMEM, CC_ETIMEOUT, CC_ERANGE, CC_ENOTSUP = range(7)
 CC_F64, CC_F32 = 8, 4
-MODES = {"fp64": 0, "mixed": 1, "surrogate": 2, "tabulated": 3, "f32x2": 4}
+MODES = {"fp64": 0, "mixed": 1, "surrogate": 2, "tabulated": 3, "f32x2": 4, "exact_growth": 5}
 
 # every symbol the public header declares
 EXPORTS = (
@@ -18,7 +18,8 @@ EXPORTS = (
     "cc_last_error_message", "cc_version", "cc_batch_create", "cc_batch_autotune", "cc_batch_run",
     "cc_batch_run_graph", "cc_batch_get_config", "cc_batch_destroy", "cc_set_table", "cc_table_nodes_rlpt",
     "cc_table_query", "cc_spline_eval", "cc_surrogate_train", "cc_surrogate_params", "cc_load_surrogate",
-    "cc_surrogate_eval", "cc_surrogate_grad",
+    "cc_surrogate_eval", "cc_surrogate_grad", "cc_histogram", "cc_field_create", "cc_field_sigma",
+    "cc_field_hessian", "cc_field_destroy",
 )
 
 
@@ -35,6 +36,11 @@ class CcStats(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "reserved"}
+
+
+class CcSpectrum(ctypes.Structure):
+    _fields_ = [("box", ctypes.c_double), ("amplitude", ctypes.c_double), ("index", ctypes.c_double),
+                ("k_cut", ctypes.c_double)]
 
 
 class CcBatchItem(ctypes.Structure):
@@ -113,6 +119,12 @@ def load() -> ctypes.CDLL:
         L.cc_table_nodes_rlpt.argtypes = [vp, vp, i32, vp, i32, vp, i32, vp, vp]
         L.cc_table_query.argtypes = [vp, vp, vp, vp, i64, vp, vp]
         L.cc_spline_eval.argtypes = [vp, vp, vp, i32, vp, i64, vp, vp]
+        L.cc_histogram.argtypes = [vp, vp, i64, vp, i32, vp, vp]
+        L.cc_field_create.argtypes = [vp, vp, i32, ctypes.POINTER(CcSpectrum), ctypes.POINTER(vp), vp]
+        L.cc_field_sigma.argtypes = [vp, d, ctypes.POINTER(d), vp]
+        L.cc_field_hessian.argtypes = [vp, d, vp, i32, i64, vp]
+        L.cc_field_destroy.argtypes = [vp]
+        L.cc_field_destroy.restype = None
         L.cc_surrogate_train.argtypes = [vp, vp, i32, i64, i64, d, ctypes.POINTER(CcTrainConfig),
                                          ctypes.POINTER(CcTrainReport), vp]
         L.cc_surrogate_params.argtypes = [vp, vp, vp]
@@ -130,7 +142,8 @@ def load() -> ctypes.CDLL:
                      "cc_get_stats", "cc_reset_stats", "cc_version", "cc_batch_create", "cc_batch_autotune",
                      "cc_batch_run", "cc_batch_run_graph", "cc_batch_get_config", "cc_set_table",
                      "cc_table_nodes_rlpt", "cc_table_query", "cc_spline_eval", "cc_surrogate_train",
-                     "cc_surrogate_params", "cc_load_surrogate", "cc_surrogate_eval", "cc_surrogate_grad"):
+                     "cc_surrogate_params", "cc_load_surrogate", "cc_surrogate_eval", "cc_surrogate_grad",
+                     "cc_histogram", "cc_field_create", "cc_field_sigma", "cc_field_hessian"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L

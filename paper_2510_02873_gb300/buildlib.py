@@ -34,6 +34,14 @@ def nvcc() -> str:
     return path
 
 
+def _rpath() -> list[str]:
+    """Run-time search path for the toolkit's libraries (cuFFT) next to the nvcc used to build."""
+    root = os.path.dirname(os.path.dirname(os.path.realpath(nvcc())))
+    dirs = [d for d in (os.path.join(root, "lib64"), os.path.join(root, "targets", "sbsa-linux", "lib"),
+                        os.path.join(root, "targets", "x86_64-linux", "lib")) if os.path.isdir(d)]
+    return [f"-Xlinker=-rpath,{d}" for d in dirs]
+
+
 def sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
@@ -71,7 +79,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))
     tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", *objs, "-o", tmp]
+    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", *objs, "-lcufft", *_rpath(), "-o", tmp]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")

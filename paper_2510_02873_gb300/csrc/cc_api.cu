@@ -57,13 +57,6 @@ int check_outputs(const double* F_max, const int32_t* idx, int64_t n) {
   return CC_OK;
 }
 
-int select_device(const cc_ctx* ctx) {
-  int cur = -1;
-  if (int rc = check_cuda(cudaGetDevice(&cur), "cudaGetDevice")) return rc;
-  if (cur != ctx->device) return check_cuda(cudaSetDevice(ctx->device), "cudaSetDevice");
-  return CC_OK;
-}
-
 int run_collapse(cc_ctx* ctx, cc_mode mode, const void* hess, int32_t dtype, int64_t n,
                  int64_t plane_stride, int64_t radius_stride, const double* sigma, int32_t R,
                  double* F_max, int32_t* idx, int32_t scale_idx0, void* stream) {
@@ -91,6 +84,8 @@ int run_collapse(cc_ctx* ctx, cc_mode mode, const void* hess, int32_t dtype, int
       return launch_surrogate_checked(ctx, a, sigma);
     case CC_MODE_F32X2:
       return launch_f32x2(a, ctx->tab);
+    case CC_MODE_EXACT_GROWTH:
+      return launch_exact(a, ctx->tab);
   }
   return set_error(CC_EINVAL, "unknown mode");
 }
@@ -128,6 +123,14 @@ int ensure_staging(cc_ctx* ctx, size_t stage_bytes, int64_t n) {
 }
 
 }  // namespace
+
+int select_device(const cc_ctx* ctx) {
+  int cur = -1;
+  if (int rc = check_cuda(cudaGetDevice(&cur), "cudaGetDevice")) return rc;
+  if (cur != ctx->device) return check_cuda(cudaSetDevice(ctx->device), "cudaSetDevice");
+  return CC_OK;
+}
+
 }  // namespace cc
 
 using namespace cc;
@@ -248,6 +251,24 @@ int cc_create(cc_ctx** out, const cc_cosmology* cosmo, int device) {
   split2(t.Dtop, t.Dtop_hi, t.Dtop_lo);
   split2(t.D0, t.D0_hi, t.D0_lo);
   split2(t.eds_slope, t.eds_hi, t.eds_lo);
+  {  // growth-ratio splines (CC_MODE_EXACT_GROWTH)
+    std::vector<double> r(3 * n), work(6 * n), c64(3 * 4 * (n - 1));
+    rc = growth_ratios_into(*cosmo, r.data(), r.data() + n, r.data() + 2 * n);
+    for (int o = 0; o < 3 && !rc; ++o)
+      rc = natural_spline_into(n, ctx->D_k.data(), r.data() + o * n, c64.data() + o * 4 * (n - 1), work.data());
+    if (rc) { cc_destroy(ctx); return set_error(rc, "growth ratio tables failed"); }
+    std::vector<float> c32(c64.size());
+    for (size_t i = 0; i < c64.size(); ++i) c32[i] = static_cast<float>(c64[i]);
+    const size_t b64 = sizeof(double) * c64.size(), b32 = sizeof(float) * c32.size();
+    if ((rc = check_cuda(cudaMalloc(&ctx->d_ratio, b64 + b32), "cudaMalloc(ratio tables)"))) { cc_destroy(ctx); return rc; }
+    rc = check_cuda(cudaMemcpy(ctx->d_ratio, c64.data(), b64, cudaMemcpyHostToDevice), "cudaMemcpy(ratio tables)");
+    if (!rc)
+      rc = check_cuda(cudaMemcpy(static_cast<unsigned char*>(ctx->d_ratio) + b64, c32.data(), b32, cudaMemcpyHostToDevice),
+                      "cudaMemcpy(ratio tables)");
+    if (rc) { cc_destroy(ctx); return rc; }
+    t.rc64 = static_cast<const Coef4*>(ctx->d_ratio);
+    t.rc32 = reinterpret_cast<const float4*>(static_cast<unsigned char*>(ctx->d_ratio) + b64);
+  }
   *out = ctx;
   return CC_OK;
 }
@@ -259,6 +280,7 @@ void cc_destroy(cc_ctx* ctx) {
   if (cur != ctx->device) cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   if (ctx->d_table) cudaFree(ctx->d_table);
+  if (ctx->d_ratio) cudaFree(ctx->d_ratio);
   if (ctx->d_counters) cudaFree(ctx->d_counters);
   for (int b = 0; b < 2; ++b) {
     if (ctx->d_stage[b]) cudaFree(ctx->d_stage[b]);

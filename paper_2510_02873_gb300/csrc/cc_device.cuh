@@ -101,24 +101,34 @@ static __device__ __noinline__ void refine_top_pair(double xx, double yy, double
   l2 = mean - rad;
 }
 
-// Largest real root of the monic cubic u^3 + b u^2 + c u + d (FP32 closed
-// form): Cardano's formula when one root is real, the trigonometric form when
-// three are.
-__device__ __forceinline__ float cubic_largest_root_f32(float b, float c, float d) {
+// ---- FP32 seeds. Newton corrections follow every seed (two on l1, two FP32
+// and one FP64 on D_c), so a relative accuracy of 1e-4 is enough and the
+// seeds use the special-function unit directly.
+// arccos by the Hastings approximation of Abramowitz & Stegun 4.4.45
+// (|error| <= 5e-5 rad on [0, 1]; acos(-x) = pi - acos(x)).
+__device__ __forceinline__ float acos_seed(float x) {
+  const float ax = fabsf(x);
+  const float p = fmaf(fmaf(fmaf(-0.0187293f, ax, 0.0742610f), ax, -0.2121144f), ax, 1.5707288f) * sqrtf(1.0f - ax);
+  return (x < 0.0f) ? 3.14159265f - p : p;
+}
+
+// Largest real root of the monic cubic u^3 + b u^2 + c u + d: Cardano's
+// formula when one root is real, the trigonometric form when three are.
+__device__ __forceinline__ float cubic_largest_root_seed(float b, float c, float d) {
   const float b3 = b * (1.0f / 3.0f);
   const float pp = fmaf(-b, b3, c);
   const float qq = fmaf(b3, fmaf(2.0f * b3, b3, -c), d);
   const float disc = fmaf(0.25f * qq, qq, pp * pp * pp * (1.0f / 27.0f));
   float t;
   if (disc > 0.0f) {
-    const float A = cbrtf(fmaf(0.5f, fabsf(qq), sqrtf(disc)));
+    const float A = __powf(fmaf(0.5f, fabsf(qq), sqrtf(disc)), 1.0f / 3.0f);  // cube root, A >= 0
     const float C = (qq > 0.0f) ? -A : A;
-    t = (C != 0.0f) ? C - pp / (3.0f * C) : 0.0f;
+    t = (C != 0.0f) ? C - __fdividef(pp, 3.0f * C) : 0.0f;
   } else {
     const float m = sqrtf(-pp * (1.0f / 3.0f));
-    float arg = (m > 0.0f) ? (-0.5f * qq) / (m * m * m) : 0.0f;
+    float arg = (m > 0.0f) ? __fdividef(-0.5f * qq, m * m * m) : 0.0f;
     arg = fminf(1.0f, fmaxf(-1.0f, arg));
-    t = 2.0f * m * cosf(acosf(arg) * (1.0f / 3.0f));
+    t = 2.0f * m * __cosf(acos_seed(arg) * (1.0f / 3.0f));
   }
   return t - b3;
 }
@@ -169,10 +179,10 @@ __device__ __forceinline__ EigenTop eigen_top_fp64(double xx, double yy, double 
   const float p2f = to_f32_trunc(s6) * (1.0f / 6.0f);
   const float detf = to_f32_trunc(det);
   const float pf = sqrtf(p2f);
-  float rf = (p2f > 0.0f) ? detf / (2.0f * p2f * pf) : 0.0f;
+  float rf = (p2f > 0.0f) ? __fdividef(detf, 2.0f * p2f * pf) : 0.0f;
   rf = fminf(1.0f, fmaxf(-1.0f, rf));
   float sn, cs;
-  sincosf(acosf(rf) * (1.0f / 3.0f), &sn, &cs);
+  __sincosf(acos_seed(rf) * (1.0f / 3.0f), &sn, &cs);
   const float x1f = 2.0f * pf * cs;                   // l1 - q
   const float x3f = -pf * fmaf(kSqrt3f, sn, cs);      // l3 - q
   // ---- FP64 Newton on g(x) = x (x^2 - 3p^2) - det; each step takes its
@@ -182,7 +192,7 @@ __device__ __forceinline__ EigenTop eigen_top_fp64(double xx, double yy, double 
   for (int it = 0; it < 2; ++it) {
     const float xf = (it == 0) ? x1f : to_f32_trunc(x);
     const float gpf = 3.0f * fmaf(xf, xf, -p2f);
-    const double yg = to_f64((gpf != 0.0f) ? 1.0f / gpf : 0.0f);
+    const double yg = to_f64((gpf != 0.0f) ? __fdividef(1.0f, gpf) : 0.0f);
     const double g = fma(x, fma(x, x, -p2x3), -det);
     x = fma(-g, yg, x);
   }
@@ -224,8 +234,8 @@ __device__ __forceinline__ Root rlpt_root_fp64(double lam1, double Pp, double S)
   const float l1f = to_f32_trunc(lam1);
   const float c2f = to_f32_trunc(c2);
   const float c3f = to_f32_trunc(c3);
-  const float uf = cubic_largest_root_f32(-l1f, c2f, c3f);
-  float Df = 1.0f / uf;
+  const float uf = cubic_largest_root_seed(-l1f, c2f, c3f);
+  float Df = __fdividef(1.0f, uf);
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
     const float Af = fmaf(fmaf(fmaf(c3f, Df, c2f), Df, -l1f), Df, 1.0f);
@@ -362,17 +372,17 @@ __device__ __forceinline__ MixedEigen mixed_eigen(float xx, float yy, float zz, 
   const float p2 = s6 * (1.0f / 6.0f), p2x3 = 0.5f * s6;
   const float det = fmaf(xz, fmaf(xy, yz, -b * xz), fmaf(a, fmaf(b, c, -yz * yz), -xy * fmaf(xy, c, -yz * xz)));
   const float pf = sqrtf(p2);
-  float rf = (p2 > 0.0f) ? det / (2.0f * p2 * pf) : 0.0f;
+  float rf = (p2 > 0.0f) ? __fdividef(det, 2.0f * p2 * pf) : 0.0f;
   rf = fminf(1.0f, fmaxf(-1.0f, rf));
   float sn, cs;
-  sincosf(acosf(rf) * (1.0f / 3.0f), &sn, &cs);
+  __sincosf(acos_seed(rf) * (1.0f / 3.0f), &sn, &cs);
   float x = 2.0f * pf * cs;
   const float x2 = pf * fmaf(kSqrt3f, sn, -cs);
   const float x3 = -pf * fmaf(kSqrt3f, sn, cs);
 #pragma unroll
   for (int it = 0; it < 2; ++it) {  // FP32 Newton on x (x^2 - 3p^2) - det
     const float gp = 3.0f * fmaf(x, x, -p2);
-    x = (gp != 0.0f) ? x - fmaf(x, fmaf(x, x, -p2x3), -det) / gp : x;
+    x = (gp != 0.0f) ? x - __fdividef(fmaf(x, fmaf(x, x, -p2x3), -det), gp) : x;
   }
   m.full = ((1.0f + rf) < kPairTauF && p2 > 0.0f) || (x - x3) < tri_thr;
   const float lam1f = q + x;
@@ -386,7 +396,7 @@ __device__ __forceinline__ MixedEigen mixed_eigen(float xx, float yy, float zz, 
     const double g = fma(dxx, fma(dyy, dzz, -dyz * dyz),
                          fma(-dxy, fma(dxy, dzz, -dyz * dxz), dxz * fma(dxy, dyz, -dyy * dxz)));
     const float gpf = 3.0f * fmaf(x, x, -p2);
-    lam1 = fma(g, to_f64(1.0f / gpf), lam1);
+    lam1 = fma(g, to_f64(__fdividef(1.0f, gpf)), lam1);
     x = to_f32_trunc(lam1 - to_f64(q));
     m.fp64 = true;
   }
@@ -480,8 +490,8 @@ __device__ __forceinline__ MixedResult collapse_point_mixed(
   if (m.full) return full_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
   const MixedCoef k = mixed_coef(m);
   // FP32 closed-form root of u^3 - l1 u^2 + c2 u + c3 (u = 1/D), two FP32 Newton steps on A_1
-  const float uf = cubic_largest_root_f32(-k.l1f, k.c2f, k.c3f);
-  const float Df = newton_f32<2>(k, 1.0f / uf);
+  const float uf = cubic_largest_root_seed(-k.l1f, k.c2f, k.c3f);
+  const float Df = newton_f32<2>(k, __fdividef(1.0f, uf));
   return mixed_finish(m, k, Df, Dk, coef, Dkf, bucket, tab);
 }
 

@@ -102,36 +102,6 @@ constexpr cf2 kM3_7 = make_const(-3.0 / 7.0);
 constexpr cf2 kM5_21 = make_const(-5.0 / 21.0);
 constexpr cf2 k37_63 = make_const(37.0 / 63.0);
 
-// ---- FP32 seeds. Two Newton corrections follow every seed, so 1e-4 relative
-// is enough: the seeds use the special-function unit directly.
-// arccos by the Hastings approximation of Abramowitz & Stegun 4.4.45
-// (|error| <= 5e-5 rad on [0, 1]; acos(-x) = pi - acos(x)).
-__device__ __forceinline__ float acos_seed(float x) {
-  const float ax = fabsf(x);
-  const float p = fmaf(fmaf(fmaf(-0.0187293f, ax, 0.0742610f), ax, -0.2121144f), ax, 1.5707288f) * sqrtf(1.0f - ax);
-  return (x < 0.0f) ? 3.14159265f - p : p;
-}
-// largest real root of u^3 + b u^2 + c u + d (Cardano / trigonometric form, as
-// cubic_largest_root_f32, with the fast seeds)
-__device__ __forceinline__ float cubic_largest_root_seed(float b, float c, float d) {
-  const float b3 = b * (1.0f / 3.0f);
-  const float pp = fmaf(-b, b3, c);
-  const float qq = fmaf(b3, fmaf(2.0f * b3, b3, -c), d);
-  const float disc = fmaf(0.25f * qq, qq, pp * pp * pp * (1.0f / 27.0f));
-  float t;
-  if (disc > 0.0f) {
-    const float A = __powf(fmaf(0.5f, fabsf(qq), sqrtf(disc)), 1.0f / 3.0f);  // cube root, A >= 0
-    const float C = (qq > 0.0f) ? -A : A;
-    t = (C != 0.0f) ? C - __fdividef(pp, 3.0f * C) : 0.0f;
-  } else {
-    const float m = sqrtf(-pp * (1.0f / 3.0f));
-    float arg = (m > 0.0f) ? __fdividef(-0.5f * qq, m * m * m) : 0.0f;
-    arg = fminf(1.0f, fmaxf(-1.0f, arg));
-    t = 2.0f * m * __cosf(acos_seed(arg) * (1.0f / 3.0f));
-  }
-  return t - b3;
-}
-
 struct Result {
   f2 a;  // a_c (meaningful when collapsed)
   bool collapsed, eds, refined;

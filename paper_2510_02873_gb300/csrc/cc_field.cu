@@ -1,0 +1,290 @@
+// cc_field.cu -- device-resident field -> smoothed Hessian planes, the FFT
+// stage ahead of the collapse computation (arXiv:2510.02873, Sec. 3: the
+// second derivatives of the potential come from FFTs, and the planned step is
+// to keep them on the device between the FFTs and the collapse kernel).
+//
+// Field: unit white noise w on an N^3 periodic grid (side `box`, C order),
+// delta_k = DFT(w) sqrt(P(k)) with P(k) = A k^n exp(-(k/k_cut)^2), Nyquist
+// modes and k = 0 zeroed. Hessian at radius R: H_ij = IDFT[(k_i k_j / k^2)
+// G(kR) delta_k] with G(kR) = exp(-k^2 R^2 / 2) (trace = smoothed density).
+// The transforms are cuFFT (D2Z once per field; six Z2D, or C2R for FP32
+// planes, per radius as one batched plan writing straight into the caller's
+// planes); the k-space products are this file's kernels. The Gaussian factor is
+// separable, G = g(k_x) g(k_y) g(k_z), so the per-mode work is products of
+// three table entries (host FP64 exp per axis) instead of an exp per mode.
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+
+#include "cc_internal.h"
+
+namespace cc {
+namespace {
+
+constexpr int kFieldMaxN = 1024;
+
+int check_cufft(cufftResult r, const char* what) {
+  if (r == CUFFT_SUCCESS) return CC_OK;
+  return set_error(r == CUFFT_ALLOC_FAILED ? CC_ENOMEM : CC_ECUDA,
+                   std::string(what) + " failed (cuFFT status " + std::to_string(static_cast<int>(r)) + ")");
+}
+
+// per-axis tables: signed wavenumbers of the full axes and of the half axis,
+// and the per-axis Gaussian factors (1 when only the wavenumbers are needed)
+struct AxisTables {
+  double k[kFieldMaxN];        // k(m), m = 0..N-1 (signed frequency)
+  double g[kFieldMaxN];        // exp(-k(m)^2 R^2 / 2)
+  double gz[kFieldMaxN / 2 + 1];
+  int N, Nz;
+  double kz0;                  // 2 pi / box (k_z = kz0 * iz)
+};
+
+__device__ __forceinline__ void decompose(int64_t idx, int N, int Nz, int& ix, int& iy, int& iz) {
+  iz = static_cast<int>(idx % Nz);
+  const int64_t r = idx / Nz;
+  iy = static_cast<int>(r % N);
+  ix = static_cast<int>(r / N);
+}
+
+// delta_k = DFT(w) sqrt(P(k)); Nyquist modes and k = 0 zeroed
+__global__ void color_kernel(double2* __restrict__ dk, int64_t nc, const AxisTables t, double A, double n_idx,
+                             double k_cut) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nc; i += stride) {
+    int ix, iy, iz;
+    decompose(i, t.N, t.Nz, ix, iy, iz);
+    const int h = t.N / 2;
+    const bool nyq = ix == h || iy == h || iz == h;
+    const double kx = t.k[ix], ky = t.k[iy], kz = t.kz0 * iz;
+    const double k2 = fma(kx, kx, fma(ky, ky, kz * kz));
+    double amp = 0.0;
+    if (!nyq && k2 > 0.0) {
+      const double k = sqrt(k2);
+      amp = sqrt(A * pow(k, n_idx) * exp(-k2 / (k_cut * k_cut)));
+    }
+    double2 v = dk[i];
+    v.x *= amp;
+    v.y *= amp;
+    dk[i] = v;
+  }
+}
+
+// the six k-space products of one radius (component order xx yy zz xy xz yz),
+// scaled by 1/N^3 for the unnormalised inverse transform
+template <typename C, typename R>
+__global__ void hessian_k_kernel(const double2* __restrict__ dk, int64_t nc, const AxisTables t, double scale,
+                                 C* __restrict__ out) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nc; i += stride) {
+    int ix, iy, iz;
+    decompose(i, t.N, t.Nz, ix, iy, iz);
+    const double kx = t.k[ix], ky = t.k[iy], kz = t.kz0 * iz;
+    const double k2 = fma(kx, kx, fma(ky, ky, kz * kz));
+    const double w = (k2 > 0.0) ? (t.g[ix] * t.g[iy] * t.gz[iz]) * scale / k2 : 0.0;
+    const double2 d = dk[i];
+    const double re = d.x * w, im = d.y * w;
+    const double f[6] = {kx * kx, ky * ky, kz * kz, kx * ky, kx * kz, ky * kz};
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      C o;
+      o.x = static_cast<R>(re * f[c]);
+      o.y = static_cast<R>(im * f[c]);
+      out[c * nc + i] = o;
+    }
+  }
+}
+
+// sum over the full k grid of P(k) G(kR)^2 (half grid, modes 0 < iz < N/2 counted twice)
+__global__ void sigma_kernel(const AxisTables t, int64_t nc, double A, double n_idx, double k_cut, double R,
+                             double* __restrict__ acc) {
+  double s = 0.0;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nc; i += stride) {
+    int ix, iy, iz;
+    decompose(i, t.N, t.Nz, ix, iy, iz);
+    const int h = t.N / 2;
+    if (ix == h || iy == h || iz == h) continue;
+    const double kx = t.k[ix], ky = t.k[iy], kz = t.kz0 * iz;
+    const double k2 = fma(kx, kx, fma(ky, ky, kz * kz));
+    if (!(k2 > 0.0)) continue;
+    const double p = A * pow(sqrt(k2), n_idx) * exp(-k2 / (k_cut * k_cut)) * exp(-k2 * R * R);
+    s += (iz == 0) ? p : 2.0 * p;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(acc, s);
+}
+
+int grid_for(int64_t n, int num_sms) {
+  return static_cast<int>(std::min<int64_t>((n + 255) / 256, static_cast<int64_t>(num_sms) * 8));
+}
+
+}  // namespace
+}  // namespace cc
+
+using namespace cc;
+
+struct cc_field {
+  cc_ctx* ctx = nullptr;
+  int N = 0;
+  cc_spectrum spec{};
+  int64_t nc = 0;                 // N * N * (N / 2 + 1)
+  double2* dk = nullptr;          // delta_k (FP64; the FP32 products are rounded from it)
+  void* work = nullptr;           // six k-space products
+  size_t work_bytes = 0;
+  double* acc = nullptr;          // sigma accumulator
+  std::map<std::pair<int, int64_t>, cufftHandle> inv_plans;  // (dtype, plane_stride) -> batched inverse
+};
+
+namespace {
+
+AxisTables axis_tables(const cc_field* f, double R) {
+  AxisTables t;
+  const int N = f->N;
+  t.N = N;
+  t.Nz = N / 2 + 1;
+  t.kz0 = 2.0 * 3.14159265358979323846 / f->spec.box;
+  for (int m = 0; m < N; ++m) {
+    const int s = (m < (N + 1) / 2) ? m : m - N;  // signed frequency (numpy fftfreq order)
+    t.k[m] = t.kz0 * s;
+    t.g[m] = std::exp(-0.5 * t.k[m] * t.k[m] * R * R);
+  }
+  for (int m = 0; m < t.Nz; ++m) t.gz[m] = std::exp(-0.5 * (t.kz0 * m) * (t.kz0 * m) * R * R);
+  return t;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cc_field_create(cc_ctx* ctx, const double* white, int32_t N, const cc_spectrum* spec, cc_field** out,
+                    void* stream) {
+  if (!ctx || !white || !spec || !out) return set_error(CC_EINVAL, "ctx, white, spec and out must be non-NULL");
+  *out = nullptr;
+  if (N < 4 || N > kFieldMaxN || N % 2) return set_error(CC_EINVAL, "N must be even, 4 <= N <= 1024");
+  if (!(spec->box > 0.0) || !(spec->amplitude > 0.0) || !(spec->k_cut > 0.0) || !std::isfinite(spec->index) ||
+      !std::isfinite(spec->box) || !std::isfinite(spec->amplitude) || !std::isfinite(spec->k_cut))
+    return set_error(CC_EINVAL, "spectrum: box, amplitude, k_cut > 0 and finite index");
+  if (reinterpret_cast<uintptr_t>(white) % 16) return set_error(CC_EINVAL, "white must be 16-byte aligned");
+  if (int rc = select_device(ctx)) return rc;
+  cc_field* f = new (std::nothrow) cc_field();
+  if (!f) return set_error(CC_ENOMEM, "host allocation failed");
+  f->ctx = ctx;
+  f->N = N;
+  f->spec = *spec;
+  f->nc = static_cast<int64_t>(N) * N * (N / 2 + 1);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = check_cuda(cudaMalloc(&f->dk, sizeof(double2) * f->nc), "cudaMalloc(delta_k)");
+  if (!rc) rc = check_cuda(cudaMalloc(&f->acc, sizeof(double)), "cudaMalloc(accumulator)");
+  cufftHandle fwd = 0;
+  bool have_plan = false;
+  if (!rc) {
+    rc = check_cufft(cufftPlan3d(&fwd, N, N, N, CUFFT_D2Z), "cufftPlan3d(D2Z)");
+    have_plan = !rc;
+  }
+  if (!rc) rc = check_cufft(cufftSetStream(fwd, st), "cufftSetStream");
+  // an out-of-place real-to-complex transform leaves its input unchanged
+  if (!rc) rc = check_cufft(cufftExecD2Z(fwd, const_cast<double*>(white), reinterpret_cast<cufftDoubleComplex*>(f->dk)),
+                            "cufftExecD2Z");
+  if (!rc) {
+    const AxisTables t = axis_tables(f, 0.0);
+    color_kernel<<<grid_for(f->nc, ctx->num_sms), 256, 0, st>>>(f->dk, f->nc, t, spec->amplitude, spec->index,
+                                                                 spec->k_cut);
+    rc = check_cuda(cudaGetLastError(), "color_kernel launch");
+  }
+  if (have_plan) {
+    // the plan may be released only after the transform has run
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    cufftDestroy(fwd);
+  }
+  if (rc) {
+    cc_field_destroy(f);
+    return rc;
+  }
+  *out = f;
+  return CC_OK;
+}
+
+int cc_field_sigma(cc_field* f, double R, double* sigma, void* stream) {
+  if (!f || !sigma) return set_error(CC_EINVAL, "field and sigma must be non-NULL");
+  if (!(R >= 0.0) || !std::isfinite(R)) return set_error(CC_EINVAL, "R must be finite and >= 0");
+  if (int rc = select_device(f->ctx)) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (int rc = check_cuda(cudaMemsetAsync(f->acc, 0, sizeof(double), st), "cudaMemsetAsync")) return rc;
+  const AxisTables t = axis_tables(f, 0.0);
+  sigma_kernel<<<grid_for(f->nc, f->ctx->num_sms), 256, 0, st>>>(t, f->nc, f->spec.amplitude, f->spec.index,
+                                                                  f->spec.k_cut, R, f->acc);
+  if (int rc = check_cuda(cudaGetLastError(), "sigma_kernel launch")) return rc;
+  double s = 0.0;
+  if (int rc = check_cuda(cudaMemcpyAsync(&s, f->acc, sizeof(double), cudaMemcpyDeviceToHost, st), "D2H sigma")) return rc;
+  if (int rc = check_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize")) return rc;
+  const double n3 = static_cast<double>(f->N) * f->N * f->N;
+  *sigma = std::sqrt(s / n3);
+  return CC_OK;
+}
+
+int cc_field_hessian(cc_field* f, double R, void* planes, int32_t dtype, int64_t plane_stride, void* stream) {
+  if (!f || !planes) return set_error(CC_EINVAL, "field and planes must be non-NULL");
+  if (dtype != CC_F64 && dtype != CC_F32) return set_error(CC_EINVAL, "dtype must be CC_F64 or CC_F32");
+  if (!(R >= 0.0) || !std::isfinite(R)) return set_error(CC_EINVAL, "R must be finite and >= 0");
+  const int64_t n3 = static_cast<int64_t>(f->N) * f->N * f->N;
+  if (plane_stride < n3) return set_error(CC_EINVAL, "plane_stride must be >= N^3");
+  if ((plane_stride * dtype) % 16 || reinterpret_cast<uintptr_t>(planes) % 16)
+    return set_error(CC_EINVAL, "planes must start on 16 bytes and plane_stride * element size be a multiple of 16");
+  if (int rc = select_device(f->ctx)) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t elem = (dtype == CC_F64) ? sizeof(double2) : sizeof(float2);
+  const size_t need = elem * 6 * static_cast<size_t>(f->nc);
+  if (need > f->work_bytes) {
+    if (f->work) cudaFree(f->work);
+    f->work = nullptr;
+    f->work_bytes = 0;
+    if (int rc = check_cuda(cudaMalloc(&f->work, need), "cudaMalloc(field work)")) return rc;
+    f->work_bytes = need;
+  }
+  const auto key = std::make_pair(static_cast<int>(dtype), plane_stride);
+  auto it = f->inv_plans.find(key);
+  if (it == f->inv_plans.end()) {
+    cufftHandle p = 0;
+    int n[3] = {f->N, f->N, f->N};
+    int inembed[3] = {f->N, f->N, f->N / 2 + 1};
+    int onembed[3] = {f->N, f->N, f->N};
+    // odist may exceed the int range of cufftPlanMany only for planes above 2^31 elements
+    if (plane_stride > INT32_MAX || f->nc > INT32_MAX) return set_error(CC_ERANGE, "grid too large for one batched plan");
+    if (int rc = check_cufft(cufftPlanMany(&p, 3, n, inembed, 1, static_cast<int>(f->nc), onembed, 1,
+                                           static_cast<int>(plane_stride), dtype == CC_F64 ? CUFFT_Z2D : CUFFT_C2R, 6),
+                             "cufftPlanMany(inverse)"))
+      return rc;
+    it = f->inv_plans.emplace(key, p).first;
+  }
+  if (int rc = check_cufft(cufftSetStream(it->second, st), "cufftSetStream")) return rc;
+  const AxisTables t = axis_tables(f, R);
+  const double scale = 1.0 / static_cast<double>(n3);
+  const int grid = grid_for(f->nc, f->ctx->num_sms);
+  if (dtype == CC_F64) {
+    hessian_k_kernel<double2, double><<<grid, 256, 0, st>>>(f->dk, f->nc, t, scale, static_cast<double2*>(f->work));
+    if (int rc = check_cuda(cudaGetLastError(), "hessian_k_kernel launch")) return rc;
+    return check_cufft(cufftExecZ2D(it->second, static_cast<cufftDoubleComplex*>(f->work), static_cast<double*>(planes)),
+                       "cufftExecZ2D");
+  }
+  hessian_k_kernel<float2, float><<<grid, 256, 0, st>>>(f->dk, f->nc, t, scale, static_cast<float2*>(f->work));
+  if (int rc = check_cuda(cudaGetLastError(), "hessian_k_kernel launch")) return rc;
+  return check_cufft(cufftExecC2R(it->second, static_cast<cufftComplex*>(f->work), static_cast<float*>(planes)),
+                     "cufftExecC2R");
+}
+
+void cc_field_destroy(cc_field* f) {
+  if (!f) return;
+  if (f->ctx) select_device(f->ctx);
+  for (auto& kv : f->inv_plans) cufftDestroy(kv.second);
+  if (f->dk) cudaFree(f->dk);
+  if (f->work) cudaFree(f->work);
+  if (f->acc) cudaFree(f->acc);
+  delete f;
+}
+
+}  // extern "C"

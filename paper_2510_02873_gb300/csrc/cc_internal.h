@@ -52,6 +52,11 @@ struct DevTable {
   // the table image at offset round_up(bytes(), 16); nullptr when absent
   const float4* dfseg;
   float Dtop_hi, Dtop_lo, D0_hi, D0_lo, eds_hi, eds_lo;  // float-float constants
+  // exact-background growth ratios r2, r3a, r3b as natural splines in D over
+  // the same knots (CC_MODE_EXACT_GROWTH): rc64[o * (n - 1) + k] (FP64) and
+  // rc32[...] (FP32 copies, {c0, c1, c2, c3}); nullptr when absent
+  const Coef4* rc64;
+  const float4* rc32;
   // bytes of the table image (coef | D | Df | bucket), staged in shared memory
   __host__ __device__ size_t bytes() const {
     return sizeof(Coef4) * (n - 1) + sizeof(double) * n + sizeof(float) * n +
@@ -82,6 +87,8 @@ int build_natural_spline(const std::vector<double>& x, const std::vector<double>
 // the same, into caller-provided arrays (no allocation); work holds 6 n doubles
 int growth_table_into(const cc_cosmology& c, double* a_k, double* D_k);
 int natural_spline_into(int n, const double* x, const double* y, double* coef, double* work);
+// r2 = D2/D1^2, r3a = D3a/D1^3, r3b = D3b/D1^3 at the knots of growth_table_into
+int growth_ratios_into(const cc_cosmology& c, double* r2, double* r3a, double* r3b);
 
 // error reporting (cc_api.cu)
 int set_error(int code, const std::string& msg);
@@ -119,12 +126,14 @@ int launch_fp64(const LaunchArgs& a, const DevTable& tab);
 int launch_mixed(const LaunchArgs& a, const DevTable& tab, const double* sigma);
 int launch_tab(const LaunchArgs& a, const DevTable& tab, const TabDev& td);
 int launch_f32x2(const LaunchArgs& a, const DevTable& tab);
+int launch_exact(const LaunchArgs& a, const DevTable& tab);
 int launch_reset_max(double* F_max, int32_t* idx, int64_t n, cudaStream_t stream, int num_sms);
 
 }  // namespace cc
 
 struct cc_ctx;
 namespace cc {
+int select_device(const cc_ctx* ctx);  // make ctx's device current (cc_api.cu)
 int launch_tab_checked(cc_ctx* ctx, const LaunchArgs& a);                          // cc_tab.cu
 int launch_surrogate_checked(cc_ctx* ctx, const LaunchArgs& a, const double* sigma);  // cc_surrogate.cu
 }
@@ -135,6 +144,7 @@ struct cc_ctx {
   cc_cosmology cosmo{};
   std::vector<double> a_k, D_k, coef;
   void* d_table = nullptr;  // coef[n-1] | D[n] | Df[n] | bucket[n_buckets]
+  void* d_ratio = nullptr;  // growth-ratio splines: FP64 Coef4[3 (n-1)] | FP32 float4[3 (n-1)]
   cc::DevCounters* d_counters = nullptr;
   cc::DevTable tab{};
   // staging of cc_collapse_multi_host (allocated on first use)

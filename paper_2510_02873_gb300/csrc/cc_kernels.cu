@@ -8,6 +8,7 @@
 // maximum over the radii of one launch kept in registers: F_max/idx are read
 // and written once per point per launch.
 #include "cc_df.cuh"
+#include "cc_exact.cuh"
 
 namespace cc {
 
@@ -39,7 +40,7 @@ __device__ __forceinline__ void add_counters(DevCounters* cnt, unsigned evals, u
   }
 }
 
-constexpr int kModeFP64 = 0, kModeMixed = 1, kModeTab = 2, kModeF32x2 = 3;
+constexpr int kModeFP64 = 0, kModeMixed = 1, kModeTab = 2, kModeF32x2 = 3, kModeExact = 4;
 
 // One thread per point (grid-stride), all R radii of the launch in registers.
 // kMode selects collapse_point_fp64, collapse_point_mixed (FP32 bulk) or
@@ -140,6 +141,16 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
           n_fp64 += res.outside;
           a = res.a;
           coll = res.collapsed;
+        } else if constexpr (kMode == kModeExact) {
+          const double xx = ld(h), yy = ld(h + plane_stride), zz = ld(h + 2 * plane_stride);
+          const double xy = ld(h + 3 * plane_stride), xz = ld(h + 4 * plane_stride);
+          const double yz = ld(h + 5 * plane_stride);
+          const exact::Result res = exact::collapse_point(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
+          n_coll += res.collapsed;
+          n_eds += res.eds;
+          n_ref += res.refined;
+          a = res.a;
+          coll = res.collapsed;
         } else {
           const double xx = ld(h), yy = ld(h + plane_stride), zz = ld(h + 2 * plane_stride);
           const double xy = ld(h + 3 * plane_stride), xz = ld(h + 4 * plane_stride);
@@ -221,6 +232,12 @@ int launch_fp64(const LaunchArgs& a, const DevTable& tab) {
 int launch_f32x2(const LaunchArgs& a, const DevTable& tab) {
   if (tab.dfseg == nullptr) return set_error(CC_ENOTSUP, "CC_MODE_F32X2 needs the float-float spline image");
   return launch_mode<kModeF32x2>(a, tab, RadiusParams{}, TabDev{});
+}
+
+int launch_exact(const LaunchArgs& a, const DevTable& tab) {
+  if (tab.rc64 == nullptr || tab.rc32 == nullptr)
+    return set_error(CC_ENOTSUP, "CC_MODE_EXACT_GROWTH needs the growth-ratio tables");
+  return launch_mode<kModeExact>(a, tab, RadiusParams{}, TabDev{});
 }
 
 int launch_tab(const LaunchArgs& a, const DevTable& tab, const TabDev& td) {

@@ -161,13 +161,6 @@ int grow(void** p, size_t* cap, size_t bytes, const char* what) {
   return CC_OK;
 }
 
-int select_device_of(const cc_ctx* ctx) {
-  int cur = -1;
-  if (int rc = check_cuda(cudaGetDevice(&cur), "cudaGetDevice")) return rc;
-  if (cur != ctx->device) return check_cuda(cudaSetDevice(ctx->device), "cudaSetDevice");
-  return CC_OK;
-}
-
 int check_axes(const double* dg, int nd, const double* xg, int nx, const double* yg, int ny) {
   if (!dg || !xg || !yg) return set_error(CC_EINVAL, "table axes must be non-NULL");
   if (nd < 4 || nd > kTabMaxD || nx < 2 || nx > kTabMaxXY || ny < 2 || ny > kTabMaxXY)
@@ -203,7 +196,7 @@ int cc_set_table(cc_ctx* ctx, const double* dgrid, int32_t nd, const double* xgr
   const size_t nv = static_cast<size_t>(nx) * ny * nd;
   for (size_t i = 0; i < nv; ++i)
     if (!std::isfinite(values[i])) return set_error(CC_EINVAL, "table values must be finite");
-  if (int rc = select_device_of(ctx)) return rc;
+  if (int rc = select_device(ctx)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   TabDev td{};
   td.nd = nd;
@@ -258,7 +251,7 @@ int cc_table_nodes_rlpt(cc_ctx* ctx, const double* dgrid, int32_t nd, const doub
   if (!ctx) return set_error(CC_EINVAL, "ctx is NULL");
   if (int rc = check_axes(dgrid, nd, xgrid, nx, ygrid, ny)) return rc;
   if (!values) return set_error(CC_EINVAL, "values is NULL");
-  if (int rc = select_device_of(ctx)) return rc;
+  if (int rc = select_device(ctx)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t nv = static_cast<size_t>(nx) * ny * nd;
   double* buf = nullptr;
@@ -285,7 +278,7 @@ int cc_table_query(cc_ctx* ctx, const double* d, const double* x, const double* 
   if (m < 0) return set_error(CC_EINVAL, "m must be >= 0");
   if (m > 0 && (!d || !x || !y || !out)) return set_error(CC_EINVAL, "NULL query or output array");
   if (m == 0) return CC_OK;
-  if (int rc = select_device_of(ctx)) return rc;
+  if (int rc = select_device(ctx)) return rc;
   const TabDev& td = ctx->tabdev;
   const size_t smem = ((td.axes_bytes() + 15) / 16) * 16;
   const int64_t need = (m + 255) / 256;
@@ -301,7 +294,7 @@ int cc_spline_eval(cc_ctx* ctx, const double* xk, const double* yk, int32_t n, c
   for (int i = 0; i + 1 < n; ++i)
     if (!(xk[i + 1] > xk[i])) return set_error(CC_EINVAL, "knots must be strictly increasing");
   if (m < 0 || (m > 0 && (!q || !out))) return set_error(CC_EINVAL, "bad query arrays");
-  if (int rc = select_device_of(ctx)) return rc;
+  if (int rc = select_device(ctx)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // scratch: xk | yk | work (2n) | coef (n-1) | xkf (n)
   const size_t bytes = sizeof(double) * 4 * n + sizeof(Coef4) * (n - 1) + sizeof(float) * n + 64;

@@ -12,6 +12,8 @@
 // mode D = a, D_x = a at a = 1e-5, normalised so that D(1) = 1. The natural
 // cubic spline of a(D) through (D_k, a_k) is stored as per-interval
 // polynomials in t = D - D_k for Horner evaluation on the device.
+// growth_ratios_into adds the second- and third-order growth factors of the
+// same background (the collapse condition with exact growth ratios).
 #include "cc_internal.h"
 
 #include <cmath>
@@ -84,6 +86,69 @@ int growth_table_into(const cc_cosmology& c, double* a_k, double* D_k) {
   for (int k = 0; k < n; ++k) D_k[k] /= y1[0];
   for (int k = 0; k + 1 < n; ++k)
     if (!(D_k[k + 1] > D_k[k]) || !std::isfinite(D_k[k])) return CC_ERANGE;
+  return CC_OK;
+}
+
+namespace {
+
+// Second- and third-order growth in x = ln a, state
+// y = (D1, D1_x, D2, D2_x, D3a, D3a_x, D3b, D3b_x):
+//   f_xx + (2 + dlnE/dx) f_x - 3/2 Omega_m(a) f = s,
+//   s = 0, -3/2 Om(a) D1^2, -3 Om(a) D1^3, -3 Om(a) (D1 D2 - D1^3)
+// (the equations of D1 with the second- and third-order sources; their EdS
+// solutions are D2 = -3/7 D1^2, D3a = -1/3 D1^3, D3b = 10/21 D1^3).
+inline void rhs8(const Background& bg, double x, const double y[8], double dy[8]) {
+  const double a = std::exp(x);
+  const double damp = 2.0 + bg.dlnE(a), w = 1.5 * bg.om_a(a);
+  const double D1 = y[0], D2 = y[2];
+  const double src[4] = {0.0, -w * D1 * D1, -2.0 * w * D1 * D1 * D1, -2.0 * w * (D1 * D2 - D1 * D1 * D1)};
+  for (int o = 0; o < 4; ++o) {
+    dy[2 * o] = y[2 * o + 1];
+    dy[2 * o + 1] = -damp * y[2 * o + 1] + w * y[2 * o] + src[o];
+  }
+}
+
+void advance8(const Background& bg, double x0, double x1, double y[8]) {
+  if (!(x1 > x0)) return;
+  const long steps = static_cast<long>(std::ceil((x1 - x0) / kMaxStep));
+  const double h = (x1 - x0) / static_cast<double>(steps);
+  for (long s = 0; s < steps; ++s) {
+    const double x = x0 + h * static_cast<double>(s);
+    double k1[8], k2[8], k3[8], k4[8], t[8];
+    rhs8(bg, x, y, k1);
+    for (int i = 0; i < 8; ++i) t[i] = y[i] + 0.5 * h * k1[i];
+    rhs8(bg, x + 0.5 * h, t, k2);
+    for (int i = 0; i < 8; ++i) t[i] = y[i] + 0.5 * h * k2[i];
+    rhs8(bg, x + 0.5 * h, t, k3);
+    for (int i = 0; i < 8; ++i) t[i] = y[i] + h * k3[i];
+    rhs8(bg, x + h, t, k4);
+    for (int i = 0; i < 8; ++i) y[i] += h * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]) / 6.0;
+  }
+}
+
+}  // namespace
+
+int growth_ratios_into(const cc_cosmology& c, double* r2, double* r3a, double* r3b) {
+  const int n = c.n_knots;
+  if (n < 2 || n > kMaxKnots || !(c.a_min > kAStart) || !(c.a_max > c.a_min) ||
+      !std::isfinite(c.omega_m) || !std::isfinite(c.omega_l) || !(c.omega_m > 0.0))
+    return CC_EINVAL;
+  Background bg{c.omega_m, 1.0 - c.omega_m - c.omega_l, c.omega_l};
+  const double xlo = std::log(c.a_min), xhi = std::log(c.a_max);
+  const double a0 = kAStart;
+  double y[8] = {a0, a0, -3.0 / 7.0 * a0 * a0, -6.0 / 7.0 * a0 * a0, -1.0 / 3.0 * a0 * a0 * a0, -a0 * a0 * a0,
+                 10.0 / 21.0 * a0 * a0 * a0, 10.0 / 7.0 * a0 * a0 * a0};
+  double x = std::log(kAStart);
+  for (int k = 0; k < n; ++k) {
+    const double xk = (k == n - 1) ? xhi : xlo + (xhi - xlo) * k / (n - 1);
+    advance8(bg, x, xk, y);
+    x = xk;
+    const double D1 = y[0];
+    r2[k] = y[2] / (D1 * D1);
+    r3a[k] = y[4] / (D1 * D1 * D1);
+    r3b[k] = y[6] / (D1 * D1 * D1);
+    if (!std::isfinite(r2[k]) || !std::isfinite(r3a[k]) || !std::isfinite(r3b[k])) return CC_ERANGE;
+  }
   return CC_OK;
 }
 

@@ -84,5 +84,5 @@ def test_null_arguments_rejected_without_device(lib):
 def test_mode_names_match_the_header():
     text = open(os.path.join(ROOT, "include", "collapse.h")).read()
     enum = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"CC_MODE_(\w+)\s*=\s*(\d+)", text)}
-    assert enum == {"fp64": 0, "mixed": 1, "surrogate": 2, "tabulated": 3, "f32x2": 4}
+    assert enum == {"fp64": 0, "mixed": 1, "surrogate": 2, "tabulated": 3, "f32x2": 4, "exact_growth": 5}
     assert enum == _lib.MODES

@@ -480,3 +480,167 @@ def test_mlp_gradient_matches_finite_differences():
     W4 = params[8576:8640]; b4 = params[8640]
     ref = silu(silu(silu(z @ W1 + b1) @ W2 + b2) @ W3 + b3) @ W4 + b4
     np.testing.assert_allclose(oracle.mlp_forward(params, z), ref, rtol=1e-13, atol=1e-13)
+
+
+def test_histogram_brute_force_and_invariants():
+    """Bin counts against a plain loop over values and edges, on values that
+    sit exactly on edges, between them, below the first and above the last."""
+    rng = np.random.default_rng(11)
+    edges = np.array([1.0, 1.5, 2.0, 3.5, 10.0])
+    F = np.concatenate([[0.0, 0.0, 1.0, 1.5, 2.0, 3.5, 10.0, 10.5, 0.999999], rng.uniform(0.0, 12.0, 500)])
+    got = oracle.histogram(F, edges)
+    want = np.zeros(len(edges) + 1, dtype=np.int64)
+    for f in F:
+        slot = 0
+        for e in edges:
+            if e <= f:
+                slot += 1
+        want[slot] += 1
+    assert np.array_equal(got, want)
+    assert got.sum() == len(F)
+    assert got[0] == np.sum(F < 1.0) and got[-1] == np.sum(F >= 10.0)
+    # refining a bin splits its count and leaves the others unchanged
+    fine = oracle.histogram(F, np.insert(edges, 2, 1.75))
+    assert fine[2] + fine[3] == got[2] and np.array_equal(np.delete(fine, [2, 3]), np.delete(got, 2))
+
+
+def test_correlated_radii_generator_statistics():
+    """hessgen's correlated-radius chain: unit-rms components keep the isotropic
+    covariance at every radius and neighbouring radii correlate by rho."""
+    import hessgen
+    n, rho = 200000, 0.8
+    sig = np.ones(3)
+    st = hessgen.hessian_stack_correlated(7, 0, sig, n, rho)
+    tr = st[:, 0] + st[:, 1] + st[:, 2]
+    assert np.allclose(tr.var(axis=1), 1.0, rtol=0.02)
+    assert np.allclose(st[:, 3].var(axis=1), 1.0 / 15.0, rtol=0.02)
+    c01 = np.corrcoef(tr[0], tr[1])[0, 1]
+    c02 = np.corrcoef(tr[0], tr[2])[0, 1]
+    assert abs(c01 - rho) < 0.01 and abs(c02 - rho ** 2) < 0.01
+    # the first radius is the independent-radius draw
+    assert np.array_equal(st[0], hessgen.hessian_planes(7, 0, 0, 1.0, n))
+
+
+# ---- field -> smoothed Hessian (numpy FFTs)
+def _cos_field(N, box, m0, phase=0.0):
+    x = np.arange(N) * (box / N)
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    k0 = 2.0 * np.pi / box * np.asarray(m0, dtype=np.float64)
+    return np.cos(k0[0] * X + k0[1] * Y + k0[2] * Z + phase), k0
+
+
+@pytest.mark.parametrize("m0,phase", [((1, -2, 3), 0.0), ((2, 0, -1), 0.7), ((0, 0, 4), -1.3)])
+def test_hessian_of_a_plane_wave(m0, phase):
+    """delta = cos(k0.x + c): H_ij = (k0_i k0_j / k0^2) exp(-k0^2 R^2 / 2) cos(k0.x + c),
+    which fixes the component order, the sign, the 1/k^2 and the window."""
+    N, box, R = 16, 10.0, 0.4
+    delta, k0 = _cos_field(N, box, m0, phase)
+    H = oracle.hessian_from_delta_k(np.fft.rfftn(delta), N, box, R)
+    k2 = float(k0 @ k0)
+    for c, (i, j) in enumerate(oracle.HESSIAN_COMPONENTS):
+        want = (k0[i] * k0[j] / k2) * np.exp(-0.5 * k2 * R * R) * delta.reshape(-1)
+        assert np.allclose(H[c], want, rtol=0, atol=1e-13)
+
+
+def test_hessian_trace_is_the_smoothed_density():
+    rng = np.random.default_rng(3)
+    N, box, R = 16, 50.0, 3.0
+    dk = oracle.field_delta_k(rng.normal(size=(N, N, N)), box, 2.0e3, -1.5, 1.0)
+    H = oracle.hessian_from_delta_k(dk, N, box, R)
+    kx, ky, kz, _ = oracle._kgrid(N, box)
+    smooth = np.fft.irfftn(dk * np.exp(-0.5 * (kx ** 2 + ky ** 2 + kz ** 2) * R * R), s=(N, N, N), axes=(0, 1, 2)).reshape(-1)
+    assert np.allclose(H[0] + H[1] + H[2], smooth, rtol=0, atol=1e-12 * np.abs(smooth).max())
+    assert np.all(np.abs(H.mean(axis=1)) < 1e-12)
+
+
+def test_field_sigma_by_parseval():
+    """White noise whose DFT has modulus exactly N^(3/2) at every mode: the
+    variance of the smoothed density is then exactly mean_k P G^2."""
+    rng = np.random.default_rng(4)
+    N, box, A, n_s, kc, R = 16, 64.0, 5.0e2, -1.0, 0.8, 2.5
+    W = np.fft.rfftn(rng.normal(size=(N, N, N)))
+    W = W / np.abs(W) * N ** 1.5
+    white = np.fft.irfftn(W, s=(N, N, N), axes=(0, 1, 2))
+    dk = oracle.field_delta_k(white, box, A, n_s, kc)
+    kx, ky, kz, _ = oracle._kgrid(N, box)
+    dR = np.fft.irfftn(dk * np.exp(-0.5 * (kx ** 2 + ky ** 2 + kz ** 2) * R * R), s=(N, N, N), axes=(0, 1, 2))
+    s = oracle.field_sigma(N, box, A, n_s, kc, R)
+    assert abs(np.sqrt(np.mean(dR ** 2)) - s) <= 1e-12 * s
+
+
+# ---- exact-background growth ratios (second and third order)
+def test_growth_ratios_eds_limit():
+    """In EdS the second- and third-order growth factors are -3/7 D^2, -1/3 D^3, 10/21 D^3 exactly."""
+    a, D, r2, r3a, r3b = oracle.growth_ratios(1.0, 0.0, 64, 1e-3, 1.0)
+    assert np.abs(r2 + 3.0 / 7.0).max() < 1e-12
+    assert np.abs(r3a + 1.0 / 3.0).max() < 1e-12
+    assert np.abs(r3b - 10.0 / 21.0).max() < 1e-12
+
+
+def test_growth_ratios_lcdm_against_published_fits():
+    """Flat LCDM: the deviations of the ratios from EdS follow the fits of
+    Bouchet, Colombi, Hivon & Juszkiewicz (1995), Omega_m(a)^(-1/143),
+    ^(-4/275), ^(-269/17875), to a few per cent of the deviation."""
+    a, D, r2, r3a, r3b = oracle.growth_ratios(0.3, 0.7, 512, 1e-3, 1.0)
+    om = 0.3 / a ** 3 / (0.3 / a ** 3 + 0.7)
+    sel = a > 0.3
+    for r, eds, expo in ((r2, -3.0 / 7.0, -1.0 / 143.0), (r3a, -1.0 / 3.0, -4.0 / 275.0),
+                         (r3b, 10.0 / 21.0, -269.0 / 17875.0)):
+        dev = r[sel] / eds - 1.0
+        fit = om[sel] ** expo - 1.0
+        assert np.all(dev > 0) and np.all(np.abs(dev - fit) <= 0.06 * fit)
+
+
+def test_growth_ratios_independent_integration():
+    """The same equations integrated by SciPy's DOP853 in ln a."""
+    from scipy.integrate import solve_ivp
+    om, ol = 0.3, 0.7
+    a, D, r2, r3a, r3b = oracle.growth_ratios(om, ol, 32, 1e-3, 1.0)
+
+    def rhs(x, y):
+        aa = np.exp(x)
+        E2 = om / aa ** 3 + (1 - om - ol) / aa ** 2 + ol
+        dlnE = (-3 * om / aa ** 3 - 2 * (1 - om - ol) / aa ** 2) / (2 * E2)
+        w = 1.5 * om / aa ** 3 / E2
+        D1, D2 = y[0], y[2]
+        src = [0.0, -w * D1 ** 2, -2 * w * D1 ** 3, -2 * w * (D1 * D2 - D1 ** 3)]
+        out = []
+        for o in range(4):
+            out += [y[2 * o + 1], -(2 + dlnE) * y[2 * o + 1] + w * y[2 * o] + src[o]]
+        return out
+
+    a0 = 1e-5
+    y0 = [a0, a0, -3 / 7 * a0 ** 2, -6 / 7 * a0 ** 2, -a0 ** 3 / 3, -a0 ** 3, 10 / 21 * a0 ** 3, 10 / 7 * a0 ** 3]
+    sol = solve_ivp(rhs, (np.log(a0), 0.0), y0, method="DOP853", rtol=1e-12, atol=1e-30, t_eval=np.log(a))
+    D1 = sol.y[0]
+    assert np.allclose(sol.y[2] / D1 ** 2, r2, rtol=1e-8, atol=0)
+    assert np.allclose(sol.y[4] / D1 ** 3, r3a, rtol=1e-8, atol=0)
+    assert np.allclose(sol.y[6] / D1 ** 3, r3b, rtol=1e-8, atol=0)
+
+
+def test_exact_growth_collapse_reduces_to_rlpt_in_eds():
+    rng = np.random.default_rng(8)
+    t = oracle.RatioTables(1.0, 0.0, 256, 1e-3, 1.0)
+    for _ in range(200):
+        lam = np.sort(rng.normal(size=3) * 3.0)[::-1]
+        d1, f1 = t.collapse_D(lam)
+        d0, f0 = oracle.collapse_D(lam, t.D_top)
+        assert (d1 > 0) == (d0 > 0)
+        if d0 > 0:
+            assert abs(d1 - d0) <= 1e-12 * d0
+
+
+def test_exact_growth_shifts_collapse_slightly_in_lcdm():
+    """LCDM ratios exceed EdS by ~1-2 % in magnitude at late times; collapse
+    growth factors move by well under a per cent and stay ordered the same."""
+    rng = np.random.default_rng(9)
+    t = oracle.RatioTables(0.3, 0.7, 512, 1e-3, 1.0)
+    shifts = []
+    for _ in range(300):
+        lam = np.sort(rng.normal(size=3) * 2.0)[::-1]
+        d1, _ = t.collapse_D(lam)
+        d0, _ = oracle.collapse_D(lam, t.D_top)
+        if d0 > 0 and d1 > 0:
+            shifts.append(d1 / d0 - 1.0)
+    shifts = np.array(shifts)
+    assert len(shifts) > 100 and np.abs(shifts).max() < 0.01 and np.abs(shifts).max() > 1e-5
