@@ -74,6 +74,8 @@ def parse():
     # --mode surrogate trains the network first (untimed) on this many points and steps
     ap.add_argument("--train-points", type=int, default=4 * 1024 * 1024)
     ap.add_argument("--train-steps", type=int, default=300)
+    # run one variant alone at --grid / --radii (profiler captures)
+    ap.add_argument("--variant", choices=["science", "field"], default=None)
     return ap.parse_args()
 
 
@@ -186,10 +188,12 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- float-float variant
-def run_f32x2_variant(ctx, hess, sig, F_ref, idx_ref, stream, steps: int) -> dict:
-    """The FP64 path's steps in float-float arithmetic (CC_MODE_F32X2) on the
-    same FP64 planes as the main workload, timed the same way, and compared
-    with the FP64 kernel's result point by point."""
+def run_f32x2_variant(ctx, hess, sig, F_ref, idx_ref, stream, steps: int, mode: str = "f32x2") -> dict:
+    """Another mode on the same FP64 planes as the main workload, timed the same
+    way, and compared with the FP64 kernel's result point by point: the FP64
+    path's steps in float-float arithmetic (CC_MODE_F32X2, held to the same
+    1e-10), or the exact-background growth ratios (CC_MODE_EXACT_GROWTH, a
+    different collapse condition: the differences are the physics, not errors)."""
     import torch
 
     n = F_ref.numel()
@@ -198,14 +202,14 @@ def run_f32x2_variant(ctx, hess, sig, F_ref, idx_ref, stream, steps: int) -> dic
     idx = torch.empty_like(idx_ref)
     for _ in range(2):
         ctx.reset_max(F, idx)
-        ctx.collapse_multi(hess, sig, F, idx, mode="f32x2")
+        ctx.collapse_multi(hess, sig, F, idx, mode=mode)
     torch.cuda.synchronize()
     times = []
     for _ in range(steps):
         ctx.reset_max(F, idx)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ctx.collapse_multi(hess, sig, F, idx, mode="f32x2")
+        ctx.collapse_multi(hess, sig, F, idx, mode=mode)
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -218,7 +222,7 @@ def run_f32x2_variant(ctx, hess, sig, F_ref, idx_ref, stream, steps: int) -> dic
         "max_rel_diff_vs_fp64_kernel": float(rel.max()), "rms_rel_diff_vs_fp64_kernel": float(rel.pow(2).mean().sqrt()),
         "collapse_decision_differs": int(((F_ref > 0) != (F > 0)).sum()),
         "argmax_differs": int((idx != idx_ref).sum()),
-        "bound_tol": 1e-10,
+        "bound_tol": 1e-10 if mode == "f32x2" else None,
     }
 
 
@@ -227,7 +231,7 @@ SCI_RHO = 0.9
 SCI_EDGES = [1.0 + 0.25 * k for k in range(41)]  # z_c bins of 0.25 from 0 to 10
 
 
-def run_science_variant(ctx, dev, stream, reps: int = 10) -> dict:
+def run_science_variant(ctx, dev, stream, reps: int = 10, grid: int = GRID, R: int = N_RADII) -> dict:
     """The paper's science check (collapsed points per redshift bin) on a
     256^3 x 25 FP64 field whose radii are correlated (AR(1) chain, rho = 0.9):
     FP64 collapse, then the counts per z_c bin on the GPU."""
@@ -236,7 +240,7 @@ def run_science_variant(ctx, dev, stream, reps: int = 10) -> dict:
     import hessgen
     import hessgen.device as hdev
 
-    n, R = GRID ** 3, N_RADII
+    n = grid ** 3
     sig = hessgen.sigma_schedule(R, S_LO, S_HI)
     hess = torch.empty((R, 6, n), dtype=torch.float64, device=dev)
     state = torch.empty((6, n), dtype=torch.float64, device=dev)
@@ -267,7 +271,7 @@ def run_science_variant(ctx, dev, stream, reps: int = 10) -> dict:
     del hess
     torch.cuda.empty_cache()
     return {
-        "workload": f"{GRID}^3 grid x {R} correlated radii (rho {SCI_RHO}), FP64 planes",
+        "workload": f"{grid}^3 grid x {R} correlated radii (rho {SCI_RHO}), FP64 planes",
         "z_edges": [round(e - 1.0, 4) for e in SCI_EDGES],
         "collapsed_per_z_bin": c[1:-1], "not_collapsed_or_z_below_0": c[0], "z_above_last_edge": c[-1],
         "collapsed_fraction": float((F > 0).double().mean()),
@@ -280,11 +284,11 @@ def run_science_variant(ctx, dev, stream, reps: int = 10) -> dict:
 
 
 # ----------------------------------------------------------------------------- field -> Hessian -> collapse
-FIELD_SPEC = dict(box=2.0 * GRID, amplitude=222.0, index=-1.5, k_cut=1.2)
+FIELD_SPEC = dict(amplitude=222.0, index=-1.5, k_cut=1.2)  # box = 2 x grid cells
 FIELD_RADII = (1.0, 12.0)
 
 
-def run_field_variant(ctx, dev, stream, reps: int = 2) -> dict:
+def run_field_variant(ctx, dev, stream, reps: int = 2, grid: int = GRID, R: int = N_RADII) -> dict:
     """One realization kept on the device from white noise to F_max: cuFFT
     smoothing into the six Hessian planes per radius, then the collapse
     launch on those planes (256^3 grid, 25 radii). FP64 planes + FP64
@@ -295,10 +299,11 @@ def run_field_variant(ctx, dev, stream, reps: int = 2) -> dict:
     import hessgen.device as hdev
     import paper_2510_02873_gb300 as cc
 
-    n, R = GRID ** 3, N_RADII
+    n = grid ** 3
+    spec = dict(FIELD_SPEC, box=2.0 * grid)
     white = torch.empty(n, dtype=torch.float64, device=dev)
     hdev.white(white, SEED + 8, 0)
-    field = cc.Field(ctx, white, **FIELD_SPEC)
+    field = cc.Field(ctx, white, **spec)
     del white
     radii = np.geomspace(FIELD_RADII[0], FIELD_RADII[1], R)
     sig = [field.sigma(x) for x in radii]
@@ -330,7 +335,7 @@ def run_field_variant(ctx, dev, stream, reps: int = 2) -> dict:
         del planes
     field.close()
     torch.cuda.empty_cache()
-    return {"workload": f"{GRID}^3 white noise -> P(k) = A k^n exp(-(k/k_c)^2) ({FIELD_SPEC}) -> "
+    return {"workload": f"{grid}^3 white noise -> P(k) = A k^n exp(-(k/k_c)^2) ({spec}) -> "
                         f"{R} Gaussian radii {FIELD_RADII[0]}..{FIELD_RADII[1]} -> Hessian planes -> collapse, all on the device",
             "sigma_range": [float(sig[-1]), float(sig[0])], **out}
 
@@ -574,6 +579,20 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.variant:
+        import torch
+
+        import hessgen.device as hdev
+        import paper_2510_02873_gb300 as cc
+        cc.buildlib.build()
+        hdev.build()
+        dev = torch.device("cuda", 0)
+        ctx = cc.Context(**COSMO, device=0)
+        fn = {"science": run_science_variant, "field": run_field_variant}[args.variant]
+        out = fn(ctx, dev, torch.cuda.current_stream(), grid=args.grid, R=args.radii)
+        print(json.dumps({"variant": args.variant, **out}), flush=True)
+        ctx.close()
+        return
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -684,6 +703,8 @@ def main():
 
     if rank == 0 and not args.no_variants and (args.grid, R) == (GRID, N_RADII) and args.mode == "fp64":
         result["variants"] = {"f32x2": run_f32x2_variant(ctx, hess, sig, F, idx, stream, args.steps)}
+        result["variants"]["exact_growth"] = run_f32x2_variant(ctx, hess, sig, F, idx, stream, args.steps,
+                                                               mode="exact_growth")
 
     # end to end through the host-buffer entry point (H2D of every radius inside the timed region)
     if not args.no_e2e and rank == 0 and args.mode == "fp64":

@@ -74,29 +74,46 @@ __global__ void color_kernel(double2* __restrict__ dk, int64_t nc, const AxisTab
 }
 
 // the six k-space products of one radius (component order xx yy zz xy xz yz),
-// scaled by 1/N^3 for the unnormalised inverse transform
-template <typename C, typename R>
-__global__ void hessian_k_kernel(const double2* __restrict__ dk, int64_t nc, const AxisTables t, double scale,
+// scaled by 1/N^3 for the unnormalised inverse transform, in FP64 for FP64
+// planes and in FP32 (from the FP32 copy of the tables) for FP32 planes
+template <typename C, typename R, typename Tab>
+__global__ void hessian_k_kernel(const double2* __restrict__ dk, int64_t nc, const Tab t, R scale,
                                  C* __restrict__ out) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nc; i += stride) {
     int ix, iy, iz;
     decompose(i, t.N, t.Nz, ix, iy, iz);
-    const double kx = t.k[ix], ky = t.k[iy], kz = t.kz0 * iz;
-    const double k2 = fma(kx, kx, fma(ky, ky, kz * kz));
-    const double w = (k2 > 0.0) ? (t.g[ix] * t.g[iy] * t.gz[iz]) * scale / k2 : 0.0;
+    const R kx = t.k[ix], ky = t.k[iy], kz = t.kz0 * static_cast<R>(iz);
+    const R k2 = fma(kx, kx, fma(ky, ky, kz * kz));
+    const R w = (k2 > R(0)) ? (t.g[ix] * t.g[iy] * t.gz[iz]) * scale / k2 : R(0);
     const double2 d = dk[i];
-    const double re = d.x * w, im = d.y * w;
-    const double f[6] = {kx * kx, ky * ky, kz * kz, kx * ky, kx * kz, ky * kz};
+    R re, im;
+    if constexpr (sizeof(R) == 8) {
+      re = d.x * w;
+      im = d.y * w;
+    } else {
+      re = __double2float_rn(d.x) * w;
+      im = __double2float_rn(d.y) * w;
+    }
+    const R f[6] = {kx * kx, ky * ky, kz * kz, kx * ky, kx * kz, ky * kz};
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       C o;
-      o.x = static_cast<R>(re * f[c]);
-      o.y = static_cast<R>(im * f[c]);
+      o.x = re * f[c];
+      o.y = im * f[c];
       out[c * nc + i] = o;
     }
   }
 }
+
+// FP32 copy of the axis tables (FP32 planes)
+struct AxisTables32 {
+  float k[kFieldMaxN];
+  float g[kFieldMaxN];
+  float gz[kFieldMaxN / 2 + 1];
+  int N, Nz;
+  float kz0;
+};
 
 // sum over the full k grid of P(k) G(kR)^2 (half grid, modes 0 < iz < N/2 counted twice)
 __global__ void sigma_kernel(const AxisTables t, int64_t nc, double A, double n_idx, double k_cut, double R,
@@ -266,12 +283,23 @@ int cc_field_hessian(cc_field* f, double R, void* planes, int32_t dtype, int64_t
   const double scale = 1.0 / static_cast<double>(n3);
   const int grid = grid_for(f->nc, f->ctx->num_sms);
   if (dtype == CC_F64) {
-    hessian_k_kernel<double2, double><<<grid, 256, 0, st>>>(f->dk, f->nc, t, scale, static_cast<double2*>(f->work));
+    hessian_k_kernel<double2, double, AxisTables><<<grid, 256, 0, st>>>(f->dk, f->nc, t, scale,
+                                                                        static_cast<double2*>(f->work));
     if (int rc = check_cuda(cudaGetLastError(), "hessian_k_kernel launch")) return rc;
     return check_cufft(cufftExecZ2D(it->second, static_cast<cufftDoubleComplex*>(f->work), static_cast<double*>(planes)),
                        "cufftExecZ2D");
   }
-  hessian_k_kernel<float2, float><<<grid, 256, 0, st>>>(f->dk, f->nc, t, scale, static_cast<float2*>(f->work));
+  AxisTables32 t32;
+  t32.N = t.N;
+  t32.Nz = t.Nz;
+  t32.kz0 = static_cast<float>(t.kz0);
+  for (int m = 0; m < t.N; ++m) {
+    t32.k[m] = static_cast<float>(t.k[m]);
+    t32.g[m] = static_cast<float>(t.g[m]);
+  }
+  for (int m = 0; m < t.Nz; ++m) t32.gz[m] = static_cast<float>(t.gz[m]);
+  hessian_k_kernel<float2, float, AxisTables32><<<grid, 256, 0, st>>>(f->dk, f->nc, t32, static_cast<float>(scale),
+                                                                      static_cast<float2*>(f->work));
   if (int rc = check_cuda(cudaGetLastError(), "hessian_k_kernel launch")) return rc;
   return check_cufft(cufftExecC2R(it->second, static_cast<cufftComplex*>(f->work), static_cast<float*>(planes)),
                      "cufftExecC2R");
