@@ -149,6 +149,7 @@ def test_surrogate_mode_parity(ctx, tables, trained):
     frac = st["fallback"] / st["evaluations"]
     print("surrogate parity", worst, "fallback fraction", frac, st)
     assert frac < 0.2
+    assert st["error_flags"] == 0 and st["evaluations"] == n * R
 
 
 def test_surrogate_gain_over_the_method_without_it(ctx, trained):
