@@ -185,7 +185,10 @@ int launch_typed(const LaunchArgs& a, const DevTable& tab, const RadiusParams& r
   size_t smem = kSmem ? ((tab.bytes() + 15) / 16) * 16 : 0;
   if (kMode == kModeTab) smem = ((tab.bytes() + 15) / 16) * 16 + ((td.axes_bytes() + 15) / 16) * 16;
   if (kMode == kModeF32x2 && kSmem) smem = ((tab.bytes() + 15) / 16) * 16 + sizeof(float4) * 2 * (tab.n - 1);
+  // resident blocks per SM, cached per shared-memory size (tables differ between contexts)
   static thread_local int occ = 0;
+  static thread_local size_t occ_smem = ~size_t{0};
+  if (smem != occ_smem) occ = 0;
   if (kSmem && smem > 48 * 1024) {
     if (int rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  static_cast<int>(smem)),
@@ -199,6 +202,7 @@ int launch_typed(const LaunchArgs& a, const DevTable& tab, const RadiusParams& r
                             "occupancy query"))
       return rc;
     occ = blocks_per_sm > 0 ? blocks_per_sm : 1;
+    occ_smem = smem;
   }
   const int64_t need = (a.n + kThreads - 1) / kThreads;
   const int64_t cap = static_cast<int64_t>(a.num_sms) * occ;
