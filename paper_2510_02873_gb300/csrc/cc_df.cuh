@@ -46,6 +46,15 @@ __device__ __forceinline__ f2 add(f2 a, f2 b) {
   return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
 __device__ __forceinline__ f2 sub(f2 a, f2 b) { return add(a, neg(b)); }
+// the same sum left unnormalised: only for sums that cannot cancel (terms of
+// one sign, or a small correction to a large value), whose hi stays the
+// rounded sum and whose lo stays a few ulp(hi). After a cancelling sum lo can
+// be as large as hi, and the products that follow would lose that precision.
+__device__ __forceinline__ f2 addu(f2 a, f2 b) {
+  const f2 s = two_sum(a.hi, b.hi);
+  return {s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
+}
+__device__ __forceinline__ f2 subu(f2 a, f2 b) { return addu(a, neg(b)); }
 // Products are returned unnormalised: {RN(ab), the rest}, |lo| a few ulp(hi)
 // at most. Every sum renormalises (Fast2Sum), and only sums are compared, so
 // the renormalisation a product would need is left to the sum that consumes it.
@@ -117,11 +126,12 @@ __device__ __forceinline__ Result collapse_point(const T* __restrict__ h, int64_
   const f2 xx = split(__ldg(h)), yy = split(__ldg(h + ps)), zz = split(__ldg(h + 2 * ps));
   const f2 xy = split(__ldg(h + 3 * ps)), xz = split(__ldg(h + 4 * ps)), yz = split(__ldg(h + 5 * ps));
   // ---- invariants of M = A - qI
+  // sums of one sign stay unnormalised (addu); sums that can cancel are renormalised
   const f2 q = mul(add(add(xx, yy), zz), k(kThird));
   const f2 a = sub(xx, q), b = sub(yy, q), c = sub(zz, q);
-  const f2 diag = add(add(sqr(a), sqr(b)), sqr(c));
-  const f2 off = add(add(sqr(xy), sqr(xz)), sqr(yz));
-  const f2 p2x3 = add(scale(diag, 0.5f), off);  // 3 p^2
+  const f2 diag = addu(addu(sqr(a), sqr(b)), sqr(c));
+  const f2 off = addu(addu(sqr(xy), sqr(xz)), sqr(yz));
+  const f2 p2x3 = addu(scale(diag, 0.5f), off);  // 3 p^2
   const f2 det = add(sub(mul(a, sub(mul(b, c), sqr(yz))), mul(xy, sub(mul(xy, c), mul(yz, xz)))),
                      mul(xz, sub(mul(xy, yz), mul(b, xz))));
   // ---- FP32 trigonometric seed of x = l1 - q
@@ -136,13 +146,13 @@ __device__ __forceinline__ Result collapse_point(const T* __restrict__ h, int64_
     const float gpf = 3.0f * fmaf(x1f, x1f, -p2f);
     const float yg = (gpf != 0.0f) ? __fdividef(1.0f, gpf) : 0.0f;
     const f2 g = sub(mul(sub(two_prod(x1f, x1f), p2x3), x1f), det);
-    x = add(make(x1f), mul(g, -yg));
+    x = addu(make(x1f), mul(g, -yg));  // a small correction
   }
   {
     const float gpf = 3.0f * fmaf(x.hi, x.hi, -p2f);
     const float yg = (gpf != 0.0f) ? __fdividef(1.0f, gpf) : 0.0f;
     const f2 g = sub(mul(x, sub(sqr(x), p2x3)), det);
-    x = add(x, mul(g, -yg));
+    x = addu(x, mul(g, -yg));
   }
   f2 qq = q;
   res.refined = (1.0f + rf) < kPairTauF && p2f > 0.0f;
@@ -181,7 +191,7 @@ __device__ __forceinline__ Result collapse_point(const T* __restrict__ h, int64_
   const float4 s0 = seg[2 * kk], s1 = seg[2 * kk + 1];
   const f2 t = sub(Dc, f2{s1.z, s1.w});
   const float u = fmaf(s1.y, t.hi, s1.x);
-  const f2 v = add(f2{s0.z, s0.w}, mul(t, u));
+  const f2 v = addu(f2{s0.z, s0.w}, mul(t, u));  // c1 dominates
   res.a = add(f2{s0.x, s0.y}, mul(t, v));
   res.eds = res.collapsed && less(Dc, f2{tab.D0_hi, tab.D0_lo});
   if (res.eds) res.a = norm(mul(Dc, f2{tab.eds_hi, tab.eds_lo}));
