@@ -70,12 +70,13 @@ def parse():
     # smaller problems for profiler captures only (the benchmark workload is the default)
     ap.add_argument("--grid", type=int, default=GRID)
     ap.add_argument("--radii", type=int, default=N_RADII)
-    ap.add_argument("--mode", choices=["fp64", "mixed", "f32x2", "surrogate", "exact_growth"], default="fp64")
+    ap.add_argument("--mode", choices=["fp64", "mixed", "f32x2", "surrogate", "exact_growth", "tabulated"],
+                    default="fp64")
     # --mode surrogate trains the network first (untimed) on this many points and steps
     ap.add_argument("--train-points", type=int, default=4 * 1024 * 1024)
     ap.add_argument("--train-steps", type=int, default=300)
     # run one variant alone at --grid / --radii (profiler captures)
-    ap.add_argument("--variant", choices=["science", "field"], default=None)
+    ap.add_argument("--variant", choices=["science", "field", "batched"], default=None)
     return ap.parse_args()
 
 
@@ -177,7 +178,8 @@ def run_reference(args):
         "unit": "evals/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * secs / len(steps), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp64": "f64", "f32x2": "f32x2 (float-float)", "mixed": "f32+f64",
-                                       "surrogate": "bf16+f32+f64", "exact_growth": "f64"}[args.mode],
+                                       "surrogate": "bf16+f32+f64", "exact_growth": "f64",
+                                       "tabulated": "f64"}[args.mode],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample_per_step": f"4096 points x {N_RADII} radii"},
         "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": value, "unit": "evals/s",
@@ -192,8 +194,10 @@ def run_f32x2_variant(ctx, hess, sig, F_ref, idx_ref, stream, steps: int, mode: 
     """Another mode on the same FP64 planes as the main workload, timed the same
     way, and compared with the FP64 kernel's result point by point: the FP64
     path's steps in float-float arithmetic (CC_MODE_F32X2, held to the same
-    1e-10), or the exact-background growth ratios (CC_MODE_EXACT_GROWTH, a
-    different collapse condition: the differences are the physics, not errors)."""
+    1e-10), the exact-background growth ratios (CC_MODE_EXACT_GROWTH, a
+    different collapse condition: the differences are the physics, not errors),
+    or the tabulated 1/D_c (CC_MODE_TABULATED: the differences are the
+    table's interpolation error)."""
     import torch
 
     n = F_ref.numel()
@@ -222,8 +226,26 @@ def run_f32x2_variant(ctx, hess, sig, F_ref, idx_ref, stream, steps: int, mode: 
         "max_rel_diff_vs_fp64_kernel": float(rel.max()), "rms_rel_diff_vs_fp64_kernel": float(rel.pow(2).mean().sqrt()),
         "collapse_decision_differs": int(((F_ref > 0) != (F > 0)).sum()),
         "argmax_differs": int((idx != idx_ref).sum()),
-        "bound_tol": 1e-10 if mode == "f32x2" else None,
+        "bound_tol": 1e-10 if mode == "f32x2" else None,  # exact growth / table: different arithmetic
     }
+
+
+# ----------------------------------------------------------------------------- tabulated table
+def table_axes(nd: int = 128, nxy: int = 64, d_max: float = 40.0, xy_max: float = 40.0):
+    """Non-uniform axes of the tabulated mode: delta sinh-spaced (dense near 0),
+    x = l1 - l2 and y = l2 - l3 quadratically spaced from 0."""
+    import numpy as np
+    t = np.linspace(-1.0, 1.0, nd)
+    dg = d_max * np.sinh(2.5 * t) / np.sinh(2.5)
+    u = np.linspace(0.0, 1.0, nxy)
+    xg = xy_max * (0.3 * u + 0.7 * u ** 2)
+    return dg, xg, xg.copy()
+
+
+def load_table(ctx):
+    """Node values 1/D_c computed on the device (cc_table_nodes_rlpt), then the table (cc_set_table)."""
+    dg, xg, yg = table_axes()
+    ctx.set_table(dg, xg, yg, ctx.table_nodes_rlpt(dg, xg, yg))
 
 
 # ----------------------------------------------------------------------------- science proxy
@@ -406,7 +428,7 @@ BATCH_SEED, BATCH_N = 2514, 48
 BATCH_GRIDS = (64, 96, 128, 192, 256, 384)
 
 
-def run_batch_variant(ctx, dev, stream, reps: int = 3) -> dict:
+def run_batch_variant(ctx, dev, stream, reps: int = 3, grids=BATCH_GRIDS, n_items: int = BATCH_N) -> dict:
     """48 realizations, grids drawn from {64..384}^3 and 8..40 radii (seeded),
     FP32 planes (240.5 GB resident), mixed precision: one persistent launch
     replayed from a CUDA graph with autotuned tiles, against one
@@ -419,8 +441,9 @@ def run_batch_variant(ctx, dev, stream, reps: int = 3) -> dict:
     import paper_2510_02873_gb300 as cc
 
     rng = np.random.default_rng(BATCH_SEED)
-    grids = rng.choice(BATCH_GRIDS, BATCH_N)
-    radii = rng.integers(8, 41, BATCH_N)
+    grid_choice = grids
+    grids = rng.choice(grid_choice, n_items)
+    radii = rng.integers(8, 41, n_items)
     items = []
     for k, (g, R) in enumerate(zip(grids, radii)):
         n, R = int(g) ** 3, int(R)
@@ -476,7 +499,7 @@ def run_batch_variant(ctx, dev, stream, reps: int = 3) -> dict:
     torch.cuda.empty_cache()
     g, l = statistics.mean(graph_ms), statistics.mean(loop_ms)
     return {
-        "workload": f"{BATCH_N} realizations, grids {{64..384}}^3, 8..40 radii (seed {BATCH_SEED}), "
+        "workload": f"{n_items} realizations, grids {{{min(grid_choice)}..{max(grid_choice)}}}^3, 8..40 radii (seed {BATCH_SEED}), "
                     f"{evals} evaluations, FP32 planes ({evals * 24 / 1e9:.1f} GB resident), mixed precision",
         "evals_per_s": evals / (g * 1e-3), "graph_replay_ms": g,
         "per_realization_launches_ms": l, "speedup_vs_per_realization": l / g,
@@ -588,8 +611,12 @@ def main():
         hdev.build()
         dev = torch.device("cuda", 0)
         ctx = cc.Context(**COSMO, device=0)
-        fn = {"science": run_science_variant, "field": run_field_variant}[args.variant]
-        out = fn(ctx, dev, torch.cuda.current_stream(), grid=args.grid, R=args.radii)
+        if args.variant == "batched":  # 12 realizations of grids up to --grid
+            out = run_batch_variant(ctx, dev, torch.cuda.current_stream(),
+                                    grids=tuple(g for g in BATCH_GRIDS if g <= args.grid), n_items=12)
+        else:
+            fn = {"science": run_science_variant, "field": run_field_variant}[args.variant]
+            out = fn(ctx, dev, torch.cuda.current_stream(), grid=args.grid, R=args.radii)
         print(json.dumps({"variant": args.variant, **out}), flush=True)
         ctx.close()
         return
@@ -621,6 +648,8 @@ def main():
         hdev.fill(h, SEED + 5, 99, 0, 1.0)
         ctx.surrogate_train(h, 1.0, steps=args.train_steps, batch=16384, lr=3e-3, seed=11)
         del h
+    if args.mode == "tabulated":
+        load_table(ctx)
     hess = torch.empty((R, 6, n), dtype=plane_dtype, device=dev)
     for r in range(R):
         hdev.fill(hess[r], SEED, rank, r, sig[r])  # realization = rank: independent problem per GPU
@@ -690,7 +719,8 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp64": "f64", "f32x2": "f32x2 (float-float)", "mixed": "f32+f64",
-                                       "surrogate": "bf16+f32+f64", "exact_growth": "f64"}[args.mode],
+                                       "surrogate": "bf16+f32+f64", "exact_growth": "f64",
+                                       "tabulated": "f64"}[args.mode],
         "data": "synthetic",
         "config": {"workload": WORKLOAD if (args.grid, R) == (GRID, N_RADII) else f"profiling case {args.grid}^3 x {R}", "points": n, "radii": R, "mode": args.mode,
                    "per_gpu": "one independent realization per GPU",
@@ -705,6 +735,9 @@ def main():
         result["variants"] = {"f32x2": run_f32x2_variant(ctx, hess, sig, F, idx, stream, args.steps)}
         result["variants"]["exact_growth"] = run_f32x2_variant(ctx, hess, sig, F, idx, stream, args.steps,
                                                                mode="exact_growth")
+        load_table(ctx)
+        result["variants"]["tabulated"] = run_f32x2_variant(ctx, hess, sig, F, idx, stream, args.steps,
+                                                            mode="tabulated")
 
     # end to end through the host-buffer entry point (H2D of every radius inside the timed region)
     if not args.no_e2e and rank == 0 and args.mode == "fp64":
