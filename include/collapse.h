@@ -66,7 +66,8 @@ extern "C" {
 
 /* ---- evaluation modes ---- */
 typedef enum {
-  CC_MODE_FP64 = 0,     /* all arithmetic in FP64 (Sec. 3 "Classic" kernel)            */
+  CC_MODE_FP64 = 0,     /* FP64 path (Sec. 3 "Classic" kernel): FP64 invariants, Newton
+                         * corrections and spline, FP32 seeds; F within 1e-10 relative   */
   CC_MODE_MIXED = 1,    /* FP32 bulk, FP64 for the sensitive branches                   */
   CC_MODE_SURROGATE = 2,/* learned surrogate with exact fallback                        */
   CC_MODE_TABULATED = 3,/* table of 1/D_c in (delta, x, y) (Sec. 3 "Tabulated" kernel)   */
@@ -100,13 +101,16 @@ typedef struct {
   uint64_t refined;       /* eigenvalue pairs re-solved by deflation (near-degenerate pair) */
   uint64_t fp64_branch;   /* MIXED: points re-evaluated in FP64                             */
   uint64_t fallback;      /* SURROGATE: points sent to the exact path                       */
-  uint32_t error_flags;   /* bit 0: bounded wait timed out; bit 1: index out of range        */
+  uint32_t error_flags;   /* device-side error bits; 0 (no kernel of this build waits on the
+                           * device or can leave its index range)                           */
   uint32_t reserved;
 } cc_stats;
 
 /* Create a context on `device`: solves the growth ODE in FP64 on the host,
- * builds the natural spline of a(D) and uploads it once (Sec. 3, Sec. 4.2).
- * Allocates device memory for the tables and counters. */
+ * builds the natural spline of a(D) and uploads it once (Sec. 3, Sec. 4.2),
+ * with its float-float image (CC_MODE_F32X2) and the second- and third-order
+ * growth-ratio splines (CC_MODE_EXACT_GROWTH). Allocates device memory for
+ * the tables and counters. */
 CC_API int cc_create(cc_ctx **out, const cc_cosmology *cosmo, int device);
 
 /* Release the context and its device memory (synchronises the device). NULL is a no-op. */

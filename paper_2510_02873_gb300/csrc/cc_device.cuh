@@ -172,11 +172,10 @@ __device__ __forceinline__ EigenTop eigen_top_fp64(double xx, double yy, double 
   const double a = xx - q, b = yy - q, c = zz - q;
   const double diag = fma(c, c, fma(b, b, a * a));
   const double off = fma(yz, yz, fma(xz, xz, xy * xy));
-  const double s6 = fma(2.0, off, diag);  // 6 p^2
-  const double p2x3 = 0.5 * s6;           // 3 p^2
+  const double p2x3 = fma(0.5, diag, off);  // 3 p^2 = |M|_F^2 / 2
   const double det = fma(xz, fma(xy, yz, -b * xz), fma(a, fma(b, c, -yz * yz), -xy * fma(xy, c, -yz * xz)));
   // ---- FP32 trigonometric seed
-  const float p2f = to_f32_trunc(s6) * (1.0f / 6.0f);
+  const float p2f = to_f32_trunc(p2x3) * (1.0f / 3.0f);
   const float detf = to_f32_trunc(det);
   const float pf = sqrtf(p2f);
   float rf = (p2f > 0.0f) ? __fdividef(detf, 2.0f * p2f * pf) : 0.0f;
@@ -288,7 +287,7 @@ struct MinA {
 };
 
 // FP64 collapse value of one point, F = 1/a_c (0 when there is no collapse).
-//   eigenvalues: invariants of M = A - qI in FP64 (q = tr/3, s6 = |M|_F^2 = 6 p^2,
+//   eigenvalues: invariants of M = A - qI in FP64 (q = tr/3, |M|_F^2 = 6 p^2,
 //     det M); l1 = q + x with x the largest root of x^3 - 3 p^2 x - det M = 0,
 //     seeded by the FP32 trigonometric solution and corrected by two FP64
 //     Newton steps (FP32 derivative at each iterate); l2 l3 and l2^2 + l3^2
