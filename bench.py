@@ -37,11 +37,11 @@ WORKLOAD = "collapse 256^3 grid x 25 radii, FP64 SoA Hessian planes (20.1 GB res
 # kernel, from ncu thread-instruction counters (dadd + dmul + 2 dfma) divided
 # by the evaluations of the captured launch (profiles/collapse_kernel_*_128cube_x4.md).
 # None until a capture of the current kernel exists.
-FP64_FLOPS_PER_EVAL = 75.0   # profiles/collapse_kernel_fp64_128cube_x4.md
+FP64_FLOPS_PER_EVAL = 71.0   # profiles/collapse_kernel_fp64_128cube_x4.md
 FP64_FLOPS_PER_EVAL_MIXED = 16.1  # profiles/collapse_kernel_mixed_256cube_x4.md
 # DRAM bytes (read + write) of one full launch of the default workload, from
 # an ncu capture of that launch (profiles/collapse_kernel_fp64_256cube_x25_dram.md).
-TRAFFIC_BYTES_DEFAULT = 20.48e9
+TRAFFIC_BYTES_DEFAULT = 20.84e9
 # FP64 FMA rate of one GB300 SM: 1.25 TFLOP/s nominal at 2070 MHz over 152 SMs
 # = 3.97 flop/clk/SM, i.e. 2 DFMA per clock per SM (confirmed by a DFMA-chain probe).
 FP64_FLOP_PER_CLK_PER_SM = 4.0

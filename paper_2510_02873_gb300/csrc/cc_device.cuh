@@ -168,12 +168,16 @@ __device__ __forceinline__ EigenTop eigen_top_fp64(double xx, double yy, double 
                                                    double yz) {
   EigenTop e;
   // ---- invariants (FP64)
+  // M = A - qI with the diagonal (a, b, c) made exactly traceless, c = -(a + b):
+  // |M|_F^2 / 2 = a^2 + a b + b^2 + off = a (a + b) + b^2 + off (no cancellation:
+  // a^2 + ab + b^2 >= 3/4 b^2)
   const double q = (xx + yy + zz) * (1.0 / 3.0);
-  const double a = xx - q, b = yy - q, c = zz - q;
-  const double diag = fma(c, c, fma(b, b, a * a));
-  const double off = fma(yz, yz, fma(xz, xz, xy * xy));
-  const double p2x3 = fma(0.5, diag, off);  // 3 p^2 = |M|_F^2 / 2
-  const double det = fma(xz, fma(xy, yz, -b * xz), fma(a, fma(b, c, -yz * yz), -xy * fma(xy, c, -yz * xz)));
+  const double a = xx - q, b = yy - q;
+  const double ab = a + b, c = -ab;
+  const double yz2 = yz * yz;
+  const double off = fma(xz, xz, fma(xy, xy, yz2));
+  const double p2x3 = fma(a, ab, fma(b, b, off));  // 3 p^2 = |M|_F^2 / 2
+  const double det = fma(xz, fma(xy, yz, -b * xz), fma(a, fma(b, c, -yz2), -xy * fma(xy, c, -yz * xz)));
   // ---- FP32 trigonometric seed
   const float p2f = to_f32_trunc(p2x3) * (1.0f / 3.0f);
   const float detf = to_f32_trunc(det);
