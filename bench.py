@@ -39,6 +39,11 @@ WORKLOAD = "collapse 256^3 grid x 25 radii, FP64 SoA Hessian planes (20.1 GB res
 # None until a capture of the current kernel exists.
 FP64_FLOPS_PER_EVAL = 71.0   # profiles/collapse_kernel_fp64_128cube_x4.md
 FP64_FLOPS_PER_EVAL_MIXED = 16.1  # profiles/collapse_kernel_mixed_256cube_x4.md
+# FP64-pipe warp instructions of every kind (DFMA, DMUL, DADD, compares) per
+# evaluation, from the same captures: the FP64 unit issues one per lane slot
+# whatever the instruction, so this count, not the flop count, sets the time.
+FP64_PIPE_INST_PER_EVAL = {"fp64": 45.9, "mixed": 9.1}
+FP64_LANES_PER_CLK_PER_SM = 2.0
 # DRAM bytes (read + write) of one full launch of the default workload, from
 # an ncu capture of that launch (profiles/collapse_kernel_fp64_256cube_x25_dram.md).
 TRAFFIC_BYTES_DEFAULT = 20.84e9
@@ -711,6 +716,16 @@ def main():
         "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full launch",
         "algorithmic_bytes": 48.0 * evals_launch + 12.0 * 2 * n,
     }
+    ipe = FP64_PIPE_INST_PER_EVAL.get(args.mode)
+    if ipe:
+        pipe_peak = FP64_LANES_PER_CLK_PER_SM * sm_count * clk_mhz * 1e6
+        pipe_rate = ipe * evals_launch / kern_avg_s
+        roofline["fp64_pipe"] = {
+            "inst_per_eval": ipe, "achieved_inst_per_s": pipe_rate, "peak_inst_per_s": pipe_peak,
+            "frac": pipe_rate / pipe_peak,
+            "basis": "ncu FP64-pipe thread instructions per evaluation x live evaluations/s, against "
+                     f"{FP64_LANES_PER_CLK_PER_SM:g} FP64 lanes/clk/SM x {sm_count} SMs x {clk_mhz:.0f} MHz",
+        }
     if clk.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = (achieved / (peak_tflops * clk["sm_mhz"] / clk_mhz)) if achieved else None
 

@@ -52,6 +52,14 @@ __device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], uint3
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// the same MMA as a pure register operation, which the scheduler may move
+// (the inference layers interleave it with the next fragment loads)
+__device__ __forceinline__ void mma_pure(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 __device__ __forceinline__ float silu(float v) { return __fdividef(v, 1.0f + __expf(-v)); }
 __device__ __forceinline__ float dsilu(float v) {
   const float s = __fdividef(1.0f, 1.0f + __expf(-v));
@@ -146,6 +154,79 @@ __device__ __forceinline__ void layer4(const uint32_t (&a)[4][4], const unsigned
   o1 = c[2];
 }
 
+// ---- inference, one 16-row tile at a time: each 8-column output tile goes
+// through SiLU into the next layer's A fragments as soon as its four k-steps
+// are done, so one 4-register accumulator is live instead of a layer's 32.
+__device__ __forceinline__ void silu_into(const float (&c)[4], int j, uint32_t (&a)[4][4]) {
+  a[j >> 1][(j & 1) * 2] = silu2_bf16(c[0], c[1]);
+  a[j >> 1][(j & 1) * 2 + 1] = silu2_bf16(c[2], c[3]);
+}
+
+// Four 8x8 BF16 matrices from shared memory in one instruction: lanes 8m..8m+7
+// give the row addresses of matrix m (16-byte rows), and lane 4g + t receives
+// row g, columns 2t and 2t + 1 of each, which is an mma.sync B fragment when
+// the rows are output units and the columns 8 consecutive k.
+__device__ __forceinline__ void ldsm_x4(const unsigned char* p, uint32_t& r0, uint32_t& r1, uint32_t& r2,
+                                        uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(p))));
+}
+
+__device__ __forceinline__ void layer1_act(float z0, float z1, float z2, int tile, const unsigned char* img,
+                                           uint32_t (&o)[4][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int r0 = 16 * tile + g, r1 = r0 + 8;
+  const float a00 = __shfl_sync(0xffffffffu, z0, r0), a01 = __shfl_sync(0xffffffffu, z1, r0);
+  const float a02 = __shfl_sync(0xffffffffu, z2, r0);
+  const float a10 = __shfl_sync(0xffffffffu, z0, r1), a11 = __shfl_sync(0xffffffffu, z1, r1);
+  const float a12 = __shfl_sync(0xffffffffu, z2, r1);
+  const uint32_t a[4] = {(t == 0) ? pack(a00, a01) : (t == 1) ? pack(a02, 0.0f) : 0u,
+                         (t == 0) ? pack(a10, a11) : (t == 1) ? pack(a12, 0.0f) : 0u, 0u, 0u};
+  const float* bias = reinterpret_cast<const float*>(img + OFF_B);
+  // lanes 0-15 address tile j (k 0-7, 8-15), lanes 16-31 tile j + 1
+  const unsigned char* wl = img + OFF_W1T + ((lane & 7) + 8 * (lane >> 4)) * STR1 * 2 + ((lane >> 3) & 1) * 16;
+#pragma unroll
+  for (int j = 0; j < 8; j += 2) {
+    const float2 b0 = *reinterpret_cast<const float2*>(bias + 8 * j + 2 * t);
+    const float2 b1 = *reinterpret_cast<const float2*>(bias + 8 * j + 8 + 2 * t);
+    float c0[4] = {b0.x, b0.y, b0.x, b0.y}, c1[4] = {b1.x, b1.y, b1.x, b1.y};
+    uint32_t w0, w1, v0, v1;
+    ldsm_x4(wl + (8 * j) * STR1 * 2, w0, w1, v0, v1);
+    mma_pure(c0, a, w0, w1);
+    mma_pure(c1, a, v0, v1);
+    silu_into(c0, j, o);
+    silu_into(c1, j + 1, o);
+  }
+}
+
+// 64 -> 64 for one tile; two output tiles (j, j + 1) at a time give two
+// independent accumulator chains, and each ldmatrix brings the B fragments of
+// two k-steps (lane L addresses row L % 8 of the tile, k offset 8 (L / 8)).
+__device__ __forceinline__ void layer64_act(const uint32_t (&a)[4][4], const unsigned char* img, int off_wt,
+                                            const float* bias, uint32_t (&o)[4][4]) {
+  const int lane = threadIdx.x & 31, t = lane & 3;
+  const unsigned char* wl = img + off_wt + (lane & 7) * STR * 2 + (lane >> 3) * 16;
+#pragma unroll
+  for (int j = 0; j < 8; j += 2) {
+    const float2 b0 = *reinterpret_cast<const float2*>(bias + 8 * j + 2 * t);
+    const float2 b1 = *reinterpret_cast<const float2*>(bias + 8 * j + 8 + 2 * t);
+    float c0[4] = {b0.x, b0.y, b0.x, b0.y}, c1[4] = {b1.x, b1.y, b1.x, b1.y};
+#pragma unroll
+    for (int s = 0; s < 4; s += 2) {
+      uint32_t w0, w1, w2, w3, v0, v1, v2, v3;
+      ldsm_x4(wl + (8 * j) * STR * 2 + s * 32, w0, w1, w2, w3);
+      ldsm_x4(wl + (8 * j + 8) * STR * 2 + s * 32, v0, v1, v2, v3);
+      mma_pure(c0, a[s], w0, w1);
+      mma_pure(c1, a[s], v0, v1);
+      mma_pure(c0, a[s + 1], w2, w3);
+      mma_pure(c1, a[s + 1], v2, v3);
+    }
+    silu_into(c0, j, o);
+    silu_into(c1, j + 1, o);
+  }
+}
+
 // The MLP for the warp's 32 points (inference: SiLU through silu2_bf16): lane
 // L's input (z0, z1, z2), its output returned. Must be called by all 32 lanes together.
 __device__ __forceinline__ float forward_warp(float z0, float z1, float z2, const unsigned char* img) {
@@ -154,18 +235,24 @@ __device__ __forceinline__ float forward_warp(float z0, float z1, float z2, cons
   float mine = 0.0f;
 #pragma unroll 1
   for (int tile = 0; tile < 2; ++tile) {
-    float c[8][4];
-    uint32_t a[4][4];
-    layer1(z0, z1, z2, tile, img, c);
-    act_pack_fast(c, a);
-    layer64(a, img, OFF_W2T, bias + 64, c);
-    act_pack_fast(c, a);
-    layer64(a, img, OFF_W3T, bias + 128, c);
-    act_pack_fast(c, a);
-    float o0, o1;
-    layer4(a, img, o0, o1);
-    const int src = (lane & 7) * 4;  // the t == 0 lane holding row (lane & 15)
-    const float v0 = __shfl_sync(0xffffffffu, o0, src), v1 = __shfl_sync(0xffffffffu, o1, src);
+    uint32_t x[4][4], y[4][4];
+    layer1_act(z0, z1, z2, tile, img, x);
+    layer64_act(x, img, OFF_W2T, bias + 64, y);
+    layer64_act(y, img, OFF_W3T, bias + 128, x);
+    // 64 -> 1 (one 8-column tile, column 0 used)
+    const float b4 = bias[192];
+    float c[4] = {b4, b4, b4, b4};
+    const unsigned char* wl = img + OFF_W4T + (lane & 7) * STR * 2 + (lane >> 3) * 16;
+#pragma unroll
+    for (int s = 0; s < 4; s += 2) {
+      uint32_t w0, w1, w2, w3;
+      ldsm_x4(wl + s * 32, w0, w1, w2, w3);
+      mma_pure(c, x[s], w0, w1);
+      mma_pure(c, x[s + 1], w2, w3);
+    }
+    // row (lane & 15) of this tile sits on lane 4 (lane & 7), in c[0] (rows 0-7) or c[2] (rows 8-15)
+    const int src = (lane & 7) * 4;
+    const float v0 = __shfl_sync(0xffffffffu, c[0], src), v1 = __shfl_sync(0xffffffffu, c[2], src);
     if ((lane >> 4) == tile) mine = ((lane & 15) < 8) ? v0 : v1;
   }
   return mine;

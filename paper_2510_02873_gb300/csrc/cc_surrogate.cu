@@ -364,7 +364,7 @@ __global__ void sur_eval_kernel(const float* __restrict__ z, int zstride, int64_
 constexpr float kCertTol = 1e-6f;  // accepted when the last Newton step is below 1e-6 D
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 collapse_sur_kernel(const T* __restrict__ hess, int64_t n, int64_t ps, int64_t rs, int R, int32_t scale_idx0,
                     DevTable tab, RadiusParams rp, SurDev sd, double* __restrict__ F_max, int32_t* __restrict__ idx,
                     DevCounters* __restrict__ cnt) {
