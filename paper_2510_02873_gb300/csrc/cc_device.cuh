@@ -263,6 +263,16 @@ __device__ __forceinline__ double recip_fp64(double a) {
 
 constexpr double kInf = __builtin_huge_val();
 
+// a(D_c) on spline interval k, or on the EdS segment below the first knot,
+// a = (a_0 / D_0) D_c, evaluated by the same Horner scheme with that segment's
+// coefficients selected in (c1 = a_0 / D_0; c0, c2, c3 and the knot 0): no
+// separate multiply is issued for the rare branch, and fma(c1, D_c, 0) rounds
+// the product once, as the multiply would.
+__device__ __forceinline__ double spline_a(const Coef4& cf, double knot, double Dc, bool eds, const DevTable& tab) {
+  const double t = Dc - (eds ? 0.0 : knot);
+  return fma(fma(fma(eds ? 0.0 : cf.c3, t, eds ? 0.0 : cf.c2), t, eds ? tab.eds_slope : cf.c1), t, eds ? 0.0 : cf.c0);
+}
+
 // Running maximum of F = 1/a_c over the radii of one launch, kept as the
 // running minimum of a_c (F is decreasing in a, so max F = 1/min a): the
 // reciprocal is taken once per point and per launch instead of once per
@@ -273,6 +283,13 @@ struct MinA {
   int r = -1;
   __device__ __forceinline__ void add(bool collapsed, double av, int radius) {
     if (collapsed && bits(av) < bits(a)) {
+      a = av;
+      r = radius;
+    }
+  }
+  // the same minimum when radii arrive out of order: ties go to the smaller radius
+  __device__ __forceinline__ void add_any_order(bool collapsed, double av, int radius) {
+    if (collapsed && (bits(av) < bits(a) || (bits(av) == bits(a) && radius < r))) {
       a = av;
       r = radius;
     }
@@ -322,11 +339,8 @@ __device__ __forceinline__ PointResult collapse_point_fp64(
   const double Dc = res.collapsed ? D : tab.Dtop;
   // ---- a(D): interval from the FP32 root, FP64 Horner
   const int k = spline_interval(Dkf, bucket, tab, res.collapsed ? rt.Df : tab.Dtopf);
-  const Coef4 cf = coef[k];
-  const double t = Dc - Dk[k];
-  double av = fma(fma(fma(cf.c3, t, cf.c2), t, cf.c1), t, cf.c0);
   res.eds = res.collapsed && bits(Dc) < bits(tab.D0);
-  if (res.eds) av = tab.eds_slope * Dc;
+  const double av = spline_a(coef[k], Dk[k], Dc, res.eds, tab);
   res.a = res.collapsed ? av : kInf;
   const double F = recip_fp64(av);
   res.F = res.collapsed ? F : 0.0;
@@ -358,17 +372,20 @@ struct MixedResult {
 
 // FP32 eigenvalue stage of the mixed path (shared with the surrogate path).
 struct MixedEigen {
-  float q, x, x2, x3, p2x3, lam1f;  // x = l1 - q (x2, x3: FP32 seeds of l2 - q, l3 - q)
-  double lam1;                      // l1, refined in FP64 when flagged
-  bool full;                        // take the whole FP64 path instead
-  bool fp64;                        // the FP64 eigenvalue refinement ran
+  float q, x, x2, x3, p2, p2x3, lam1f;  // x = l1 - q (x2, x3: FP32 seeds of l2 - q, l3 - q)
+  double lam1;                          // l1, refined in FP64 when flagged
+  bool full;                            // take the whole FP64 path instead
+  bool need64;                          // l1 needs the FP64 refinement (mixed_refine64)
+  bool fp64;                            // the FP64 eigenvalue refinement ran
 };
 
-__device__ __forceinline__ MixedEigen mixed_eigen(float xx, float yy, float zz, float xy, float xz, float yz,
-                                                  float tri_thr) {
+// The FP32 part: invariants, trigonometric eigenvalues, two FP32 Newton
+// steps, and the flags that send a point to the FP64 refinement or to the
+// whole FP64 path.
+__device__ __forceinline__ MixedEigen mixed_eigen_f32(float xx, float yy, float zz, float xy, float xz, float yz,
+                                                      float tri_thr) {
   MixedEigen m;
   m.fp64 = false;
-  // ---- FP32 invariants and trigonometric eigenvalues
   const float q = (xx + yy + zz) * (1.0f / 3.0f);
   const float a = xx - q, b = yy - q, c = zz - q;
   const float s6 = fmaf(2.0f, fmaf(yz, yz, fmaf(xz, xz, xy * xy)), fmaf(c, c, fmaf(b, b, a * a)));
@@ -389,27 +406,40 @@ __device__ __forceinline__ MixedEigen mixed_eigen(float xx, float yy, float zz, 
   }
   m.full = ((1.0f + rf) < kPairTauF && p2 > 0.0f) || (x - x3) < tri_thr;
   const float lam1f = q + x;
-  double lam1 = to_f64(lam1f);
   const float est = kMixedEstCoef * p2 * pf / fmaxf((x - x2) * (x - x3) * fabsf(lam1f), 1e-30f);
-  if (!m.full && est > kMixedEstTau) {
-    // one FP64 Newton step on g(l) = det(A - l I); g'(l) = -3 (x^2 - p^2) from FP32
-    const double dxx = to_f64(xx) - lam1, dyy = to_f64(yy) - lam1;
-    const double dzz = to_f64(zz) - lam1;
-    const double dxy = to_f64(xy), dxz = to_f64(xz), dyz = to_f64(yz);
-    const double g = fma(dxx, fma(dyy, dzz, -dyz * dyz),
-                         fma(-dxy, fma(dxy, dzz, -dyz * dxz), dxz * fma(dxy, dyz, -dyy * dxz)));
-    const float gpf = 3.0f * fmaf(x, x, -p2);
-    lam1 = fma(g, to_f64(__fdividef(1.0f, gpf)), lam1);
-    x = to_f32_trunc(lam1 - to_f64(q));
-    m.fp64 = true;
-  }
+  m.need64 = !m.full && est > kMixedEstTau;
   m.q = q;
   m.x = x;
   m.x2 = x2;
   m.x3 = x3;
+  m.p2 = p2;
   m.p2x3 = p2x3;
   m.lam1f = lam1f;
-  m.lam1 = lam1;
+  m.lam1 = to_f64(lam1f);
+  return m;
+}
+
+// One FP64 Newton step on g(l) = det(A - l I) from the FP32 l1 (g'(l) =
+// -3 (x^2 - p^2) from FP32), the FP32 entries widened to FP64 (products of
+// two FP32 numbers are exact in FP64).
+__device__ __forceinline__ void mixed_refine64(MixedEigen& m, float xx, float yy, float zz, float xy, float xz,
+                                               float yz) {
+  const double lam1 = m.lam1;
+  const double dxx = to_f64(xx) - lam1, dyy = to_f64(yy) - lam1;
+  const double dzz = to_f64(zz) - lam1;
+  const double dxy = to_f64(xy), dxz = to_f64(xz), dyz = to_f64(yz);
+  const double g = fma(dxx, fma(dyy, dzz, -dyz * dyz),
+                       fma(-dxy, fma(dxy, dzz, -dyz * dxz), dxz * fma(dxy, dyz, -dyy * dxz)));
+  const float gpf = 3.0f * fmaf(m.x, m.x, -m.p2);
+  m.lam1 = fma(g, to_f64(__fdividef(1.0f, gpf)), lam1);
+  m.x = to_f32_trunc(m.lam1 - to_f64(m.q));
+  m.fp64 = true;
+}
+
+__device__ __forceinline__ MixedEigen mixed_eigen(float xx, float yy, float zz, float xy, float xz, float yz,
+                                                  float tri_thr) {
+  MixedEigen m = mixed_eigen_f32(xx, yy, zz, xy, xz, yz, tri_thr);
+  if (m.need64) mixed_refine64(m, xx, yy, zz, xy, xz, yz);
   return m;
 }
 
@@ -458,12 +488,17 @@ __device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const M
   const long long bD = bits(D);
   res.collapsed = m.lam1f > 0.0f && bD > 0 && bD <= bits(tab.Dtop);
   const double Dc = res.collapsed ? D : tab.Dtop;
-  const int kk = spline_interval(Dkf, bucket, tab, res.collapsed ? Df : tab.Dtopf);
+  const float Dcf = res.collapsed ? Df : tab.Dtopf;
+  const int kk = spline_interval(Dkf, bucket, tab, Dcf);
   const Coef4 cf = coef[kk];
-  const double t = Dc - Dk[kk];
-  double av = fma(fma(fma(cf.c3, t, cf.c2), t, cf.c1), t, cf.c0);
   res.eds = res.collapsed && bits(Dc) < bits(tab.D0);
-  if (res.eds) av = tab.eds_slope * Dc;
+  // c2 + c3 t in FP32 (c2, c3 rounded to FP32 in the float-float image): with
+  // |t| <= h ~ 0.014 D these terms are ~1e-4 of a, so their FP32 rounding moves
+  // a by ~1e-12 relative; c0 + t (c1 + t u) in FP64 (the EdS segment as in spline_a)
+  const float2 c23 = __ldg(reinterpret_cast<const float2*>(tab.dfseg + 2 * kk + 1));
+  const float u = res.eds ? 0.0f : fmaf(c23.y, Dcf - Dkf[kk], c23.x);
+  const double t = Dc - (res.eds ? 0.0 : Dk[kk]);
+  const double av = fma(fma(to_f64(u), t, res.eds ? tab.eds_slope : cf.c1), t, res.eds ? 0.0 : cf.c0);
   res.a = res.collapsed ? av : kInf;
   res.F = res.collapsed ? to_f64(1.0f / to_f32_trunc(av)) : 0.0;
   return res;
@@ -598,9 +633,8 @@ __device__ __forceinline__ TabResult collapse_point_tab(
   res.collapsed = bits(lam1) > 0 && root && bD > 0 && bD <= bits(tab.Dtop);
   const double Dc = res.collapsed ? D : tab.Dtop;
   const int k = spline_interval(Dkf, bucket, tab, to_f32_trunc(Dc));
-  double av = horner(coef[k], Dc - Dk[k]);
   res.eds = res.collapsed && bits(Dc) < bits(tab.D0);
-  if (res.eds) av = tab.eds_slope * Dc;
+  const double av = spline_a(coef[k], Dk[k], Dc, res.eds, tab);
   res.a = res.collapsed ? av : kInf;
   res.F = res.collapsed ? recip_fp64(av) : 0.0;
   return res;

@@ -110,11 +110,8 @@ __device__ __forceinline__ Result collapse_point(double xx, double yy, double zz
   res.collapsed = bits(lam1) > 0 && bD > 0 && bD <= bits(tab.Dtop);
   const double Dc = res.collapsed ? D : tab.Dtop;
   const int kk = spline_interval(Dkf, bucket, tab, res.collapsed ? to_f32_trunc(D) : tab.Dtopf);
-  const Coef4 cf = coef[kk];
-  const double t = Dc - Dk[kk];
-  double av = fma(fma(fma(cf.c3, t, cf.c2), t, cf.c1), t, cf.c0);
   res.eds = res.collapsed && bits(Dc) < bits(tab.D0);
-  if (res.eds) av = tab.eds_slope * Dc;
+  const double av = spline_a(coef[kk], Dk[kk], Dc, res.eds, tab);
   res.a = res.collapsed ? av : kInf;
   return res;
 }

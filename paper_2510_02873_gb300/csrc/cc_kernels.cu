@@ -42,6 +42,119 @@ __device__ __forceinline__ void add_counters(DevCounters* cnt, unsigned evals, u
 
 constexpr int kModeFP64 = 0, kModeMixed = 1, kModeTab = 2, kModeF32x2 = 3, kModeExact = 4;
 
+// ---- mixed path with the hard evaluations deferred. About 0.5 % of the
+// evaluations need FP64 work beyond the polish and the spline (the FP64
+// refinement of l1, or the whole FP64 path near degeneracy); run in place,
+// one such lane makes its warp issue that FP64 code for all 32 lanes, and
+// with 32 lanes one warp in six does so at every radius. Instead the lane
+// queues (lane, radius) in shared memory and drops out of that radius; the
+// warp runs the queued evaluations 32 at a time, all lanes busy, when the
+// queue fills and after the last radius, and hands each result to the lane
+// that owns the point. The results are those of collapse_point_mixed; the
+// running minimum takes them out of radius order (ties to the smaller radius).
+constexpr int kDeferQ = 64;  // queue entries per warp: lane << 8 | radius
+
+struct MixedCounts {
+  unsigned coll = 0, eds = 0, ref = 0, fp64 = 0;
+  __device__ __forceinline__ void add(const MixedResult& res) {
+    coll += res.collapsed;
+    eds += res.eds;
+    ref += res.refined;
+    fp64 += res.fp64;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ void mixed_flush(const T* __restrict__ warp_base, int64_t plane_stride, int64_t radius_stride,
+                                            const RadiusParams& rp, const unsigned short* q, int count,
+                                            const double* __restrict__ Dk, const Coef4* __restrict__ coef,
+                                            const float* __restrict__ Dkf, const unsigned short* __restrict__ bucket,
+                                            const DevTable& tab, MinA& best, MixedCounts& cn) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  for (int base = 0; base < count; base += 32) {
+    const int i = base + lane;
+    double av = kInf;
+    int rr = -1, owner = -1, coll = 0;
+    if (i < count) {
+      const unsigned e = q[i];
+      owner = static_cast<int>(e >> 8);
+      rr = static_cast<int>(e & 255u);
+      const T* h = warp_base + owner + static_cast<int64_t>(rr) * radius_stride;
+      const float xx = ldf(h), yy = ldf(h + plane_stride), zz = ldf(h + 2 * plane_stride);
+      const float xy = ldf(h + 3 * plane_stride), xz = ldf(h + 4 * plane_stride);
+      const float yz = ldf(h + 5 * plane_stride);
+      const MixedResult res = collapse_point_mixed(xx, yy, zz, xy, xz, yz, rp.tri_thr[rr], Dk, coef, Dkf, bucket, tab);
+      cn.add(res);
+      av = res.a;
+      coll = res.collapsed;
+    }
+    const int m = min(32, count - base);
+    for (int j = 0; j < m; ++j) {
+      const int o = __shfl_sync(0xffffffffu, owner, j);
+      const double a_j = __shfl_sync(0xffffffffu, av, j);
+      const int r_j = __shfl_sync(0xffffffffu, rr, j);
+      const int c_j = __shfl_sync(0xffffffffu, coll, j);
+      if (lane == o) best.add_any_order(c_j != 0, a_j, r_j);
+    }
+  }
+  __syncwarp();
+}
+
+// All 32 lanes of the warp call this together (inactive lanes with active = false).
+template <typename T>
+__device__ __forceinline__ void mixed_point_deferred(const T* __restrict__ hess, int64_t p, bool active, int R,
+                                                     int64_t plane_stride, int64_t radius_stride,
+                                                     const RadiusParams& rp, const double* __restrict__ Dk,
+                                                     const Coef4* __restrict__ coef, const float* __restrict__ Dkf,
+                                                     const unsigned short* __restrict__ bucket, const DevTable& tab,
+                                                     unsigned short* q, MinA& best, MixedCounts& cn) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  const T* warp_base = hess + (p - lane);
+  int count = 0;  // warp-uniform
+  int r = 0;
+  // one call site of the flush (it inlines the whole FP64 path): the radius
+  // loop stops when radius r's hard lanes do not fit, the queue is run, and
+  // those lanes become the first entries of the next round
+  for (;;) {
+    unsigned pending = 0;
+    for (; r < R; ++r) {
+      bool hard = false;
+      if (active) {
+        const T* h = hess + p + static_cast<int64_t>(r) * radius_stride;
+        const float xx = ldf(h), yy = ldf(h + plane_stride), zz = ldf(h + 2 * plane_stride);
+        const float xy = ldf(h + 3 * plane_stride), xz = ldf(h + 4 * plane_stride);
+        const float yz = ldf(h + 5 * plane_stride);
+        const MixedEigen m = mixed_eigen_f32(xx, yy, zz, xy, xz, yz, rp.tri_thr[r]);
+        hard = m.full || m.need64;
+        if (!hard) {
+          const MixedCoef k = mixed_coef(m);
+          const float uf = cubic_largest_root_seed(-k.l1f, k.c2f, k.c3f);
+          const float Df = newton_f32<2>(k, __fdividef(1.0f, uf));
+          const MixedResult res = mixed_finish(m, k, Df, Dk, coef, Dkf, bucket, tab);
+          cn.add(res);
+          best.add(res.collapsed, res.a, r);
+        }
+      }
+      const unsigned hb = __ballot_sync(0xffffffffu, hard);
+      if (hb) {
+        if (count + __popc(hb) > kDeferQ) {
+          pending = hb;
+          break;
+        }
+        if (hard) q[count + __popc(hb & below)] = static_cast<unsigned short>((lane << 8) | r);
+        count += __popc(hb);
+      }
+    }
+    mixed_flush(warp_base, plane_stride, radius_stride, rp, q, count, Dk, coef, Dkf, bucket, tab, best, cn);
+    if (!pending) break;
+    if ((pending >> lane) & 1u) q[__popc(pending & below)] = static_cast<unsigned short>((lane << 8) | r);
+    count = __popc(pending);
+    ++r;
+  }
+}
+
 // One thread per point (grid-stride), all R radii of the launch in registers.
 // kMode selects collapse_point_fp64, collapse_point_mixed (FP32 bulk) or
 // collapse_point_tab (tabulated 1/D_c; its axes follow the spline table in
@@ -111,6 +224,20 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
       }
       best.store(F_max + p, idx + p, scale_idx0);
       n_eval += R;
+    } else if constexpr (kMode == kModeMixed) {
+      __shared__ unsigned short defer_q[kThreads / 32][kDeferQ];
+      MinA best;
+      MixedCounts cn;
+      mixed_point_deferred(hess, p, active, R, plane_stride, radius_stride, rp, Dk, coef, Dkf, bucket, tab,
+                           defer_q[threadIdx.x >> 5], best, cn);
+      n_coll += cn.coll;
+      n_eds += cn.eds;
+      n_ref += cn.ref;
+      n_fp64 += cn.fp64;
+      if (active) {
+        best.store<true>(F_max + p, idx + p, scale_idx0);
+        n_eval += R;
+      }
     } else if (kMode != kModeF32x2 && active) {
       MinA best;
       const T* base = hess + p;

@@ -157,3 +157,64 @@ def test_mixed_config3_full_size_sampled(ctx, tables):
     print("config3 sampled", s, st, "fp64 fraction", st["fp64_branch"] / (n * R))
     del hess
     torch.cuda.empty_cache()
+
+
+def _degenerate_matrices(rng, scales=(0.5, 2.0, 8.0)):
+    spectra = []
+    for s in scales:
+        spectra += [[s, s, s], [s, 0, 0], [s, s, -s], [s, -s, -s], [0.05 * s, 0.04 * s, -2 * s]]
+        for eps in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7):
+            spectra += [[s, s * (1 - eps), -0.4 * s], [s, 0.2 * s, 0.2 * s * (1 - eps)],
+                        [s * (1 + eps), s, s * (1 - eps)], [0.03 * s, 0.03 * s * (1 - eps), -3 * s]]
+    Ms = []
+    for lam in spectra:
+        Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        Ms.append(Q @ np.diag(lam) @ Q.T)
+    Ms = np.array(Ms)
+    return np.stack([Ms[:, 0, 0], Ms[:, 1, 1], Ms[:, 2, 2], Ms[:, 0, 1], Ms[:, 0, 2], Ms[:, 1, 2]])
+
+
+def test_mixed_deferred_queue_overflow_and_ties(ctx, tables):
+    """Warps whose lanes are mostly 'hard' (FP64 refinement or the whole FP64
+    path) at every radius: the per-warp queue of deferred evaluations fills
+    several times per point, and the same matrices at every radius make every
+    collapsing point an exact tie, which the earliest radius must win."""
+    rng = np.random.default_rng(23)
+    hard = _degenerate_matrices(rng)                      # 6 x 87
+    easy = hessgen.hessian_stack(31, 0, [1.0], 100)[0]    # 6 x 100 (FP64)
+    planes = np.concatenate([hard] * 3 + [easy] + [hard] * 3, axis=1)
+    perm = rng.permutation(planes.shape[1])
+    planes = planes[:, perm].astype(np.float32)
+    R = 12
+    stack = np.repeat(planes[None], R, axis=0)
+    F_all, fl = oracle_per_radius(tables, stack[:1])
+    F, idx, st = run_mixed(ctx, stack, [1.0] * R, plane_stride=(planes.shape[1] + 3) // 4 * 4)
+    F_ref = F_all[0]
+    amb = (fl[0] & oracle.FLAGS_AMBIGUOUS) != 0
+    edge = ((F_ref > 0) & (F_ref < 1.0 + 4 * REL_TOL_MIXED)) | ((F > 0) & (F < 1.0 + 4 * REL_TOL_MIXED))
+    ok = ~amb & ~edge
+    assert float(rel_err(F, F_ref)[ok].max()) <= REL_TOL_MIXED
+    assert np.all(idx[F > 0] == 0), "exact ties must keep the earliest radius"
+    assert np.all(idx[F == 0] == -1)
+    assert st["evaluations"] == planes.shape[1] * R
+    # the hard share is large: many deferred evaluations per warp and radius
+    assert st["fp64_branch"] > 0.15 * planes.shape[1] * R
+
+
+def test_mixed_deferred_mixed_radii(ctx, tables):
+    """Hard matrices scattered over random (point, radius) cells of a random
+    field: deferred and in-place evaluations of one point meet in the running
+    maximum out of radius order."""
+    rng = np.random.default_rng(29)
+    n, R = 3000, 9
+    sig = hessgen.sigma_schedule(R, 0.3, 5.0)
+    stack = hessgen.hessian_stack(2529, 0, sig, n, dtype=np.float32)
+    hard = _degenerate_matrices(rng).astype(np.float32)
+    cells = rng.integers(0, n * R, 2500)
+    for c, j in zip(cells, rng.integers(0, hard.shape[1], cells.size)):
+        r, p = divmod(int(c), n)
+        stack[r, :, p] = hard[:, j] * np.float32(sig[r])
+    F_all, fl = oracle_per_radius(tables, stack)
+    F, idx, st = run_mixed(ctx, stack, sig, plane_stride=n + 4)
+    s = compare_mixed(F, idx, F_all, fl)
+    print("mixed deferred, scattered hard cells", s, "fp64 fraction", st["fp64_branch"] / (n * R))
