@@ -33,6 +33,10 @@ constexpr int FWD_BYTES = OFF_B + 784;
 constexpr int OFF_W2B = FWD_BYTES;                       // [64][STR]: W2b[k][n] = W2[k][n] (backward)
 constexpr int OFF_W3B = OFF_W2B + H * STR * 2;
 constexpr int ALL_BYTES = OFF_W3B + H * STR * 2;
+// the inference image: the forward part again with W1..W3 and b1..b3 halved
+// (W4 and b4 as they are), read by the inference kernels only
+constexpr int OFF_INF = ALL_BYTES;
+constexpr int IMG_BYTES = OFF_INF + FWD_BYTES;
 static_assert(FWD_BYTES % 16 == 0 && ALL_BYTES % 16 == 0, "16-byte staging");
 
 __device__ __forceinline__ uint32_t pack(float lo, float hi) {
@@ -94,25 +98,18 @@ __device__ __forceinline__ void act_pack(const float (&c)[8][4], uint32_t (&a)[4
 
 // Inference SiLU on packed BF16 pairs: silu(v) = v sigmoid(v) = h + h tanh(h)
 // with h = v/2, one tanh.approx.bf16x2 (two results per special-function
-// instruction) and one bf16x2 FMA. The result is the BF16 A fragment either
-// way; the hardware tanh adds an error of the order of that rounding. The
-// training kernels keep the FP32 SiLU of act_pack (they need silu' as well).
-__device__ __forceinline__ uint32_t silu2_bf16(float v0, float v1) {
-  const uint32_t h = pack(0.5f * v0, 0.5f * v1);
+// instruction) and one bf16x2 FMA. The inference image holds W1..W3 and
+// b1..b3 halved (exact in BF16 and FP32, so the accumulators are exactly
+// v/2 = h): a pair costs one pack, one tanh and one FMA. The result is the
+// BF16 A fragment either way; the hardware tanh adds an error of the order of
+// that rounding. The training kernels keep the FP32 SiLU of act_pack on the
+// unscaled image (they need silu' as well).
+__device__ __forceinline__ uint32_t silu2_half(float h0, float h1) {
+  const uint32_t h = pack(h0, h1);
   uint32_t t, r;
   asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(h));
   asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(r) : "r"(h), "r"(t));
   return r;
-}
-
-__device__ __forceinline__ void act_pack_fast(const float (&c)[8][4], uint32_t (&a)[4][4]) {
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    a[s][0] = silu2_bf16(c[2 * s][0], c[2 * s][1]);
-    a[s][1] = silu2_bf16(c[2 * s][2], c[2 * s][3]);
-    a[s][2] = silu2_bf16(c[2 * s + 1][0], c[2 * s + 1][1]);
-    a[s][3] = silu2_bf16(c[2 * s + 1][2], c[2 * s + 1][3]);
-  }
 }
 
 // layer 1 (3 inputs, padded to one k16 step) for one tile; rows r0 = 16 tile + g, r1 = r0 + 8
@@ -158,8 +155,8 @@ __device__ __forceinline__ void layer4(const uint32_t (&a)[4][4], const unsigned
 // through SiLU into the next layer's A fragments as soon as its four k-steps
 // are done, so one 4-register accumulator is live instead of a layer's 32.
 __device__ __forceinline__ void silu_into(const float (&c)[4], int j, uint32_t (&a)[4][4]) {
-  a[j >> 1][(j & 1) * 2] = silu2_bf16(c[0], c[1]);
-  a[j >> 1][(j & 1) * 2 + 1] = silu2_bf16(c[2], c[3]);
+  a[j >> 1][(j & 1) * 2] = silu2_half(c[0], c[1]);
+  a[j >> 1][(j & 1) * 2 + 1] = silu2_half(c[2], c[3]);
 }
 
 // Four 8x8 BF16 matrices from shared memory in one instruction: lanes 8m..8m+7
@@ -227,7 +224,7 @@ __device__ __forceinline__ void layer64_act(const uint32_t (&a)[4][4], const uns
   }
 }
 
-// The MLP for the warp's 32 points (inference: SiLU through silu2_bf16): lane
+// The MLP for the warp's 32 points (inference image, SiLU through silu2_half): lane
 // L's input (z0, z1, z2), its output returned. Must be called by all 32 lanes together.
 __device__ __forceinline__ float forward_warp(float z0, float z1, float z2, const unsigned char* img) {
   const int lane = threadIdx.x & 31;

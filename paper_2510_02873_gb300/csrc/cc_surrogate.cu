@@ -289,29 +289,43 @@ sur_train_kernel(const float4* __restrict__ data, int64_t ntrain, uint64_t seed,
 
 // parameter i -> its places in the BF16 image
 __device__ __forceinline__ void put_image(int i, float v, unsigned char* img) {
+  // training image (unscaled) and inference image (layers 1-3 halved)
+  const bool half = i < P_W4;
   const __nv_bfloat16 b = __float2bfloat16_rn(v);
-  auto at = [&](int off) { *reinterpret_cast<__nv_bfloat16*>(img + off) = b; };
+  const __nv_bfloat16 bi = __float2bfloat16_rn(half ? 0.5f * v : v);
+  const float vi = half ? 0.5f * v : v;
+  auto at = [&](int off) {
+    *reinterpret_cast<__nv_bfloat16*>(img + off) = b;
+  };
+  auto at_fwd = [&](int off) {
+    *reinterpret_cast<__nv_bfloat16*>(img + off) = b;
+    *reinterpret_cast<__nv_bfloat16*>(img + OFF_INF + off) = bi;
+  };
+  auto bias = [&](int k) {
+    reinterpret_cast<float*>(img + OFF_B)[k] = v;
+    reinterpret_cast<float*>(img + OFF_INF + OFF_B)[k] = vi;
+  };
   if (i < P_B1) {
     const int k = i / H, n = i % H;
-    at(OFF_W1T + (n * STR1 + k) * 2);
+    at_fwd(OFF_W1T + (n * STR1 + k) * 2);
   } else if (i < P_W2) {
-    reinterpret_cast<float*>(img + OFF_B)[i - P_B1] = v;
+    bias(i - P_B1);
   } else if (i < P_B2) {
     const int k = (i - P_W2) / H, n = (i - P_W2) % H;
-    at(OFF_W2T + (n * STR + k) * 2);
+    at_fwd(OFF_W2T + (n * STR + k) * 2);
     at(OFF_W2B + (k * STR + n) * 2);
   } else if (i < P_W3) {
-    reinterpret_cast<float*>(img + OFF_B)[64 + i - P_B2] = v;
+    bias(64 + i - P_B2);
   } else if (i < P_B3) {
     const int k = (i - P_W3) / H, n = (i - P_W3) % H;
-    at(OFF_W3T + (n * STR + k) * 2);
+    at_fwd(OFF_W3T + (n * STR + k) * 2);
     at(OFF_W3B + (k * STR + n) * 2);
   } else if (i < P_W4) {
-    reinterpret_cast<float*>(img + OFF_B)[128 + i - P_B3] = v;
+    bias(128 + i - P_B3);
   } else if (i < P_B4) {
-    at(OFF_W4T + (i - P_W4) * 2);
+    at_fwd(OFF_W4T + (i - P_W4) * 2);
   } else {
-    reinterpret_cast<float*>(img + OFF_B)[192] = v;
+    bias(192);
   }
 }
 
@@ -341,7 +355,7 @@ __global__ void sur_adam_kernel(float* __restrict__ p, float* __restrict__ m, fl
 __global__ void sur_eval_kernel(const float* __restrict__ z, int zstride, int64_t n, const unsigned char* __restrict__ img_g,
                                 float* __restrict__ out, float* __restrict__ sumsq, int* __restrict__ maxerr) {
   extern __shared__ __align__(16) unsigned char sm[];
-  stage(sm, img_g, FWD_BYTES);
+  stage(sm, img_g + OFF_INF, FWD_BYTES);
   __syncthreads();
   const int64_t n_round = (n + 31) & ~static_cast<int64_t>(31);
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n_round;
@@ -379,7 +393,7 @@ collapse_sur_kernel(const T* __restrict__ hess, int64_t n, int64_t ps, int64_t r
     if (threadIdx.x < tail)
       reinterpret_cast<unsigned char*>(dst + words)[threadIdx.x] = reinterpret_cast<const unsigned char*>(src + words)[threadIdx.x];
   }
-  stage(sm + tb, sd.img, FWD_BYTES);
+  stage(sm + tb, sd.img + OFF_INF, FWD_BYTES);
   __syncthreads();
   const Coef4* coef = reinterpret_cast<const Coef4*>(sm);
   const double* Dk = reinterpret_cast<const double*>(coef + (tab.n - 1));
@@ -473,11 +487,11 @@ struct SurState {
 
 int ensure_surrogate(cc_ctx* ctx) {
   if (ctx->d_mlp_img) return CC_OK;
-  if (int rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&ctx->d_mlp_img), ALL_BYTES), "cudaMalloc(mlp image)")) return rc;
+  if (int rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&ctx->d_mlp_img), IMG_BYTES), "cudaMalloc(mlp image)")) return rc;
   if (int rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&ctx->d_mlp_param), sizeof(float) * (4 * NPARAM + 8)),
                           "cudaMalloc(mlp params)"))
     return rc;
-  if (int rc = check_cuda(cudaMemset(ctx->d_mlp_img, 0, ALL_BYTES), "cudaMemset")) return rc;
+  if (int rc = check_cuda(cudaMemset(ctx->d_mlp_img, 0, IMG_BYTES), "cudaMemset")) return rc;
   return check_cuda(cudaMemset(ctx->d_mlp_param, 0, sizeof(float) * (4 * NPARAM + 8)), "cudaMemset");
 }
 
