@@ -156,11 +156,13 @@ __device__ __forceinline__ void mixed_point_deferred(const T* __restrict__ hess,
 }
 
 // One thread per point (grid-stride), all R radii of the launch in registers.
-// kMode selects collapse_point_fp64, collapse_point_mixed (FP32 bulk) or
-// collapse_point_tab (tabulated 1/D_c; its axes follow the spline table in
-// shared memory).
+// kMode selects collapse_point_fp64, the mixed path (FP32 bulk, its rare
+// FP64-heavy evaluations deferred through mixed_point_deferred), the
+// float-float path (dfl::collapse_point), the exact-growth path
+// (exact::collapse_point) or collapse_point_tab (tabulated 1/D_c; its axes
+// follow the spline table in shared memory).
 // FP64 and mixed: 64 registers, 4 blocks of 256 threads per SM (measured
-// faster than 3 blocks at 69-72 registers for the mixed path, equal for FP64);
+// faster than 3 blocks at 69-85 registers for the mixed path, equal for FP64);
 // the tabulated path keeps its 98 registers.
 template <typename T, bool kSmem, int kMode>
 __global__ void __launch_bounds__(kThreads, kMode == 2 ? 1 : 4)
