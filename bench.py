@@ -543,17 +543,20 @@ def run_surrogate_variant(ctx, dev, stream, steps: int = 3000) -> dict:
     sig = hessgen.sigma_schedule(R, S_LO, S_HI)
     planes = torch.empty((6, n), dtype=torch.float32, device=dev)
     outs = {m: (torch.zeros(n, dtype=torch.float64, device=dev), torch.full((n,), -1, dtype=torch.int32, device=dev))
-            for m in ("surrogate", "mixed", "fp64")}
+            for m in ("surrogate", "surrogate_tcgen05", "mixed", "fp64")}
     ms = {m: 0.0 for m in outs}
-    stats = {m: {"evaluations": 0, "fallback": 0, "fp64_branch": 0} for m in outs}
+    stats = {m: {"evaluations": 0, "fallback": 0, "fp64_branch": 0, "error_flags": 0} for m in outs}
     for r in range(R):
         hdev.fill(planes, SEED + 6, 0, r, sig[r])
         for m, (F, idx) in outs.items():
             ctx.reset_stats()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if m == "surrogate_tcgen05":
+                ctx.set_surrogate_engine("tcgen05")
             e0.record(stream)
-            ctx.collapse_scale(planes, sig[r], F, idx, r, mode=m)
+            ctx.collapse_scale(planes, sig[r], F, idx, r, mode=m.split("_")[0])
             e1.record(stream)
+            ctx.set_surrogate_engine("mma_sync")
             torch.cuda.synchronize()
             ms[m] += e0.elapsed_time(e1)
             st = ctx.stats()
@@ -568,6 +571,7 @@ def run_surrogate_variant(ctx, dev, stream, steps: int = 3000) -> dict:
 
     s_max, s_rms = rel(Fs, F64)
     x_max, x_rms = rel(Fx, F64)
+    t_max, _ = rel(outs["surrogate_tcgen05"][0], F64)
     evals = float(n) * R
     del planes, outs
     torch.cuda.empty_cache()
@@ -575,6 +579,12 @@ def run_surrogate_variant(ctx, dev, stream, steps: int = 3000) -> dict:
         "workload": f"{SUR_GRID}^3 grid x {SUR_RADII} radii, FP32 planes streamed per radius (10.9 GB each)",
         "train": {**rep, "seconds": train_s, "steps": steps, "batch": 16384},
         "evals_per_s": evals / (ms["surrogate"] * 1e-3),
+        "engine": "mma_sync",
+        "tcgen05_engine": {"evals_per_s": evals / (ms["surrogate_tcgen05"] * 1e-3),
+                           "max_rel_diff_vs_fp64": t_max,
+                           "fallback_fraction": stats["surrogate_tcgen05"]["fallback"]
+                           / stats["surrogate_tcgen05"]["evaluations"],
+                           "error_flags": stats["surrogate_tcgen05"]["error_flags"]},
         "mixed_evals_per_s": evals / (ms["mixed"] * 1e-3),
         "fp64_evals_per_s": evals / (ms["fp64"] * 1e-3),
         "gain_over_method_without_network": ms["mixed"] / ms["surrogate"],

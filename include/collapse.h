@@ -101,8 +101,9 @@ typedef struct {
   uint64_t refined;       /* eigenvalue pairs re-solved by deflation (near-degenerate pair) */
   uint64_t fp64_branch;   /* MIXED: points re-evaluated in FP64                             */
   uint64_t fallback;      /* SURROGATE: points sent to the exact path                       */
-  uint32_t error_flags;   /* device-side error bits; 0 (no kernel of this build waits on the
-                           * device or can leave its index range)                           */
+  uint32_t error_flags;   /* device-side error bits: 1 = a bounded wait for tensor-core
+                           * completion ran out in the CC_SURROGATE_TCGEN05 kernel (that
+                           * launch's results are incomplete); 0 otherwise                   */
   uint32_t reserved;
 } cc_stats;
 
@@ -257,6 +258,18 @@ CC_API int cc_surrogate_params(const cc_ctx *ctx, float *params, float *hull);
 
 /* Install a surrogate from host parameters and hull (layout as above). */
 CC_API int cc_load_surrogate(cc_ctx *ctx, const float *params, const float *hull);
+
+/* Kernel that runs CC_MODE_SURROGATE. Both evaluate the same network with
+ * BF16 operands and FP32 accumulation, and both results meet the mixed path's
+ * tolerance; they differ in how the MMAs are issued:
+ *   CC_SURROGATE_MMA_SYNC (default): warp-level mma.sync m16n8k16, 32 points
+ *     per warp as two 16-row tiles, activations chained in registers;
+ *   CC_SURROGATE_TCGEN05: fifth-generation tensor cores, one M = 128 tile of
+ *     points per CTA, accumulators in tensor memory, weights staged by a
+ *     bulk copy, each layer's bias carried by two extra K columns.
+ * Returns CC_EINVAL for another value. */
+typedef enum { CC_SURROGATE_MMA_SYNC = 0, CC_SURROGATE_TCGEN05 = 1 } cc_surrogate_engine;
+CC_API int cc_set_surrogate_engine(cc_ctx *ctx, int32_t engine);
 
 /* f(z) for n device inputs z (n x 3) into out (device), on the tensor-core path. */
 CC_API int cc_surrogate_eval(cc_ctx *ctx, const float *z, int64_t n, float *out, void *stream);

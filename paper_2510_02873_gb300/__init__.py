@@ -335,6 +335,15 @@ class Context:
             raise ValueError("params must have 8641 entries and hull 6")
         _lib.check(_lib.load().cc_load_surrogate(self._h, params.ctypes.data, hull.ctypes.data), "cc_load_surrogate")
 
+    SURROGATE_ENGINES = {"mma_sync": 0, "tcgen05": 1}
+
+    def set_surrogate_engine(self, engine: str):
+        """Kernel for mode="surrogate": "mma_sync" (default) or "tcgen05"."""
+        if engine not in self.SURROGATE_ENGINES:
+            raise ValueError(f"engine must be one of {sorted(self.SURROGATE_ENGINES)}")
+        _lib.check(_lib.load().cc_set_surrogate_engine(self._h, self.SURROGATE_ENGINES[engine]),
+                   "cc_set_surrogate_engine")
+
     def surrogate_eval(self, z, out, stream=None):
         """z: float32 CUDA tensor (n, 3); out: float32 CUDA tensor (n,)."""
         _lib.check(_lib.load().cc_surrogate_eval(self._h, z.data_ptr(), z.shape[0], out.data_ptr(),

@@ -18,6 +18,7 @@ EXPORTS = (
     "cc_last_error_message", "cc_version", "cc_batch_create", "cc_batch_autotune", "cc_batch_run",
     "cc_batch_run_graph", "cc_batch_get_config", "cc_batch_destroy", "cc_set_table", "cc_table_nodes_rlpt",
     "cc_table_query", "cc_spline_eval", "cc_surrogate_train", "cc_surrogate_params", "cc_load_surrogate",
+    "cc_set_surrogate_engine",
     "cc_surrogate_eval", "cc_surrogate_grad", "cc_histogram", "cc_field_create", "cc_field_sigma",
     "cc_field_hessian", "cc_field_destroy",
 )
@@ -129,6 +130,7 @@ def load() -> ctypes.CDLL:
                                          ctypes.POINTER(CcTrainReport), vp]
         L.cc_surrogate_params.argtypes = [vp, vp, vp]
         L.cc_load_surrogate.argtypes = [vp, vp, vp]
+        L.cc_set_surrogate_engine.argtypes = [vp, i32]
         L.cc_surrogate_eval.argtypes = [vp, vp, i64, vp, vp]
         L.cc_surrogate_grad.argtypes = [vp, vp, vp, i32, vp, vp]
         L.cc_reset_stats.argtypes = [vp, vp]
@@ -143,7 +145,7 @@ def load() -> ctypes.CDLL:
                      "cc_batch_run", "cc_batch_run_graph", "cc_batch_get_config", "cc_set_table",
                      "cc_table_nodes_rlpt", "cc_table_query", "cc_spline_eval", "cc_surrogate_train",
                      "cc_surrogate_params", "cc_load_surrogate", "cc_surrogate_eval", "cc_surrogate_grad",
-                     "cc_histogram", "cc_field_create", "cc_field_sigma", "cc_field_hessian"):
+                     "cc_set_surrogate_engine", "cc_histogram", "cc_field_create", "cc_field_sigma", "cc_field_hessian"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L

@@ -17,6 +17,7 @@
 
 #include "cc_device.cuh"
 #include "cc_mlp.cuh"
+#include "cc_umma.cuh"
 
 namespace cc {
 namespace {
@@ -35,6 +36,33 @@ struct WarpScratch {
 };
 constexpr int kGradBytes = ((NPARAM * 4 + 15) / 16) * 16;
 constexpr size_t kTrainSmem = ALL_BYTES + kGradBytes + sizeof(WarpScratch) * kTrainWarps;
+
+// ---- image of the network for the tensor-memory kernel (collapse_sur_tc_kernel):
+// the four weight matrices as MMA B operands (N rows = output units, K
+// columns), K-major core-matrix layout (cc_umma.cuh). Layers 1-3 are halved
+// (their accumulators are then h = v / 2, see silu2_half); each layer's bias
+// rides on two extra K columns, hi = RN_bf16(b) and lo = RN_bf16(b - hi),
+// which meet two columns of ones in the activation tile.
+namespace tc {
+constexpr int kRows = 128;                          // tile rows = threads = tensor-memory lanes
+constexpr int kKA = 80;                             // activation tile: 64 units | 1 | 1 | 14 zeros
+constexpr int kSboA = 16 * kKA;                     // row-group stride of K = 80 operands
+constexpr int kSbo1 = 16 * 16;                      // of the K = 16 first layer
+constexpr int kW1 = 0;                              // 64 x 16: W1^T / 2, b1 / 2 at k = 3, 4
+constexpr int kW2 = kW1 + 64 * 16 * 2;              // 64 x 80: W2^T / 2, b2 / 2 at k = 64, 65
+constexpr int kW3 = kW2 + 64 * kKA * 2;             // 64 x 80
+constexpr int kW4 = kW3 + 64 * kKA * 2;             // 16 x 80: row 0 = W4, b4 at k = 64, 65
+constexpr int kImgBytes = kW4 + 16 * kKA * 2;
+constexpr int kA = kImgBytes;                       // the activation tile follows in shared memory
+constexpr int kSmemBytes = kA + kRows * kKA * 2;
+constexpr int kTmemCols = 64;
+constexpr int kWaitTries = 1 << 22;                 // polls of an mbarrier before giving up
+constexpr unsigned kErrWait = 1u;                   // DevCounters::error_flags bit
+constexpr int kCtasPerSm = 4;                       // 46.7 KB shared memory, 64 TMEM columns, 128 registers
+constexpr int OFF_TC = IMG_BYTES;                   // in the global image
+constexpr int IMG_TOTAL = OFF_TC + kImgBytes;
+static_assert(OFF_TC % 16 == 0 && kImgBytes % 16 == 0, "bulk copy alignment");
+}  // namespace tc
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {  // splitmix64 finaliser
   x += 0x9E3779B97F4A7C15ull;
@@ -288,7 +316,37 @@ sur_train_kernel(const float4* __restrict__ data, int64_t ntrain, uint64_t seed,
 }
 
 // parameter i -> its places in the BF16 image
+// the tensor-memory kernel's image (tc namespace): weight (n, k) of the
+// operand at byte base, and a bias as its hi and lo halves at k and k + 1
+__device__ __forceinline__ void put_tc(unsigned char* tci, int base, int sbo, int n, int k, float v) {
+  *reinterpret_cast<__nv_bfloat16*>(tci + base + umma::offset(n, k, sbo)) = __float2bfloat16_rn(v);
+}
+__device__ __forceinline__ void put_tc_bias(unsigned char* tci, int base, int sbo, int n, int k, float v) {
+  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+  *reinterpret_cast<__nv_bfloat16*>(tci + base + umma::offset(n, k, sbo)) = hi;
+  *reinterpret_cast<__nv_bfloat16*>(tci + base + umma::offset(n, k + 1, sbo)) =
+      __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
 __device__ __forceinline__ void put_image(int i, float v, unsigned char* img) {
+  unsigned char* tci = img + tc::OFF_TC;
+  if (i < P_B1) {
+    put_tc(tci, tc::kW1, tc::kSbo1, i % H, i / H, 0.5f * v);
+  } else if (i < P_W2) {
+    put_tc_bias(tci, tc::kW1, tc::kSbo1, i - P_B1, 3, 0.5f * v);
+  } else if (i < P_B2) {
+    put_tc(tci, tc::kW2, tc::kSboA, (i - P_W2) % H, (i - P_W2) / H, 0.5f * v);
+  } else if (i < P_W3) {
+    put_tc_bias(tci, tc::kW2, tc::kSboA, i - P_B2, 64, 0.5f * v);
+  } else if (i < P_B3) {
+    put_tc(tci, tc::kW3, tc::kSboA, (i - P_W3) % H, (i - P_W3) / H, 0.5f * v);
+  } else if (i < P_W4) {
+    put_tc_bias(tci, tc::kW3, tc::kSboA, i - P_B3, 64, 0.5f * v);
+  } else if (i < P_B4) {
+    put_tc(tci, tc::kW4, tc::kSboA, 0, i - P_W4, v);
+  } else {
+    put_tc_bias(tci, tc::kW4, tc::kSboA, 0, 64, v);
+  }
   // training image (unscaled) and inference image (layers 1-3 halved)
   const bool half = i < P_W4;
   const __nv_bfloat16 b = __float2bfloat16_rn(v);
@@ -373,9 +431,67 @@ __global__ void sur_eval_kernel(const float* __restrict__ z, int zstride, int64_
   }
 }
 
-// ---- inference: CC_MODE_SURROGATE collapse kernel. All lanes of a warp stay in
-// the loops so that the warp-wide MLP sees 32 rows every radius.
+// ---- inference: CC_MODE_SURROGATE collapse kernels.
 constexpr float kCertTol = 1e-6f;  // accepted when the last Newton step is below 1e-6 D
+
+// From the FP32 eigen stage and the network's output f = log(D sigma): three
+// FP32 Newton steps from D = exp(f) / sigma, accepted when the residual
+// certificate holds (and the input lies in the training hull), then the FP64
+// polish and spline of the mixed path; the exact FP64 path otherwise.
+__device__ __forceinline__ MixedResult sur_finish(const MixedEigen& m, float f, float is, bool inside, float xx,
+                                                  float yy, float zz, float xy, float xz, float yz,
+                                                  const double* __restrict__ Dk, const Coef4* __restrict__ coef,
+                                                  const float* __restrict__ Dkf,
+                                                  const unsigned short* __restrict__ bucket, const DevTable& tab,
+                                                  unsigned& n_fb) {
+  MixedResult res;
+  if (m.full) {
+    res = full_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
+  } else if (!(m.lam1f > 0.0f)) {
+    res.F = 0.0;
+    res.a = kInf;
+    res.collapsed = res.eds = res.refined = false;
+    res.fp64 = m.fp64;
+  } else {
+    const MixedCoef k = mixed_coef(m);
+    bool ok = inside;
+    float Df = 0.0f;
+    if (ok) {
+      Df = newton_f32<3>(k, __expf(f) * is);
+      const float Af = fmaf(fmaf(fmaf(k.c3f, Df, k.c2f), Df, -k.l1f), Df, 1.0f);
+      const float dAf = fmaf(fmaf(3.0f * k.c3f, Df, 2.0f * k.c2f), Df, -k.l1f);
+      ok = Df > 0.0f && isfinite(Df) && fabsf(Af) <= kCertTol * fabsf(dAf * Df);
+    }
+    if (ok) {
+      res = mixed_finish(m, k, Df, Dk, coef, Dkf, bucket, tab);
+    } else {
+      res = full_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
+      ++n_fb;
+    }
+  }
+  return res;
+}
+
+__device__ __forceinline__ void sur_counters(DevCounters* cnt, unsigned n_eval, unsigned n_coll, unsigned n_eds,
+                                             unsigned n_ref, unsigned n_fp64, unsigned n_fb) {
+  n_eval = __reduce_add_sync(0xffffffffu, n_eval);
+  n_coll = __reduce_add_sync(0xffffffffu, n_coll);
+  n_eds = __reduce_add_sync(0xffffffffu, n_eds);
+  n_ref = __reduce_add_sync(0xffffffffu, n_ref);
+  n_fp64 = __reduce_add_sync(0xffffffffu, n_fp64);
+  n_fb = __reduce_add_sync(0xffffffffu, n_fb);
+  if ((threadIdx.x & 31) == 0) {
+    if (n_eval) atomicAdd(&cnt->evaluations, static_cast<unsigned long long>(n_eval));
+    if (n_coll) atomicAdd(&cnt->collapsed, static_cast<unsigned long long>(n_coll));
+    if (n_eds) atomicAdd(&cnt->eds_branch, static_cast<unsigned long long>(n_eds));
+    if (n_ref) atomicAdd(&cnt->refined, static_cast<unsigned long long>(n_ref));
+    if (n_fp64) atomicAdd(&cnt->fp64_branch, static_cast<unsigned long long>(n_fp64));
+    if (n_fb) atomicAdd(&cnt->fallback, static_cast<unsigned long long>(n_fb));
+  }
+}
+
+// The warp-level form: mma.sync m16n8k16 on register fragments. All lanes of
+// a warp stay in the loops so that the warp-wide MLP sees 32 rows every radius.
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 3)
@@ -423,31 +539,7 @@ collapse_sur_kernel(const T* __restrict__ hess, int64_t n, int64_t ps, int64_t r
       __syncwarp();
       const float f = mlp::forward_warp(z0, z1, z2, img);
       if (!active) continue;
-      MixedResult res;
-      if (m.full) {
-        res = full_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
-      } else if (!(m.lam1f > 0.0f)) {
-        res.F = 0.0;
-        res.a = kInf;
-        res.collapsed = res.eds = res.refined = false;
-        res.fp64 = m.fp64;
-      } else {
-        const MixedCoef k = mixed_coef(m);
-        bool ok = inside;
-        float Df = 0.0f;
-        if (ok) {
-          Df = newton_f32<3>(k, __expf(f) * is);
-          const float Af = fmaf(fmaf(fmaf(k.c3f, Df, k.c2f), Df, -k.l1f), Df, 1.0f);
-          const float dAf = fmaf(fmaf(3.0f * k.c3f, Df, 2.0f * k.c2f), Df, -k.l1f);
-          ok = Df > 0.0f && isfinite(Df) && fabsf(Af) <= kCertTol * fabsf(dAf * Df);
-        }
-        if (ok) {
-          res = mixed_finish(m, k, Df, Dk, coef, Dkf, bucket, tab);
-        } else {
-          res = full_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
-          ++n_fb;
-        }
-      }
+      const MixedResult res = sur_finish(m, f, is, inside, xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab, n_fb);
       n_coll += res.collapsed;
       n_eds += res.eds;
       n_ref += res.refined;
@@ -459,20 +551,157 @@ collapse_sur_kernel(const T* __restrict__ hess, int64_t n, int64_t ps, int64_t r
       n_eval += R;
     }
   }
-  n_eval = __reduce_add_sync(0xffffffffu, n_eval);
-  n_coll = __reduce_add_sync(0xffffffffu, n_coll);
-  n_eds = __reduce_add_sync(0xffffffffu, n_eds);
-  n_ref = __reduce_add_sync(0xffffffffu, n_ref);
-  n_fp64 = __reduce_add_sync(0xffffffffu, n_fp64);
-  n_fb = __reduce_add_sync(0xffffffffu, n_fb);
-  if ((threadIdx.x & 31) == 0) {
-    if (n_eval) atomicAdd(&cnt->evaluations, static_cast<unsigned long long>(n_eval));
-    if (n_coll) atomicAdd(&cnt->collapsed, static_cast<unsigned long long>(n_coll));
-    if (n_eds) atomicAdd(&cnt->eds_branch, static_cast<unsigned long long>(n_eds));
-    if (n_ref) atomicAdd(&cnt->refined, static_cast<unsigned long long>(n_ref));
-    if (n_fp64) atomicAdd(&cnt->fp64_branch, static_cast<unsigned long long>(n_fp64));
-    if (n_fb) atomicAdd(&cnt->fallback, static_cast<unsigned long long>(n_fb));
+  sur_counters(cnt, n_eval, n_coll, n_eds, n_ref, n_fp64, n_fb);
+}
+
+// The tensor-memory form (tcgen05). A CTA of 128 threads owns a tile of 128
+// consecutive points, thread i the point tile * 128 + i, for all the radii of
+// the launch. Per radius each thread writes its point's network input as row
+// i of the activation tile in shared memory; one thread issues the layer's
+// M = 128 MMAs (K = 16 for layer 1, 80 for the others, N = 64, or 16 for the
+// last layer) into a 64-column accumulator in tensor memory and commits them
+// to an mbarrier; every thread then loads its row of the accumulator
+// (tcgen05.ld, lane = row), applies SiLU and writes the row back as the next
+// layer's input. The weights arrive once per CTA by one bulk copy; the bias of
+// every layer is an extra pair of K columns (hi, lo) against two columns of
+// ones, so the accumulators need no initialisation and the epilogue no adds.
+// Five CTAs (45 KB shared memory, 64 tensor-memory columns each) share an SM,
+// so one CTA's SiLU and FP32 work overlap the others' MMAs. Every mbarrier
+// wait is bounded; a wait that runs out stops the CTA and sets an error bit.
+template <typename T>
+__global__ void __launch_bounds__(tc::kRows, tc::kCtasPerSm)
+collapse_sur_tc_kernel(const T* __restrict__ hess, int64_t n, int64_t ps, int64_t rs, int R, int32_t scale_idx0,
+                       DevTable tab, RadiusParams rp, SurDev sd, double* __restrict__ F_max,
+                       int32_t* __restrict__ idx, DevCounters* __restrict__ cnt) {
+  using namespace tc;
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ __align__(8) uint64_t bar_ld, bar_mma;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  unsigned char* sA = sm + kA;
+  if (tid == 0) {
+    umma::mbar_init(&bar_ld, 1);
+    umma::mbar_init(&bar_mma, 1);
   }
+  __syncwarp();
+  if (warp == 0) umma::tmem_alloc<kTmemCols>(&tmem_slot);
+  // the constant columns of this thread's activation row: 64, 65 = 1 (bias hi, lo), 66..79 = 0
+  *reinterpret_cast<uint4*>(sA + umma::offset(tid, 64, kSboA)) = make_uint4(pack(1.0f, 1.0f), 0u, 0u, 0u);
+  *reinterpret_cast<uint4*>(sA + umma::offset(tid, 72, kSboA)) = make_uint4(0u, 0u, 0u, 0u);
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  if (tid == 0) umma::bulk_load(sm, sd.img + OFF_TC, kImgBytes, &bar_ld);
+  int bad = umma::mbar_wait(&bar_ld, 0, kWaitTries) ? 0 : 1;
+  const uint32_t tmem = tmem_slot;
+  const uint32_t trow = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+  const uint32_t aA = umma::smem_addr(sA), aW = umma::smem_addr(sm);
+  constexpr uint32_t kIdesc64 = umma::idesc_bf16_f32(kRows, 64), kIdesc16 = umma::idesc_bf16_f32(kRows, 16);
+  uint32_t phase = 0;
+  unsigned n_eval = 0, n_coll = 0, n_eds = 0, n_ref = 0, n_fp64 = 0, n_fb = 0;
+  const int64_t ntiles = (n + kRows - 1) / kRows;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    bad = __syncthreads_or(bad);
+    if (bad) break;
+    const int64_t p = tile * kRows + tid;
+    const bool active = p < n;
+    MinA best;
+    const T* base = hess + (active ? p : 0);
+    for (int r = 0; r < R; ++r) {
+      const T* h = base + static_cast<int64_t>(r) * rs;
+      float xx = 0.f, yy = 0.f, zz = 0.f, xy = 0.f, xz = 0.f, yz = 0.f;
+      if (active) {
+        xx = static_cast<float>(__ldg(h)); yy = static_cast<float>(__ldg(h + ps));
+        zz = static_cast<float>(__ldg(h + 2 * ps)); xy = static_cast<float>(__ldg(h + 3 * ps));
+        xz = static_cast<float>(__ldg(h + 4 * ps)); yz = static_cast<float>(__ldg(h + 5 * ps));
+      }
+      const MixedEigen m = mixed_eigen(xx, yy, zz, xy, xz, yz, rp.tri_thr[r]);
+      const float is = rp.inv_sigma[r];
+      const float z0 = m.lam1f * is, z1 = (m.q + m.x2) * is, z2 = (m.q + m.x3) * is;
+      const bool inside = z0 >= sd.lo[0] && z0 <= sd.hi[0] && z1 >= sd.lo[1] && z1 <= sd.hi[1] &&
+                          z2 >= sd.lo[2] && z2 <= sd.hi[2];
+      // layer-1 input row: z0 z1 z2, ones at k = 3, 4 (bias hi, lo), zeros to k = 15
+      *reinterpret_cast<uint4*>(sA + umma::offset(tid, 0, kSboA)) =
+          make_uint4(pack(z0, z1), pack(z2, 1.0f), pack(1.0f, 0.0f), 0u);
+      *reinterpret_cast<uint4*>(sA + umma::offset(tid, 8, kSboA)) = make_uint4(0u, 0u, 0u, 0u);
+      float f = 0.0f;
+#pragma unroll
+      for (int layer = 0; layer < 4; ++layer) {
+        // the rows written by every thread (generic proxy) become MMA operands (async proxy)
+        umma::fence_smem_async();
+        umma::fence_before_sync();
+        bad = __syncthreads_or(bad);
+        umma::fence_after_sync();
+        if (bad) break;
+        if (tid == 0) {
+          if (layer == 0) {
+            umma::mma_bf16(tmem, umma::desc(aA, 128, kSboA), umma::desc(aW + kW1, 128, kSbo1), kIdesc64, false);
+          } else {
+            const uint32_t w = aW + (layer == 1 ? kW2 : layer == 2 ? kW3 : kW4);
+#pragma unroll
+            for (int s = 0; s < kKA / 16; ++s)
+              umma::mma_bf16(tmem, umma::desc(aA + 256 * s, 128, kSboA), umma::desc(w + 256 * s, 128, kSboA),
+                             layer == 3 ? kIdesc16 : kIdesc64, s > 0);
+          }
+          umma::commit(&bar_mma);
+        }
+        // every thread watches the mbarrier (measured faster than one warp
+        // watching and a CTA barrier releasing the others)
+        if (!umma::mbar_wait(&bar_mma, phase, kWaitTries)) bad = 1;
+        phase ^= 1u;
+        __syncwarp();
+        umma::fence_after_sync();
+        if (layer < 3) {
+          // h = (pre-activation) / 2 of this thread's 64 units -> SiLU -> next input row
+#pragma unroll
+          for (int c0 = 0; c0 < 64; c0 += 32) {
+            uint32_t v0[16], v1[16];
+            umma::ld16(trow + c0, v0);
+            umma::ld16(trow + c0 + 16, v1);
+            umma::wait_ld();
+            uint32_t w[16];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              w[j] = silu2_half(__uint_as_float(v0[2 * j]), __uint_as_float(v0[2 * j + 1]));
+              w[8 + j] = silu2_half(__uint_as_float(v1[2 * j]), __uint_as_float(v1[2 * j + 1]));
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              *reinterpret_cast<uint4*>(sA + umma::offset(tid, c0 + 8 * q, kSboA)) =
+                  make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+          }
+        } else {
+          f = __uint_as_float(umma::ld1(trow));
+          umma::wait_ld();
+        }
+        // this thread's accumulator loads are complete before the next MMA overwrites them
+        umma::fence_before_sync();
+      }
+      bad = __syncthreads_or(bad);
+      if (bad) break;
+      if (!active) continue;
+      const MixedResult res =
+          sur_finish(m, f, is, inside, xx, yy, zz, xy, xz, yz, tab.D, tab.coef, tab.Df, tab.bucket, tab, n_fb);
+      n_coll += res.collapsed;
+      n_eds += res.eds;
+      n_ref += res.refined;
+      n_fp64 += res.fp64;
+      best.add(res.collapsed, res.a, r);
+    }
+    if (bad) break;
+    if (active) {
+      best.store<true>(F_max + p, idx + p, scale_idx0);
+      n_eval += R;
+    }
+  }
+  sur_counters(cnt, n_eval, n_coll, n_eds, n_ref, n_fp64, n_fb);
+  if (bad && tid == 0) atomicOr(&cnt->error_flags, kErrWait);
+  // every tensor-memory load of the CTA has completed and every MMA was waited
+  // for (or the CTA gave up on it): the tensor memory can go
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  if (warp == 0) umma::tmem_free<kTmemCols>(tmem);
 }
 
 int launch_grid(int64_t n, int threads, int cap) {
@@ -487,11 +716,11 @@ struct SurState {
 
 int ensure_surrogate(cc_ctx* ctx) {
   if (ctx->d_mlp_img) return CC_OK;
-  if (int rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&ctx->d_mlp_img), IMG_BYTES), "cudaMalloc(mlp image)")) return rc;
+  if (int rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&ctx->d_mlp_img), tc::IMG_TOTAL), "cudaMalloc(mlp image)")) return rc;
   if (int rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&ctx->d_mlp_param), sizeof(float) * (4 * NPARAM + 8)),
                           "cudaMalloc(mlp params)"))
     return rc;
-  if (int rc = check_cuda(cudaMemset(ctx->d_mlp_img, 0, IMG_BYTES), "cudaMemset")) return rc;
+  if (int rc = check_cuda(cudaMemset(ctx->d_mlp_img, 0, tc::IMG_TOTAL), "cudaMemset")) return rc;
   return check_cuda(cudaMemset(ctx->d_mlp_param, 0, sizeof(float) * (4 * NPARAM + 8)), "cudaMemset");
 }
 
@@ -516,6 +745,27 @@ void init_params(std::vector<float>& p, uint64_t seed, float b4) {
 
 template <typename T>
 int launch_sur_typed(cc_ctx* ctx, const LaunchArgs& a, const RadiusParams& rp) {
+  SurDev sd;
+  sd.img = ctx->d_mlp_img;
+  for (int i = 0; i < 3; ++i) {
+    sd.lo[i] = ctx->sur_hull[i];
+    sd.hi[i] = ctx->sur_hull[3 + i];
+  }
+  if (ctx->sur_engine == CC_SURROGATE_TCGEN05) {
+    auto kern = collapse_sur_tc_kernel<T>;
+    if (int rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100),
+                            "cudaFuncSetAttribute"))
+      return rc;
+    // resident CTAs per SM from the shared-memory footprint (the occupancy
+    // calculator does not follow the carveout preference set above)
+    const int64_t need = (a.n + tc::kRows - 1) / tc::kRows;
+    const int64_t cap = static_cast<int64_t>(a.num_sms) * tc::kCtasPerSm;
+    const int grid = static_cast<int>(need < cap ? need : cap);
+    kern<<<grid, tc::kRows, tc::kSmemBytes, a.stream>>>(static_cast<const T*>(a.hess), a.n, a.plane_stride,
+                                                         a.radius_stride, a.R, a.scale_idx0, ctx->tab, rp, sd,
+                                                         a.F_max, a.idx, a.counters);
+    return check_cuda(cudaGetLastError(), "collapse_sur_tc_kernel launch");
+  }
   auto kern = collapse_sur_kernel<T>;
   const size_t smem = ((ctx->tab.bytes() + 15) / 16) * 16 + FWD_BYTES;
   if (smem > 48 * 1024)
@@ -527,12 +777,6 @@ int launch_sur_typed(cc_ctx* ctx, const LaunchArgs& a, const RadiusParams& rp) {
   const int64_t need = (a.n + kThreads - 1) / kThreads;
   const int64_t cap = static_cast<int64_t>(a.num_sms) * (occ > 0 ? occ : 1);
   const int grid = static_cast<int>(need < cap ? need : cap);
-  SurDev sd;
-  sd.img = ctx->d_mlp_img;
-  for (int i = 0; i < 3; ++i) {
-    sd.lo[i] = ctx->sur_hull[i];
-    sd.hi[i] = ctx->sur_hull[3 + i];
-  }
   kern<<<grid, kThreads, smem, a.stream>>>(static_cast<const T*>(a.hess), a.n, a.plane_stride, a.radius_stride, a.R,
                                            a.scale_idx0, ctx->tab, rp, sd, a.F_max, a.idx, a.counters);
   return check_cuda(cudaGetLastError(), "collapse_sur_kernel launch");
@@ -564,6 +808,14 @@ using namespace cc;
 using namespace cc::mlp;
 
 extern "C" {
+
+int cc_set_surrogate_engine(cc_ctx* ctx, int32_t engine) {
+  if (!ctx) return set_error(CC_EINVAL, "ctx is NULL");
+  if (engine != CC_SURROGATE_MMA_SYNC && engine != CC_SURROGATE_TCGEN05)
+    return set_error(CC_EINVAL, "engine must be CC_SURROGATE_MMA_SYNC or CC_SURROGATE_TCGEN05");
+  ctx->sur_engine = engine;
+  return CC_OK;
+}
 
 int cc_surrogate_train(cc_ctx* ctx, const void* hess, int32_t dtype, int64_t n, int64_t plane_stride, double sigma,
                        const cc_train_config* cfg, cc_train_report* report, void* stream) {

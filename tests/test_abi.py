@@ -86,3 +86,11 @@ def test_mode_names_match_the_header():
     enum = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"CC_MODE_(\w+)\s*=\s*(\d+)", text)}
     assert enum == {"fp64": 0, "mixed": 1, "surrogate": 2, "tabulated": 3, "f32x2": 4, "exact_growth": 5}
     assert enum == _lib.MODES
+
+
+def test_surrogate_engine_names_match_the_header(lib):
+    import paper_2510_02873_gb300 as cc
+    text = open(os.path.join(ROOT, "include", "collapse.h")).read()
+    enum = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"CC_SURROGATE_(\w+)\s*=\s*(\d+)", text)}
+    assert enum == cc.Context.SURROGATE_ENGINES == {"mma_sync": 0, "tcgen05": 1}
+    assert lib.cc_set_surrogate_engine(None, 0) == _lib.CC_EINVAL
