@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--radii", type=int, default=N_RADII)
     ap.add_argument("--mode", choices=["fp64", "mixed", "f32x2", "surrogate", "exact_growth", "tabulated"],
                     default="fp64")
+    ap.add_argument("--surrogate-engine", choices=["mma_sync", "tcgen05"], default="mma_sync",
+                    help="kernel for --mode surrogate (cc_set_surrogate_engine)")
     # --mode surrogate trains the network first (untimed) on this many points and steps
     ap.add_argument("--train-points", type=int, default=4 * 1024 * 1024)
     ap.add_argument("--train-steps", type=int, default=300)
@@ -662,6 +664,7 @@ def main():
         h = torch.empty((6, args.train_points), dtype=torch.float32, device=dev)
         hdev.fill(h, SEED + 5, 99, 0, 1.0)
         ctx.surrogate_train(h, 1.0, steps=args.train_steps, batch=16384, lr=3e-3, seed=11)
+        ctx.set_surrogate_engine(args.surrogate_engine)
         del h
     if args.mode == "tabulated":
         load_table(ctx)
@@ -748,6 +751,7 @@ def main():
                                        "tabulated": "f64"}[args.mode],
         "data": "synthetic",
         "config": {"workload": WORKLOAD if (args.grid, R) == (GRID, N_RADII) else f"profiling case {args.grid}^3 x {R}", "points": n, "radii": R, "mode": args.mode,
+                   **({"surrogate_engine": args.surrogate_engine} if args.mode == "surrogate" else {}),
                    "per_gpu": "one independent realization per GPU",
                    "l2": f"inputs {6 * hess.element_size() * n * R / 1e9:.1f} GB per step vs 129 MB L2 (no flush needed)"},
         "roofline": roofline,

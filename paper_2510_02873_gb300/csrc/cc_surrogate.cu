@@ -51,14 +51,16 @@ constexpr int kSbo1 = 16 * 16;                      // of the K = 16 first layer
 constexpr int kW1 = 0;                              // 64 x 16: W1^T / 2, b1 / 2 at k = 3, 4
 constexpr int kW2 = kW1 + 64 * 16 * 2;              // 64 x 80: W2^T / 2, b2 / 2 at k = 64, 65
 constexpr int kW3 = kW2 + 64 * kKA * 2;             // 64 x 80
-constexpr int kW4 = kW3 + 64 * kKA * 2;             // 16 x 80: row 0 = W4, b4 at k = 64, 65
-constexpr int kImgBytes = kW4 + 16 * kKA * 2;
+constexpr int kW4 = kW3 + 64 * kKA * 2;             // 8 x 80: row 0 = W4, b4 at k = 64, 65; the
+                                                    // N = 16 MMA reads it with row-group stride 0,
+                                                    // so rows 8-15 repeat rows 0-7
+constexpr int kImgBytes = kW4 + 8 * kKA * 2;
 constexpr int kA = kImgBytes;                       // the activation tile follows in shared memory
 constexpr int kSmemBytes = kA + kRows * kKA * 2;
 constexpr int kTmemCols = 64;
 constexpr int kWaitTries = 1 << 22;                 // polls of an mbarrier before giving up
 constexpr unsigned kErrWait = 1u;                   // DevCounters::error_flags bit
-constexpr int kCtasPerSm = 4;                       // 46.7 KB shared memory, 64 TMEM columns, 128 registers
+constexpr int kCtasPerSm = 5;                       // 45.4 KB shared memory, 64 TMEM columns, 96 registers
 constexpr int OFF_TC = IMG_BYTES;                   // in the global image
 constexpr int IMG_TOTAL = OFF_TC + kImgBytes;
 static_assert(OFF_TC % 16 == 0 && kImgBytes % 16 == 0, "bulk copy alignment");
@@ -640,8 +642,9 @@ collapse_sur_tc_kernel(const T* __restrict__ hess, int64_t n, int64_t ps, int64_
             const uint32_t w = aW + (layer == 1 ? kW2 : layer == 2 ? kW3 : kW4);
 #pragma unroll
             for (int s = 0; s < kKA / 16; ++s)
-              umma::mma_bf16(tmem, umma::desc(aA + 256 * s, 128, kSboA), umma::desc(w + 256 * s, 128, kSboA),
-                             layer == 3 ? kIdesc16 : kIdesc64, s > 0);
+              umma::mma_bf16(tmem, umma::desc(aA + 256 * s, 128, kSboA),
+                             umma::desc(w + 256 * s, 128, layer == 3 ? 0 : kSboA), layer == 3 ? kIdesc16 : kIdesc64,
+                             s > 0);
           }
           umma::commit(&bar_mma);
         }
