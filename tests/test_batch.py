@@ -4,7 +4,7 @@ import pytest
 
 import hessgen
 import oracle
-from parity import compare_max, oracle_per_radius
+from parity import compare_max, compare_reduced, oracle_per_radius
 
 pytestmark = pytest.mark.gpu
 
@@ -132,3 +132,55 @@ def test_batch_rejects_bad_items(cc, ctx):
         cc.Batch(ctx, [(hess, [-1.0] * hess.shape[0], F, idx)], mode="mixed")
     with pytest.raises(cc.CollapseError):
         cc.Batch(ctx, items, mode="surrogate")
+
+
+def test_batch_config4_full_size_sampled(cc, ctx):
+    """The 48-realization workload as the bench times it: grids drawn from
+    {64..384}^3 and 8..40 radii (seed 2514), FP32 planes (240 GB resident),
+    mixed precision, autotuned tiles, one persistent launch replayed from a
+    CUDA graph; sampled points of every realization against the oracle."""
+    import hessgen.device as hdev
+    rng = np.random.default_rng(2514)
+    grids = rng.choice((64, 96, 128, 192, 256, 384), 48)
+    radii = rng.integers(8, 41, 48)
+    items = []
+    for k, (g, R) in enumerate(zip(grids, radii)):
+        n, R = int(g) ** 3, int(R)
+        sig = hessgen.sigma_schedule(R, 0.2, 6.0)
+        hess = torch.empty((R, 6, n), dtype=torch.float32, device="cuda")
+        for r in range(R):
+            hdev.fill(hess[r], 2514, k, r, sig[r])
+        items.append((hess, sig, torch.zeros(n, dtype=torch.float64, device="cuda"),
+                      torch.full((n,), -1, dtype=torch.int32, device="cuda")))
+    b = cc.Batch(ctx, items, mode="mixed")
+    stream = torch.cuda.Stream()
+    b.autotune(None, stream)
+    for _, _, F, idx in items:
+        F.zero_()
+        idx.fill_(-1)
+    torch.cuda.synchronize()
+    ctx.reset_stats()
+    with torch.cuda.stream(stream):
+        b.run_graph(stream)
+    stream.synchronize()
+    st = ctx.stats()
+    assert st["evaluations"] == sum(int(g) ** 3 * int(R) for g, R in zip(grids, radii))
+    assert st["error_flags"] == 0
+    t = oracle.Tables(0.3, 0.7, 512, 1e-3, 1.0)
+    pick = np.random.default_rng(6)
+    worst = 0.0
+    for k, (hess, sig, F, idx) in enumerate(items):
+        n = hess.shape[2]
+        pts = np.unique(np.concatenate([pick.integers(0, n, 150), [0, n - 1]]))
+        host = np.stack([hessgen.hessian_points(2514, k, r, sig[r], pts, dtype=np.float32)
+                         for r in range(len(sig))])
+        dev = hess[:, :, torch.from_numpy(pts).cuda()].cpu().numpy()
+        # the device and host generators agree to the last FP32 place
+        assert np.all(np.abs(dev.astype(np.float64) - host) <= np.spacing(np.abs(host)).astype(np.float64) * 1.0001)
+        F_all, fl = oracle_per_radius(t, host)
+        s = compare_reduced(F.cpu().numpy()[pts], idx.cpu().numpy()[pts], F_all, fl)
+        worst = max(worst, s["max_rel_err"])
+    print("config 4 full size, sampled: max rel err", worst, st)
+    b.close()
+    del items
+    torch.cuda.empty_cache()

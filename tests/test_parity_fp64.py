@@ -253,3 +253,24 @@ def test_config2_full_size_sampled(ctx, tables, mode):
     print("config2 sampled", mode, s, st)
     del hess
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_eds_segment_below_first_knot(ctx, tables, mode):
+    """Fields strong enough that D_c falls below the first knot D_0 at some
+    radii (a_c = a_0 D_c / D_0, taken through the spline's Horner scheme with
+    that segment's coefficients): parity, and the same count of EdS-branch
+    evaluations as the oracle."""
+    D0 = tables.D[0]
+    sig = [0.5 / D0, 1.5 / D0, 4.0 / D0]
+    n = 4096
+    stack = hessgen.hessian_stack(2600, 0, sig, n)
+    F_all, fl = oracle_per_radius(tables, stack)
+    n_eds = int(((fl & oracle.FLAG_EDS) != 0).sum())
+    assert n_eds > 1000
+    ctx.reset_stats()
+    F, idx = gpu_multi(ctx, stack, sig, mode=mode)
+    st = ctx.stats()
+    s = compare_max(F, idx, F_all, fl)
+    assert st["eds_branch"] == n_eds
+    print("EdS segment", mode, s, "eds evaluations", n_eds)

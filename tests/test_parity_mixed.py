@@ -218,3 +218,20 @@ def test_mixed_deferred_mixed_radii(ctx, tables):
     F, idx, st = run_mixed(ctx, stack, sig, plane_stride=n + 4)
     s = compare_mixed(F, idx, F_all, fl)
     print("mixed deferred, scattered hard cells", s, "fp64 fraction", st["fp64_branch"] / (n * R))
+
+
+def test_mixed_eds_segment_below_first_knot(ctx, tables):
+    """The mixed path's spline (FP32 tail, FP64 head) on the EdS segment below
+    the first knot."""
+    D0 = tables.D[0]
+    sig = [0.5 / D0, 1.5 / D0, 4.0 / D0]
+    n = 4096
+    stack = hessgen.hessian_stack(2600, 0, sig, n, dtype=np.float32)
+    F_all, fl = oracle_per_radius(tables, stack)
+    n_eds = int(((fl & oracle.FLAG_EDS) != 0).sum())
+    assert n_eds > 1000
+    F, idx, st = run_mixed(ctx, stack, sig)
+    s = compare_mixed(F, idx, F_all, fl)
+    # a point within the tolerance of D_0 may land on either side
+    assert abs(st["eds_branch"] - n_eds) <= 2
+    print("mixed EdS segment", s, st["eds_branch"], n_eds)

@@ -8,7 +8,7 @@ import pytest
 
 import hessgen
 import oracle
-from parity import oracle_per_radius, rel_err, running_max
+from parity import compare_reduced, oracle_per_radius, rel_err, running_max
 
 pytestmark = pytest.mark.gpu
 
@@ -219,3 +219,41 @@ def test_surrogate_gain_over_the_method_without_it(ctx, trained):
     print(f"surrogate gain over the closed-form seed: {gain:.3f}x "
           f"(mixed {times['mixed']:.2f} ms, surrogate {times['surrogate']:.2f} ms)")
     assert gain > 0
+
+
+@pytest.mark.parametrize("engine", ["mma_sync", "tcgen05"])
+def test_surrogate_config5_full_size_sampled(ctx, tables, trained, engine):
+    """768^3 grid x 40 radii of FP32 planes, streamed one radius at a time
+    (10.9 GB each) through collapse_scale as the bench times them; sampled
+    points against the oracle."""
+    import hessgen.device as hdev
+    n, R, seed = 768 ** 3, 40, 2518
+    sig = hessgen.sigma_schedule(R, 0.2, 6.0)
+    planes = torch.empty((6, n), dtype=torch.float32, device="cuda")
+    F = torch.zeros(n, dtype=torch.float64, device="cuda")
+    idx = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    rng = np.random.default_rng(8)
+    pts = np.unique(np.concatenate([rng.integers(0, n, 6000), [0, n - 1]]))
+    pts_t = torch.from_numpy(pts).cuda()
+    host = np.empty((R, 6, len(pts)), dtype=np.float32)
+    ctx.set_surrogate_engine(engine)
+    ctx.reset_stats()
+    try:
+        for r in range(R):
+            hdev.fill(planes, seed, 0, r, sig[r])
+            ctx.collapse_scale(planes, sig[r], F, idx, r, mode="surrogate")
+            host[r] = hessgen.hessian_points(seed, 0, r, sig[r], pts, dtype=np.float32)
+            dev = planes[:, pts_t].cpu().numpy()
+            assert np.all(np.abs(dev.astype(np.float64) - host[r]) <=
+                          np.spacing(np.abs(host[r])).astype(np.float64) * 1.0001)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_surrogate_engine("mma_sync")
+    st = ctx.stats()
+    assert st["evaluations"] == n * R and st["error_flags"] == 0
+    assert st["fallback"] < 0.01 * n * R
+    F_all, fl = oracle_per_radius(tables, host)
+    s = compare_reduced(F.cpu().numpy()[pts], idx.cpu().numpy()[pts], F_all, fl)
+    print("config 5 full size, sampled", engine, s, "fallback fraction", st["fallback"] / (n * R))
+    del planes
+    torch.cuda.empty_cache()
