@@ -262,11 +262,12 @@ CC_API int cc_load_surrogate(cc_ctx *ctx, const float *params, const float *hull
 /* Kernel that runs CC_MODE_SURROGATE. Both evaluate the same network with
  * BF16 operands and FP32 accumulation, and both results meet the mixed path's
  * tolerance; they differ in how the MMAs are issued:
- *   CC_SURROGATE_MMA_SYNC (default): warp-level mma.sync m16n8k16, 32 points
- *     per warp as two 16-row tiles, activations chained in registers;
- *   CC_SURROGATE_TCGEN05: fifth-generation tensor cores, one M = 128 tile of
- *     points per CTA, accumulators in tensor memory, weights staged by a
- *     bulk copy, each layer's bias carried by two extra K columns.
+ *   CC_SURROGATE_TCGEN05 (default): fifth-generation tensor cores; groups of
+ *     128 threads each own an M = 128 tile of points, accumulators in tensor
+ *     memory, four groups per CTA sharing weights staged by one bulk copy,
+ *     each layer's bias carried by two extra K columns;
+ *   CC_SURROGATE_MMA_SYNC: warp-level mma.sync m16n8k16, 32 points per warp
+ *     as two 16-row tiles, activations chained in registers.
  * Returns CC_EINVAL for another value. */
 typedef enum { CC_SURROGATE_MMA_SYNC = 0, CC_SURROGATE_TCGEN05 = 1 } cc_surrogate_engine;
 CC_API int cc_set_surrogate_engine(cc_ctx *ctx, int32_t engine);

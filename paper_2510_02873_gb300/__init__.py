@@ -338,7 +338,7 @@ class Context:
     SURROGATE_ENGINES = {"mma_sync": 0, "tcgen05": 1}
 
     def set_surrogate_engine(self, engine: str):
-        """Kernel for mode="surrogate": "mma_sync" (default) or "tcgen05"."""
+        """Kernel for mode="surrogate": "tcgen05" (default) or "mma_sync"."""
         if engine not in self.SURROGATE_ENGINES:
             raise ValueError(f"engine must be one of {sorted(self.SURROGATE_ENGINES)}")
         _lib.check(_lib.load().cc_set_surrogate_engine(self._h, self.SURROGATE_ENGINES[engine]),

@@ -167,7 +167,7 @@ struct cc_ctx {
   cc::TabDev tabdev{};
   // surrogate (cc_surrogate_train / cc_load_surrogate)
   bool sur_valid = false;
-  int sur_engine = 0;  // cc_surrogate_engine
+  int sur_engine = 1;  // cc_surrogate_engine: CC_SURROGATE_TCGEN05
   unsigned char* d_mlp_img = nullptr;
   float* d_mlp_param = nullptr;  // params | adam m | adam v | grad | loss, stats
   void* d_train = nullptr;       // training records (float4) | count | hull

@@ -55,12 +55,14 @@ constexpr int kW4 = kW3 + 64 * kKA * 2;             // 8 x 80: row 0 = W4, b4 at
                                                     // N = 16 MMA reads it with row-group stride 0,
                                                     // so rows 8-15 repeat rows 0-7
 constexpr int kImgBytes = kW4 + 8 * kKA * 2;
-constexpr int kA = kImgBytes;                       // the activation tile follows in shared memory
-constexpr int kSmemBytes = kA + kRows * kKA * 2;
+constexpr int kA = kImgBytes;                       // the groups' activation tiles follow in shared memory
+constexpr int kATileBytes = kRows * kKA * 2;
+constexpr int kGroups = 4;                          // groups of 128 threads per CTA, sharing the weights
+constexpr int kSmemBytes = kA + kGroups * kATileBytes;
 constexpr int kTmemCols = 64;
 constexpr int kWaitTries = 1 << 22;                 // polls of an mbarrier before giving up
 constexpr unsigned kErrWait = 1u;                   // DevCounters::error_flags bit
-constexpr int kCtasPerSm = 5;                       // 45.4 KB shared memory, 64 TMEM columns, 96 registers
+constexpr int kCtasPerSm = 2;                       // 103 KB shared memory, 256 TMEM columns, 64 registers
 constexpr int OFF_TC = IMG_BYTES;                   // in the global image
 constexpr int IMG_TOTAL = OFF_TC + kImgBytes;
 static_assert(OFF_TC % 16 == 0 && kImgBytes % 16 == 0, "bulk copy alignment");
@@ -556,56 +558,78 @@ collapse_sur_kernel(const T* __restrict__ hess, int64_t n, int64_t ps, int64_t r
   sur_counters(cnt, n_eval, n_coll, n_eds, n_ref, n_fp64, n_fb);
 }
 
-// The tensor-memory form (tcgen05). A CTA of 128 threads owns a tile of 128
-// consecutive points, thread i the point tile * 128 + i, for all the radii of
-// the launch. Per radius each thread writes its point's network input as row
-// i of the activation tile in shared memory; one thread issues the layer's
-// M = 128 MMAs (K = 16 for layer 1, 80 for the others, N = 64, or 16 for the
-// last layer) into a 64-column accumulator in tensor memory and commits them
-// to an mbarrier; every thread then loads its row of the accumulator
-// (tcgen05.ld, lane = row), applies SiLU and writes the row back as the next
-// layer's input. The weights arrive once per CTA by one bulk copy; the bias of
-// every layer is an extra pair of K columns (hi, lo) against two columns of
-// ones, so the accumulators need no initialisation and the epilogue no adds.
-// Five CTAs (45 KB shared memory, 64 tensor-memory columns each) share an SM,
-// so one CTA's SiLU and FP32 work overlap the others' MMAs. Every mbarrier
-// wait is bounded; a wait that runs out stops the CTA and sets an error bit.
+// barrier of the 128 threads of group g (named barrier 1 + g); returns the OR
+// of v over them
+__device__ __forceinline__ int group_sync_or(int g, int v) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.s32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, 128, p;\n\t"
+      "selp.s32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"(v), "r"(g + 1)
+      : "memory");
+  return r;
+}
+
+// The tensor-memory form (tcgen05). A CTA holds kGroups groups of 128
+// threads that share one copy of the weights (one bulk copy per CTA) and run
+// independently: a group owns a tile of 128 consecutive points, thread i the
+// point tile * 128 + i, for all the radii of the launch. Per radius each
+// thread writes its point's network input as row i of the group's activation
+// tile in shared memory; one thread of the group issues the layer's M = 128
+// MMAs (K = 16 for layer 1, 80 for the others, N = 64, or 16 for the last
+// layer) into the group's 64 tensor-memory columns and commits them to the
+// group's mbarrier; every thread then loads its row of the accumulator
+// (tcgen05.ld; the group's warps cover the four lane quadrants), applies SiLU
+// and writes the row back as the next layer's input. The bias of every layer
+// is an extra pair of K columns (hi, lo) against two columns of ones, so the
+// accumulators need no initialisation and the epilogue no adds. Eight groups
+// per SM (two CTAs of 512 threads, 103 KB shared memory and 256 tensor-memory
+// columns each) keep other groups' SiLU and FP32 work running while one waits
+// for its MMAs. Every wait is bounded; a wait that runs out stops the group
+// and sets an error bit.
 template <typename T>
-__global__ void __launch_bounds__(tc::kRows, tc::kCtasPerSm)
+__global__ void __launch_bounds__(tc::kRows * tc::kGroups, tc::kCtasPerSm)
 collapse_sur_tc_kernel(const T* __restrict__ hess, int64_t n, int64_t ps, int64_t rs, int R, int32_t scale_idx0,
                        DevTable tab, RadiusParams rp, SurDev sd, double* __restrict__ F_max,
                        int32_t* __restrict__ idx, DevCounters* __restrict__ cnt) {
   using namespace tc;
   extern __shared__ __align__(16) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bar_ld, bar_mma;
+  __shared__ __align__(8) uint64_t bar_ld, bar_mma[kGroups];
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5;
-  unsigned char* sA = sm + kA;
+  const int g = tid >> 7, row = tid & (kRows - 1);
+  unsigned char* sA = sm + kA + g * kATileBytes;
   if (tid == 0) {
     umma::mbar_init(&bar_ld, 1);
-    umma::mbar_init(&bar_mma, 1);
+    for (int i = 0; i < kGroups; ++i) umma::mbar_init(&bar_mma[i], 1);
   }
   __syncwarp();
-  if (warp == 0) umma::tmem_alloc<kTmemCols>(&tmem_slot);
+  if (warp == 0) umma::tmem_alloc<kTmemCols * kGroups>(&tmem_slot);
   // the constant columns of this thread's activation row: 64, 65 = 1 (bias hi, lo), 66..79 = 0
-  *reinterpret_cast<uint4*>(sA + umma::offset(tid, 64, kSboA)) = make_uint4(pack(1.0f, 1.0f), 0u, 0u, 0u);
-  *reinterpret_cast<uint4*>(sA + umma::offset(tid, 72, kSboA)) = make_uint4(0u, 0u, 0u, 0u);
+  *reinterpret_cast<uint4*>(sA + umma::offset(row, 64, kSboA)) = make_uint4(pack(1.0f, 1.0f), 0u, 0u, 0u);
+  *reinterpret_cast<uint4*>(sA + umma::offset(row, 72, kSboA)) = make_uint4(0u, 0u, 0u, 0u);
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
   if (tid == 0) umma::bulk_load(sm, sd.img + OFF_TC, kImgBytes, &bar_ld);
   int bad = umma::mbar_wait(&bar_ld, 0, kWaitTries) ? 0 : 1;
-  const uint32_t tmem = tmem_slot;
-  const uint32_t trow = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+  // columns g * 64 .. g * 64 + 63; lanes 32 (warp % 4) .. + 31
+  const uint32_t tmem = tmem_slot + static_cast<uint32_t>(g * kTmemCols);
+  const uint32_t trow = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
   const uint32_t aA = umma::smem_addr(sA), aW = umma::smem_addr(sm);
+  uint64_t* bar = &bar_mma[g];
   constexpr uint32_t kIdesc64 = umma::idesc_bf16_f32(kRows, 64), kIdesc16 = umma::idesc_bf16_f32(kRows, 16);
   uint32_t phase = 0;
   unsigned n_eval = 0, n_coll = 0, n_eds = 0, n_ref = 0, n_fp64 = 0, n_fb = 0;
   const int64_t ntiles = (n + kRows - 1) / kRows;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    bad = __syncthreads_or(bad);
+  const int64_t tstride = static_cast<int64_t>(gridDim.x) * kGroups;
+  for (int64_t tile = static_cast<int64_t>(blockIdx.x) * kGroups + g; tile < ntiles; tile += tstride) {
+    bad = group_sync_or(g, bad);
     if (bad) break;
-    const int64_t p = tile * kRows + tid;
+    const int64_t p = tile * kRows + row;
     const bool active = p < n;
     MinA best;
     const T* base = hess + (active ? p : 0);
@@ -623,19 +647,20 @@ collapse_sur_tc_kernel(const T* __restrict__ hess, int64_t n, int64_t ps, int64_
       const bool inside = z0 >= sd.lo[0] && z0 <= sd.hi[0] && z1 >= sd.lo[1] && z1 <= sd.hi[1] &&
                           z2 >= sd.lo[2] && z2 <= sd.hi[2];
       // layer-1 input row: z0 z1 z2, ones at k = 3, 4 (bias hi, lo), zeros to k = 15
-      *reinterpret_cast<uint4*>(sA + umma::offset(tid, 0, kSboA)) =
+      *reinterpret_cast<uint4*>(sA + umma::offset(row, 0, kSboA)) =
           make_uint4(pack(z0, z1), pack(z2, 1.0f), pack(1.0f, 0.0f), 0u);
-      *reinterpret_cast<uint4*>(sA + umma::offset(tid, 8, kSboA)) = make_uint4(0u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(sA + umma::offset(row, 8, kSboA)) = make_uint4(0u, 0u, 0u, 0u);
       float f = 0.0f;
 #pragma unroll
       for (int layer = 0; layer < 4; ++layer) {
-        // the rows written by every thread (generic proxy) become MMA operands (async proxy)
+        // the rows written by every thread of the group (generic proxy) become
+        // MMA operands (async proxy)
         umma::fence_smem_async();
         umma::fence_before_sync();
-        bad = __syncthreads_or(bad);
+        bad = group_sync_or(g, bad);
         umma::fence_after_sync();
         if (bad) break;
-        if (tid == 0) {
+        if (row == 0) {
           if (layer == 0) {
             umma::mma_bf16(tmem, umma::desc(aA, 128, kSboA), umma::desc(aW + kW1, 128, kSbo1), kIdesc64, false);
           } else {
@@ -646,32 +671,26 @@ collapse_sur_tc_kernel(const T* __restrict__ hess, int64_t n, int64_t ps, int64_
                              umma::desc(w + 256 * s, 128, layer == 3 ? 0 : kSboA), layer == 3 ? kIdesc16 : kIdesc64,
                              s > 0);
           }
-          umma::commit(&bar_mma);
+          umma::commit(bar);
         }
         // every thread watches the mbarrier (measured faster than one warp
-        // watching and a CTA barrier releasing the others)
-        if (!umma::mbar_wait(&bar_mma, phase, kWaitTries)) bad = 1;
+        // watching and a barrier releasing the others)
+        if (!umma::mbar_wait(bar, phase, kWaitTries)) bad = 1;
         phase ^= 1u;
         __syncwarp();
         umma::fence_after_sync();
         if (layer < 3) {
           // h = (pre-activation) / 2 of this thread's 64 units -> SiLU -> next input row
 #pragma unroll
-          for (int c0 = 0; c0 < 64; c0 += 32) {
-            uint32_t v0[16], v1[16];
-            umma::ld16(trow + c0, v0);
-            umma::ld16(trow + c0 + 16, v1);
+          for (int c0 = 0; c0 < 64; c0 += 16) {
+            uint32_t v[16];
+            umma::ld16(trow + c0, v);
             umma::wait_ld();
-            uint32_t w[16];
+            uint32_t w[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              w[j] = silu2_half(__uint_as_float(v0[2 * j]), __uint_as_float(v0[2 * j + 1]));
-              w[8 + j] = silu2_half(__uint_as_float(v1[2 * j]), __uint_as_float(v1[2 * j + 1]));
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              *reinterpret_cast<uint4*>(sA + umma::offset(tid, c0 + 8 * q, kSboA)) =
-                  make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+            for (int j = 0; j < 8; ++j) w[j] = silu2_half(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+            *reinterpret_cast<uint4*>(sA + umma::offset(row, c0, kSboA)) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4*>(sA + umma::offset(row, c0 + 8, kSboA)) = make_uint4(w[4], w[5], w[6], w[7]);
           }
         } else {
           f = __uint_as_float(umma::ld1(trow));
@@ -680,7 +699,7 @@ collapse_sur_tc_kernel(const T* __restrict__ hess, int64_t n, int64_t ps, int64_
         // this thread's accumulator loads are complete before the next MMA overwrites them
         umma::fence_before_sync();
       }
-      bad = __syncthreads_or(bad);
+      bad = group_sync_or(g, bad);
       if (bad) break;
       if (!active) continue;
       const MixedResult res =
@@ -698,13 +717,13 @@ collapse_sur_tc_kernel(const T* __restrict__ hess, int64_t n, int64_t ps, int64_
     }
   }
   sur_counters(cnt, n_eval, n_coll, n_eds, n_ref, n_fp64, n_fb);
-  if (bad && tid == 0) atomicOr(&cnt->error_flags, kErrWait);
+  if (bad && row == 0) atomicOr(&cnt->error_flags, kErrWait);
   // every tensor-memory load of the CTA has completed and every MMA was waited
-  // for (or the CTA gave up on it): the tensor memory can go
+  // for (or its group gave up on it): the tensor memory can go
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
-  if (warp == 0) umma::tmem_free<kTmemCols>(tmem);
+  if (warp == 0) umma::tmem_free<kTmemCols * kGroups>(tmem_slot);
 }
 
 int launch_grid(int64_t n, int threads, int cap) {
@@ -759,12 +778,15 @@ int launch_sur_typed(cc_ctx* ctx, const LaunchArgs& a, const RadiusParams& rp) {
     if (int rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100),
                             "cudaFuncSetAttribute"))
       return rc;
+    if (int rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes),
+                            "cudaFuncSetAttribute"))
+      return rc;
     // resident CTAs per SM from the shared-memory footprint (the occupancy
     // calculator does not follow the carveout preference set above)
-    const int64_t need = (a.n + tc::kRows - 1) / tc::kRows;
+    const int64_t need = ((a.n + tc::kRows - 1) / tc::kRows + tc::kGroups - 1) / tc::kGroups;
     const int64_t cap = static_cast<int64_t>(a.num_sms) * tc::kCtasPerSm;
     const int grid = static_cast<int>(need < cap ? need : cap);
-    kern<<<grid, tc::kRows, tc::kSmemBytes, a.stream>>>(static_cast<const T*>(a.hess), a.n, a.plane_stride,
+    kern<<<grid, tc::kRows * tc::kGroups, tc::kSmemBytes, a.stream>>>(static_cast<const T*>(a.hess), a.n, a.plane_stride,
                                                          a.radius_stride, a.R, a.scale_idx0, ctx->tab, rp, sd,
                                                          a.F_max, a.idx, a.counters);
     return check_cuda(cudaGetLastError(), "collapse_sur_tc_kernel launch");

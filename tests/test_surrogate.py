@@ -149,7 +149,7 @@ def test_surrogate_mode_parity(ctx, tables, trained, engine):
     try:
         F, idx, st = run(ctx, stack, sig, "surrogate")
     finally:
-        ctx.set_surrogate_engine("mma_sync")
+        ctx.set_surrogate_engine("tcgen05")
     worst = compare(F, idx, F_all, fl)
     frac = st["fallback"] / st["evaluations"]
     print("surrogate parity", engine, worst, "fallback fraction", frac, st)
@@ -177,7 +177,7 @@ def test_surrogate_engines_agree(ctx, trained):
         ctx.collapse_multi(h, sig, F, idx, mode="surrogate")
         torch.cuda.synchronize()
         out[engine] = (F.cpu().numpy(), idx.cpu().numpy(), ctx.stats())
-    ctx.set_surrogate_engine("mma_sync")
+    ctx.set_surrogate_engine("tcgen05")
     (Fa, ia, sa), (Fb, ib, sb) = out["mma_sync"], out["tcgen05"]
     assert sa["error_flags"] == 0 and sb["error_flags"] == 0
     # away from the a_max edge (F ~ 1) the same points collapse
@@ -248,7 +248,7 @@ def test_surrogate_config5_full_size_sampled(ctx, tables, trained, engine):
                           np.spacing(np.abs(host[r])).astype(np.float64) * 1.0001)
         torch.cuda.synchronize()
     finally:
-        ctx.set_surrogate_engine("mma_sync")
+        ctx.set_surrogate_engine("tcgen05")
     st = ctx.stats()
     assert st["evaluations"] == n * R and st["error_flags"] == 0
     assert st["fallback"] < 0.01 * n * R
