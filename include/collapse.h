@@ -264,8 +264,8 @@ CC_API int cc_load_surrogate(cc_ctx *ctx, const float *params, const float *hull
  * tolerance; they differ in how the MMAs are issued:
  *   CC_SURROGATE_TCGEN05 (default): fifth-generation tensor cores; groups of
  *     128 threads each own an M = 128 tile of points, accumulators in tensor
- *     memory, four groups per CTA sharing weights staged by one bulk copy,
- *     each layer's bias carried by two extra K columns;
+ *     memory, eight groups per CTA (one CTA per SM) sharing weights staged by
+ *     one bulk copy, each layer's bias carried by two extra K columns;
  *   CC_SURROGATE_MMA_SYNC: warp-level mma.sync m16n8k16, 32 points per warp
  *     as two 16-row tiles, activations chained in registers.
  * Returns CC_EINVAL for another value. */

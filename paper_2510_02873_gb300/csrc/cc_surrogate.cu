@@ -57,12 +57,13 @@ constexpr int kW4 = kW3 + 64 * kKA * 2;             // 8 x 80: row 0 = W4, b4 at
 constexpr int kImgBytes = kW4 + 8 * kKA * 2;
 constexpr int kA = kImgBytes;                       // the groups' activation tiles follow in shared memory
 constexpr int kATileBytes = kRows * kKA * 2;
-constexpr int kGroups = 4;                          // groups of 128 threads per CTA, sharing the weights
-constexpr int kSmemBytes = kA + kGroups * kATileBytes;
+constexpr int kGroups = 8;                          // groups of 128 threads per CTA, sharing the weights
+constexpr int kTab = kA + kGroups * kATileBytes;    // then the spline table (coef | D | Df | bucket)
+constexpr int kSmemBytes = kTab;                    // + the table's bytes, rounded to 16
 constexpr int kTmemCols = 64;
 constexpr int kWaitTries = 1 << 22;                 // polls of an mbarrier before giving up
 constexpr unsigned kErrWait = 1u;                   // DevCounters::error_flags bit
-constexpr int kCtasPerSm = 2;                       // 103 KB shared memory, 256 TMEM columns, 64 registers
+constexpr int kCtasPerSm = 1;                       // ~208 KB shared memory, 512 TMEM columns, 64 registers
 constexpr int OFF_TC = IMG_BYTES;                   // in the global image
 constexpr int IMG_TOTAL = OFF_TC + kImgBytes;
 static_assert(OFF_TC % 16 == 0 && kImgBytes % 16 == 0, "bulk copy alignment");
@@ -585,11 +586,12 @@ __device__ __forceinline__ int group_sync_or(int g, int v) {
 // (tcgen05.ld; the group's warps cover the four lane quadrants), applies SiLU
 // and writes the row back as the next layer's input. The bias of every layer
 // is an extra pair of K columns (hi, lo) against two columns of ones, so the
-// accumulators need no initialisation and the epilogue no adds. Eight groups
-// per SM (two CTAs of 512 threads, 103 KB shared memory and 256 tensor-memory
-// columns each) keep other groups' SiLU and FP32 work running while one waits
-// for its MMAs. Every wait is bounded; a wait that runs out stops the group
-// and sets an error bit.
+// accumulators need no initialisation and the epilogue no adds. One CTA of
+// eight groups per SM (1024 threads at 64 registers, all 512 tensor-memory
+// columns, the weights and the spline table staged once in shared memory)
+// keeps other groups' SiLU and FP32 work running while one waits for its
+// MMAs. Every wait is bounded; a wait that runs out stops the group and sets
+// an error bit.
 template <typename T>
 __global__ void __launch_bounds__(tc::kRows * tc::kGroups, tc::kCtasPerSm)
 collapse_sur_tc_kernel(const T* __restrict__ hess, int64_t n, int64_t ps, int64_t rs, int R, int32_t scale_idx0,
@@ -611,11 +613,21 @@ collapse_sur_tc_kernel(const T* __restrict__ hess, int64_t n, int64_t ps, int64_
   // the constant columns of this thread's activation row: 64, 65 = 1 (bias hi, lo), 66..79 = 0
   *reinterpret_cast<uint4*>(sA + umma::offset(row, 64, kSboA)) = make_uint4(pack(1.0f, 1.0f), 0u, 0u, 0u);
   *reinterpret_cast<uint4*>(sA + umma::offset(row, 72, kSboA)) = make_uint4(0u, 0u, 0u, 0u);
+  {  // the spline table (coef | D | Df | bucket) into shared memory, 16-byte words
+    const int words = static_cast<int>((tab.bytes() + 15) / 16);
+    const uint4* src = reinterpret_cast<const uint4*>(tab.coef);
+    uint4* dst = reinterpret_cast<uint4*>(sm + kTab);
+    for (int i = tid; i < words; i += blockDim.x) dst[i] = src[i];
+  }
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
   if (tid == 0) umma::bulk_load(sm, sd.img + OFF_TC, kImgBytes, &bar_ld);
   int bad = umma::mbar_wait(&bar_ld, 0, kWaitTries) ? 0 : 1;
+  const Coef4* coef = reinterpret_cast<const Coef4*>(sm + kTab);
+  const double* Dk = reinterpret_cast<const double*>(coef + (tab.n - 1));
+  const float* Dkf = reinterpret_cast<const float*>(Dk + tab.n);
+  const unsigned short* bucket = reinterpret_cast<const unsigned short*>(Dkf + tab.n);
   // columns g * 64 .. g * 64 + 63; lanes 32 (warp % 4) .. + 31
   const uint32_t tmem = tmem_slot + static_cast<uint32_t>(g * kTmemCols);
   const uint32_t trow = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
@@ -703,7 +715,7 @@ collapse_sur_tc_kernel(const T* __restrict__ hess, int64_t n, int64_t ps, int64_
       if (bad) break;
       if (!active) continue;
       const MixedResult res =
-          sur_finish(m, f, is, inside, xx, yy, zz, xy, xz, yz, tab.D, tab.coef, tab.Df, tab.bucket, tab, n_fb);
+          sur_finish(m, f, is, inside, xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab, n_fb);
       n_coll += res.collapsed;
       n_eds += res.eds;
       n_ref += res.refined;
@@ -778,7 +790,9 @@ int launch_sur_typed(cc_ctx* ctx, const LaunchArgs& a, const RadiusParams& rp) {
     if (int rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100),
                             "cudaFuncSetAttribute"))
       return rc;
-    if (int rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes),
+    const size_t smem = tc::kSmemBytes + ((ctx->tab.bytes() + 15) / 16) * 16;
+    if (int rc = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(smem)),
                             "cudaFuncSetAttribute"))
       return rc;
     // resident CTAs per SM from the shared-memory footprint (the occupancy
@@ -786,7 +800,7 @@ int launch_sur_typed(cc_ctx* ctx, const LaunchArgs& a, const RadiusParams& rp) {
     const int64_t need = ((a.n + tc::kRows - 1) / tc::kRows + tc::kGroups - 1) / tc::kGroups;
     const int64_t cap = static_cast<int64_t>(a.num_sms) * tc::kCtasPerSm;
     const int grid = static_cast<int>(need < cap ? need : cap);
-    kern<<<grid, tc::kRows * tc::kGroups, tc::kSmemBytes, a.stream>>>(static_cast<const T*>(a.hess), a.n, a.plane_stride,
+    kern<<<grid, tc::kRows * tc::kGroups, smem, a.stream>>>(static_cast<const T*>(a.hess), a.n, a.plane_stride,
                                                          a.radius_stride, a.R, a.scale_idx0, ctx->tab, rp, sd,
                                                          a.F_max, a.idx, a.counters);
     return check_cuda(cudaGetLastError(), "collapse_sur_tc_kernel launch");
