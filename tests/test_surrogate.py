@@ -257,3 +257,30 @@ def test_surrogate_config5_full_size_sampled(ctx, tables, trained, engine):
     print("config 5 full size, sampled", engine, s, "fallback fraction", st["fallback"] / (n * R))
     del planes
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("engine", ["mma_sync", "tcgen05"])
+@pytest.mark.parametrize("n", [1, 100, 300])
+def test_surrogate_small_and_fp64_planes(ctx, tables, trained, engine, n):
+    """Fewer points than one tile (or one warp), FP64 planes (rounded to FP32
+    at load, as the mixed path does), both engines."""
+    R = 3
+    sig = hessgen.sigma_schedule(R, 0.5, 4.0)
+    stack = hessgen.hessian_stack(2560 + n, 0, sig, n)
+    F_all, fl = oracle_per_radius(tables, stack.astype(np.float32))
+    ps = (n + 1) // 2 * 2  # 16-byte plane stride for FP64
+    buf = torch.zeros((R, 6, ps), dtype=torch.float64, device="cuda")
+    buf[:, :, :n] = torch.from_numpy(stack).cuda()
+    F = torch.empty(n, dtype=torch.float64, device="cuda")
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    ctx.reset_max(F, idx)
+    ctx.reset_stats()
+    ctx.set_surrogate_engine(engine)
+    try:
+        ctx.collapse_multi(buf[:, :, :n], sig, F, idx, mode="surrogate")
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_surrogate_engine("tcgen05")
+    st = ctx.stats()
+    assert st["evaluations"] == n * R and st["error_flags"] == 0
+    compare_reduced(F.cpu().numpy(), idx.cpu().numpy(), F_all, fl)
