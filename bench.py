@@ -62,6 +62,20 @@ def _measured_hbm_gbs():
 HBM_GBS = _measured_hbm_gbs()
 
 
+def _measured_bf16_tflops():
+    """Dense BF16 GEMM rate measured on this machine type (burst; MEASURED_PEAKS.json)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+BF16_TFLOPS = _measured_bf16_tflops()
+# the network's algorithmic work per evaluation: 2 (3 x 64 + 64 x 64 + 64 x 64 + 64 x 1) flops
+MLP_FLOPS_PER_EVAL = 2.0 * (3 * 64 + 64 * 64 * 2 + 64)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -163,9 +177,20 @@ def cpu_oracle_rate(seconds: float, first_point: int = 0, points_per_chunk: int 
         evals += len(pts) * N_RADII
         p0 += points_per_chunk
     cores = os.cpu_count()
-    return {"value": evals / elapsed, "unit": "evals/s", "cores": cores, "kind": "oracle",
-            "sample": f"{p0 - first_point} points x {N_RADII} radii of the workload "
-                      f"({evals} evaluations, {elapsed:.1f} s, OpenMP over {cores} threads)"}
+    out = {"value": evals / elapsed, "unit": "evals/s", "cores": cores, "kind": "oracle",
+           "sample": f"{p0 - first_point} points x {N_RADII} radii of the workload "
+                     f"({evals} evaluations, {elapsed:.1f} s, OpenMP over {cores} threads)"}
+    if seconds > 0:
+        # one thread on the next chunk of points
+        pts = np.arange(p0, p0 + 512, dtype=np.int64)
+        stack = np.stack([hessgen.hessian_points(SEED, 0, r, sig[r], pts) for r in range(N_RADII)])
+        F = np.zeros(len(pts))
+        idx = np.full(len(pts), -1, dtype=np.int32)
+        t0 = time.perf_counter()
+        for r in range(N_RADII):
+            t.collapse_scale(stack[r], F, idx, r, nthreads=1)
+        out["single_thread_value"] = len(pts) * N_RADII / (time.perf_counter() - t0)
+    return out
 
 
 def run_reference(args):
@@ -426,6 +451,15 @@ def run_mixed_variant(ctx, dev, stream, reps: int = 3) -> dict:
         "edge_points_excluded": int(edge.sum()),
         "argmax_diff_fraction": float((ix != ir).double().mean()),
         "fp64_branch_fraction": out["mixed"]["fp64_branch_fraction"],
+        "roofline": {
+            "hbm": {"bytes_per_eval": 24, "achieved_gbs": 24.0 * out["mixed"]["evals_per_s"] / 1e9,
+                    "peak_gbs": HBM_GBS,
+                    "frac": 24.0 * out["mixed"]["evals_per_s"] / 1e9 / HBM_GBS if HBM_GBS else None},
+            "fp64_pipe": {"inst_per_eval": FP64_PIPE_INST_PER_EVAL["mixed"],
+                          "frac": FP64_PIPE_INST_PER_EVAL["mixed"] * out["mixed"]["evals_per_s"]
+                          / (FP64_LANES_PER_CLK_PER_SM * 152 * 2070e6)},
+            "note": "issue-bound (73 % of issue slots, profiles/collapse_kernel_mixed_128cube_x30.md)",
+        },
         "bound_tol": 3e-5,
     }
 
@@ -583,6 +617,11 @@ def run_surrogate_variant(ctx, dev, stream, steps: int = 3000) -> dict:
         "evals_per_s": evals / (ms["surrogate"] * 1e-3),
         "engine": "tcgen05",
         "error_flags": stats["surrogate"]["error_flags"],
+        "tensor": {"algorithmic_flops_per_eval": MLP_FLOPS_PER_EVAL,
+                   "achieved_tflops": MLP_FLOPS_PER_EVAL * evals / (ms["surrogate"] * 1e-3) / 1e12,
+                   "peak_tflops": BF16_TFLOPS, "peak_basis": "measured dense BF16 GEMM (burst)",
+                   "frac": (MLP_FLOPS_PER_EVAL * evals / (ms["surrogate"] * 1e-3) / 1e12 / BF16_TFLOPS)
+                   if BF16_TFLOPS else None},
         "mma_sync_engine": {"evals_per_s": evals / (ms["surrogate_mma_sync"] * 1e-3),
                             "max_rel_diff_vs_fp64": t_max,
                             "fallback_fraction": stats["surrogate_mma_sync"]["fallback"]
