@@ -46,7 +46,7 @@ FP64_PIPE_INST_PER_EVAL = {"fp64": 45.0, "mixed": 8.3}
 FP64_LANES_PER_CLK_PER_SM = 2.0
 # DRAM bytes (read + write) of one full launch of the default workload, from
 # an ncu capture of that launch (profiles/collapse_kernel_fp64_256cube_x25_dram.md).
-TRAFFIC_BYTES_DEFAULT = 20.84e9
+TRAFFIC_BYTES_DEFAULT = 20.83e9
 # FP64 FMA rate of one GB300 SM: 1.25 TFLOP/s nominal at 2070 MHz over 152 SMs
 # = 3.97 flop/clk/SM, i.e. 2 DFMA per clock per SM (confirmed by a DFMA-chain probe).
 FP64_FLOP_PER_CLK_PER_SM = 4.0

@@ -104,11 +104,25 @@ static __device__ __noinline__ void refine_top_pair(double xx, double yy, double
 // ---- FP32 seeds. Newton corrections follow every seed (two on l1, two FP32
 // and one FP64 on D_c), so a relative accuracy of 1e-4 is enough and the
 // seeds use the special-function unit directly.
+
+// square root and reciprocal of a seed: the hardware's approximate forms (one
+// special-function instruction each, relative error near 2^-22) instead of
+// the correctly rounded ones, which take several more instructions
+__device__ __forceinline__ float sqrt_seed(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rcp_seed(float x) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 // arccos by the Hastings approximation of Abramowitz & Stegun 4.4.45
 // (|error| <= 5e-5 rad on [0, 1]; acos(-x) = pi - acos(x)).
 __device__ __forceinline__ float acos_seed(float x) {
   const float ax = fabsf(x);
-  const float p = fmaf(fmaf(fmaf(-0.0187293f, ax, 0.0742610f), ax, -0.2121144f), ax, 1.5707288f) * sqrtf(1.0f - ax);
+  const float p = fmaf(fmaf(fmaf(-0.0187293f, ax, 0.0742610f), ax, -0.2121144f), ax, 1.5707288f) * sqrt_seed(1.0f - ax);
   return (x < 0.0f) ? 3.14159265f - p : p;
 }
 
@@ -121,11 +135,11 @@ __device__ __forceinline__ float cubic_largest_root_seed(float b, float c, float
   const float disc = fmaf(0.25f * qq, qq, pp * pp * pp * (1.0f / 27.0f));
   float t;
   if (disc > 0.0f) {
-    const float A = __powf(fmaf(0.5f, fabsf(qq), sqrtf(disc)), 1.0f / 3.0f);  // cube root, A >= 0
+    const float A = __powf(fmaf(0.5f, fabsf(qq), sqrt_seed(disc)), 1.0f / 3.0f);  // cube root, A >= 0
     const float C = (qq > 0.0f) ? -A : A;
     t = (C != 0.0f) ? C - __fdividef(pp, 3.0f * C) : 0.0f;
   } else {
-    const float m = sqrtf(-pp * (1.0f / 3.0f));
+    const float m = sqrt_seed(-pp * (1.0f / 3.0f));
     float arg = (m > 0.0f) ? __fdividef(-0.5f * qq, m * m * m) : 0.0f;
     arg = fminf(1.0f, fmaxf(-1.0f, arg));
     t = 2.0f * m * __cosf(acos_seed(arg) * (1.0f / 3.0f));
@@ -181,7 +195,7 @@ __device__ __forceinline__ EigenTop eigen_top_fp64(double xx, double yy, double 
   // ---- FP32 trigonometric seed
   const float p2f = to_f32_trunc(p2x3) * (1.0f / 3.0f);
   const float detf = to_f32_trunc(det);
-  const float pf = sqrtf(p2f);
+  const float pf = sqrt_seed(p2f);
   float rf = (p2f > 0.0f) ? __fdividef(detf, 2.0f * p2f * pf) : 0.0f;
   rf = fminf(1.0f, fmaxf(-1.0f, rf));
   float sn, cs;
@@ -251,7 +265,7 @@ __device__ __forceinline__ Root rlpt_root_fp64(double lam1, double Pp, double S)
   r.Df = Df;
   const double D0 = to_f64(Df);
   const double A1 = fma(fma(fma(c3, D0, c2), D0, -lam1), D0, 1.0);
-  r.D = fma(-A1, to_f64(1.0f / dAf), D0);
+  r.D = fma(-A1, to_f64(rcp_seed(dAf)), D0);
   return r;
 }
 
@@ -391,7 +405,7 @@ __device__ __forceinline__ MixedEigen mixed_eigen_f32(float xx, float yy, float 
   const float s6 = fmaf(2.0f, fmaf(yz, yz, fmaf(xz, xz, xy * xy)), fmaf(c, c, fmaf(b, b, a * a)));
   const float p2 = s6 * (1.0f / 6.0f), p2x3 = 0.5f * s6;
   const float det = fmaf(xz, fmaf(xy, yz, -b * xz), fmaf(a, fmaf(b, c, -yz * yz), -xy * fmaf(xy, c, -yz * xz)));
-  const float pf = sqrtf(p2);
+  const float pf = sqrt_seed(p2);
   float rf = (p2 > 0.0f) ? __fdividef(det, 2.0f * p2 * pf) : 0.0f;
   rf = fminf(1.0f, fmaxf(-1.0f, rf));
   float sn, cs;
@@ -484,7 +498,7 @@ __device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const M
   const float dAf = fmaf(fmaf(3.0f * k.c3f, Df, 2.0f * k.c2f), Df, -k.l1f);
   double D = to_f64(Df);
   const double A1 = fma(fma(fma(to_f64(k.c3f), D, to_f64(k.c2f)), D, -m.lam1), D, 1.0);
-  D = fma(-A1, to_f64(1.0f / dAf), D);
+  D = fma(-A1, to_f64(rcp_seed(dAf)), D);
   const long long bD = bits(D);
   res.collapsed = m.lam1f > 0.0f && bD > 0 && bD <= bits(tab.Dtop);
   const double Dc = res.collapsed ? D : tab.Dtop;
@@ -623,7 +637,7 @@ __device__ __forceinline__ TabResult collapse_point_tab(
   bool root = true;
   if (!res.outside) {
     const double u = tab_interp(td, ax, tcoef, delta, xv, yv);
-    const double r0 = to_f64(1.0f / to_f32_trunc(u));
+    const double r0 = to_f64(rcp_seed(to_f32_trunc(u)));
     D = fma(r0, fma(-u, r0, 1.0), r0);  // 1/u: FP32 reciprocal + one FP64 Newton step
     root = bits(u) > 0;
   } else {

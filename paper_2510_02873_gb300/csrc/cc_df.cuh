@@ -136,7 +136,7 @@ __device__ __forceinline__ Result collapse_point(const T* __restrict__ h, int64_
                      mul(xz, sub(mul(xy, yz), mul(b, xz))));
   // ---- FP32 trigonometric seed of x = l1 - q
   const float p2f = p2x3.hi * (1.0f / 3.0f);
-  const float pf = sqrtf(p2f);
+  const float pf = sqrt_seed(p2f);
   float rf = (p2f > 0.0f) ? __fdividef(det.hi, 2.0f * p2f * pf) : 0.0f;
   rf = fminf(1.0f, fmaxf(-1.0f, rf));
   const float x1f = 2.0f * pf * __cosf(acos_seed(rf) * (1.0f / 3.0f));
