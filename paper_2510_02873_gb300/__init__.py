@@ -190,16 +190,23 @@ class Batch:
         self.nitems = len(items)
 
     def autotune(self, cache_path=None, stream=None):
+        """Time candidate block sizes and tiles per grid size on these
+        realizations and keep the fastest (cc_batch_autotune); with a cache
+        file, reuse or record the choice. Overwrites the outputs."""
         path = cache_path.encode() if cache_path else None
         _lib.check(_lib.load().cc_batch_autotune(self._h, path, _stream_ptr(stream)), "cc_batch_autotune")
 
     def run(self, stream=None):
+        """One persistent launch over every realization (cc_batch_run)."""
         _lib.check(_lib.load().cc_batch_run(self._h, _stream_ptr(stream)), "cc_batch_run")
 
     def run_graph(self, stream=None):
+        """The same launch from a CUDA graph, captured on first use and
+        replayed afterwards (cc_batch_run_graph)."""
         _lib.check(_lib.load().cc_batch_run_graph(self._h, _stream_ptr(stream)), "cc_batch_run_graph")
 
     def config(self):
+        """(threads per block, [tile points per realization]) in use."""
         blk = ctypes.c_int32()
         tiles = (ctypes.c_int32 * self.nitems)()
         _lib.check(_lib.load().cc_batch_get_config(self._h, ctypes.byref(blk), tiles, self.nitems),
@@ -207,6 +214,7 @@ class Batch:
         return int(blk.value), list(tiles)
 
     def close(self):
+        """Free the plan (cc_batch_destroy); the caller's tensors are untouched."""
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib.load().cc_batch_destroy(self._h)
             self._h = None
@@ -223,11 +231,15 @@ class Context:
     """Owns one cc_ctx (tables on the device) for the given cosmology."""
 
     def __init__(self, omega_m=0.3, omega_l=0.7, n_knots=512, a_min=1e-3, a_max=1.0, device=0):
+        """Flat LCDM (omega_m + omega_l = 1 not required), growth table of
+        n_knots knots log-spaced in a over [a_min, a_max], on CUDA device
+        `device` (cc_create)."""
         self.n_knots = n_knots
         self.device = device
         self._h = cc_create(omega_m, omega_l, n_knots, a_min, a_max, device)
 
     def close(self):
+        """Release the device tables and scratch (cc_destroy)."""
         if getattr(self, "_h", None) is not None and self._h.value:
             cc_destroy(self._h)
             self._h = None
@@ -249,18 +261,27 @@ class Context:
         return self._h
 
     def growth_table(self):
+        """(a_k, D_k) of the growth table, host arrays (cc_get_growth_table)."""
         return cc_get_growth_table(self._h, self.n_knots)
 
     def reset_max(self, F_max, idx, stream=None):
+        """F_max = 0 and idx = -1 on the device (cc_reset_max)."""
         cc_reset_max(self._h, F_max, idx, None, stream)
 
     def collapse_scale(self, hess, sigma_R, F_max, idx, scale_idx, mode="fp64", stream=None):
+        """One radius: hess (6, n) CUDA planes (float64 or float32), sigma_R
+        its rms; F_max/idx updated where F > F_max (cc_collapse_scale)."""
         cc_collapse_scale(self._h, mode, hess, sigma_R, F_max, idx, scale_idx, stream)
 
     def collapse_multi(self, hess, sigma, F_max, idx, scale_idx0=0, mode="fp64", stream=None):
+        """All radii in one fused launch: hess (R, 6, n) CUDA planes, sigma
+        (R,); the running maximum stays in registers (cc_collapse_multi)."""
         cc_collapse_multi(self._h, mode, hess, sigma, F_max, idx, scale_idx0, stream)
 
     def collapse_multi_host(self, hess, sigma, F_max, idx, scale_idx0=0, mode="fp64", stream=None):
+        """The same from pinned host planes and host F_max/idx: the copies
+        of radius r + 1 overlap the launch of radius r; synchronises
+        (cc_collapse_multi_host)."""
         cc_collapse_multi_host(self._h, mode, hess, sigma, F_max, idx, scale_idx0, stream)
 
     # ---- tabulated collapse and interpolation routines
@@ -273,6 +294,7 @@ class Context:
                    "cc_set_table")
 
     def table_nodes_rlpt(self, dgrid, xgrid, ygrid, stream=None) -> np.ndarray:
+        """u = 1/D_c by R-LPT at every (x, y, delta) node, computed on the device; (nx, ny, nd) host array."""
         dg, xg, yg = (np.ascontiguousarray(a, dtype=np.float64) for a in (dgrid, xgrid, ygrid))
         out = np.empty((len(xg), len(yg), len(dg)))
         _lib.check(_lib.load().cc_table_nodes_rlpt(self._h, dg.ctypes.data, len(dg), xg.ctypes.data, len(xg),
@@ -322,6 +344,7 @@ class Context:
         return rep.as_dict()
 
     def surrogate_params(self):
+        """The network's FP32 master parameters (8641) and training hull (6), host arrays."""
         params = np.empty(self.MLP_NPARAM, dtype=np.float32)
         hull = np.empty(6, dtype=np.float32)
         _lib.check(_lib.load().cc_surrogate_params(self._h, params.ctypes.data, hull.ctypes.data),
@@ -329,6 +352,7 @@ class Context:
         return params, hull
 
     def load_surrogate(self, params, hull):
+        """Install a network from host parameters (8641 floats) and hull (lo[3], hi[3])."""
         params = np.ascontiguousarray(params, dtype=np.float32)
         hull = np.ascontiguousarray(hull, dtype=np.float32)
         if params.size != self.MLP_NPARAM or hull.size != 6:
@@ -350,6 +374,7 @@ class Context:
                                                  _stream_ptr(stream)), "cc_surrogate_eval")
 
     def surrogate_grad(self, z, t):
+        """One minibatch gradient of the training kernel on host samples z (n, 3), t (n,): (grad, loss)."""
         z = np.ascontiguousarray(z, dtype=np.float32)
         t = np.ascontiguousarray(t, dtype=np.float32)
         grad = np.empty(self.MLP_NPARAM, dtype=np.float32)
@@ -359,9 +384,11 @@ class Context:
         return float(loss.value), grad
 
     def stats(self, stream=None) -> dict:
+        """Device counters since the last reset_stats (cc_get_stats; synchronises the stream)."""
         return cc_get_stats(self._h, stream)
 
     def reset_stats(self, stream=None):
+        """Zero the device counters (cc_reset_stats)."""
         cc_reset_stats(self._h, stream)
 
 
@@ -386,6 +413,7 @@ class Field:
         self._h = h.value
 
     def sigma(self, R: float, stream=None) -> float:
+        """rms of delta smoothed at radius R (Gaussian filter), from the device field."""
         out = ctypes.c_double()
         _lib.check(_lib.load().cc_field_sigma(self._h, float(R), ctypes.byref(out), _stream_ptr(stream)),
                    "cc_field_sigma")
@@ -403,6 +431,7 @@ class Field:
                                                 _stream_ptr(stream)), "cc_field_hessian")
 
     def close(self) -> None:
+        """Release the device field (cc_field_destroy)."""
         if self._h:
             _lib.load().cc_field_destroy(self._h)
             self._h = None
