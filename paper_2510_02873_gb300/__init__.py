@@ -374,7 +374,7 @@ class Context:
                                                  _stream_ptr(stream)), "cc_surrogate_eval")
 
     def surrogate_grad(self, z, t):
-        """One minibatch gradient of the training kernel on host samples z (n, 3), t (n,): (grad, loss)."""
+        """One minibatch gradient of the training kernel on host samples z (n, 3), t (n,): (loss, grad)."""
         z = np.ascontiguousarray(z, dtype=np.float32)
         t = np.ascontiguousarray(t, dtype=np.float32)
         grad = np.empty(self.MLP_NPARAM, dtype=np.float32)
