@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -154,6 +155,35 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle
+def _cpu_times():
+    """Per-core (busy, steal, total) jiffies from /proc/stat, or None where the
+    host has none. busy = user + nice + system + irq + softirq."""
+    try:
+        with open("/proc/stat") as f:
+            rows = [line.split() for line in f if re.match(r"cpu\d+ ", line)]
+    except OSError:
+        return None
+    out = []
+    for row in rows:
+        v = [int(x) for x in row[1:9]]
+        out.append((v[0] + v[1] + v[2] + v[5] + v[6], v[7], sum(v)))
+    return out
+
+
+def _cpu_share(before, after) -> dict | None:
+    """What the host's cores did between two _cpu_times() snapshots: mean busy
+    and steal fractions over all cores and the least busy core's fraction."""
+    if not before or not after or len(before) != len(after):
+        return None
+    per = []
+    for (b0, s0, t0), (b1, s1, t1) in zip(before, after):
+        dt = max(t1 - t0, 1)
+        per.append(((b1 - b0) / dt, (s1 - s0) / dt))
+    return {"busy_frac": round(sum(p[0] for p in per) / len(per), 3),
+            "steal_frac": round(sum(p[1] for p in per) / len(per), 3),
+            "min_core_busy_frac": round(min(p[0] for p in per), 3)}
+
+
 def cpu_oracle_rate(seconds: float, first_point: int = 0, points_per_chunk: int = 2048):
     """The FP64 oracle on consecutive chunks of the workload's points (all 25
     radii each), until `seconds` of CPU work. Inputs are drawn before timing."""
@@ -165,21 +195,30 @@ def cpu_oracle_rate(seconds: float, first_point: int = 0, points_per_chunk: int 
     t = oracle.Tables(**{k: COSMO[k] for k in ("omega_m", "omega_l", "n_knots", "a_min", "a_max")})
     sig = hessgen.sigma_schedule(N_RADII, S_LO, S_HI)
     evals, elapsed, p0 = 0, 0.0, first_point
+    cpu_acc = None  # per-core jiffies summed over the timed calls only
     while evals == 0 or elapsed < seconds:
         pts = np.arange(p0, p0 + points_per_chunk, dtype=np.int64)
         stack = np.stack([hessgen.hessian_points(SEED, 0, r, sig[r], pts) for r in range(N_RADII)])
         F = np.zeros(len(pts))
         idx = np.full(len(pts), -1, dtype=np.int32)
+        c0 = _cpu_times()
         t0 = time.perf_counter()
         for r in range(N_RADII):
             t.collapse_scale(stack[r], F, idx, r)
         elapsed += time.perf_counter() - t0
+        c1 = _cpu_times()
+        if c0 and c1:
+            cpu_acc = [tuple(a + (y - x) for a, x, y in zip(acc, u, w))
+                       for acc, u, w in zip(cpu_acc or [(0, 0, 0)] * len(c0), c0, c1)]
         evals += len(pts) * N_RADII
         p0 += points_per_chunk
     cores = os.cpu_count()
     out = {"value": evals / elapsed, "unit": "evals/s", "cores": cores, "kind": "oracle",
            "sample": f"{p0 - first_point} points x {N_RADII} radii of the workload "
                      f"({evals} evaluations, {elapsed:.1f} s, OpenMP over {cores} threads)"}
+    if cpu_acc:
+        # the host's cores over the timed calls (all processes, from /proc/stat)
+        out["host_cpu"] = _cpu_share([(0, 0, 0)] * len(cpu_acc), cpu_acc)
     if seconds > 0:
         # one thread on the next chunk of points
         pts = np.arange(p0, p0 + 512, dtype=np.int64)
@@ -218,6 +257,12 @@ def run_reference(args):
                          "sample": f"{args.steps} steps of 4096 points x {N_RADII} radii"},
         "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    shares = [r["host_cpu"] for r in steps if r.get("host_cpu")]
+    if shares:
+        line["cpu_baseline"]["host_cpu"] = {
+            "busy_frac": round(statistics.mean(h["busy_frac"] for h in shares), 3),
+            "steal_frac": round(statistics.mean(h["steal_frac"] for h in shares), 3),
+            "min_core_busy_frac": min(h["min_core_busy_frac"] for h in shares)}
     print(json.dumps(line), flush=True)
 
 
