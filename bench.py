@@ -184,10 +184,16 @@ def _cpu_share(before, after) -> dict | None:
             "min_core_busy_frac": round(min(p[0] for p in per), 3)}
 
 
-def cpu_oracle_rate(seconds: float, first_point: int = 0, points_per_chunk: int = 2048):
+def cpu_oracle_rate(seconds: float, first_point: int = 0, points_per_chunk: int | None = None):
     """The FP64 oracle on consecutive chunks of the workload's points (all 25
-    radii each), until `seconds` of CPU work. Inputs are drawn before timing."""
+    radii each), until `seconds` of CPU work. Inputs are drawn before timing.
+    The oracle hands out points to its threads 256 at a time, so the default
+    chunk gives every host core four such blocks per radius (a chunk of 2048
+    points kept 8 of 16 cores busy)."""
     import numpy as np
+
+    if points_per_chunk is None:
+        points_per_chunk = 1024 * (os.cpu_count() or 1)
 
     import hessgen
     import oracle
