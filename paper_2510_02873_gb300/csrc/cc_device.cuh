@@ -488,31 +488,41 @@ __device__ __forceinline__ float newton_f32(const MixedCoef& k, float Df) {
 
 // From an FP32 root Df: one FP64 Newton step (the root polish), the FP64
 // a(D) spline and F.
+//   polish: A_1(D0) at D0 = Df in FP64 except c3 D0 + c2, which is formed in
+//     FP32 (c2 and c3 are FP32 values here; that rounding is of the size of
+//     theirs);
+//   spline: the polished root enters only through t = D - D_k, formed in the
+//     same FP64 FMA as the Newton step, t = (D0 - D_k) - A_1 / A_1', with
+//     D0 - D_k = (Df - hi(D_k)) - lo(D_k) in FP32 (the first difference is
+//     exact, the second rounds by ~2^-24 |t| <= 1e-9 D). Then a = c0 + t v
+//     with v = c1 + t (c2 + c3 t) in FP32 and c0 + t v in FP64: c1 t is at
+//     most ~1.4e-2 of a over an interval, so v's FP32 rounding (and taking
+//     the unpolished t there) moves a by ~1e-9 relative. On the EdS segment
+//     below the first knot, a = (a_0 / D_0) D is the same FMA with
+//     v = hi(a_0 / D_0), t = D and the head lo(a_0 / D_0) D formed in FP32;
+//   the collapse and EdS tests take Df: the FP32 and the polished root fall on
+//     the same side of D_top or D_0 except within ~1e-7 of them, where the two
+//     sides give the same a (a_max at D_top; the spline is continuous at D_0).
 __device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const MixedCoef& k, float Df,
-                                                    const double* __restrict__ Dk, const Coef4* __restrict__ coef,
-                                                    const float* __restrict__ Dkf,
+                                                    const Coef4* __restrict__ coef, const float* __restrict__ Dkf,
                                                     const unsigned short* __restrict__ bucket, const DevTable& tab) {
   MixedResult res;
   res.refined = false;
   res.fp64 = m.fp64;
   const float dAf = fmaf(fmaf(3.0f * k.c3f, Df, 2.0f * k.c2f), Df, -k.l1f);
-  double D = to_f64(Df);
-  const double A1 = fma(fma(fma(to_f64(k.c3f), D, to_f64(k.c2f)), D, -m.lam1), D, 1.0);
-  D = fma(-A1, to_f64(rcp_seed(dAf)), D);
-  const long long bD = bits(D);
-  res.collapsed = m.lam1f > 0.0f && bD > 0 && bD <= bits(tab.Dtop);
-  const double Dc = res.collapsed ? D : tab.Dtop;
+  const double D0 = to_f64(Df);
+  const double A1 = fma(fma(to_f64(fmaf(k.c3f, Df, k.c2f)), D0, -m.lam1), D0, 1.0);
+  res.collapsed = m.lam1f > 0.0f && Df > 0.0f && Df <= tab.Dtopf;
   const float Dcf = res.collapsed ? Df : tab.Dtopf;
   const int kk = spline_interval(Dkf, bucket, tab, Dcf);
-  const Coef4 cf = coef[kk];
-  res.eds = res.collapsed && bits(Dc) < bits(tab.D0);
-  // c2 + c3 t in FP32 (c2, c3 rounded to FP32 in the float-float image): with
-  // |t| <= h ~ 0.014 D these terms are ~1e-4 of a, so their FP32 rounding moves
-  // a by ~1e-12 relative; c0 + t (c1 + t u) in FP64 (the EdS segment as in spline_a)
-  const float2 c23 = __ldg(reinterpret_cast<const float2*>(tab.dfseg + 2 * kk + 1));
-  const float u = res.eds ? 0.0f : fmaf(c23.y, Dcf - Dkf[kk], c23.x);
-  const double t = Dc - (res.eds ? 0.0 : Dk[kk]);
-  const double av = fma(fma(to_f64(u), t, res.eds ? tab.eds_slope : cf.c1), t, res.eds ? 0.0 : cf.c0);
+  res.eds = res.collapsed && Df < Dkf[0];
+  const float4 s0 = __ldg(tab.dfseg + 2 * kk);      // {hi(c0), lo(c0), hi(c1), lo(c1)}
+  const float4 s1 = __ldg(tab.dfseg + 2 * kk + 1);  // {c2, c3, hi(D_k), lo(D_k)}
+  const float t0 = res.eds ? Dcf : __fsub_rn(__fsub_rn(Dcf, s1.z), s1.w);
+  const float v = res.eds ? tab.eds_hi : fmaf(fmaf(s1.y, t0, s1.x), t0, s0.z);
+  const double head = res.eds ? to_f64(tab.eds_lo * Dcf) : coef[kk].c0;
+  const double t = fma(-A1, to_f64(rcp_seed(dAf)), to_f64(t0));
+  const double av = fma(to_f64(v), t, head);
   res.a = res.collapsed ? av : kInf;
   res.F = res.collapsed ? to_f64(1.0f / to_f32_trunc(av)) : 0.0;
   return res;
@@ -544,7 +554,7 @@ __device__ __forceinline__ MixedResult collapse_point_mixed(
   // FP32 closed-form root of u^3 - l1 u^2 + c2 u + c3 (u = 1/D), two FP32 Newton steps on A_1
   const float uf = cubic_largest_root_seed(-k.l1f, k.c2f, k.c3f);
   const float Df = newton_f32<2>(k, __fdividef(1.0f, uf));
-  return mixed_finish(m, k, Df, Dk, coef, Dkf, bucket, tab);
+  return mixed_finish(m, k, Df, coef, Dkf, bucket, tab);
 }
 
 // ---------------------------------------------------------------------------

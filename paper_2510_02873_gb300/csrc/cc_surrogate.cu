@@ -468,7 +468,7 @@ __device__ __forceinline__ MixedResult sur_finish(const MixedEigen& m, float f, 
       ok = Df > 0.0f && isfinite(Df) && fabsf(Af) <= kCertTol * fabsf(dAf * Df);
     }
     if (ok) {
-      res = mixed_finish(m, k, Df, Dk, coef, Dkf, bucket, tab);
+      res = mixed_finish(m, k, Df, coef, Dkf, bucket, tab);
     } else {
       res = full_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
       ++n_fb;
