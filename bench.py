@@ -39,11 +39,11 @@ WORKLOAD = "collapse 256^3 grid x 25 radii, FP64 SoA Hessian planes (20.1 GB res
 # by the evaluations of the captured launch (profiles/collapse_kernel_*_128cube_x4.md).
 # None until a capture of the current kernel exists.
 FP64_FLOPS_PER_EVAL = 70.0   # profiles/collapse_kernel_fp64_128cube_x4.md
-FP64_FLOPS_PER_EVAL_MIXED = 13.1  # profiles/collapse_kernel_mixed_128cube_x30.md
+FP64_FLOPS_PER_EVAL_MIXED = 8.1  # profiles/collapse_kernel_mixed_128cube_x30.md
 # FP64-pipe warp instructions of every kind (DFMA, DMUL, DADD, compares) per
 # evaluation, from the same captures: the FP64 unit issues one per lane slot
 # whatever the instruction, so this count, not the flop count, sets the time.
-FP64_PIPE_INST_PER_EVAL = {"fp64": 45.0, "mixed": 8.3}
+FP64_PIPE_INST_PER_EVAL = {"fp64": 45.0, "mixed": 5.1}
 FP64_LANES_PER_CLK_PER_SM = 2.0
 # DRAM bytes (read + write) of one full launch of the default workload, from
 # an ncu capture of that launch (profiles/collapse_kernel_fp64_256cube_x25_dram.md).
