@@ -55,6 +55,15 @@ __device__ __forceinline__ double to_f64(float f) {
   if (mag >= 0x7f800000u) hi = sign | 0x7ff00000u | ((mag >> 3) & 0x000fffffu);
   return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
 }
+// to_f64_normal: the same widening without the special cases, for operands
+// that are normal FP32 numbers wherever the result is used (five integer
+// instructions instead of ten). Zero and subnormals map to a number below
+// 2^-126 in magnitude with their sign; infinities and NaNs to finite values.
+__device__ __forceinline__ double to_f64_normal(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned hi = (((u & 0x7fffffffu) >> 3) + (896u << 20)) | (u & 0x80000000u);
+  return __hiloint2double(static_cast<int>(hi), static_cast<int>(u << 29));
+}
 
 // Re-solve l1 >= l2 when they are nearly equal: l3 (isolated) gives an
 // eigenvector v3 as the largest cross product of two rows of A - l3 I; A
@@ -429,7 +438,7 @@ __device__ __forceinline__ MixedEigen mixed_eigen_f32(float xx, float yy, float 
   m.p2 = p2;
   m.p2x3 = p2x3;
   m.lam1f = lam1f;
-  m.lam1 = to_f64(lam1f);
+  m.lam1 = to_f64_normal(lam1f);  // exact wherever l1 > 0 can collapse (a normal lam1f)
   return m;
 }
 
@@ -447,6 +456,7 @@ __device__ __forceinline__ void mixed_refine64(MixedEigen& m, float xx, float yy
   const float gpf = 3.0f * fmaf(m.x, m.x, -m.p2);
   m.lam1 = fma(g, to_f64(__fdividef(1.0f, gpf)), lam1);
   m.x = to_f32_trunc(m.lam1 - to_f64(m.q));
+  m.lam1f = to_f32_trunc(m.lam1);
   m.fp64 = true;
 }
 
@@ -468,7 +478,7 @@ __device__ __forceinline__ MixedCoef mixed_coef(const MixedEigen& m) {
   const float S = fmaf(2.0f, q, -x);                     // l2 + l3
   const float Q2 = fmaf(-2.0f, Pp, S * S);               // l2^2 + l3^2
   MixedCoef k;
-  k.l1f = to_f32_trunc(m.lam1);
+  k.l1f = m.lam1f;
   k.c2f = (-3.0f / 7.0f) * Pp;
   k.c3f = k.l1f * fmaf(-5.0f / 21.0f, Q2, Pp * (1.0f / 9.0f));
   return k;
@@ -502,7 +512,10 @@ __device__ __forceinline__ float newton_f32(const MixedCoef& k, float Df) {
 //     v = hi(a_0 / D_0), t = D and the head lo(a_0 / D_0) D formed in FP32;
 //   the collapse and EdS tests take Df: the FP32 and the polished root fall on
 //     the same side of D_top or D_0 except within ~1e-7 of them, where the two
-//     sides give the same a (a_max at D_top; the spline is continuous at D_0).
+//     sides give the same a (a_max at D_top; the spline is continuous at D_0);
+//   FP32 -> FP64 by to_f64_normal: for a collapsing point Df, A_1'(Df) and v
+//     are normal numbers, and a zero t0, c3 Df + c2 or lo(a_0 / D_0) D shifts
+//     t, A_1 or a by less than 2^-126.
 __device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const MixedCoef& k, float Df,
                                                     const Coef4* __restrict__ coef, const float* __restrict__ Dkf,
                                                     const unsigned short* __restrict__ bucket, const DevTable& tab) {
@@ -510,8 +523,8 @@ __device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const M
   res.refined = false;
   res.fp64 = m.fp64;
   const float dAf = fmaf(fmaf(3.0f * k.c3f, Df, 2.0f * k.c2f), Df, -k.l1f);
-  const double D0 = to_f64(Df);
-  const double A1 = fma(fma(to_f64(fmaf(k.c3f, Df, k.c2f)), D0, -m.lam1), D0, 1.0);
+  const double D0 = to_f64_normal(Df);
+  const double A1 = fma(fma(to_f64_normal(fmaf(k.c3f, Df, k.c2f)), D0, -m.lam1), D0, 1.0);
   res.collapsed = m.lam1f > 0.0f && Df > 0.0f && Df <= tab.Dtopf;
   const float Dcf = res.collapsed ? Df : tab.Dtopf;
   const int kk = spline_interval(Dkf, bucket, tab, Dcf);
@@ -520,9 +533,9 @@ __device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const M
   const float4 s1 = __ldg(tab.dfseg + 2 * kk + 1);  // {c2, c3, hi(D_k), lo(D_k)}
   const float t0 = res.eds ? Dcf : __fsub_rn(__fsub_rn(Dcf, s1.z), s1.w);
   const float v = res.eds ? tab.eds_hi : fmaf(fmaf(s1.y, t0, s1.x), t0, s0.z);
-  const double head = res.eds ? to_f64(tab.eds_lo * Dcf) : coef[kk].c0;
-  const double t = fma(-A1, to_f64(rcp_seed(dAf)), to_f64(t0));
-  const double av = fma(to_f64(v), t, head);
+  const double head = res.eds ? to_f64_normal(tab.eds_lo * Dcf) : coef[kk].c0;
+  const double t = fma(-A1, to_f64_normal(rcp_seed(dAf)), to_f64_normal(t0));
+  const double av = fma(to_f64_normal(v), t, head);
   res.a = res.collapsed ? av : kInf;
   res.F = res.collapsed ? to_f64(1.0f / to_f32_trunc(av)) : 0.0;
   return res;
