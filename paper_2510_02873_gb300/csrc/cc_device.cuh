@@ -395,11 +395,12 @@ struct MixedResult {
 
 // FP32 eigenvalue stage of the mixed path (shared with the surrogate path).
 struct MixedEigen {
-  float q, x, x2, x3, p2, p2x3, lam1f;  // x = l1 - q (x2, x3: FP32 seeds of l2 - q, l3 - q)
-  double lam1;                          // l1, refined in FP64 when flagged
-  bool full;                            // take the whole FP64 path instead
-  bool need64;                          // l1 needs the FP64 refinement (mixed_refine64)
-  bool fp64;                            // the FP64 eigenvalue refinement ran
+  float q, x, x2, x3, p2, p2x3;  // x = l1 - q (x2, x3: FP32 seeds of l2 - q, l3 - q)
+  float lam1f;                    // l1 in FP32 (truncated from lam1 after the FP64 refinement)
+  double lam1;                    // l1, refined in FP64 when flagged
+  bool full;                      // take the whole FP64 path instead
+  bool need64;                    // l1 needs the FP64 refinement (mixed_refine64)
+  bool fp64;                      // the FP64 eigenvalue refinement ran
 };
 
 // The FP32 part: invariants, trigonometric eigenvalues, two FP32 Newton
