@@ -26,7 +26,7 @@ namespace cc {
 constexpr float kSqrt3f = 1.7320508075688772935f;
 // 1 + r (FP32) below this: l1 and l2 are too close for a Newton step from the
 // FP32 trigonometric seed to converge quadratically; the pair is re-solved by
-// deflation in FP64 instead (about 3e-4 of isotropic Gaussian points).
+// deflation in FP64 instead (about 5e-5 of the evaluations on isotropic Gaussian Hessians).
 constexpr float kPairTauF = 1e-4f;
 
 __device__ __forceinline__ long long bits(double x) { return __double_as_longlong(x); }
