@@ -235,3 +235,23 @@ def test_mixed_eds_segment_below_first_knot(ctx, tables):
     # a point within the tolerance of D_0 may land on either side
     assert abs(st["eds_branch"] - n_eds) <= 2
     print("mixed EdS segment", s, st["eds_branch"], n_eds)
+
+
+def test_mixed_non_finite_inputs_give_no_collapse(ctx, tables):
+    """NaN planes give no collapse and infinite ones a finite F (the FP32 ->
+    FP64 widenings of the mixed finish skip the special cases); the clean
+    points of the same warps keep their oracle values."""
+    n = 256
+    stack = np.zeros((1, 6, n), dtype=np.float32)
+    stack[0, 0, :] = 2.0  # plane wave: l1 = 2, D_c = 1/2
+    stack[0, :, ::4] = np.nan
+    stack[0, 0, 1::4] = np.inf
+    stack[0, 1, 3::8] = -np.inf
+    F, idx, st = run_mixed(ctx, stack, [1.0])
+    assert st["error_flags"] == 0
+    assert np.all(np.isfinite(F)) and np.all(F >= 0)
+    assert np.all(F[::4] == 0) and np.all(idx[::4] == -1)
+    clean = np.arange(2, n, 4)
+    F_all, fl = oracle_per_radius(tables, stack[:, :, clean].astype(np.float64))
+    assert np.all(F_all[0] > 0)
+    assert np.max(rel_err(F[clean], F_all[0])) <= REL_TOL_MIXED

@@ -284,3 +284,34 @@ def test_surrogate_small_and_fp64_planes(ctx, tables, trained, engine, n):
     st = ctx.stats()
     assert st["evaluations"] == n * R and st["error_flags"] == 0
     compare_reduced(F.cpu().numpy(), idx.cpu().numpy(), F_all, fl)
+
+
+@pytest.mark.parametrize("engine", ["mma_sync", "tcgen05"])
+def test_surrogate_non_finite_inputs_give_no_collapse(ctx, tables, trained, engine):
+    """NaN planes give no collapse, infinite ones a finite F, and the clean
+    points of the same tile keep their oracle values, with either engine."""
+    n = 256
+    stack = np.zeros((1, 6, n), dtype=np.float32)
+    stack[0, 0, :] = 2.0
+    stack[0, 1, :] = -0.5
+    stack[0, :, ::4] = np.nan
+    stack[0, 0, 1::4] = np.inf
+    h = torch.from_numpy(stack).cuda()
+    F = torch.empty(n, dtype=torch.float64, device="cuda")
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    ctx.reset_max(F, idx)
+    ctx.reset_stats()
+    ctx.set_surrogate_engine(engine)
+    try:
+        ctx.collapse_multi(h, [1.0], F, idx, mode="surrogate")
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_surrogate_engine("tcgen05")
+    assert ctx.stats()["error_flags"] == 0
+    F, idx = F.cpu().numpy(), idx.cpu().numpy()
+    assert np.all(np.isfinite(F)) and np.all(F >= 0)
+    assert np.all(F[::4] == 0) and np.all(idx[::4] == -1)
+    clean = np.concatenate([np.arange(2, n, 4), np.arange(3, n, 4)])
+    F_all, fl = oracle_per_radius(tables, stack[:, :, clean].astype(np.float64))
+    assert np.all(F_all[0] > 0)
+    assert np.max(rel_err(F[clean], F_all[0])) <= REL_TOL
