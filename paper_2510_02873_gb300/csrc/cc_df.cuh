@@ -54,7 +54,6 @@ __device__ __forceinline__ f2 addu(f2 a, f2 b) {
   const f2 s = two_sum(a.hi, b.hi);
   return {s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
 }
-__device__ __forceinline__ f2 subu(f2 a, f2 b) { return addu(a, neg(b)); }
 // Products are returned unnormalised: {RN(ab), the rest}, |lo| a few ulp(hi)
 // at most. Every sum renormalises (Fast2Sum), and only sums are compared, so
 // the renormalisation a product would need is left to the sum that consumes it.
