@@ -388,6 +388,38 @@ def test_collapse_condition_is_monotone_for_sorted_eigenvalues():
     assert np.all((c2 > 0) == (lam[:4000, 1] * lam[:4000, 2] < 0))
 
 
+# ---------------------------------------------------------------------------- P12
+def test_newton_step_certifies_the_root_error():
+    """The surrogate's acceptance test: at D near the collapse root D*, the
+    Newton step |A_1(D) / A_1'(D)| equals |D - D*| up to a term quadratic in
+    the error (A_1 is a cubic, so the step error is bounded by the second
+    derivative), and it is exact when D = D*. Checked against the oracle's root
+    on random sorted triples at relative offsets 1e-3 .. 1e-7."""
+    rng = _rng(14)
+    lam = -np.sort(-rng.normal(size=(3000, 3)) * 1.5, axis=1)
+    lam = lam[lam[:, 0] > 0]
+    D_top = 1e6
+    checked = 0
+    for l in lam:
+        Ds, flags = oracle.collapse_D(l, D_top)
+        if not (0 < Ds < D_top):
+            continue
+        c = oracle.axis_coeffs(l, 0)
+        A = lambda D: c[0] + D * (c[1] + D * (c[2] + D * c[3]))
+        dA = lambda D: c[1] + D * (2 * c[2] + D * 3 * c[3])
+        d2A = lambda D: 2 * c[2] + 6 * c[3] * D
+        assert abs(A(Ds)) <= 1e-12 * (1 + abs(c[1] * Ds))
+        for rel in (1e-3, -1e-3, 1e-5, -1e-5, 1e-7):
+            D = Ds * (1 + rel)
+            step = abs(A(D) / dA(D))
+            err = abs(D - Ds)
+            # |step - err| <= max|A''| err^2 / (2 |A'(D)|) on [D*, D]
+            curv = max(abs(d2A(Ds)), abs(d2A(D)))
+            assert abs(step - err) <= curv * err * err / (2 * abs(dA(D))) * 1.01 + 1e-15 * Ds
+        checked += 1
+    assert checked > 1000
+
+
 # ------------------------------------------------------------------- tabulated
 def test_cubic_largest_root_matches_numpy():
     rng = _rng(13)
