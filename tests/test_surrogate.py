@@ -315,3 +315,52 @@ def test_surrogate_non_finite_inputs_give_no_collapse(ctx, tables, trained, engi
     F_all, fl = oracle_per_radius(tables, stack[:, :, clean].astype(np.float64))
     assert np.all(F_all[0] > 0)
     assert np.max(rel_err(F[clean], F_all[0])) <= REL_TOL
+
+
+def test_surrogate_invalid_arguments_are_rejected(ctx):
+    """Each surrogate entry point refuses what its header rules out: a fresh
+    context has no network for CC_MODE_SURROGATE, eval, grad or params; the
+    engine must be one of the two; loaded parameters must be finite and the
+    hull ordered; training needs enough points and a valid configuration."""
+    import paper_2510_02873_gb300 as cc
+    from paper_2510_02873_gb300 import _lib
+    L = _lib.load()
+    fresh = cc.Context(0.3, 0.7, 512, 1e-3, 1.0, device=0)
+    try:
+        n = 64
+        h = torch.zeros((1, 6, n), dtype=torch.float32, device="cuda")
+        F = torch.empty(n, dtype=torch.float64, device="cuda")
+        idx = torch.empty(n, dtype=torch.int32, device="cuda")
+        fresh.reset_max(F, idx)
+        with pytest.raises(cc.CollapseError):
+            fresh.collapse_multi(h, [1.0], F, idx, mode="surrogate")
+        z = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+        out = torch.empty(n, dtype=torch.float32, device="cuda")
+        with pytest.raises(cc.CollapseError):
+            fresh.surrogate_eval(z, out)
+        with pytest.raises(cc.CollapseError):
+            fresh.surrogate_grad(np.zeros((n, 3)), np.zeros(n))
+        with pytest.raises(cc.CollapseError):
+            fresh.surrogate_params()
+        assert L.cc_set_surrogate_engine(fresh.handle, 2) == _lib.CC_EINVAL
+        assert L.cc_set_surrogate_engine(fresh.handle, -1) == _lib.CC_EINVAL
+        with pytest.raises(ValueError):
+            fresh.set_surrogate_engine("wmma")
+        p = np.zeros(cc.Context.MLP_NPARAM, dtype=np.float32)
+        with pytest.raises(cc.CollapseError):
+            fresh.load_surrogate(np.full_like(p, np.nan), [0, 0, 0, 1, 1, 1])
+        with pytest.raises(cc.CollapseError):
+            fresh.load_surrogate(p, [0, 0, 2, 1, 1, 1])
+        small = torch.zeros((6, 512), dtype=torch.float32, device="cuda")
+        with pytest.raises(cc.CollapseError):
+            fresh.surrogate_train(small, 1.0, steps=1, batch=64)
+        big = torch.zeros((6, 4096), dtype=torch.float32, device="cuda")
+        with pytest.raises(cc.CollapseError):
+            fresh.surrogate_train(big, 1.0, steps=1, batch=100)  # not a multiple of 64
+        # after a valid load the calls work
+        fresh.load_surrogate(p, [0, -1, -1, 1, 1, 1])
+        fresh.surrogate_eval(z, out)
+        torch.cuda.synchronize()
+        assert torch.all(torch.isfinite(out))
+    finally:
+        fresh.close()
