@@ -430,8 +430,8 @@ __device__ __forceinline__ MixedEigen mixed_eigen_f32(float xx, float yy, float 
   }
   m.full = ((1.0f + rf) < kPairTauF && p2 > 0.0f) || (x - x3) < tri_thr;
   const float lam1f = q + x;
-  const float est = kMixedEstCoef * p2 * pf / fmaxf((x - x2) * (x - x3) * fabsf(lam1f), 1e-30f);
-  m.need64 = !m.full && est > kMixedEstTau;
+  // the estimate over |l1| against kMixedEstTau, compared as a product (no division)
+  m.need64 = !m.full && kMixedEstCoef * p2 * pf > kMixedEstTau * fmaxf((x - x2) * (x - x3) * fabsf(lam1f), 1e-30f);
   m.q = q;
   m.x = x;
   m.x2 = x2;
