@@ -545,7 +545,7 @@ def run_mixed_variant(ctx, dev, stream, reps: int = 3) -> dict:
             "fp64_pipe": {"inst_per_eval": FP64_PIPE_INST_PER_EVAL["mixed"],
                           "frac": FP64_PIPE_INST_PER_EVAL["mixed"] * out["mixed"]["evals_per_s"]
                           / (FP64_LANES_PER_CLK_PER_SM * 152 * 2070e6)},
-            "note": "issue-bound (72 % of issue slots, profiles/collapse_kernel_mixed_128cube_x30.md)",
+            "note": "issue-bound (71 % of issue slots, profiles/collapse_kernel_mixed_128cube_x30.md)",
         },
         "bound_tol": 3e-5,
     }
