@@ -26,6 +26,22 @@ def test_reference_arm_json_line():
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
 
 
+def test_cpu_baseline_keeps_every_host_core_busy():
+    """The CPU baseline's sample gives every host core work: its chunks hold
+    four of the oracle's 256-point blocks per core, and the cores' busy share
+    over the timed calls (from /proc/stat, where the host has it) is reported
+    with the rate."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.cpu_oracle_rate(0.0)
+    cores = os.cpu_count() or 1
+    assert r["value"] > 0 and r["cores"] == cores
+    assert r["sample"].startswith(f"{1024 * cores} points")
+    if os.path.exists("/proc/stat"):
+        h = r["host_cpu"]
+        assert 0.0 <= h["steal_frac"] <= 1.0 and 0.0 <= h["min_core_busy_frac"] <= h["busy_frac"] <= 1.0
+
+
 def test_reference_arm_other_ranks_exit_quietly():
     env = dict(os.environ, RANK="1", WORLD_SIZE="2")
     out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
