@@ -39,11 +39,19 @@
  * agreement with SciPy's natural spline; bilinear exactness; the growth ODE
  * against the Heath integral and the EdS solution; brute force on 8^3 x 3.
  *
- * PARITY UNPINNED (partially): or_axis_coeffs. The per-axis split of the
- * second- and third-order terms (l_j l_k and l_i (l_j^2 + l_k^2)) is a reading;
- * only its spherical and plane-wave limits, its symmetry in the other two
- * axes, its degree and its second-order trace are pinned. Nothing outside the
- * reading fixes the split itself.
+ * Third-order pins: the stretches satisfy the Einstein-de Sitter Lagrangian
+ * equation of motion of a homogeneous ellipsoid to third order in D, which
+ * fixes the trace of each order (at third order the textbook 3LPT divergence
+ * (1/3) mu3 - (10/21) mu2(phi1, phi2)); and they equal the eigenvalues of the
+ * deformation tensor built in any frame from H, its cofactor matrix and the
+ * mixed cofactor of H and adj(H) (the local split, stated without eigenvalues).
+ *
+ * PARITY UNPINNED (partially): the choice of the local split in
+ * or_axis_coeffs. The equation of motion fixes only the trace of each order;
+ * which share of it each axis takes (here the cofactor rule: axis i receives
+ * the principal minor of the other two axes) is the reading. Monaco et al.
+ * 2002 may instead use ellipsoid shape factors; that source is not available,
+ * so nothing outside the reading fixes the per-axis distribution.
  */
 #ifndef COLLAPSE_ORACLE_H
 #define COLLAPSE_ORACLE_H

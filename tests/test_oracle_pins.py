@@ -676,3 +676,198 @@ def test_exact_growth_shifts_collapse_slightly_in_lcdm():
             shifts.append(d1 / d0 - 1.0)
     shifts = np.array(shifts)
     assert len(shifts) > 100 and np.abs(shifts).max() < 0.01 and np.abs(shifts).max() > 1e-5
+
+
+# ------------------------------------------------------ third-order terms of the stretch
+# The collapse condition is the axis stretch A_i(D) = 1 + psi_i(D) of a
+# homogeneous ellipsoid in its eigenframe, truncated at third order in D
+# (Sec. 3: third-order LPT; the formula itself is not printed). Two facts
+# outside the oracle pin its higher orders:
+#   (1) the Lagrangian equation of motion. For x_i = (1 + psi_i) q_i in an
+#       Einstein-de Sitter background (D = a, time in ln D), the divergence of
+#       the comoving acceleration equals -3/2 times the density contrast:
+#         sum_i [D^2 psi_i'' + 3/2 D psi_i'] / (1 + psi_i) = -3/2 (1/J - 1),
+#       J = prod_i (1 + psi_i). Order by order in D this fixes the trace
+#       sum_i psi_i^(n) given the lower orders; at third order it reproduces
+#       the textbook divergence (1/3) mu3 - (10/21) mu2(phi1, phi2) of 3LPT
+#       (Bouchet, Colombi, Hivon & Juszkiewicz 1995; Catelan 1995).
+#   (2) the per-axis split of each order is the local reading: in any frame
+#       the deformation tensor is
+#         T(D) = I - D H - 3/7 D^2 adj(H) + D^3 [det(H)/9 I - 5/21 M(H, adj H)],
+#       adj = cofactor matrix (trace mu2, the 2LPT source), M(A, B) =
+#       adj(A + B) - adj(A) - adj(B) the mixed cofactor (half its trace is
+#       mu2(phi1, phi2), the 3LPT source), and A_i are the eigenvalues of T.
+# (1) is physics; (2) states the reading independently of the eigenframe
+# formula. Together they leave only the choice of the local split itself
+# unpinned (the alternative being ellipsoid shape factors).
+
+def _series_mul(a, b):
+    return np.convolve(a, b)[:4]
+
+
+def _series_inv(a):
+    """1/a for a truncated power series with a[0] != 0 (coefficients of D^0..D^3)."""
+    out = np.zeros(4)
+    out[0] = 1.0 / a[0]
+    for n in range(1, 4):
+        out[n] = -sum(a[k] * out[n - k] for k in range(1, n + 1)) / a[0]
+    return out
+
+
+def _eom_residual(stretch):
+    """Coefficients of D^1..D^3 of LHS - RHS of the EdS Lagrangian equation
+    above, for the three per-axis stretch polynomials stretch[i] = A_i (D^0..D^3)."""
+    n = np.arange(4)
+    lhs = np.zeros(4)
+    J = np.array([1.0, 0.0, 0.0, 0.0])
+    for A in stretch:
+        A = np.asarray(A, dtype=np.float64)
+        # D^2 psi'' + 3/2 D psi' has coefficient n (n - 1) c_n + 3/2 n c_n = n (n + 1/2) c_n
+        num = n * (n + 0.5) * A
+        num[0] = 0.0
+        lhs += _series_mul(num, _series_inv(A))
+        J = _series_mul(J, A)
+    rhs = -1.5 * (_series_inv(J) - np.array([1.0, 0.0, 0.0, 0.0]))
+    return (lhs - rhs)[1:]
+
+
+def _adjugate(A):
+    C = np.empty((3, 3))
+    for i in range(3):
+        for j in range(3):
+            minor = np.delete(np.delete(A, i, axis=0), j, axis=1)
+            C[i, j] = (-1) ** (i + j) * np.linalg.det(minor)
+    return C.T
+
+
+def _cofactor_rule_residual(coeffs_fn, rng, trials=200):
+    """max over random symmetric H in random frames and several D of
+    |A_i(D) from coeffs_fn(sorted eigenvalues) - i-th eigenvalue of T(D)| / scale."""
+    worst = 0.0
+    for _ in range(trials):
+        lam = -np.sort(-rng.normal(size=3) * rng.lognormal(0, 0.7))
+        Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        H = Q @ np.diag(lam) @ Q.T
+        adjH = _adjugate(H)
+        Mmix = _adjugate(H + adjH) - _adjugate(H) - _adjugate(adjH)
+        scale = max(1.0, np.abs(lam).max()) ** 3
+        for D in (0.3, 1.0, 1.7):
+            T = np.eye(3) - D * H - 3.0 / 7.0 * D ** 2 * adjH + D ** 3 * (np.linalg.det(H) / 9.0 * np.eye(3)
+                                                                      - 5.0 / 21.0 * Mmix)
+            # T shares H's eigenvectors: its value along eigenvector i is A_i(D)
+            for i in range(3):
+                v = Q[:, i]
+                Ti = v @ T @ v
+                c = coeffs_fn(lam, i)
+                Ai = c[0] + D * (c[1] + D * (c[2] + D * c[3]))
+                worst = max(worst, abs(Ai - Ti) / (scale * max(1.0, D ** 3)),
+                            np.abs(T @ v - Ti * v).max() / (scale * max(1.0, D ** 3)))
+    return worst
+
+
+def _eom_worst(coeffs_fn, rng, trials=300):
+    worst = 0.0
+    for _ in range(trials):
+        lam = rng.normal(size=3) * rng.lognormal(0, 0.7)
+        res = _eom_residual([coeffs_fn(lam, i) for i in range(3)])
+        worst = max(worst, np.abs(res).max() / max(1.0, np.abs(lam).max()) ** 3)
+    return worst
+
+
+def test_stretch_satisfies_lagrangian_equation_to_third_order():
+    """Orders D, D^2, D^3 of the EdS Lagrangian equation of motion vanish for
+    the oracle's stretches on random (unsorted, any-sign) eigenvalue triples.
+    The D^3 order holds only if sum_i c3_i = 22/21 mu3 - 5/21 delta mu2, the
+    textbook 3LPT divergence written in eigenvalues; this fixes the 1/9 and
+    5/21 coefficients separately (the spherical limit fixes one combination)."""
+    rng = _rng(21)
+    assert _eom_worst(oracle.axis_coeffs, rng) < 1e-13
+    # the textbook 3LPT divergence, evaluated from its potentials in the eigenframe
+    for _ in range(100):
+        lam = rng.normal(size=3)
+        phi2 = np.array([lam[1] * lam[2], lam[0] * lam[2], lam[0] * lam[1]])  # adj(H) in the eigenframe
+        mu3 = np.prod(lam)
+        mu2_12 = 0.5 * (lam.sum() * phi2.sum() - (lam * phi2).sum())
+        tr3 = sum(oracle.axis_coeffs(lam, i)[3] for i in range(3))
+        assert abs(tr3 - (mu3 / 3.0 - 10.0 / 21.0 * mu2_12)) <= 1e-14 * max(1.0, np.abs(lam).max()) ** 3
+
+
+def test_stretch_follows_the_covariant_local_split():
+    """The per-axis stretch of the oracle equals the eigenvalues of the
+    deformation tensor built in an arbitrary frame from H, its cofactor matrix
+    and the mixed cofactor (the local reading, stated without eigenvalues)."""
+    assert _cofactor_rule_residual(oracle.axis_coeffs, _rng(22)) < 1e-12
+
+
+def test_third_order_pins_reject_planted_mistakes():
+    """Plausible mistakes in the stretch, planted in a copy of the oracle's
+    coefficients, each fail at least one pin. The swapped split
+    l_i^2 (l_j + l_k) keeps the spherical limit, the plane wave, the symmetry,
+    the second order and the trace; only the covariant split rejects it."""
+    def base(lam, i):
+        return oracle.axis_coeffs(lam, i)
+
+    def swapped(lam, i):
+        c = base(lam, i)
+        j, k = (i + 1) % 3, (i + 2) % 3
+        c[3] += 5.0 / 21.0 * (lam[i] * (lam[j] ** 2 + lam[k] ** 2) - lam[i] ** 2 * (lam[j] + lam[k]))
+        return c
+
+    def reweighted(lam, i):  # mu3/9 -> (1/9 + a) mu3, 5/21 -> 5/21 + a/2: same spherical value
+        c = base(lam, i)
+        j, k = (i + 1) % 3, (i + 2) % 3
+        a = 0.05
+        c[3] += a * np.prod(lam) - a / 2 * lam[i] * (lam[j] ** 2 + lam[k] ** 2)
+        return c
+
+    def isotropic_second_order(lam, i):  # same 2LPT trace, split evenly
+        c = base(lam, i)
+        mu2 = lam[0] * lam[1] + lam[0] * lam[2] + lam[1] * lam[2]
+        j, k = (i + 1) % 3, (i + 2) % 3
+        c[2] = -3.0 / 7.0 * mu2 / 3.0
+        return c
+
+    def dropped_mu3(lam, i):
+        c = base(lam, i)
+        c[3] -= np.prod(lam) / 9.0
+        return c
+
+    for name, fn in (("swapped", swapped), ("reweighted", reweighted),
+                     ("isotropic_second_order", isotropic_second_order), ("dropped_mu3", dropped_mu3)):
+        eom = _eom_worst(fn, _rng(23), trials=100)
+        cov = _cofactor_rule_residual(fn, _rng(24), trials=60)
+        assert max(eom, cov) > 1e-4, name
+    # the swapped split is invisible to the equation of motion: only the split rule catches it
+    assert _eom_worst(swapped, _rng(25), trials=100) < 1e-13
+
+
+def test_exact_growth_stretch_is_strictly_decreasing():
+    """With the LCDM growth ratios the stretch A_1 of sorted eigenvalues with
+    l1 > 0 is still strictly decreasing on (0, D_top], on a sample spanning
+    extreme anisotropy: the collapse root is unique, so the oracle's scan on
+    4096 uniform nodes cannot step over a pair of roots. An independent scan on
+    a finer grid finds the same root."""
+    brentq = pytest.importorskip("scipy.optimize").brentq
+    t = oracle.RatioTables(0.3, 0.7, 512, 1e-3, 1.0)
+    rng = _rng(26)
+    lam = rng.normal(size=(4000, 3)) * rng.lognormal(0, 1.5, size=(4000, 1))
+    lam *= rng.lognormal(0, 1.2, size=(4000, 3))
+    lam = -np.sort(-lam, axis=1)
+    lam = lam[lam[:, 0] > 0][:150]
+    grid = np.concatenate([np.geomspace(1e-6, 1e-2, 200) * t.D_top, np.linspace(0.0, 1.0, 2049)[1:] * t.D_top])
+    grid = np.unique(grid)
+    roots = 0
+    for l in lam:
+        A = np.array([t.axis_stretch(l, 0, D) for D in grid])
+        assert np.all(np.diff(A) < 0), l
+        Dc, f = t.collapse_D(l)
+        if A[-1] <= 0:
+            j = int(np.argmax(A <= 0))
+            lo = grid[j - 1] if j > 0 else 0.0
+            ref = brentq(lambda D: t.axis_stretch(l, 0, D), lo, grid[j], xtol=1e-300, rtol=1e-15)
+            assert f & oracle.FLAG_COLLAPSED
+            assert abs(Dc - ref) <= 4e-15 * ref
+            roots += 1
+        else:
+            assert Dc == 0.0
+    assert roots > 30
