@@ -195,8 +195,9 @@ CC_API int cc_collapse_multi_noalloc(const cc_cosmology *cosmo, cc_mode mode, co
 
 /* Copy a table to the context and build its natural splines along delta on the
  * device (the paper rebuilds them at every smoothing radius, Sec. 4.2). Later
- * CC_MODE_TABULATED launches use it; points outside [d_0, d_last] x [0, x_last]
- * x [0, y_last] fall back to the R-LPT root. Device memory for the table is
+ * CC_MODE_TABULATED launches use it; points outside [d_0, d_last] x [x_0, x_last]
+ * x [y_0, y_last] (the first and last knot of each axis) fall back to the
+ * R-LPT root. Device memory for the table is
  * allocated on first use and kept by the context. Calls on one context are
  * stream-ordered: do not replace a table that launches on another stream still read. */
 CC_API int cc_set_table(cc_ctx *ctx, const double *dgrid, int32_t nd, const double *xgrid, int32_t nx,

@@ -697,8 +697,11 @@ double or_F_tab_point(const or_tables *t, const or_tab *tab, const double h[6], 
     double D_top = t->D[t->n - 1];
     int inside = delta >= tab->dg[0] && delta <= tab->dg[tab->nd - 1] && x <= tab->xg[tab->nx - 1] &&
                  y <= tab->yg[tab->ny - 1] && x >= tab->xg[0] && y >= tab->yg[0];
+    /* on a face of the hull either side is a valid answer; x and y are >= 0,
+     * so a face at x = 0 or y = 0 has no outside */
     if (or_near(delta, tab->dg[0]) || or_near(delta, tab->dg[tab->nd - 1]) ||
-        or_near(x, tab->xg[tab->nx - 1]) || or_near(y, tab->yg[tab->ny - 1]))
+        or_near(x, tab->xg[tab->nx - 1]) || or_near(y, tab->yg[tab->ny - 1]) ||
+        (tab->xg[0] > 0.0 && or_near(x, tab->xg[0])) || (tab->yg[0] > 0.0 && or_near(y, tab->yg[0])))
       f |= OR_FLAG_HULL_EDGE;
     double Dc = 0.0;
     if (inside) {

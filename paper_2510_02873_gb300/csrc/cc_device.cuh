@@ -656,7 +656,10 @@ __device__ __forceinline__ TabResult collapse_point_tab(
   yv = bits(yv) > 0 ? yv : 0.0;
   xv = bits(xv) > 0 ? xv : 0.0;
   const double delta = xx + yy + zz;
-  res.outside = !(delta >= td.d_lo && delta <= td.d_hi && bits(xv) <= bits(td.x_hi) && bits(yv) <= bits(td.y_hi));
+  // inside the hull [d_0, d_last] x [x_0, x_last] x [y_0, y_last]: xv, yv and
+  // the axis bounds are >= 0, so their bit patterns order like their values
+  res.outside = !(delta >= td.d_lo && delta <= td.d_hi && bits(xv) >= bits(td.x_lo) && bits(xv) <= bits(td.x_hi) &&
+                  bits(yv) >= bits(td.y_lo) && bits(yv) <= bits(td.y_hi));
   double D;
   bool root = true;
   if (!res.outside) {

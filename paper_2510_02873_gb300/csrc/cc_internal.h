@@ -74,7 +74,7 @@ struct TabDev {
   const Coef4* coef;   // [(ix * ny + iy) * (nd - 1) + k]
   int nd, nx, ny;
   int d_steps, x_steps, y_steps;  // largest power of two <= n - 2 (branch-free searches)
-  double d_lo, d_hi, x_hi, y_hi;
+  double d_lo, d_hi, x_lo, x_hi, y_lo, y_hi;  // the table's hull (first and last knot of each axis)
   __host__ __device__ size_t axes_bytes() const {
     return sizeof(double) * (nd + nx + ny + (nx - 1) + (ny - 1)) + sizeof(float) * nd;
   }

@@ -239,7 +239,9 @@ int cc_set_table(cc_ctx* ctx, const double* dgrid, int32_t nd, const double* xgr
   td.y_steps = pow2_steps(ny);
   td.d_lo = dgrid[0];
   td.d_hi = dgrid[nd - 1];
+  td.x_lo = xgrid[0];
   td.x_hi = xgrid[nx - 1];
+  td.y_lo = ygrid[0];
   td.y_hi = ygrid[ny - 1];
   ctx->tabdev = td;
   ctx->tab_valid = true;
