@@ -28,6 +28,11 @@
  *     cc_strerror() names the code; cc_last_error_message() gives detail.
  *   - One context per device; a context is not thread-safe (serialise calls
  *     on one context, or use one context per host thread).
+ *   - Supported input range: eigenvalue magnitudes of H up to 1e6 (in units
+ *     where D(a = 1) = 1; collapse needs at least ~0.7, and points with l1 <= 0
+ *     never collapse). The FP32 seeds of every path form sixth powers of the
+ *     eigenvalues, which leave the FP32 range near 2.6e6; beyond 1e6 results
+ *     are not guaranteed. Non-finite components give no collapse (F = 0).
  *   - Plane layout: component c of point p at radius r is
  *       hess[r * radius_stride + c * plane_stride + p]   (elements, not bytes);
  *     plane_stride >= n, radius_stride >= 6 * plane_stride. Each plane must
@@ -81,7 +86,10 @@ typedef enum {
 
 /* Flat LCDM-like background: E^2 = Om a^-3 + (1 - Om - OL) a^-2 + OL.
  * n_knots log-spaced scale factors in [a_min, a_max] (2 <= n_knots <= 4096,
- * 1e-5 < a_min < a_max); D is normalised to D(a = 1) = 1. */
+ * 1e-5 < a_min < a_max); D is normalised to D(a = 1) = 1. The device tables
+ * (cc_create, cc_collapse_multi_noalloc) also need D to at most double between
+ * neighbouring knots (n_knots >= 11 for a_max / a_min = 1000; the paper's 512
+ * knots give 1.3 %); coarser tables return CC_EINVAL. */
 typedef struct {
   double omega_m;
   double omega_l;
@@ -160,9 +168,9 @@ CC_API int cc_collapse_multi_host(cc_ctx *ctx, cc_mode mode, const void *hess_ho
                            int32_t scale_idx0, void *stream);
 
 /* No counterpart in the paper. A variant of cc_collapse_multi for callers that
- * cannot allocate device memory (code under CUDA stream capture, code whose
- * device memory is owned by another framework's allocator, or loops that cannot
- * take cudaMalloc's implicit synchronisation). It needs no context and makes no
+ * cannot allocate device memory (code whose device memory is owned by another
+ * framework's caching allocator, or loops that cannot take the implicit device
+ * synchronisation of cudaMalloc/cudaFree). It needs no context and makes no
  * allocation of any kind: the spline table for `cosmo` and the launch counters
  * live in a file-scope static device array of 53.5 KB that every GPU loading
  * the library holds until exit. Inputs and outputs are the caller's device

@@ -168,6 +168,15 @@ int cc_create(cc_ctx** out, const cc_cosmology* cosmo, int device) {
   if (rc) { delete ctx; return set_error(rc, "growth table: invalid cosmology or knot range"); }
   rc = build_natural_spline(ctx->D_k, ctx->a_k, ctx->coef);
   if (rc) { delete ctx; return set_error(rc, "spline build failed"); }
+  if (f32_knots_within_factor2(cosmo->n_knots, ctx->D_k.data())) {
+    delete ctx;
+    return set_error(CC_EINVAL, "growth-table knots too coarse: D may at most double between neighbouring knots "
+                                "(raise n_knots)");
+  }
+  // the device polynomials are expanded about the FP32 knots e_k
+  std::vector<double> e_k(cosmo->n_knots);
+  for (int k = 0; k < cosmo->n_knots; ++k) e_k[k] = static_cast<double>(static_cast<float>(ctx->D_k[k]));
+  expand_about_f32_knots(cosmo->n_knots, ctx->D_k.data(), ctx->coef.data());
   if ((rc = check_cuda(cudaSetDevice(device), "cudaSetDevice"))) { delete ctx; return rc; }
   if ((rc = check_cuda(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device),
                        "cudaDeviceGetAttribute"))) { delete ctx; return rc; }
@@ -206,7 +215,7 @@ int cc_create(cc_ctx** out, const cc_cosmology* cosmo, int device) {
   }
   std::vector<unsigned char> host(total);
   std::memcpy(host.data(), ctx->coef.data(), coef_bytes);
-  std::memcpy(host.data() + coef_bytes, ctx->D_k.data(), d_bytes);
+  std::memcpy(host.data() + coef_bytes, e_k.data(), d_bytes);
   std::memcpy(host.data() + coef_bytes + d_bytes, df.data(), df_bytes);
   std::memcpy(host.data() + coef_bytes + d_bytes + df_bytes, bucket.data(), b_bytes);
   {  // float-float image: value = hi + lo with hi = RN32(value), lo = RN32(value - hi)
@@ -222,7 +231,7 @@ int cc_create(cc_ctx** out, const cc_cosmology* cosmo, int device) {
       split(c[1], s[2], s[3]);
       s[4] = static_cast<float>(c[2]);
       s[5] = static_cast<float>(c[3]);
-      split(ctx->D_k[k], s[6], s[7]);
+      split(e_k[k], s[6], s[7]);  // exact in FP32: lo = 0
     }
   }
   rc = check_cuda(cudaMemcpy(ctx->d_table, host.data(), total, cudaMemcpyHostToDevice), "cudaMemcpy(table)");
@@ -243,6 +252,7 @@ int cc_create(cc_ctx** out, const cc_cosmology* cosmo, int device) {
   t.Dtop = ctx->D_k[n - 1];
   t.eds_slope = ctx->a_k[0] / ctx->D_k[0];
   t.Dtopf = static_cast<float>(t.Dtop);
+  t.Dtop_t = t.Dtop - e_k[n - 2];
   t.dfseg = reinterpret_cast<const float4*>(base + seg_off);
   auto split2 = [](double v, float& hi, float& lo) {
     hi = static_cast<float>(v);
@@ -256,6 +266,7 @@ int cc_create(cc_ctx** out, const cc_cosmology* cosmo, int device) {
     rc = growth_ratios_into(*cosmo, r.data(), r.data() + n, r.data() + 2 * n);
     for (int o = 0; o < 3 && !rc; ++o)
       rc = natural_spline_into(n, ctx->D_k.data(), r.data() + o * n, c64.data() + o * 4 * (n - 1), work.data());
+    for (int o = 0; o < 3 && !rc; ++o) expand_about_f32_knots(n, ctx->D_k.data(), c64.data() + o * 4 * (n - 1));
     if (rc) { cc_destroy(ctx); return set_error(rc, "growth ratio tables failed"); }
     std::vector<float> c32(c64.size());
     for (size_t i = 0; i < c64.size(); ++i) c32[i] = static_cast<float>(c64[i]);

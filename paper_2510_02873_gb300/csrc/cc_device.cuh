@@ -179,9 +179,9 @@ struct PointResult {
 };
 
 struct EigenTop {
-  double q, x, p2x3, det;  // tr/3, l1 - q, 3 p^2, det(A - qI)
+  double s, q, x, p2x3, det;  // tr, tr/3, l1 - q, 3 p^2, det(A - qI)
   float p2f;
-  bool refined;            // l1 ~ l2 re-solved by deflation
+  bool refined;               // l1 ~ l2 re-solved by deflation
 };
 
 // Largest eigenvalue l1 = q + x of the symmetric matrix in FP64 (FP32 trigonometric
@@ -191,15 +191,21 @@ __device__ __forceinline__ EigenTop eigen_top_fp64(double xx, double yy, double 
                                                    double yz) {
   EigenTop e;
   // ---- invariants (FP64)
-  // M = A - qI with the diagonal (a, b, c) made exactly traceless, c = -(a + b):
-  // |M|_F^2 / 2 = a^2 + a b + b^2 + off = a (a + b) + b^2 + off (no cancellation:
-  // a^2 + ab + b^2 >= 3/4 b^2)
-  const double q = (xx + yy + zz) * (1.0 / 3.0);
-  const double a = xx - q, b = yy - q;
-  const double ab = a + b, c = -ab;
+  // M = A - qI, q = s/3 with s the trace; its diagonal a = xx - s/3, b, c each
+  // in one FMA from s (a single rounding, and no separate subtraction from a
+  // rounded q). |M|_F^2 / 2 = a^2 + a b + b^2 + off = a (a + b) + b^2 + off
+  // with a + b = -c (no cancellation: a^2 + ab + b^2 >= 3/4 b^2); the three
+  // rounded entries sum to d = O(eps |s|) instead of zero, which moves p^2 and
+  // det M by O(eps |s| p), the size of the rounding of the entries themselves.
+  // Only a matrix isotropic to within that rounding (|a|, |b| ~ |d|) can then
+  // give 3 p^2 < 0; it is set to 0 there (its sign bit, an integer test).
+  const double s = xx + yy + zz;
+  const double q = s * (1.0 / 3.0);
+  const double a = fma(s, -1.0 / 3.0, xx), b = fma(s, -1.0 / 3.0, yy), c = fma(s, -1.0 / 3.0, zz);
   const double yz2 = yz * yz;
   const double off = fma(xz, xz, fma(xy, xy, yz2));
-  const double p2x3 = fma(a, ab, fma(b, b, off));  // 3 p^2 = |M|_F^2 / 2
+  double p2x3 = fma(a, -c, fma(b, b, off));  // 3 p^2 = |M|_F^2 / 2
+  p2x3 = bits(p2x3) < 0 ? 0.0 : p2x3;
   const double det = fma(xz, fma(xy, yz, -b * xz), fma(a, fma(b, c, -yz2), -xy * fma(xy, c, -yz * xz)));
   // ---- FP32 trigonometric seed
   const float p2f = to_f32_trunc(p2x3) * (1.0f / 3.0f);
@@ -235,6 +241,7 @@ __device__ __forceinline__ EigenTop eigen_top_fp64(double xx, double yy, double 
     refine_top_pair(xx, yy, zz, xy, xz, yz, q + x3, l1r, l2r);
     x = l1r - q;
   }
+  e.s = s;
   e.q = q;
   e.x = x;
   e.p2x3 = p2x3;
@@ -330,40 +337,83 @@ struct MinA {
   }
 };
 
+// Finiteness of an FP64 value from its bit pattern (exponent not all ones).
+__device__ __forceinline__ bool finite_bits(double v) {
+  return (bits(v) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+}
+
+// a on the spline interval whose polynomial is expanded about the FP32 knot
+// e_k (t = D - e_k), or on the EdS segment below the first knot,
+// a = (a_0 / D_0) D with t = D: the same Horner scheme with that segment's
+// coefficients selected in (c1 = a_0 / D_0, c0 = c2 = c3 = 0).
+__device__ __forceinline__ double spline_a_t(const Coef4& cf, double t, bool eds, const DevTable& tab) {
+  return fma(fma(fma(eds ? 0.0 : cf.c3, t, eds ? 0.0 : cf.c2), t, eds ? tab.eds_slope : cf.c1), t, eds ? 0.0 : cf.c0);
+}
+
 // FP64 collapse value of one point, F = 1/a_c (0 when there is no collapse).
-//   eigenvalues: invariants of M = A - qI in FP64 (q = tr/3, |M|_F^2 = 6 p^2,
-//     det M); l1 = q + x with x the largest root of x^3 - 3 p^2 x - det M = 0,
-//     seeded by the FP32 trigonometric solution and corrected by two FP64
-//     Newton steps (FP32 derivative at each iterate); l2 l3 and l2^2 + l3^2
-//     from the invariants
-//     (l2 + l3 = 2q - x, l2 l3 = q (q - x) + x^2 - 3 p^2);
-//   collapse: A_1(D) = 1 - l1 D + c2 D^2 + c3 D^3, root seeded in FP32 from the
-//     FP64 coefficients rounded to FP32 (closed form in u = 1/D, two FP32
-//     Newton steps) and corrected by one FP64 Newton step;
-//   spline: interval from the FP32 search, FP64 Horner; F by one FP64 Newton
-//     step of the reciprocal from the FP32 reciprocal.
+//   eigenvalues: invariants of M = A - qI in FP64 (s = tr, q = s/3,
+//     |M|_F^2 = 6 p^2, det M); l1 = q + x with x the largest root of
+//     x^3 - 3 p^2 x - det M = 0, seeded by the FP32 trigonometric solution and
+//     corrected by two FP64 Newton steps (FP32 derivative at each iterate);
+//   collapse: A_1(D) = 1 - l1 D + c2 D^2 + c3 D^3 from the centred invariants
+//     (w = x^2 - 3p^2 = (l2 - q)(l3 - q), l2 l3 = q (q - x) + w,
+//     c2 = -3/7 l2 l3, c3 = l1 K with 63 K = -23 l2 l3 + 15 (3 w - 3p^2), which is
+//     l1 (l2 l3 / 9 - 5/21 (l2^2 + l3^2)) written without l2 + l3); the root is
+//     seeded in FP32 from the FP64 coefficients rounded to FP32 (closed form in
+//     u = 1/D, two FP32 Newton steps) and corrected by one FP64 Newton step;
+//   spline: the table's polynomials are expanded about the FP32 knots e_k, so
+//     the FP32 root Df gives t0 = Df - e_k exactly in FP32 (knots within a
+//     factor 2 of each other), and the FP64 Newton step lands directly on
+//     t = D - e_k (on the EdS segment t = D); FP64 Horner in t;
+//   collapse test: l1 > 0 and Df > 0 (FP32 and FP64 roots agree in sign and in
+//     their interval to ~1e-7), and on the last interval t <= D_top - e_{n-2}
+//     on the FP64 bit pattern (exact); EdS segment where Df < e_0 (the two
+//     formulas meet at D_0, so taking the FP32 decision within ~1e-7 D_0 of it
+//     moves a by ~1e-14 relative);
+//   F by one FP64 Newton step of the reciprocal from the FP32 reciprocal.
 __device__ __forceinline__ PointResult collapse_point_fp64(
     double xx, double yy, double zz, double xy, double xz, double yz, const double* __restrict__ Dk,
     const Coef4* __restrict__ coef, const float* __restrict__ Dkf,
     const unsigned short* __restrict__ bucket, const DevTable& tab) {
+  (void)Dk;
   PointResult res;
   const EigenTop e = eigen_top_fp64(xx, yy, zz, xy, xz, yz);
   res.refined = e.refined;
-  const double q = e.q, x = e.x, p2x3 = e.p2x3;
-  // ---- collapse condition coefficients (FP64) and root
-  const double lam1 = q + x;
-  const double Pp = fma(q, q - x, fma(x, x, -p2x3));  // l2 l3
-  const double S = fma(2.0, q, -x);                    // l2 + l3
-  const Root rt = rlpt_root_fp64(lam1, Pp, S);
-  const double D = rt.D;
-  // ---- collapse test on bit patterns: l1 > 0, 0 < D <= D_top
-  const long long bD = bits(D);
-  res.collapsed = bits(lam1) > 0 && bD > 0 && bD <= bits(tab.Dtop);
-  const double Dc = res.collapsed ? D : tab.Dtop;
-  // ---- a(D): interval from the FP32 root, FP64 Horner
-  const int k = spline_interval(Dkf, bucket, tab, res.collapsed ? rt.Df : tab.Dtopf);
-  res.eds = res.collapsed && bits(Dc) < bits(tab.D0);
-  const double av = spline_a(coef[k], Dk[k], Dc, res.eds, tab);
+  const double s = e.s, x = e.x, p2x3 = e.p2x3;
+  // ---- collapse condition coefficients (FP64)
+  const double lam1 = fma(s, 1.0 / 3.0, x);
+  const double qmx = fma(s, 1.0 / 3.0, -x);
+  const double w = fma(x, x, -p2x3);
+  const double Pp = fma(e.q, qmx, w);                      // l2 l3
+  const double v = fma(w, 3.0, -p2x3);
+  const double K = fma(v, 15.0 / 63.0, Pp * (-23.0 / 63.0));
+  const double c2 = Pp * (-3.0 / 7.0);
+  const double c3 = lam1 * K;
+  // ---- FP32 root seed from the FP64 coefficients rounded to FP32: largest
+  // root of u^3 - l1 u^2 + c2 u + c3 (u = 1/D), polished on A_1(D) in FP32
+  const float l1f = to_f32_trunc(lam1);
+  const float c2f = to_f32_trunc(c2);
+  const float c3f = to_f32_trunc(c3);
+  const float uf = cubic_largest_root_seed(-l1f, c2f, c3f);
+  float Df = __fdividef(1.0f, uf);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const float Af = fmaf(fmaf(fmaf(c3f, Df, c2f), Df, -l1f), Df, 1.0f);
+    const float dAf = fmaf(fmaf(3.0f * c3f, Df, 2.0f * c2f), Df, -l1f);
+    Df -= __fdividef(Af, dAf);
+  }
+  const float dAf = fmaf(fmaf(3.0f * c3f, Df, 2.0f * c2f), Df, -l1f);
+  // ---- interval, then one FP64 Newton step on A_1 that yields t = D - e_k
+  const int k = spline_interval(Dkf, bucket, tab, Df);
+  res.eds = Df < Dkf[0];
+  const float t0 = res.eds ? Df : __fsub_rn(Df, Dkf[k]);
+  const double D0 = to_f64(Df);
+  const double A1 = fma(fma(fma(c3, D0, c2), D0, -lam1), D0, 1.0);
+  const double t = fma(-A1, to_f64(rcp_seed(dAf)), to_f64_normal(t0));
+  // ---- collapse test: l1 > 0, 0 < D <= D_top
+  res.collapsed = bits(lam1) > 0 && Df > 0.0f && (k < tab.n - 2 || bits(t) <= bits(tab.Dtop_t)) && finite_bits(t);
+  res.eds = res.eds && res.collapsed;
+  const double av = spline_a_t(coef[k], t, res.eds, tab);
   res.a = res.collapsed ? av : kInf;
   const double F = recip_fp64(av);
   res.F = res.collapsed ? F : 0.0;
@@ -639,10 +689,15 @@ __device__ __forceinline__ TabResult collapse_point_tab(
   const double Pp = fma(q, q - x, fma(x, x, -p2x3));  // l2 l3
   const double S = fma(2.0, q, -x);                    // l2 + l3
   // y = l2 - l3 from (l2 + l3)^2 - 4 l2 l3; near l2 = l3 that difference
-  // cancels, so the pair is re-solved by deflation around the isolated l1
+  // cancels: its rounding is ~eps (S^2 + 4 |l2 l3|), which for a nearly
+  // isotropic matrix (p -> 0) is not small next to p^2. Below 1e-10 of those
+  // scales the pair is re-solved by deflation around the isolated l1 (and
+  // stays S/2 each when no eigenvalue is isolated); the test is in FP32.
   const double D2 = fma(S, S, -4.0 * Pp);
+  const float Sf = to_f32_trunc(S);
+  const float d2_scale = fmaf(Sf, Sf, fmaf(4.0f, fabsf(to_f32_trunc(Pp)), to_f32_trunc(p2x3)));
   double l2, l3;
-  if (D2 < 1e-10 * p2x3) {
+  if (to_f32_trunc(D2) < 1e-10f * d2_scale) {
     l2 = 0.5 * S;
     l3 = 0.5 * S;
     refine_top_pair(xx, yy, zz, xy, xz, yz, lam1, l2, l3);

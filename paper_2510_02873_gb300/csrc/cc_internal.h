@@ -35,7 +35,9 @@ struct alignas(32) Coef4 {
 };
 
 // Inverse growth spline on the device: knots D_k (n) and per-interval
-// polynomial coefficients a = c0 + c1 t + c2 t^2 + c3 t^3, t = D - D_k (n - 1).
+// polynomial coefficients a = c0 + c1 t + c2 t^2 + c3 t^3 (n - 1), expanded
+// about e_k = D_k rounded to FP32, t = D - e_k; the image's D array holds e_k
+// (D0 and Dtop below are the exact first and last knots).
 struct DevTable {
   const Coef4* coef;              // n - 1 intervals
   const double* D;                // n knots
@@ -47,6 +49,7 @@ struct DevTable {
   double a0, D0, Dtop;            // first scale factor, first and last knot
   double eds_slope;               // a0 / D0
   float Dtopf;                    // D_top rounded to FP32 (interval search)
+  double Dtop_t;                  // D_top - e_{n-2}: t of D_top on the last interval
   // float-float image of the spline (CC_MODE_F32X2): two float4 per interval,
   // {c0 hi, c0 lo, c1 hi, c1 lo}, {c2, c3, D_k hi, D_k lo}, stored right after
   // the table image at offset round_up(bytes(), 16); nullptr when absent
@@ -89,6 +92,14 @@ int growth_table_into(const cc_cosmology& c, double* a_k, double* D_k);
 int natural_spline_into(int n, const double* x, const double* y, double* coef, double* work);
 // r2 = D2/D1^2, r3a = D3a/D1^3, r3b = D3b/D1^3 at the knots of growth_table_into
 int growth_ratios_into(const cc_cosmology& c, double* r2, double* r3a, double* r3b);
+// The device evaluates every per-interval polynomial in t = D - e_k with
+// e_k = the knot x_k rounded to FP32, so that an FP32 root Df in interval k
+// gives t = Df - e_k exactly (Sterbenz) when e_{k+1} <= 2 e_k.
+// f32_knots_within_factor2: CC_OK when the FP32 knots are positive, increasing
+// and within a factor 2 of their neighbours, CC_EINVAL otherwise.
+int f32_knots_within_factor2(int n, const double* x);
+// re-expand the n - 1 cubics c0 + c1 t + c2 t^2 + c3 t^3 (t = D - x_k) about e_k
+void expand_about_f32_knots(int n, const double* x, double* coef);
 
 // error reporting (cc_api.cu)
 int set_error(int code, const std::string& msg);

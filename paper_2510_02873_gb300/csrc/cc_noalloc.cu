@@ -1,10 +1,10 @@
 // cc_noalloc.cu -- a context-free variant of cc_collapse_multi that allocates nothing.
 //
-// Why it exists: cudaMalloc is off limits for some callers. Code that runs
-// under CUDA stream capture, code that lives inside another framework whose
-// caching allocator owns all device memory, and tight loops that cannot
-// afford the implicit device synchronisation of cudaMalloc/cudaFree all need
-// to hand the library their own input and output buffers and nothing more.
+// Why it exists: cudaMalloc is off limits for some callers. Code that lives
+// inside another framework whose caching allocator owns all device memory, and
+// tight loops that cannot afford the implicit device synchronisation of
+// cudaMalloc/cudaFree, need to hand the library their own input and output
+// buffers and nothing more.
 // cc_create cannot serve them: it allocates the spline table and the counters.
 //
 // This entry point keeps its scratch (the spline table image and the launch
@@ -55,7 +55,7 @@ DeviceState g_state[kMaxDevices];
 double g_a[kStaticMaxKnots], g_D[kStaticMaxKnots];
 double g_coef[4 * (kStaticMaxKnots - 1)];
 double g_work[6 * kStaticMaxKnots];
-unsigned char g_image[kStaticTableBytes];
+alignas(32) unsigned char g_image[kStaticTableBytes];
 
 bool same_cosmology(const cc_cosmology& a, const cc_cosmology& b) {
   return a.omega_m == b.omega_m && a.omega_l == b.omega_l && a.n_knots == b.n_knots &&
@@ -68,6 +68,8 @@ int build_image(const cc_cosmology& c, unsigned char* base, DevTable& tab, size_
   const int n = c.n_knots;
   if (int rc = growth_table_into(c, g_a, g_D)) return rc;
   if (int rc = natural_spline_into(n, g_D, g_a, g_coef, g_work)) return rc;
+  if (int rc = f32_knots_within_factor2(n, g_D)) return rc;
+  expand_about_f32_knots(n, g_D, g_coef);  // the device polynomials are expanded about the FP32 knots
   const int nb = kBucketsPerKnot * n;
   const double l2lo = std::log2(g_D[0]), l2hi = std::log2(g_D[n - 1]);
   const double width = (l2hi - l2lo) / nb;
@@ -76,7 +78,8 @@ int build_image(const cc_cosmology& c, unsigned char* base, DevTable& tab, size_
   const size_t df_bytes = sizeof(float) * n;
   bytes = coef_bytes + d_bytes + df_bytes + sizeof(unsigned short) * nb;
   std::memcpy(g_image, g_coef, coef_bytes);
-  std::memcpy(g_image + coef_bytes, g_D, d_bytes);
+  double* e = reinterpret_cast<double*>(g_image + coef_bytes);
+  for (int k = 0; k < n; ++k) e[k] = static_cast<double>(static_cast<float>(g_D[k]));
   float* df = reinterpret_cast<float*>(g_image + coef_bytes + d_bytes);
   for (int k = 0; k < n; ++k) df[k] = static_cast<float>(g_D[k]);
   unsigned short* bucket = reinterpret_cast<unsigned short*>(g_image + coef_bytes + d_bytes + df_bytes);
@@ -99,6 +102,7 @@ int build_image(const cc_cosmology& c, unsigned char* base, DevTable& tab, size_
   tab.Dtop = g_D[n - 1];
   tab.eds_slope = g_a[0] / g_D[0];
   tab.Dtopf = static_cast<float>(tab.Dtop);
+  tab.Dtop_t = tab.Dtop - static_cast<double>(static_cast<float>(g_D[n - 2]));
   return CC_OK;
 }
 

@@ -204,6 +204,26 @@ int natural_spline_into(int n, const double* x, const double* y, double* coef, d
   return CC_OK;
 }
 
+int f32_knots_within_factor2(int n, const double* x) {
+  for (int k = 0; k + 1 < n; ++k) {
+    const double e0 = static_cast<double>(static_cast<float>(x[k]));
+    const double e1 = static_cast<double>(static_cast<float>(x[k + 1]));
+    if (!(e0 > 0.0) || !(e1 > e0) || !(e1 <= 2.0 * e0)) return CC_EINVAL;
+  }
+  return CC_OK;
+}
+
+void expand_about_f32_knots(int n, const double* x, double* coef) {
+  for (int k = 0; k + 1 < n; ++k) {
+    double* c = coef + 4 * k;
+    const double d = static_cast<double>(static_cast<float>(x[k])) - x[k];
+    const double c0 = c[0], c1 = c[1], c2 = c[2], c3 = c[3];
+    c[0] = c0 + d * (c1 + d * (c2 + d * c3));
+    c[1] = c1 + d * (2.0 * c2 + 3.0 * d * c3);
+    c[2] = c2 + 3.0 * d * c3;
+  }
+}
+
 int build_natural_spline(const std::vector<double>& x, const std::vector<double>& y,
                          std::vector<double>& coef /* 4 per interval */) {
   const int n = static_cast<int>(x.size());
