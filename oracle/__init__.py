@@ -106,6 +106,8 @@ def lib():
             L.or_tab_free.argtypes = [ctypes.POINTER(_Tab)]
             L.or_tab_query.argtypes = [ctypes.POINTER(_Tab), d, d, d]
             L.or_tab_query.restype = d
+            L.or_tab_query_many.argtypes = [ctypes.POINTER(_Tab), vp, vp, vp, i64, vp, i]
+            L.or_spline_eval_many.argtypes = [i, vp, vp, vp, vp, i64, vp, i]
             L.or_mlp_forward.argtypes = [vp, vp]
             L.or_mlp_forward.restype = d
             L.or_mlp_loss_grad.argtypes = [vp, vp, vp, i, vp]
@@ -160,6 +162,14 @@ def spline_eval(x, y, M, t) -> np.ndarray:
     L = lib()
     t = np.atleast_1d(np.asarray(t, dtype=np.float64))
     return np.array([L.or_spline_eval(len(x), _p(x), _p(y), _p(M), float(v)) for v in t])
+
+
+def spline_eval_many(x, y, M, t, nthreads: int = 0) -> np.ndarray:
+    """spline_eval at many points in one call (OpenMP over the points)."""
+    x, y, M, t = _f64(x), _f64(y), _f64(M), _f64(np.atleast_1d(t))
+    out = np.empty(len(t))
+    lib().or_spline_eval_many(len(x), _p(x), _p(y), _p(M), _p(t), len(t), _p(out), nthreads)
+    return out
 
 
 def bilinear(xg, yg, z, x, y) -> np.ndarray:
@@ -317,6 +327,13 @@ class Tab:
         L = lib()
         return np.array([L.or_tab_query(ctypes.byref(self._t), float(a), float(b), float(c))
                          for a, b, c in zip(np.atleast_1d(delta), np.atleast_1d(x), np.atleast_1d(y))])
+
+    def query_many(self, delta, x, y, nthreads: int = 0) -> np.ndarray:
+        """query at many points in one call (OpenMP over the points)."""
+        d, x, y = _f64(np.atleast_1d(delta)), _f64(np.atleast_1d(x)), _f64(np.atleast_1d(y))
+        out = np.empty(len(d))
+        lib().or_tab_query_many(ctypes.byref(self._t), _p(d), _p(x), _p(y), len(d), _p(out), nthreads)
+        return out
 
     def F_points(self, tables: "Tables", hess: np.ndarray, nthreads: int = 0):
         hess = _f64(hess)

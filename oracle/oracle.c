@@ -681,6 +681,22 @@ double or_tab_query(const or_tab *t, double delta, double x, double y) {
   return or_bilinear(2, xg2, 2, yg2, zz, x, y);
 }
 
+void or_tab_query_many(const or_tab *t, const double *delta, const double *x, const double *y, int64_t m,
+                       double *out, int nthreads) {
+  int nt = or_threads(nthreads);
+  (void)nt;
+#pragma omp parallel for schedule(static) num_threads(nt)
+  for (int64_t i = 0; i < m; ++i) out[i] = or_tab_query(t, delta[i], x[i], y[i]);
+}
+
+void or_spline_eval_many(int n, const double *x, const double *y, const double *M, const double *t, int64_t m,
+                         double *out, int nthreads) {
+  int nt = or_threads(nthreads);
+  (void)nt;
+#pragma omp parallel for schedule(static) num_threads(nt)
+  for (int64_t i = 0; i < m; ++i) out[i] = or_spline_eval(n, x, y, M, t[i]);
+}
+
 static int or_near(double v, double edge) {
   return fabs(v - edge) <= 1e-12 * fmax(1.0, fabs(edge));
 }

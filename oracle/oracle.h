@@ -79,6 +79,9 @@ double or_growth_at(double omega_m, double omega_l, double a); /* D(a)/D(1), sam
 /* ---- cubic spline with prescribed end second derivatives (natural: 0, 0) ---- */
 int or_spline_build(int n, const double *x, const double *y, double M0, double Mn, double *M);
 double or_spline_eval(int n, const double *x, const double *y, const double *M, double t);
+/* the same at m points t (OpenMP over the points; nthreads <= 0: all) */
+void or_spline_eval_many(int n, const double *x, const double *y, const double *M, const double *t, int64_t m,
+                         double *out, int nthreads);
 
 /* ---- bilinear interpolation on a non-uniform grid, z[ix*ny + iy] ---- */
 double or_bilinear(int nx, const double *xg, int ny, const double *yg, const double *z,
@@ -174,6 +177,9 @@ int  or_tab_init(or_tab *t, int nd, const double *dg, int nx, const double *xg, 
                  const double *val);
 void or_tab_free(or_tab *t);
 double or_tab_query(const or_tab *t, double delta, double x, double y);
+/* the same at m points (OpenMP over the points; nthreads <= 0: all) */
+void or_tab_query_many(const or_tab *t, const double *delta, const double *x, const double *y, int64_t m,
+                       double *out, int nthreads);
 double or_F_tab_point(const or_tables *t, const or_tab *tab, const double h[6], int *flags);
 void or_F_tab_points(const or_tables *t, const or_tab *tab, const double *hess, int64_t n, int64_t plane_stride,
                      double *F, int32_t *flags, int nthreads);

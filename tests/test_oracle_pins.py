@@ -871,3 +871,30 @@ def test_exact_growth_stretch_is_strictly_decreasing():
         else:
             assert Dc == 0.0
     assert roots > 30
+
+
+def test_vectorised_toy_queries_equal_the_scalar_ones():
+    """spline_eval_many / Tab.query_many (one OpenMP call over the points, used
+    to time the CPU side of the interpolation toys) return exactly the values
+    of the scalar routines."""
+    rng = _rng(27)
+    x = np.sort(rng.uniform(0, 1, 512))
+    y = x * x
+    M = oracle.spline_build(x, y)
+    t = rng.uniform(x[0], x[-1], 2000)
+    assert np.array_equal(oracle.spline_eval_many(x, y, M, t), oracle.spline_eval(x, y, M, t))
+    dg = np.sort(rng.uniform(-1, 1, 128))
+    xg = np.sort(rng.uniform(0, 1, 64))
+    yg = np.sort(rng.uniform(0, 1, 64))
+    val = np.repeat((xg[:, None] ** 2 + yg[None, :] ** 2)[:, :, None], 128, axis=2)
+    tab = oracle.Tab(dg, xg, yg, val)
+    d, a, b = rng.uniform(dg[0], dg[-1], 2000), rng.uniform(xg[0], xg[-1], 2000), rng.uniform(yg[0], yg[-1], 2000)
+    got = tab.query_many(d, a, b)
+    assert np.array_equal(got, tab.query(d, a, b))
+    # the paper's 2D toy: constant along delta, so the spline reproduces the node values and
+    # only the bilinear O(h^2) error remains (convex function: over-estimated)
+    err = got - (a * a + b * b)
+    ix = np.searchsorted(xg, a, side="right") - 1
+    iy = np.searchsorted(yg, b, side="right") - 1
+    hx, hy = xg[ix + 1] - xg[ix], yg[iy + 1] - yg[iy]
+    assert np.all(err >= -1e-14) and np.all(err <= (hx ** 2 + hy ** 2) / 4 + 1e-14)
