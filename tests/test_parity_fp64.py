@@ -136,6 +136,31 @@ def test_degenerate_and_special_spectra(ctx, tables, mode):
 
 
 @pytest.mark.parametrize("mode", MODES)
+def test_supported_eigenvalue_range_ends(ctx, tables, mode):
+    """The header's supported range, eigenvalue magnitudes up to 1e6: random
+    and structured spectra scaled to 1e-6 .. 1e6 (collapse from ~0.7 up, deep
+    in the EdS segment at the top end; nothing collapses at the bottom end),
+    in random frames and on the diagonal."""
+    rng = np.random.default_rng(17)
+    spectra = []
+    for scale in (1e-6, 1e-3, 0.7, 30.0, 1e3, 1e5, 1e6):
+        base = [[1.0, 0.3, -0.2], [1.0, 1.0, 1.0], [1.0, 0.0, 0.0], [0.6, -0.5, -1.0], [1.0, 1.0 - 1e-9, -0.4],
+                [0.01, -0.9, -1.0]]
+        base += list(-np.sort(-rng.normal(size=(40, 3)), axis=1))
+        spectra += [list(np.asarray(b) * scale) for b in base]
+    Ms = np.concatenate([_rotated(spectra, rng), np.array([np.diag(l) for l in spectra])])
+    stack = _planes_from_matrices(Ms)[None]
+    F_all, fl = oracle_per_radius(tables, stack)
+    F, idx = gpu_multi(ctx, stack, [1.0], mode=mode)
+    s = compare_max(F, idx, F_all, fl)
+    m = len(spectra) // 7
+    top = np.concatenate([np.arange(6 * m, 7 * m), len(spectra) + np.arange(6 * m, 7 * m)])
+    bottom = np.concatenate([np.arange(m), len(spectra) + np.arange(m)])
+    assert (F[top] > 1e4).sum() > m and np.all(F[bottom] == 0)
+    print("eigenvalue range", mode, s)
+
+
+@pytest.mark.parametrize("mode", MODES)
 def test_non_finite_inputs_give_no_collapse(ctx, mode):
     n = 64
     stack = np.zeros((1, 6, n))
