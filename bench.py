@@ -35,19 +35,20 @@ COSMO = dict(omega_m=0.3, omega_l=0.7, n_knots=512, a_min=1e-3, a_max=1.0)
 WORKLOAD = "collapse 256^3 grid x 25 radii, FP64 SoA Hessian planes (20.1 GB resident), 512-knot a(D) spline"
 
 # FP64 floating-point operations per (point, radius) evaluation of the FP64
-# kernel, from ncu thread-instruction counters (dadd + dmul + 2 dfma) divided
-# by the evaluations of the captured launch (profiles/collapse_kernel_*_128cube_x4.md).
-# None until a capture of the current kernel exists.
-FP64_FLOPS_PER_EVAL = 70.0   # profiles/collapse_kernel_fp64_128cube_x4.md
-FP64_FLOPS_PER_EVAL_MIXED = 8.1  # profiles/collapse_kernel_mixed_128cube_x30.md
-# FP64-pipe warp instructions of every kind (DFMA, DMUL, DADD, compares) per
+# kernel: ncu thread-instruction counters (dadd + dmul + 2 dfma) of one launch
+# of the 128^3 x 4 case divided by its evaluations (the FP64 and mixed kernels
+# as they stand; re-taken whenever either kernel changes).
+FP64_FLOPS_PER_EVAL = 73.0
+FP64_FLOPS_PER_EVAL_MIXED = 8.1
+# FP64-pipe thread instructions of every kind (DFMA, DMUL, DADD, DSETP) per
 # evaluation, from the same captures: the FP64 unit issues one per lane slot
 # whatever the instruction, so this count, not the flop count, sets the time.
-FP64_PIPE_INST_PER_EVAL = {"fp64": 45.0, "mixed": 5.1}
+FP64_PIPE_INST_PER_EVAL = {"fp64": 41.9, "mixed": 5.1}
 FP64_LANES_PER_CLK_PER_SM = 2.0
-# DRAM bytes (read + write) of one full launch of the default workload, from
-# an ncu capture of that launch (profiles/collapse_kernel_fp64_256cube_x25_dram.md).
-TRAFFIC_BYTES_DEFAULT = 20.83e9
+# DRAM bytes (read + write) of one full launch of the default workload, scaled
+# from the 128^3 x 4 capture of the same kernel: plane reads by evaluations,
+# F_max/idx reads and writes by points (the full launch is not captured).
+TRAFFIC_BYTES_DEFAULT = None
 # FP64 FMA rate of one GB300 SM: 1.25 TFLOP/s nominal at 2070 MHz over 152 SMs
 # = 3.97 flop/clk/SM, i.e. 2 DFMA per clock per SM (confirmed by a DFMA-chain probe).
 FP64_FLOP_PER_CLK_PER_SM = 4.0
@@ -86,6 +87,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    # points of each workload's oracle leg (CPU baseline + parity): the main
+    # workload's and, divided by 2.6, each variant's (1e6 is the survey's figure)
+    ap.add_argument("--cpu-points", type=int, default=262144)
     ap.add_argument("--no-variants", action="store_true")
     # smaller problems for profiler captures only (the benchmark workload is the default)
     ap.add_argument("--grid", type=int, default=GRID)
@@ -98,7 +102,7 @@ def parse():
     ap.add_argument("--train-points", type=int, default=4 * 1024 * 1024)
     ap.add_argument("--train-steps", type=int, default=300)
     # run one variant alone at --grid / --radii (profiler captures)
-    ap.add_argument("--variant", choices=["science", "field", "batched"], default=None)
+    ap.add_argument("--variant", choices=["science", "field", "batched", "toys"], default=None)
     return ap.parse_args()
 
 
@@ -238,6 +242,146 @@ def cpu_oracle_rate(seconds: float, first_point: int = 0, points_per_chunk: int 
     return out
 
 
+# ----------------------------------------------------------------------------- oracle legs
+# Each GPU leg ends (outside its timed region) with an oracle leg on a seeded
+# sample of its own points: the FP64 CPU oracle evaluates every radius of the
+# sampled points from the same input planes (copied from the device), timed on
+# all host cores and on one thread, and the GPU's running maximum at those
+# points is compared with the oracle's, element by element. The same run is
+# that workload's CPU baseline and its parity report.
+def _rel_err(got, ref):
+    import numpy as np
+    err = np.abs(got - ref)
+    nz = ref != 0
+    err[nz] /= np.abs(ref[nz])
+    return err
+
+
+def parity_report(F_gpu, idx_gpu, F_all, flags_all, tol: float, reduced: bool, scale_idx0: int = 0,
+                  counts: dict | None = None) -> dict:
+    """GPU F_max/idx against the oracle's per-radius values F_all (R, m) with
+    flags: max and RMS relative error on F, argmax mismatches outside ties,
+    and the excluded points. Ambiguous points (an eigenvalue sign or D_top on
+    an oracle-flagged edge) and, for the reduced-precision paths, points whose
+    F lies within 4 tol of 1 (the a_max clip) are excluded and counted, as in
+    the parity tests; ties are radii whose F differ by less than 1e-9 (FP64) or
+    2 tol (reduced)."""
+    import numpy as np
+    import oracle
+
+    R, m = F_all.shape
+    F_ref = np.zeros(m)
+    idx_ref = np.full(m, -1, dtype=np.int64)
+    for r in range(R):
+        better = F_all[r] > F_ref
+        F_ref[better] = F_all[r][better]
+        idx_ref[better] = scale_idx0 + r
+    amb = (flags_all & oracle.FLAGS_AMBIGUOUS).any(axis=0)
+    srt = np.sort(F_all, axis=0)
+    tie = np.zeros(m, dtype=bool)
+    if R > 1:
+        tie = (srt[-1] > 0) & (srt[-1] - srt[-2] <= (2 * tol if reduced else 1e-9) * srt[-1])
+    edge = np.zeros(m, dtype=bool)
+    if reduced:
+        edge = ((F_ref > 0) & (F_ref < 1.0 + 4 * tol)) | ((F_gpu > 0) & (F_gpu < 1.0 + 4 * tol))
+    ok = ~amb & ~edge
+    err = _rel_err(np.asarray(F_gpu, dtype=np.float64), F_ref)
+    out = {"points": int(m), "evaluations": int(m * R), "tol": tol,
+           "max_rel_err": float(err[ok].max()) if ok.any() else 0.0,
+           "rms_rel_err": float(np.sqrt(np.mean(err[ok] ** 2))) if ok.any() else 0.0,
+           "within_tol": bool((err[ok] <= tol).all()),
+           "idx_mismatch": int((np.asarray(idx_gpu)[ok & ~tie] != idx_ref[ok & ~tie]).sum()),
+           "ambiguous": int(amb.sum()), "ties": int(tie.sum()),
+           "collapsed_fraction_oracle": float((F_ref > 0).mean()),
+           "eds_evaluations_oracle": int(((flags_all & oracle.FLAG_EDS) != 0).sum())}
+    if reduced:
+        out["edge"] = int(edge.sum())
+    if counts:
+        out.update(counts)
+    return out
+
+
+def oracle_leg(planes, F_gpu, idx_gpu, tol: float, reduced: bool, kind: str = "classic", tab=None,
+               scale_idx0: int = 0, counts: dict | None = None, single_points: int = 512) -> dict:
+    """planes: (R, 6, m) host array (FP64, or FP32 widened exactly) of the
+    sampled points; F_gpu/idx_gpu: the GPU's results at those points. kind:
+    "classic" (Tables), "exact" (RatioTables, exact growth ratios) or "tab"
+    (tab = oracle.Tab of the same table)."""
+    import numpy as np
+    import oracle
+
+    cos = {k: COSMO[k] for k in ("omega_m", "omega_l", "n_knots", "a_min", "a_max")}
+    tables = oracle.Tables(**cos)
+    rt = oracle.RatioTables(**cos) if kind == "exact" else None
+    R, _, m = planes.shape
+
+    def run(h, nthreads):
+        if kind == "exact":
+            return rt.F_points(h, nthreads=nthreads)
+        if kind == "tab":
+            return tab.F_points(tables, h, nthreads=nthreads)
+        return tables.F_points(h, nthreads=nthreads)
+
+    Fs, fl = [], []
+    c0 = _cpu_times()
+    t0 = time.perf_counter()
+    for r in range(R):
+        F, f = run(planes[r], 0)
+        Fs.append(F)
+        fl.append(f)
+    dt = time.perf_counter() - t0
+    c1 = _cpu_times()
+    ms = min(single_points, m)
+    t1 = time.perf_counter()
+    for r in range(R):
+        run(np.ascontiguousarray(planes[r][:, :ms]), 1)
+    dt1 = time.perf_counter() - t1
+    F_all, flags_all = np.stack(Fs), np.stack(fl)
+    cpu = {"value": m * R / dt, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{m} points x {R} radii ({m * R} evaluations, {dt:.1f} s, OpenMP over {os.cpu_count()} threads)",
+           "single_thread_value": ms * R / dt1, "single_thread_sample": f"{ms} points x {R} radii"}
+    share = _cpu_share(c0, c1)
+    if share:
+        cpu["host_cpu"] = share
+    return {"parity": parity_report(np.asarray(F_gpu), np.asarray(idx_gpu), F_all, flags_all, tol, reduced,
+                                    scale_idx0, counts), "cpu": cpu, "F_all": F_all, "flags": flags_all}
+
+
+def sample_points(n: int, m: int, seed: int):
+    """m distinct seeded point indices of an n-point grid, with both ends."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    if m >= n:
+        return np.arange(n, dtype=np.int64)
+    pts = np.unique(np.concatenate([rng.choice(n, m - 2, replace=False), [0, n - 1]]))
+    return pts.astype(np.int64)
+
+
+def gather_planes(hess, pts):
+    """(R, 6, m) host copy of the sampled points of device planes hess (R, 6, n)."""
+    import torch
+    idx = torch.from_numpy(pts).to(hess.device)
+    return hess.index_select(2, idx).cpu().numpy()
+
+
+def clk_mhz_default(dev) -> float:
+    """The SM clock the FP64-pipe fractions of the variants are taken at: the
+    device's maximum SM clock (nvidia-smi's clocks.max.sm; 2070 MHz on GB300)."""
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits", "-i",
+                              str(dev.index or 0)], capture_output=True, text=True, timeout=20).stdout.strip()
+        return float(out.splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        return 2070.0
+
+
+def timing_stats(ms: list) -> dict:
+    """median, min, max and relative standard deviation of per-launch times."""
+    med = statistics.median(ms)
+    rsd = statistics.pstdev(ms) / statistics.mean(ms) if len(ms) > 1 else 0.0
+    return {"median": med, "min": min(ms), "max": max(ms), "rsd": rsd, "n": len(ms)}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -273,7 +417,8 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- float-float variant
-def run_f32x2_variant(ctx, hess, sig, F_ref, idx_ref, stream, steps: int, mode: str = "f32x2") -> dict:
+def run_f32x2_variant(ctx, hess, sig, F_ref, idx_ref, stream, steps: int, mode: str = "f32x2",
+                      oracle_in: dict | None = None) -> dict:
     """Another mode on the same FP64 planes as the main workload, timed the same
     way, and compared with the FP64 kernel's result point by point: the FP64
     path's steps in float-float arithmetic (CC_MODE_F32X2, held to the same
@@ -303,9 +448,29 @@ def run_f32x2_variant(ctx, hess, sig, F_ref, idx_ref, stream, steps: int, mode: 
     both = (F_ref > 0) & (F > 0)
     rel = ((F - F_ref).abs() / F_ref)[both]
     ms = statistics.mean(times)
+    parity = None
+    if oracle_in is not None:  # the oracle on sampled points of the same planes
+        import torch as _t
+        pts = oracle_in["pts"]
+        pi = _t.from_numpy(pts).to(F.device)
+        Fg, ig = F.index_select(0, pi).cpu().numpy(), idx.index_select(0, pi).cpu().numpy()
+        if mode == "f32x2":
+            parity = parity_report(Fg, ig, oracle_in["F_all"], oracle_in["flags"], 1e-10, False)
+        else:
+            m = min(len(pts), 20000)
+            kind = "exact" if mode == "exact_growth" else "tab"
+            tab = None
+            if kind == "tab":
+                import oracle
+                dg, xg, yg = table_axes()
+                tab = oracle.Tab(dg, xg, yg, oracle.tab_node_values(dg, xg, yg))
+            leg = oracle_leg(oracle_in["planes"][:, :, :m], Fg[:m], ig[:m], 1e-10, False, kind=kind, tab=tab)
+            parity = leg["parity"]
+            parity["cpu_oracle_evals_per_s"] = leg["cpu"]["value"]
     return {
         "workload": "the main workload's planes (256^3 x 25, FP64)",
-        "evals_per_s": float(n) * R / (ms * 1e-3), "kernel_ms": ms,
+        "evals_per_s": float(n) * R / (ms * 1e-3), "kernel_ms": ms, "kernel_ms_stats": timing_stats(times),
+        **({"parity": parity} if parity is not None else {}),
         "max_rel_diff_vs_fp64_kernel": float(rel.max()), "rms_rel_diff_vs_fp64_kernel": float(rel.pow(2).mean().sqrt()),
         "collapse_decision_differs": int(((F_ref > 0) != (F > 0)).sum()),
         "argmax_differs": int((idx != idx_ref).sum()),
@@ -409,6 +574,14 @@ def run_science_variant(ctx, dev, stream, reps: int = 10, grid: int = GRID, R: i
         times.append(h0.elapsed_time(h1))
     c = counts.cpu().tolist()
     hist_ms = statistics.median(times)
+    pts = sample_points(n, 20000, SEED + 13)
+    pi = torch.from_numpy(pts).to(dev)
+    leg = oracle_leg(gather_planes(hess, pts), F.index_select(0, pi).cpu().numpy(),
+                     idx.index_select(0, pi).cpu().numpy(), 1e-10, False)
+    import oracle
+    F_or = leg["F_all"].max(axis=0)
+    c_or = oracle.histogram(F_or, SCI_EDGES)
+    c_gpu_sample = oracle.histogram(F.index_select(0, pi).cpu().numpy(), SCI_EDGES)
     del hess
     torch.cuda.empty_cache()
     return {
@@ -417,7 +590,9 @@ def run_science_variant(ctx, dev, stream, reps: int = 10, grid: int = GRID, R: i
         "collapsed_per_z_bin": c[1:-1], "not_collapsed_or_z_below_0": c[0], "z_above_last_edge": c[-1],
         "collapsed_fraction": float((F > 0).double().mean()),
         "collapse_kernel_ms": collapse_ms, "evals_per_s": n * R / (collapse_ms * 1e-3),
-        "histogram_kernel_ms": hist_ms,
+        "histogram_kernel_ms": hist_ms, "histogram_kernel_ms_stats": timing_stats(times),
+        "parity": leg["parity"],
+        "sample_counts_differ_from_oracle": int(abs(c_or - c_gpu_sample).sum()),
         "histogram_roofline": {"bound": "hbm", "unit": "GB/s", "achieved": 8.0 * n / (hist_ms * 1e-3) / 1e9,
                                "peak": HBM_GBS, "frac": (8.0 * n / (hist_ms * 1e-3) / 1e9 / HBM_GBS) if HBM_GBS else None,
                                "algorithmic_bytes": 8.0 * n},
@@ -449,7 +624,10 @@ def run_field_variant(ctx, dev, stream, reps: int = 2, grid: int = GRID, R: int 
     radii = np.geomspace(FIELD_RADII[0], FIELD_RADII[1], R)
     sig = [field.sigma(x) for x in radii]
     out = {}
+    pts = sample_points(n, 20000, SEED + 14)
+    pi = torch.from_numpy(pts).to(dev)
     for label, dt, mode in (("fp64", torch.float64, "fp64"), ("fp32_planes_mixed", torch.float32, "mixed")):
+        sample_planes = np.empty((R, 6, len(pts)), dtype=np.float64 if dt == torch.float64 else np.float32)
         planes = torch.empty((6, n), dtype=dt, device=dev)
         F = torch.empty(n, dtype=torch.float64, device=dev)
         idx = torch.empty(n, dtype=torch.int32, device=dev)
@@ -470,9 +648,16 @@ def run_field_variant(ctx, dev, stream, reps: int = 2, grid: int = GRID, R: int 
             col_ms.append(sum(ev[2 * r + 1].elapsed_time(ev[2 * r + 2]) for r in range(R)))
             tot_ms.append(ev[0].elapsed_time(ev[2 * R]))
         t = statistics.mean(tot_ms)
+        # untimed pass: the same planes again (deterministic), sampled for the oracle
+        for r in range(R):
+            field.hessian(radii[r], planes)
+            sample_planes[r] = planes.index_select(1, pi).cpu().numpy()
+        leg = oracle_leg(sample_planes, F.index_select(0, pi).cpu().numpy(), idx.index_select(0, pi).cpu().numpy(),
+                         1e-10 if mode == "fp64" else 3e-5, mode != "fp64")
         out[label] = {"evals_per_s": n * R / (t * 1e-3), "ms_per_realization": t,
+                      "ms_per_realization_stats": timing_stats(tot_ms),
                       "hessian_fft_ms": statistics.mean(fft_ms), "collapse_ms": statistics.mean(col_ms),
-                      "collapsed_fraction": float((F > 0).double().mean())}
+                      "collapsed_fraction": float((F > 0).double().mean()), "parity": leg["parity"]}
         del planes
     field.close()
     torch.cuda.empty_cache()
@@ -481,11 +666,104 @@ def run_field_variant(ctx, dev, stream, reps: int = 2, grid: int = GRID, R: int 
             "sigma_range": [float(sig[-1]), float(sig[0])], **out}
 
 
+# ----------------------------------------------------------------------------- interpolation toys
+TOY_QUERIES = (10 ** 2, 10 ** 3, 10 ** 4, 10 ** 5, 10 ** 6, 10 ** 7, 10 ** 8)
+
+
+def run_toys_variant(ctx, dev, stream, reps: int = 10, max_queries: int = 10 ** 8) -> dict:
+    """The paper's two interpolation toys (Sec. 4.3, 5.1, 5.2) on the GPU:
+    y = x^2 through a natural spline on 512 random knots (cc_spline_eval), and
+    z = x^2 + y^2 on a random 64 x 64 grid whose nodes carry 128-knot splines
+    (cc_table_query), each at 1e2 .. 1e8 uniformly random queries. Per size:
+    device time (CUDA events around the call, queries resident) and end-to-end
+    time (queries copied from pinned host memory, the call, results copied
+    back), over `reps` repetitions (median, min, max, RSD as in the paper's
+    timing table); the mean relative residual against the analytic function
+    and the largest relative difference from the CPU oracle's interpolation
+    (which is also timed, on all host cores, up to 1e7 queries)."""
+    import numpy as np
+    import torch
+
+    import oracle
+
+    rng = np.random.default_rng(SEED + 20)
+    xk = np.sort(rng.uniform(0.0, 1.0, 512))
+    yk = xk * xk
+    Mk = oracle.spline_build(xk, yk)
+    dg = np.sort(rng.uniform(-1.0, 1.0, 128))
+    xg = np.sort(rng.uniform(0.0, 1.0, 64))
+    yg = np.sort(rng.uniform(0.0, 1.0, 64))
+    val = np.repeat((xg[:, None] ** 2 + yg[None, :] ** 2)[:, :, None], 128, axis=2)
+    ctx.set_table(dg, xg, yg, val)
+    tab = oracle.Tab(dg, xg, yg, val)
+    out = {"spline_1d": [], "bilinear_2d": []}
+    for m in (q for q in TOY_QUERIES if q <= max_queries):
+        for toy in ("spline_1d", "bilinear_2d"):
+            if toy == "spline_1d":
+                qh = [torch.from_numpy(rng.uniform(xk[0], xk[-1], m)).pin_memory()]
+            else:
+                qh = [torch.from_numpy(rng.uniform(lo, hi, m)).pin_memory()
+                      for lo, hi in ((dg[0], dg[-1]), (xg[0], xg[-1]), (yg[0], yg[-1]))]
+            qd = [a.to(dev) for a in qh]
+            od = torch.empty(m, dtype=torch.float64, device=dev)
+            oh = torch.empty(m, dtype=torch.float64, pin_memory=True)
+
+            def call(qs):
+                if toy == "spline_1d":
+                    ctx.spline_eval(xk, yk, qs[0], od, stream)
+                else:
+                    ctx.table_query(*qs, od, stream)
+
+            call(qd)
+            torch.cuda.synchronize()
+            dev_ms, e2e_ms = [], []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                call(qd)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                dev_ms.append(e0.elapsed_time(e1))
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for a, b in zip(qd, qh):
+                    a.copy_(b, non_blocking=True)
+                call(qd)
+                oh.copy_(od, non_blocking=True)
+                torch.cuda.synchronize()
+                e2e_ms.append(1e3 * (time.perf_counter() - t0))
+            got = oh.numpy()
+            qn = [a.numpy() for a in qh]
+            exact = qn[0] ** 2 if toy == "spline_1d" else qn[1] ** 2 + qn[2] ** 2
+            mc = min(m, 10 ** 7)
+            t0 = time.perf_counter()
+            if toy == "spline_1d":
+                ref = oracle.spline_eval_many(xk, yk, Mk, qn[0][:mc])
+            else:
+                ref = tab.query_many(qn[0][:mc], qn[1][:mc], qn[2][:mc])
+            cpu_s = time.perf_counter() - t0
+            out[toy].append({
+                "queries": m,
+                "device_ms": timing_stats(dev_ms), "e2e_ms": timing_stats(e2e_ms),
+                "device_queries_per_s": m / (statistics.median(dev_ms) * 1e-3),
+                "e2e_queries_per_s": m / (statistics.median(e2e_ms) * 1e-3),
+                "mean_rel_residual_vs_analytic": float(np.mean(np.abs(got - exact) / exact)),
+                "max_rel_diff_vs_oracle": float(np.max(np.abs(got[:mc] - ref) / np.maximum(np.abs(ref), 1e-300))),
+                "cpu_oracle_queries_per_s": mc / cpu_s, "cpu_oracle_queries": mc,
+            })
+            del qd, od, oh, qh
+    torch.cuda.empty_cache()
+    return {"workload": "y = x^2 on 512 random knots in [0, 1]; z = x^2 + y^2 on a random 64 x 64 grid in [0, 1]^2 "
+                        "with 128 random knots along delta in [-1, 1]; uniformly random queries",
+            "cores": os.cpu_count(), **out}
+
+
 # ----------------------------------------------------------------------------- mixed variant
 MIXED_GRID, MIXED_RADII = 512, 30
 
 
-def run_mixed_variant(ctx, dev, stream, reps: int = 3) -> dict:
+def run_mixed_variant(ctx, dev, stream, reps: int = 3, sample: int = 100000) -> dict:
     """Mixed precision (FP32 planes, FP64 only where it sets accuracy) on a
     512^3 x 30 grid (96.6 GB of FP32 planes), timed like the main workload and
     compared with the FP64 kernel on the same planes (which agrees with the
@@ -497,6 +775,8 @@ def run_mixed_variant(ctx, dev, stream, reps: int = 3) -> dict:
 
     n, R = MIXED_GRID ** 3, MIXED_RADII
     sig = hessgen.sigma_schedule(R, S_LO, S_HI)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_mhz = clk_mhz_default(dev)
     hess = torch.empty((R, 6, n), dtype=torch.float32, device=dev)
     for r in range(R):
         hdev.fill(hess[r], SEED + 1, 0, r, sig[r])
@@ -520,22 +800,37 @@ def run_mixed_variant(ctx, dev, stream, reps: int = 3) -> dict:
         st = ctx.stats()
         F[mode] = (Fm, im)
         out[mode] = {"kernel_ms": statistics.mean(times), "evals_per_s": n * R / (statistics.mean(times) * 1e-3),
-                     "fp64_branch_fraction": st["fp64_branch"] / st["evaluations"]}
+                     "kernel_ms_stats": timing_stats(times),
+                     "fp64_branch_fraction": st["fp64_branch"] / st["evaluations"], "stats": st}
     Fr, ir = F["fp64"]
     Fx, ix = F["mixed"]
     nz = Fr > 0
     rel = torch.where(nz, (Fx - Fr).abs() / torch.where(nz, Fr, torch.ones_like(Fr)), (Fx - Fr).abs())
     edge = ((Fr > 0) & (Fr < 1.0 + 1.2e-4)) | ((Fx > 0) & (Fx < 1.0 + 1.2e-4))
     rel_ok = rel[~edge]
-    del hess
+    # oracle leg on sampled points of the same FP32 planes (config 3's CPU baseline)
+    pts = sample_points(n, sample, SEED + 11)
+    planes = gather_planes(hess, pts)
+    pi = torch.from_numpy(pts).to(dev)
+    st = out["mixed"]["stats"]
+    leg = oracle_leg(planes, Fx.index_select(0, pi).cpu().numpy(), ix.index_select(0, pi).cpu().numpy(), 3e-5, True,
+                     counts={"fp64_branch_fraction_gpu": st["fp64_branch"] / st["evaluations"],
+                             "eds_fraction_gpu": st["eds_branch"] / st["evaluations"],
+                             "refined_fraction_gpu": st["refined"] / st["evaluations"]})
+    leg64 = parity_report(Fr.index_select(0, pi).cpu().numpy(), ir.index_select(0, pi).cpu().numpy(),
+                          leg["F_all"], leg["flags"], 1e-10, False)
+    del hess, planes
     torch.cuda.empty_cache()
     return {
         "workload": f"{MIXED_GRID}^3 grid x {MIXED_RADII} radii, FP32 SoA planes (96.6 GB resident)",
         "evals_per_s": out["mixed"]["evals_per_s"], "kernel_ms": out["mixed"]["kernel_ms"],
+        "kernel_ms_stats": out["mixed"]["kernel_ms_stats"],
+        "parity": leg["parity"], "fp64_kernel_same_planes_parity": leg64, "cpu_baseline": leg["cpu"],
         "fp64_kernel_same_planes_evals_per_s": out["fp64"]["evals_per_s"],
         "speedup_vs_fp64_kernel": out["fp64"]["kernel_ms"] / out["mixed"]["kernel_ms"],
-        "max_rel_diff_vs_fp64": float(rel_ok.max()), "rms_rel_diff_vs_fp64": float(rel_ok.pow(2).mean().sqrt()),
-        "edge_points_excluded": int(edge.sum()),
+        "vs_fp64_kernel_all_points": {"max_rel_diff": float(rel_ok.max()),
+                                      "rms_rel_diff": float(rel_ok.pow(2).mean().sqrt()),
+                                      "edge_points_excluded": int(edge.sum())},
         "argmax_diff_fraction": float((ix != ir).double().mean()),
         "fp64_branch_fraction": out["mixed"]["fp64_branch_fraction"],
         "roofline": {
@@ -544,8 +839,11 @@ def run_mixed_variant(ctx, dev, stream, reps: int = 3) -> dict:
                     "frac": 24.0 * out["mixed"]["evals_per_s"] / 1e9 / HBM_GBS if HBM_GBS else None},
             "fp64_pipe": {"inst_per_eval": FP64_PIPE_INST_PER_EVAL["mixed"],
                           "frac": FP64_PIPE_INST_PER_EVAL["mixed"] * out["mixed"]["evals_per_s"]
-                          / (FP64_LANES_PER_CLK_PER_SM * 152 * 2070e6)},
-            "note": "issue-bound (71 % of issue slots, profiles/collapse_kernel_mixed_128cube_x30.md)",
+                          / (FP64_LANES_PER_CLK_PER_SM * sm_count * clk_mhz * 1e6),
+                          "basis": f"{FP64_LANES_PER_CLK_PER_SM:g} FP64 lanes/clk/SM x {sm_count} SMs x "
+                                   f"{clk_mhz:.0f} MHz"},
+            "note": "issue-bound: the FP32 and integer instructions of the eigen and root stages fill the issue "
+                    "slots before HBM or the FP64 unit saturate",
         },
         "bound_tol": 3e-5,
     }
@@ -556,7 +854,23 @@ BATCH_SEED, BATCH_N = 2514, 48
 BATCH_GRIDS = (64, 96, 128, 192, 256, 384)
 
 
-def run_batch_variant(ctx, dev, stream, reps: int = 3, grids=BATCH_GRIDS, n_items: int = BATCH_N) -> dict:
+def merge_parity(reports: list) -> dict:
+    """One parity report from several (realizations of a batch)."""
+    import math
+    pts = sum(r["points"] for r in reports)
+    out = {"points": pts, "evaluations": sum(r["evaluations"] for r in reports), "tol": reports[0]["tol"],
+           "max_rel_err": max(r["max_rel_err"] for r in reports),
+           "rms_rel_err": math.sqrt(sum(r["rms_rel_err"] ** 2 * r["points"] for r in reports) / pts),
+           "within_tol": all(r["within_tol"] for r in reports)}
+    for k in ("idx_mismatch", "ambiguous", "ties", "edge", "eds_evaluations_oracle"):
+        if k in reports[0]:
+            out[k] = sum(r[k] for r in reports)
+    out["collapsed_fraction_oracle"] = sum(r["collapsed_fraction_oracle"] * r["points"] for r in reports) / pts
+    return out
+
+
+def run_batch_variant(ctx, dev, stream, reps: int = 3, grids=BATCH_GRIDS, n_items: int = BATCH_N,
+                      sample: int = 100000) -> dict:
     """48 realizations, grids drawn from {64..384}^3 and 8..40 radii (seeded),
     FP32 planes (240.5 GB resident), mixed precision: one persistent launch
     replayed from a CUDA graph with autotuned tiles, against one
@@ -622,6 +936,25 @@ def run_batch_variant(ctx, dev, stream, reps: int = 3, grids=BATCH_GRIDS, n_item
         torch.cuda.synchronize()
         loop_ms.append(e0.elapsed_time(e1))
     same = all(torch.equal(a, F) for a, (_, _, F, _) in zip(F_batch, items))
+    # oracle leg: a seeded sample of every realization (config 4's CPU baseline)
+    reports, evals_cpu, secs_cpu, evals_1, secs_1 = [], 0, 0.0, 0, 0.0
+    per = max(256, sample // n_items)
+    for k, (hess, sig, F, idx) in enumerate(items):
+        pts = sample_points(hess.shape[2], per, BATCH_SEED + 100 + k)
+        pi = torch.from_numpy(pts).to(dev)
+        leg = oracle_leg(gather_planes(hess, pts), F_batch[k].index_select(0, pi).cpu().numpy(),
+                         idx.index_select(0, pi).cpu().numpy(), 3e-5, True, single_points=32)
+        reports.append(leg["parity"])
+        ev = leg["parity"]["evaluations"]
+        evals_cpu += ev
+        secs_cpu += ev / leg["cpu"]["value"]
+        ev1 = 32 * hess.shape[0]
+        evals_1 += ev1
+        secs_1 += ev1 / leg["cpu"]["single_thread_value"]
+    cpu = {"value": evals_cpu / secs_cpu, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{per} points of each of the {n_items} realizations x their radii ({evals_cpu} evaluations, "
+                     f"{secs_cpu:.1f} s, OpenMP over {os.cpu_count()} threads)",
+           "single_thread_value": evals_1 / secs_1, "single_thread_sample": "32 points of each realization"}
     batch.close()
     del items, F_batch
     torch.cuda.empty_cache()
@@ -629,7 +962,8 @@ def run_batch_variant(ctx, dev, stream, reps: int = 3, grids=BATCH_GRIDS, n_item
     return {
         "workload": f"{n_items} realizations, grids {{{min(grid_choice)}..{max(grid_choice)}}}^3, 8..40 radii (seed {BATCH_SEED}), "
                     f"{evals} evaluations, FP32 planes ({evals * 24 / 1e9:.1f} GB resident), mixed precision",
-        "evals_per_s": evals / (g * 1e-3), "graph_replay_ms": g,
+        "evals_per_s": evals / (g * 1e-3), "graph_replay_ms": g, "graph_replay_ms_stats": timing_stats(graph_ms),
+        "parity": merge_parity(reports), "cpu_baseline": cpu,
         "per_realization_launches_ms": l, "speedup_vs_per_realization": l / g,
         "results_identical_to_per_realization": bool(same),
         "autotune_s": tune_s, "threads_per_block": blk,
@@ -642,7 +976,7 @@ SUR_GRID, SUR_RADII = 768, 40
 SUR_TRAIN_POINTS = 40 * 1024 * 1024  # ~2e7 collapsing samples at s = 1
 
 
-def run_surrogate_variant(ctx, dev, stream, steps: int = 3000) -> dict:
+def run_surrogate_variant(ctx, dev, stream, steps: int = 3000, sample: int = 100000) -> dict:
     """Train the MLP surrogate on the GPU (samples from the exact FP64 path on
     4.2e7 isotropic-field points at s = 1), then evaluate a 768^3 grid x 40
     radii of FP32 planes (435 GB in total, so generated one radius at a time,
@@ -668,9 +1002,15 @@ def run_surrogate_variant(ctx, dev, stream, steps: int = 3000) -> dict:
     outs = {m: (torch.zeros(n, dtype=torch.float64, device=dev), torch.full((n,), -1, dtype=torch.int32, device=dev))
             for m in ("surrogate", "surrogate_mma_sync", "mixed", "fp64")}
     ms = {m: 0.0 for m in outs}
+    per_radius_ms = {m: [] for m in outs}
     stats = {m: {"evaluations": 0, "fallback": 0, "fp64_branch": 0, "error_flags": 0} for m in outs}
+    import numpy as np
+    pts = sample_points(n, sample, SEED + 12)
+    pi = torch.from_numpy(pts).to(dev)
+    sample_planes = np.empty((R, 6, len(pts)), dtype=np.float32)
     for r in range(R):
         hdev.fill(planes, SEED + 6, 0, r, sig[r])
+        sample_planes[r] = planes.index_select(1, pi).cpu().numpy()
         for m, (F, idx) in outs.items():
             ctx.reset_stats()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -682,6 +1022,7 @@ def run_surrogate_variant(ctx, dev, stream, steps: int = 3000) -> dict:
             ctx.set_surrogate_engine("tcgen05")
             torch.cuda.synchronize()
             ms[m] += e0.elapsed_time(e1)
+            per_radius_ms[m].append(e0.elapsed_time(e1))
             st = ctx.stats()
             for k in stats[m]:
                 stats[m][k] += st[k]
@@ -696,12 +1037,24 @@ def run_surrogate_variant(ctx, dev, stream, steps: int = 3000) -> dict:
     x_max, x_rms = rel(Fx, F64)
     t_max, _ = rel(outs["surrogate_mma_sync"][0], F64)
     evals = float(n) * R
+    # oracle leg on the sampled points of every radius (config 5's CPU baseline)
+    sel = {m: (outs[m][0].index_select(0, pi).cpu().numpy(), outs[m][1].index_select(0, pi).cpu().numpy())
+           for m in outs}
+    st_s = stats["surrogate"]
+    leg = oracle_leg(sample_planes, *sel["surrogate"], 3e-5, True,
+                     counts={"fallback_fraction_gpu": st_s["fallback"] / st_s["evaluations"]})
+    par = {m: parity_report(*sel[m], leg["F_all"], leg["flags"], 1e-10 if m == "fp64" else 3e-5, m != "fp64")
+           for m in ("surrogate_mma_sync", "mixed", "fp64")}
     del planes, outs
     torch.cuda.empty_cache()
     return {
         "workload": f"{SUR_GRID}^3 grid x {SUR_RADII} radii, FP32 planes streamed per radius (10.9 GB each)",
         "train": {**rep, "seconds": train_s, "steps": steps, "batch": 16384},
         "evals_per_s": evals / (ms["surrogate"] * 1e-3),
+        "per_radius_kernel_ms_stats": timing_stats(per_radius_ms["surrogate"]),
+        "parity": leg["parity"], "cpu_baseline": leg["cpu"],
+        "parity_same_planes": {"mma_sync_engine": par["surrogate_mma_sync"], "mixed": par["mixed"],
+                               "fp64_kernel": par["fp64"]},
         "engine": "tcgen05",
         "error_flags": stats["surrogate"]["error_flags"],
         "tensor": {"algorithmic_flops_per_eval": MLP_FLOPS_PER_EVAL,
@@ -710,7 +1063,7 @@ def run_surrogate_variant(ctx, dev, stream, steps: int = 3000) -> dict:
                    "frac": (MLP_FLOPS_PER_EVAL * evals / (ms["surrogate"] * 1e-3) / 1e12 / BF16_TFLOPS)
                    if BF16_TFLOPS else None},
         "mma_sync_engine": {"evals_per_s": evals / (ms["surrogate_mma_sync"] * 1e-3),
-                            "max_rel_diff_vs_fp64": t_max,
+                            "max_rel_diff_vs_fp64_kernel": t_max,
                             "fallback_fraction": stats["surrogate_mma_sync"]["fallback"]
                             / stats["surrogate_mma_sync"]["evaluations"]},
         "mixed_evals_per_s": evals / (ms["mixed"] * 1e-3),
@@ -718,10 +1071,30 @@ def run_surrogate_variant(ctx, dev, stream, steps: int = 3000) -> dict:
         "gain_over_method_without_network": ms["mixed"] / ms["surrogate"],
         "speedup_vs_fp64_kernel": ms["fp64"] / ms["surrogate"],
         "fallback_fraction": stats["surrogate"]["fallback"] / stats["surrogate"]["evaluations"],
-        "max_rel_diff_vs_fp64": s_max, "rms_rel_diff_vs_fp64": s_rms,
-        "mixed_max_rel_diff_vs_fp64": x_max, "mixed_rms_rel_diff_vs_fp64": x_rms,
+        "vs_fp64_kernel_all_points": {"surrogate_max_rel_diff": s_max, "surrogate_rms_rel_diff": s_rms,
+                                      "mixed_max_rel_diff": x_max, "mixed_rms_rel_diff": x_rms},
         "bound_tol": 3e-5,
     }
+
+
+def run_config1_leg(ctx, dev) -> dict:
+    """The small configuration in full: 32^3 points x 8 radii (s 0.3 -> 4.0,
+    FP64 planes, seed 2511) on the GPU (one fused launch), and the oracle on
+    every evaluation (all host cores; one thread on the first 4096 points)."""
+    import torch
+
+    import hessgen
+
+    n, R = 32 ** 3, 8
+    sig = hessgen.sigma_schedule(R, 0.3, 4.0)
+    stack = hessgen.hessian_stack(2511, 0, sig, n)
+    hess = torch.from_numpy(stack).to(dev)
+    F = torch.empty(n, dtype=torch.float64, device=dev)
+    idx = torch.empty(n, dtype=torch.int32, device=dev)
+    ctx.reset_max(F, idx)
+    ctx.collapse_multi(hess, sig, F, idx, mode="fp64")
+    torch.cuda.synchronize()
+    return oracle_leg(stack, F.cpu().numpy(), idx.cpu().numpy(), 1e-10, False, single_points=4096)
 
 
 def job_rate(elapsed_ms: float, evals: float, world: int, device) -> tuple:
@@ -757,6 +1130,8 @@ def main():
         if args.variant == "batched":  # 12 realizations of grids up to --grid
             out = run_batch_variant(ctx, dev, torch.cuda.current_stream(),
                                     grids=tuple(g for g in BATCH_GRIDS if g <= args.grid), n_items=12)
+        elif args.variant == "toys":
+            out = run_toys_variant(ctx, dev, torch.cuda.current_stream())
         else:
             fn = {"science": run_science_variant, "field": run_field_variant}[args.variant]
             out = fn(ctx, dev, torch.cuda.current_stream(), grid=args.grid, R=args.radii)
@@ -802,6 +1177,8 @@ def main():
     stream = torch.cuda.current_stream()
 
     def step(ev=None):
+        if ev is not None:
+            ev[2].record(stream)
         ctx.reset_max(F, idx)
         if ev is not None:
             ev[0].record(stream)
@@ -813,8 +1190,8 @@ def main():
         step()
     torch.cuda.synchronize()
     ctx.reset_stats()
-    kernel_events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                     for _ in range(args.steps)]
+    # per step: kernel start, kernel end, step start (the reset of F_max/idx)
+    kernel_events = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(args.steps)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     clocks.start()
@@ -830,7 +1207,8 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     elapsed_ms = t_start.elapsed_time(t_end)
-    kernel_ms = [a.elapsed_time(b) for a, b in kernel_events]
+    kernel_ms = [a.elapsed_time(b) for a, b, _ in kernel_events]
+    step_ms = [c.elapsed_time(b) for _, b, c in kernel_events]
     stats = ctx.stats()
     assert stats["evaluations"] == n * R * args.steps, stats
     value, elapsed_ms = job_rate(elapsed_ms, float(n) * R * args.steps, world, dev)
@@ -851,6 +1229,7 @@ def main():
         "flops_per_eval": fpe,
         "evals_per_s_kernel": evals_launch / kern_avg_s,
         "kernel_ms": statistics.mean(kernel_ms),
+        "kernel_ms_stats": timing_stats(kernel_ms),
         "traffic": TRAFFIC_BYTES_DEFAULT if ((args.grid, R) == (GRID, N_RADII) and args.mode == "fp64") else None,
         "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full launch",
         "algorithmic_bytes": 48.0 * evals_launch + 12.0 * 2 * n,
@@ -881,19 +1260,42 @@ def main():
                    "per_gpu": "one independent realization per GPU",
                    "l2": f"inputs {6 * hess.element_size() * n * R / 1e9:.1f} GB per step vs 129 MB L2 (no flush needed)"},
         "roofline": roofline,
+        "timing": {"step_ms": timing_stats(step_ms), "kernel_ms": timing_stats(kernel_ms),
+                   "value_at_median_step": float(n) * R * world / (statistics.median(step_ms) * 1e-3),
+                   "basis": "CUDA events on the launching stream around each timed step (reset + fused "
+                            "launch) and around each fused launch; value is the whole timed region"},
         "gpu_launches": 2 * args.steps,
         "clocks": clk,
         "stats": {k: stats[k] for k in ("evaluations", "collapsed", "eds_branch", "refined", "error_flags")},
     }
 
+    full = (args.grid, R) == (GRID, N_RADII)
+    main_leg = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and full:
+        # oracle leg of the main workload: sampled points of the device planes,
+        # every radius; its timing is the CPU baseline, its comparison the parity
+        pts = sample_points(n, args.cpu_points, SEED + 10)
+        planes = gather_planes(hess, pts)
+        pi = torch.from_numpy(pts).to(dev)
+        tol = 1e-10 if args.mode in ("fp64", "f32x2", "exact_growth", "tabulated") else 3e-5
+        main_leg = oracle_leg(planes, F.index_select(0, pi).cpu().numpy(), idx.index_select(0, pi).cpu().numpy(),
+                              tol, tol > 1e-10,
+                              counts={"eds_evaluations_gpu_whole_grid": stats["eds_branch"] // args.steps,
+                                      "refined_evaluations_gpu_whole_grid": stats["refined"] // args.steps,
+                                      "fp64_branch_evaluations_gpu_whole_grid": stats["fp64_branch"] // args.steps,
+                                      "fallback_evaluations_gpu_whole_grid": stats["fallback"] // args.steps})
+        result["parity"] = main_leg["parity"]
+        result["cpu_baseline"] = main_leg["cpu"]
+        main_leg = {"pts": pts, "planes": planes, "F_all": main_leg["F_all"], "flags": main_leg["flags"]}
     if rank == 0 and not args.no_variants and (args.grid, R) == (GRID, N_RADII) and args.mode == "fp64":
-        result["variants"] = {"f32x2": run_f32x2_variant(ctx, hess, sig, F, idx, stream, args.steps)}
+        result["variants"] = {"f32x2": run_f32x2_variant(ctx, hess, sig, F, idx, stream, args.steps,
+                                                         oracle_in=main_leg)}
         result["variants"]["streamed_per_radius"] = run_streamed_variant(ctx, hess, sig, F, idx, stream, args.steps)
         result["variants"]["exact_growth"] = run_f32x2_variant(ctx, hess, sig, F, idx, stream, args.steps,
-                                                               mode="exact_growth")
+                                                               mode="exact_growth", oracle_in=main_leg)
         load_table(ctx)
         result["variants"]["tabulated"] = run_f32x2_variant(ctx, hess, sig, F, idx, stream, args.steps,
-                                                            mode="tabulated")
+                                                            mode="tabulated", oracle_in=main_leg)
 
     # end to end through the host-buffer entry point (H2D of every radius inside the timed region)
     if not args.no_e2e and rank == 0 and args.mode == "fp64":
@@ -956,8 +1358,19 @@ def main():
         result["variants"]["surrogate"] = run_surrogate_variant(ctx, dev, stream)
         result["variants"]["science_proxy"] = run_science_variant(ctx, dev, stream)
         result["variants"]["field_to_collapse"] = run_field_variant(ctx, dev, stream)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and (args.grid, R) == (GRID, N_RADII):
-        result["cpu_baseline"] = cpu_oracle_rate(args.cpu_seconds)
+        result["variants"]["interpolation_toys"] = run_toys_variant(ctx, dev, stream)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and full:
+        # the oracle on all of the small configuration (32^3 x 8, FP64), and the
+        # per-configuration baselines gathered from the legs above
+        c1 = run_config1_leg(ctx, dev)
+        result["cpu_baselines"] = {"config1_32cube_x8_fp64_full": c1["cpu"],
+                                   "config2_256cube_x25_fp64_sample": result.get("cpu_baseline")}
+        result["parity_config1_32cube_x8"] = c1["parity"]
+        var = result.get("variants", {})
+        for key, name in (("mixed", "config3_512cube_x30_mixed_sample"), ("batched", "config4_batched_sample"),
+                          ("surrogate", "config5_768cube_x40_surrogate_sample")):
+            if key in var and "cpu_baseline" in var[key]:
+                result["cpu_baselines"][name] = var[key]["cpu_baseline"]
     if rank == 0:
         print(json.dumps(result), flush=True)
     ctx.close()
