@@ -111,7 +111,9 @@ typedef struct {
   uint64_t fallback;      /* SURROGATE: points sent to the exact path                       */
   uint32_t error_flags;   /* device-side error bits: 1 = a bounded wait for tensor-core
                            * completion ran out in the CC_SURROGATE_TCGEN05 kernel (that
-                           * launch's results are incomplete); 0 otherwise                   */
+                           * launch's results are incomplete); 2 = (library built with
+                           * CC_DEBUG only) a table index left its range and was
+                           * clamped; 0 otherwise                                             */
   uint32_t reserved;
 } cc_stats;
 
@@ -225,8 +227,9 @@ CC_API int cc_table_query(cc_ctx *ctx, const double *d, const double *x, const d
 
 /* The cubic-spline routine on its own (the paper's y(x) toy, Sec. 4.3): a
  * natural cubic spline through n host knots (2 <= n <= 4096, strictly
- * increasing xk) built on the device, evaluated at m device queries q into out
- * (device); outside the knots the end intervals extrapolate. */
+ * increasing xk), built on the host in FP64 (one O(n) tridiagonal solve) and
+ * uploaded with the call, evaluated on the device at m device queries q into
+ * out (device); outside the knots the end intervals extrapolate. */
 CC_API int cc_spline_eval(cc_ctx *ctx, const double *xk, const double *yk, int32_t n, const double *q,
                           int64_t m, double *out, void *stream);
 
@@ -265,8 +268,34 @@ CC_API int cc_surrogate_train(cc_ctx *ctx, const void *hess, int32_t dtype, int6
  * and hull (lo[3], hi[3]) of the current surrogate, to host memory. */
 CC_API int cc_surrogate_params(const cc_ctx *ctx, float *params, float *hull);
 
-/* Install a surrogate from host parameters and hull (layout as above). */
+/* Install a surrogate from host parameters and hull (layout as above). It
+ * carries no optimiser state: training cannot resume from it (use a checkpoint). */
 CC_API int cc_load_surrogate(cc_ctx *ctx, const float *params, const float *hull);
+
+/* Checkpoint of the training state (no counterpart in the paper): a versioned
+ * host blob holding the schedule (seed, learning rate, batch, held-out share,
+ * length of the learning-rate schedule), the Adam step count, the hull, and
+ * the FP32 parameters with both Adam moments. The minibatch sampler is
+ * counter-based (indices hashed from the seed and the step), so the step is
+ * its whole state.
+ *   cc_surrogate_checkpoint: blob NULL -> *bytes receives the size; otherwise
+ *     *bytes >= that size, the blob is written and *bytes set to its size.
+ *     CC_EINVAL before any training (or after cc_load_surrogate).
+ *   cc_surrogate_restore: installs a blob written by cc_surrogate_checkpoint
+ *     (any context, any device); CC_EINVAL for a blob that is not one, of
+ *     another size or with values out of range, CC_ENOTSUP for another version.
+ *   cc_surrogate_train_resume: continues training from the context's state
+ *     (after cc_surrogate_train or cc_surrogate_restore) for `steps` more Adam
+ *     steps on samples of the given planes (rebuilt as in cc_surrogate_train);
+ *     the learning rate follows the warm-up + cosine schedule of length
+ *     schedule_steps (0: the stored length, extended to cover the new steps).
+ *     The hull becomes the union of the stored one and the new samples'.
+ *     Synchronises `stream`. */
+CC_API int cc_surrogate_checkpoint(const cc_ctx *ctx, void *blob, size_t *bytes);
+CC_API int cc_surrogate_restore(cc_ctx *ctx, const void *blob, size_t bytes);
+CC_API int cc_surrogate_train_resume(cc_ctx *ctx, const void *hess, int32_t dtype, int64_t n, int64_t plane_stride,
+                                     double sigma, int32_t steps, int32_t schedule_steps, cc_train_report *report,
+                                     void *stream);
 
 /* Kernel that runs CC_MODE_SURROGATE. Both evaluate the same network with
  * BF16 operands and FP32 accumulation, and both results meet the mixed path's

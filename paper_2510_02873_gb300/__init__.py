@@ -343,6 +343,33 @@ class Context:
                                                   _stream_ptr(stream)), "cc_surrogate_train")
         return rep.as_dict()
 
+    def surrogate_train_resume(self, hess, sigma, steps, schedule_steps=0, stream=None) -> dict:
+        """Continue training from the context's state (after surrogate_train or
+        surrogate_restore) for `steps` Adam steps on samples of hess (CUDA
+        (6, n) at rms sigma); schedule_steps: length of the learning-rate
+        schedule (0 = the stored one, extended to cover the new steps)."""
+        if hess.dim() != 2 or hess.shape[0] != 6 or hess.stride(1) != 1 or not hess.is_cuda:
+            raise ValueError("hess must be a CUDA (6, n) tensor with unit stride along points")
+        rep = _lib.CcTrainReport()
+        _lib.check(_lib.load().cc_surrogate_train_resume(self._h, hess.data_ptr(), _dtype_code(hess), hess.shape[1],
+                                                         hess.stride(0), float(sigma), int(steps), int(schedule_steps),
+                                                         ctypes.byref(rep), _stream_ptr(stream)),
+                   "cc_surrogate_train_resume")
+        return rep.as_dict()
+
+    def surrogate_checkpoint(self) -> bytes:
+        """The training state as a versioned blob (cc_surrogate_checkpoint)."""
+        size = ctypes.c_size_t(0)
+        _lib.check(_lib.load().cc_surrogate_checkpoint(self._h, None, ctypes.byref(size)), "cc_surrogate_checkpoint")
+        buf = ctypes.create_string_buffer(size.value)
+        _lib.check(_lib.load().cc_surrogate_checkpoint(self._h, buf, ctypes.byref(size)), "cc_surrogate_checkpoint")
+        return buf.raw[:size.value]
+
+    def surrogate_restore(self, blob: bytes):
+        """Install a training state written by surrogate_checkpoint (cc_surrogate_restore)."""
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        _lib.check(_lib.load().cc_surrogate_restore(self._h, buf, len(blob)), "cc_surrogate_restore")
+
     def surrogate_params(self):
         """The network's FP32 master parameters (8641) and training hull (6), host arrays."""
         params = np.empty(self.MLP_NPARAM, dtype=np.float32)

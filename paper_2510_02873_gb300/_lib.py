@@ -18,7 +18,7 @@ EXPORTS = (
     "cc_last_error_message", "cc_version", "cc_batch_create", "cc_batch_autotune", "cc_batch_run",
     "cc_batch_run_graph", "cc_batch_get_config", "cc_batch_destroy", "cc_set_table", "cc_table_nodes_rlpt",
     "cc_table_query", "cc_spline_eval", "cc_surrogate_train", "cc_surrogate_params", "cc_load_surrogate",
-    "cc_set_surrogate_engine",
+    "cc_set_surrogate_engine", "cc_surrogate_checkpoint", "cc_surrogate_restore", "cc_surrogate_train_resume",
     "cc_surrogate_eval", "cc_surrogate_grad", "cc_histogram", "cc_field_create", "cc_field_sigma",
     "cc_field_hessian", "cc_field_destroy",
 )
@@ -79,7 +79,10 @@ _lib = None
 
 
 def lib_path() -> str:
-    return _build.LIB_PATH
+    """The release library, or with CC_LIBCOLLAPSE_DEBUG=1 in the environment
+    the checking variant (build(debug=True): table index checks that set bit 2
+    of cc_stats.error_flags)."""
+    return _build.LIB_PATH_DEBUG if os.environ.get("CC_LIBCOLLAPSE_DEBUG") == "1" else _build.LIB_PATH
 
 
 def load() -> ctypes.CDLL:
@@ -130,6 +133,9 @@ def load() -> ctypes.CDLL:
                                          ctypes.POINTER(CcTrainReport), vp]
         L.cc_surrogate_params.argtypes = [vp, vp, vp]
         L.cc_load_surrogate.argtypes = [vp, vp, vp]
+        L.cc_surrogate_checkpoint.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.cc_surrogate_restore.argtypes = [vp, vp, ctypes.c_size_t]
+        L.cc_surrogate_train_resume.argtypes = [vp, vp, i32, i64, i64, d, i32, i32, ctypes.POINTER(CcTrainReport), vp]
         L.cc_set_surrogate_engine.argtypes = [vp, i32]
         L.cc_surrogate_eval.argtypes = [vp, vp, i64, vp, vp]
         L.cc_surrogate_grad.argtypes = [vp, vp, vp, i32, vp, vp]
@@ -145,7 +151,8 @@ def load() -> ctypes.CDLL:
                      "cc_batch_run", "cc_batch_run_graph", "cc_batch_get_config", "cc_set_table",
                      "cc_table_nodes_rlpt", "cc_table_query", "cc_spline_eval", "cc_surrogate_train",
                      "cc_surrogate_params", "cc_load_surrogate", "cc_surrogate_eval", "cc_surrogate_grad",
-                     "cc_set_surrogate_engine", "cc_histogram", "cc_field_create", "cc_field_sigma", "cc_field_hessian"):
+                     "cc_set_surrogate_engine", "cc_surrogate_checkpoint", "cc_surrogate_restore",
+                     "cc_surrogate_train_resume", "cc_histogram", "cc_field_create", "cc_field_sigma", "cc_field_hessian"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L

@@ -2,6 +2,10 @@
 
 Each translation unit is compiled in parallel, then linked against the shared
 CUDA runtime so that the library and PyTorch use one runtime instance.
+build(debug=True) makes the checking variant in _build_debug/: every kernel
+compiled with -DCC_DEBUG, whose table index checks set bit 2 of
+cc_stats.error_flags and clamp the index instead of reading outside a table
+(the binding loads it when CC_LIBCOLLAPSE_DEBUG=1).
 """
 from __future__ import annotations
 
@@ -16,6 +20,8 @@ PKG_DIR = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG_DIR, "csrc")
 BUILD_DIR = os.path.join(PKG_DIR, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libcollapse.so")
+BUILD_DIR_DEBUG = os.path.join(PKG_DIR, "_build_debug")
+LIB_PATH_DEBUG = os.path.join(BUILD_DIR_DEBUG, "libcollapse.so")
 INCLUDE = os.path.join(os.path.dirname(PKG_DIR), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -51,15 +57,16 @@ def _deps() -> list[str]:
         [os.path.join(INCLUDE, "collapse.h")]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB_PATH):
+def up_to_date(debug: bool = False) -> bool:
+    lib = LIB_PATH_DEBUG if debug else LIB_PATH
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB_PATH)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
+def _compile(src: str, extra: list[str], build_dir: str = BUILD_DIR) -> str:
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     cmd = [nvcc(), *ARCH, *COMMON, *extra, "-c", src, "-o", obj]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
@@ -69,22 +76,24 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    """Compile every .cu/.cpp under csrc/ and link libcollapse.so."""
-    if not force and up_to_date():
-        return LIB_PATH
-    os.makedirs(BUILD_DIR, exist_ok=True)
-    extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+def build(force: bool = False, verbose_ptxas: bool = False, debug: bool = False) -> str:
+    """Compile every .cu/.cpp under csrc/ and link libcollapse.so (the
+    checking variant with debug=True)."""
+    lib_path, build_dir = (LIB_PATH_DEBUG, BUILD_DIR_DEBUG) if debug else (LIB_PATH, BUILD_DIR)
+    if not force and up_to_date(debug):
+        return lib_path
+    os.makedirs(build_dir, exist_ok=True)
+    extra = (["-Xptxas", "-v"] if verbose_ptxas else []) + (["-DCC_DEBUG"] if debug else [])
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, extra, build_dir), srcs))
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", *objs, "-lcufft", *_rpath(), "-o", tmp]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -71,7 +71,7 @@ __device__ __forceinline__ void run_point(const BatchItemDev& it, int64_t p, con
 }
 
 template <bool kMixed, int kBlock>
-__global__ void __launch_bounds__(kBlock, 1024 / kBlock)  // 64 registers, like collapse_kernel
+__global__ void __launch_bounds__(kBlock, (kMixed ? 1536 : 1024) / kBlock)
 batched_kernel(const BatchItemDev* __restrict__ items, int nitems, int64_t total_tiles,
                unsigned long long* __restrict__ work, DevTable tab, DevCounters* __restrict__ cnt) {
   extern __shared__ Coef4 smem_tab[];
@@ -216,8 +216,10 @@ int launch_batch_t(cc_batch* b, cudaStream_t st) {
   if (int rc = check_cuda(cudaMemsetAsync(b->d_work, 0, sizeof(unsigned long long), st), "cudaMemsetAsync(work)"))
     return rc;
   if (grid <= 0) return CC_OK;
+  DevTable t = tab;  // the index checks of debug builds report into the context's flags
+  t.dbg = &b->ctx->d_counters->error_flags;
   kern<<<grid, kBlock, smem, st>>>(b->d_items, static_cast<int>(b->items.size()), b->total_tiles, b->d_work,
-                                   tab, b->ctx->d_counters);
+                                   t, b->ctx->d_counters);
   return check_cuda(cudaGetLastError(), "batched_kernel launch");
 }
 

@@ -166,9 +166,13 @@ __device__ __forceinline__ int spline_interval(const float* __restrict__ Dkf,
                                                const DevTable& tab, float Df) {
   float fb = (__log2f(Df) - tab.log2_D0) * tab.inv_bucket_width;
   fb = fminf(fmaxf(fb, 0.0f), static_cast<float>(tab.n_buckets - 1));
-  int k = bucket[static_cast<int>(fb)];
+  int b = static_cast<int>(fb);
+  CC_DBG_CLAMP(b, 0, tab.n_buckets - 1, tab.dbg);
+  int k = bucket[b];
+  CC_DBG_CLAMP(k, 0, tab.n - 2, tab.dbg);
 #pragma unroll
   for (int s = 0; s < 2; ++s) k += (k < tab.n - 2 && Dkf[k + 1] <= Df) ? 1 : 0;
+  CC_DBG_CLAMP(k, 0, tab.n - 2, tab.dbg);
   return k;
 }
 
@@ -657,6 +661,9 @@ __device__ __forceinline__ double tab_interp(const TabDev& td, const double* __r
     const int j = kd + step;
     kd = (j <= td.nd - 2 && dgf[j] <= df) ? j : kd;
   }
+  CC_DBG_CLAMP(ix, 0, td.nx - 2, td.dbg);
+  CC_DBG_CLAMP(iy, 0, td.ny - 2, td.dbg);
+  CC_DBG_CLAMP(kd, 0, td.nd - 2, td.dbg);
   const double t = delta - dg[kd];
   const size_t nseg = static_cast<size_t>(td.nd - 1);
   const size_t s00 = (static_cast<size_t>(ix) * td.ny + iy) * nseg + kd;

@@ -16,6 +16,28 @@ constexpr int kThreads = 256;            // threads per block of the collapse ke
 constexpr int kSmemTableMaxBytes = 64 * 1024;
 constexpr int kBucketsPerKnot = 4;  // log2-D buckets per knot (bucket finer than knot spacing)
 
+// Bits of cc_stats.error_flags.
+constexpr unsigned kErrWait = 1u;   // a bounded tensor-core wait ran out (CC_SURROGATE_TCGEN05)
+constexpr unsigned kErrIndex = 2u;  // debug builds: an index left its table (clamped, see CC_DBG_CLAMP)
+
+// Debug builds (compiled with -DCC_DEBUG): an index outside [lo, hi] sets
+// kErrIndex in the launch's error flags and is clamped into range, so the
+// access stays inside its table and the launch completes; release builds
+// compile the check away. `flags` is the launch's &counters->error_flags.
+#ifdef CC_DEBUG
+#define CC_DBG_CLAMP(i, lo, hi, flags)                       \
+  do {                                                        \
+    if ((i) < (lo) || (i) > (hi)) {                           \
+      if ((flags) != nullptr) atomicOr((flags), cc::kErrIndex); \
+      (i) = ((i) < (lo)) ? (lo) : (hi);                       \
+    }                                                         \
+  } while (0)
+#else
+#define CC_DBG_CLAMP(i, lo, hi, flags) \
+  do {                                 \
+  } while (0)
+#endif
+
 // Device-side counters; same layout as cc_stats.
 struct DevCounters {
   unsigned long long evaluations;
@@ -60,6 +82,7 @@ struct DevTable {
   // rc32[...] (FP32 copies, {c0, c1, c2, c3}); nullptr when absent
   const Coef4* rc64;
   const float4* rc32;
+  unsigned int* dbg;              // the launch's error flags (index checks of debug builds)
   // bytes of the table image (coef | D | Df | bucket), staged in shared memory
   __host__ __device__ size_t bytes() const {
     return sizeof(Coef4) * (n - 1) + sizeof(double) * n + sizeof(float) * n +
@@ -78,6 +101,7 @@ struct TabDev {
   int nd, nx, ny;
   int d_steps, x_steps, y_steps;  // largest power of two <= n - 2 (branch-free searches)
   double d_lo, d_hi, x_lo, x_hi, y_lo, y_hi;  // the table's hull (first and last knot of each axis)
+  unsigned int* dbg;                          // the launch's error flags (index checks of debug builds)
   __host__ __device__ size_t axes_bytes() const {
     return sizeof(double) * (nd + nx + ny + (nx - 1) + (ny - 1)) + sizeof(float) * nd;
   }
@@ -184,6 +208,11 @@ struct cc_ctx {
   void* d_train = nullptr;       // training records (float4) | count | hull
   size_t train_cap = 0;
   float sur_hull[6] = {0, 0, 0, 0, 0, 0};
+  // training state (cc_surrogate_train / _resume / _restore): configuration,
+  // Adam steps taken and the length of the learning-rate schedule
+  bool sur_trained = false;
+  cc_train_config sur_cfg{};
+  int64_t sur_step = 0, sur_schedule = 0;
   // interpolation toy (cc_spline_eval)
   void* d_spl = nullptr;
   size_t spl_cap = 0;

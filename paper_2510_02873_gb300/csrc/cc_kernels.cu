@@ -80,6 +80,7 @@ __device__ __forceinline__ void mixed_flush(const T* __restrict__ warp_base, int
       const unsigned e = q[i];
       owner = static_cast<int>(e >> 8);
       rr = static_cast<int>(e & 255u);
+      CC_DBG_CLAMP(owner, 0, 31, tab.dbg);
       const T* h = warp_base + owner + static_cast<int64_t>(rr) * radius_stride;
       const float xx = ldf(h), yy = ldf(h + plane_stride), zz = ldf(h + 2 * plane_stride);
       const float xy = ldf(h + 3 * plane_stride), xz = ldf(h + 4 * plane_stride);
@@ -143,7 +144,9 @@ __device__ __forceinline__ void mixed_point_deferred(const T* __restrict__ hess,
           pending = hb;
           break;
         }
-        if (hard) q[count + __popc(hb & below)] = static_cast<unsigned short>((lane << 8) | r);
+        int slot = count + __popc(hb & below);
+        CC_DBG_CLAMP(slot, 0, kDeferQ - 1, tab.dbg);
+        if (hard) q[slot] = static_cast<unsigned short>((lane << 8) | r);
         count += __popc(hb);
       }
     }
@@ -161,11 +164,14 @@ __device__ __forceinline__ void mixed_point_deferred(const T* __restrict__ hess,
 // float-float path (dfl::collapse_point), the exact-growth path
 // (exact::collapse_point) or collapse_point_tab (tabulated 1/D_c; its axes
 // follow the spline table in shared memory).
-// FP64 and mixed: 64 registers, 4 blocks of 256 threads per SM (measured
-// faster than 3 blocks at 69-85 registers for the mixed path, equal for FP64);
-// the tabulated path keeps its 98 registers.
+// FP64 path: 64 registers, 4 blocks of 256 threads per SM (5 blocks at 48
+// registers measured equal: the FP64 unit is the limit). Mixed path: 40
+// registers and 6 blocks per SM, 4 % faster than 4 blocks at 64 registers
+// despite spills (its warps stall on global loads and on FP32 dependencies,
+// which more resident warps hide; 8 blocks at 32 registers spill too much).
+// The tabulated path keeps its 98 registers.
 template <typename T, bool kSmem, int kMode>
-__global__ void __launch_bounds__(kThreads, kMode == 2 ? 1 : 4)
+__global__ void __launch_bounds__(kThreads, kMode == 2 ? 1 : (kMode == 1 ? 6 : 4))
 collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
                 int64_t radius_stride, int R, int32_t scale_idx0, DevTable tab, RadiusParams rp,
                 TabDev td, double* __restrict__ F_max, int32_t* __restrict__ idx,
@@ -336,8 +342,12 @@ int launch_typed(const LaunchArgs& a, const DevTable& tab, const RadiusParams& r
   const int64_t need = (a.n + kThreads - 1) / kThreads;
   const int64_t cap = static_cast<int64_t>(a.num_sms) * occ;
   const int grid = static_cast<int>(need < cap ? need : cap);
+  DevTable t = tab;  // the index checks of debug builds report into this launch's flags
+  t.dbg = &a.counters->error_flags;
+  TabDev tdl = td;
+  tdl.dbg = t.dbg;
   kern<<<grid, kThreads, smem, a.stream>>>(static_cast<const T*>(a.hess), a.n, a.plane_stride,
-                                           a.radius_stride, a.R, a.scale_idx0, tab, rp, td, a.F_max,
+                                           a.radius_stride, a.R, a.scale_idx0, t, rp, tdl, a.F_max,
                                            a.idx, a.counters);
   return check_cuda(cudaGetLastError(), "collapse_kernel launch");
 }

@@ -62,7 +62,6 @@ constexpr int kTab = kA + kGroups * kATileBytes;    // then the spline table (co
 constexpr int kSmemBytes = kTab;                    // + the table's bytes, rounded to 16
 constexpr int kTmemCols = 64;
 constexpr int kWaitTries = 1 << 22;                 // polls of an mbarrier before giving up
-constexpr unsigned kErrWait = 1u;                   // DevCounters::error_flags bit
 constexpr int kCtasPerSm = 1;                       // ~208 KB shared memory, 512 TMEM columns, 64 registers
 constexpr int OFF_TC = IMG_BYTES;                   // in the global image
 constexpr int IMG_TOTAL = OFF_TC + kImgBytes;
@@ -800,8 +799,10 @@ int launch_sur_typed(cc_ctx* ctx, const LaunchArgs& a, const RadiusParams& rp) {
     const int64_t need = ((a.n + tc::kRows - 1) / tc::kRows + tc::kGroups - 1) / tc::kGroups;
     const int64_t cap = static_cast<int64_t>(a.num_sms) * tc::kCtasPerSm;
     const int grid = static_cast<int>(need < cap ? need : cap);
+    DevTable t = ctx->tab;  // the index checks of debug builds report into this launch's flags
+    t.dbg = &a.counters->error_flags;
     kern<<<grid, tc::kRows * tc::kGroups, smem, a.stream>>>(static_cast<const T*>(a.hess), a.n, a.plane_stride,
-                                                         a.radius_stride, a.R, a.scale_idx0, ctx->tab, rp, sd,
+                                                         a.radius_stride, a.R, a.scale_idx0, t, rp, sd,
                                                          a.F_max, a.idx, a.counters);
     return check_cuda(cudaGetLastError(), "collapse_sur_tc_kernel launch");
   }
@@ -816,8 +817,10 @@ int launch_sur_typed(cc_ctx* ctx, const LaunchArgs& a, const RadiusParams& rp) {
   const int64_t need = (a.n + kThreads - 1) / kThreads;
   const int64_t cap = static_cast<int64_t>(a.num_sms) * (occ > 0 ? occ : 1);
   const int grid = static_cast<int>(need < cap ? need : cap);
+  DevTable t = ctx->tab;
+  t.dbg = &a.counters->error_flags;
   kern<<<grid, kThreads, smem, a.stream>>>(static_cast<const T*>(a.hess), a.n, a.plane_stride, a.radius_stride, a.R,
-                                           a.scale_idx0, ctx->tab, rp, sd, a.F_max, a.idx, a.counters);
+                                           a.scale_idx0, t, rp, sd, a.F_max, a.idx, a.counters);
   return check_cuda(cudaGetLastError(), "collapse_sur_kernel launch");
 }
 
@@ -841,35 +844,24 @@ int launch_surrogate_checked(cc_ctx* ctx, const LaunchArgs& a, const double* sig
   return CC_OK;
 }
 
-}  // namespace cc
+// ---- training (shared by cc_surrogate_train and cc_surrogate_train_resume)
+struct TrainSet {
+  float4* recs = nullptr;  // training records (z, target), then the held-out ones
+  int64_t total = 0, ntrain = 0, nval = 0;
+  float hull[6] = {0, 0, 0, 0, 0, 0};
+};
 
-using namespace cc;
-using namespace cc::mlp;
-
-extern "C" {
-
-int cc_set_surrogate_engine(cc_ctx* ctx, int32_t engine) {
-  if (!ctx) return set_error(CC_EINVAL, "ctx is NULL");
-  if (engine != CC_SURROGATE_MMA_SYNC && engine != CC_SURROGATE_TCGEN05)
-    return set_error(CC_EINVAL, "engine must be CC_SURROGATE_MMA_SYNC or CC_SURROGATE_TCGEN05");
-  ctx->sur_engine = engine;
-  return CC_OK;
-}
-
-int cc_surrogate_train(cc_ctx* ctx, const void* hess, int32_t dtype, int64_t n, int64_t plane_stride, double sigma,
-                       const cc_train_config* cfg, cc_train_report* report, void* stream) {
-  if (!ctx || !hess || !cfg) return set_error(CC_EINVAL, "ctx, hess and cfg are required");
+// Samples of the exact FP64 path on the caller's planes (every point with
+// l1 > 0 and D_c s < 1e4), the last val_fraction of them held out.
+int build_training_set(cc_ctx* ctx, const void* hess, int32_t dtype, int64_t n, int64_t plane_stride, double sigma,
+                       float val_fraction, TrainSet& ts, void* stream) {
   if (dtype != CC_F64 && dtype != CC_F32) return set_error(CC_EINVAL, "dtype must be CC_F64 or CC_F32");
   if (n < 1024 || plane_stride < n || !(sigma > 0.0)) return set_error(CC_EINVAL, "need n >= 1024, plane_stride >= n, sigma > 0");
-  if (cfg->steps < 1 || cfg->batch < 64 || cfg->batch % 64 || !(cfg->lr > 0.0f) || !(cfg->val_fraction > 0.0f) ||
-      !(cfg->val_fraction < 0.5f))
-    return set_error(CC_EINVAL, "train config: steps >= 1, batch a multiple of 64, lr > 0, 0 < val_fraction < 0.5");
   int cur = -1;
   cudaGetDevice(&cur);
   if (cur != ctx->device) cudaSetDevice(ctx->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (int rc = ensure_surrogate(ctx)) return rc;
-  // ---- training set
   const size_t rec_bytes = sizeof(float4) * static_cast<size_t>(n);
   if (rec_bytes > ctx->train_cap) {
     if (ctx->d_train) cudaFree(ctx->d_train);
@@ -896,43 +888,43 @@ int cc_surrogate_train(cc_ctx* ctx, const void* hess, int32_t dtype, int64_t n, 
   if (int rc = check_cuda(cudaMemcpyAsync(&cnt, count, sizeof(cnt), cudaMemcpyDeviceToHost, st), "D2H count")) return rc;
   if (int rc = check_cuda(cudaMemcpyAsync(hull_h, hull, sizeof(hull_h), cudaMemcpyDeviceToHost, st), "D2H hull")) return rc;
   if (int rc = check_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize")) return rc;
-  const int64_t total = static_cast<int64_t>(cnt < static_cast<unsigned long long>(n) ? cnt : n);
-  const int64_t nval = static_cast<int64_t>(total * cfg->val_fraction);
-  const int64_t ntrain = total - nval;
-  if (ntrain < cfg->batch || nval < 32) return set_error(CC_EINVAL, "too few collapsing points to train on");
-  // ---- initial parameters: b4 = mean target of the first samples
-  std::vector<float4> head(static_cast<size_t>(std::min<int64_t>(ntrain, 65536)));
-  if (int rc = check_cuda(cudaMemcpy(head.data(), recs, sizeof(float4) * head.size(), cudaMemcpyDeviceToHost), "D2H head")) return rc;
-  double tmean = 0.0;
-  for (const auto& r : head) tmean += r.w;
-  tmean /= static_cast<double>(head.size());
-  std::vector<float> p0;
-  init_params(p0, cfg->seed, static_cast<float>(tmean));
+  ts.recs = recs;
+  ts.total = static_cast<int64_t>(cnt < static_cast<unsigned long long>(n) ? cnt : n);
+  ts.nval = static_cast<int64_t>(ts.total * val_fraction);
+  ts.ntrain = ts.total - ts.nval;
+  for (int i = 0; i < 6; ++i) ts.hull[i] = unordered(hull_h[i]);
+  return CC_OK;
+}
+
+// Adam steps ctx->sur_step .. ctx->sur_step + steps - 1 of the warm-up + cosine
+// schedule of length ctx->sur_schedule (minibatch indices hashed from the seed
+// and the step: the sampler's state is the step), then the held-out error.
+int train_and_validate(cc_ctx* ctx, const TrainSet& ts, int64_t steps, cc_train_report* report, cudaStream_t st) {
+  const cc_train_config& cfg = ctx->sur_cfg;
   float* P = ctx->d_mlp_param;
   float* Mv = P + NPARAM;
   float* Vv = Mv + NPARAM;
   float* G = Vv + NPARAM;
   float* loss = G + NPARAM;
-  if (int rc = check_cuda(cudaMemcpyAsync(P, p0.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice, st), "H2D params")) return rc;
-  if (int rc = check_cuda(cudaMemsetAsync(Mv, 0, sizeof(float) * (3 * NPARAM + 8), st), "cudaMemsetAsync")) return rc;
-  sur_image_kernel<<<(NPARAM + 255) / 256, 256, 0, st>>>(P, ctx->d_mlp_img);
   if (int rc = check_cuda(cudaFuncSetAttribute(sur_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                static_cast<int>(kTrainSmem)), "cudaFuncSetAttribute"))
     return rc;
-  // ---- training: Adam, warm-up then cosine decay
-  const int blocks = cfg->batch / (32 * kTrainWarps);
-  const float inv_batch = 1.0f / static_cast<float>(cfg->batch);
+  const int blocks = cfg.batch / (32 * kTrainWarps);
+  const float inv_batch = 1.0f / static_cast<float>(cfg.batch);
   std::vector<float> losses;
-  for (int s = 0; s < cfg->steps; ++s) {
-    if (s == 0 || s == cfg->steps - 1)
+  const int64_t s0 = ctx->sur_step, s1 = s0 + steps;
+  ctx->sur_trained = false;  // until the steps are done
+  for (int64_t s = s0; s < s1; ++s) {
+    const bool record = (s == s0 || s == s1 - 1);
+    if (record)
       if (int rc = check_cuda(cudaMemsetAsync(loss, 0, sizeof(float), st), "cudaMemsetAsync")) return rc;
-    sur_train_kernel<<<blocks, 32 * kTrainWarps, kTrainSmem, st>>>(recs, ntrain, cfg->seed, s, 0, inv_batch,
-                                                                   ctx->d_mlp_img, G, loss);
+    sur_train_kernel<<<blocks, 32 * kTrainWarps, kTrainSmem, st>>>(ts.recs, ts.ntrain, cfg.seed, static_cast<int>(s), 0,
+                                                                   inv_batch, ctx->d_mlp_img, G, loss);
     const double warm = std::min(1.0, (s + 1) / 100.0);
-    const double lr = cfg->lr * warm * 0.5 * (1.0 + std::cos(3.141592653589793 * s / cfg->steps)) + 1e-6;
+    const double lr = cfg.lr * warm * 0.5 * (1.0 + std::cos(3.141592653589793 * s / ctx->sur_schedule)) + 1e-6;
     const float b1t = static_cast<float>(std::pow(0.9, s + 1)), b2t = static_cast<float>(std::pow(0.999, s + 1));
     sur_adam_kernel<<<(NPARAM + 255) / 256, 256, 0, st>>>(P, Mv, Vv, G, static_cast<float>(lr), b1t, b2t, ctx->d_mlp_img);
-    if (s == 0 || s == cfg->steps - 1) {
+    if (record) {
       float l = 0.f;
       if (int rc = check_cuda(cudaMemcpyAsync(&l, loss, sizeof(float), cudaMemcpyDeviceToHost, st), "D2H loss")) return rc;
       if (int rc = check_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize")) return rc;
@@ -940,30 +932,177 @@ int cc_surrogate_train(cc_ctx* ctx, const void* hess, int32_t dtype, int64_t n, 
     }
   }
   if (int rc = check_cuda(cudaGetLastError(), "training launch")) return rc;
+  ctx->sur_step = s1;
+  ctx->sur_trained = true;
   // ---- validation on the held-out records
   float* stats = loss + 2;
   if (int rc = check_cuda(cudaMemsetAsync(stats, 0, sizeof(float) * 2, st), "cudaMemsetAsync")) return rc;
-  sur_eval_kernel<<<launch_grid(nval, 256, ctx->num_sms * 4), 256, FWD_BYTES, st>>>(
-      reinterpret_cast<const float*>(recs + ntrain), 4, nval, ctx->d_mlp_img, nullptr, stats,
+  sur_eval_kernel<<<launch_grid(ts.nval, 256, ctx->num_sms * 4), 256, FWD_BYTES, st>>>(
+      reinterpret_cast<const float*>(ts.recs + ts.ntrain), 4, ts.nval, ctx->d_mlp_img, nullptr, stats,
       reinterpret_cast<int*>(stats + 1));
   float stats_h[2];
   if (int rc = check_cuda(cudaMemcpyAsync(stats_h, stats, sizeof(stats_h), cudaMemcpyDeviceToHost, st), "D2H stats")) return rc;
   if (int rc = check_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize")) return rc;
-  for (int i = 0; i < 6; ++i) ctx->sur_hull[i] = unordered(hull_h[i]);
   ctx->sur_valid = true;
   if (report) {
-    report->samples = total;
-    report->train_samples = ntrain;
-    report->val_samples = nval;
+    report->samples = ts.total;
+    report->train_samples = ts.ntrain;
+    report->val_samples = ts.nval;
     report->loss_first = losses.empty() ? 0.f : losses.front();
     report->loss_last = losses.empty() ? 0.f : losses.back();
-    report->val_rms = std::sqrt(stats_h[0] / static_cast<float>(nval));
+    report->val_rms = std::sqrt(stats_h[0] / static_cast<float>(ts.nval));
     std::memcpy(&report->val_max, &stats_h[1], sizeof(float));
     for (int i = 0; i < 3; ++i) {
       report->hull_lo[i] = ctx->sur_hull[i];
       report->hull_hi[i] = ctx->sur_hull[3 + i];
     }
   }
+  return CC_OK;
+}
+
+// ---- checkpoint blob: header, then FP32 parameters, Adam first and second moments
+constexpr char kCkptMagic[8] = {'C', 'C', 'S', 'U', 'R', 'C', 'K', '\0'};
+constexpr uint32_t kCkptVersion = 1;
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, nparam;
+  int64_t step, schedule_steps;  // Adam steps taken, length of the learning-rate schedule
+  uint64_t seed;                 // minibatch sampler key (its counter is the step)
+  float lr, val_fraction;
+  int32_t batch, reserved;
+  float hull[6];
+};
+static_assert(sizeof(CkptHeader) % 8 == 0, "header keeps the arrays 8-byte aligned");
+constexpr size_t kCkptBytes = sizeof(CkptHeader) + sizeof(float) * 3 * NPARAM;
+
+}  // namespace cc
+
+using namespace cc;
+using namespace cc::mlp;
+
+extern "C" {
+
+int cc_set_surrogate_engine(cc_ctx* ctx, int32_t engine) {
+  if (!ctx) return set_error(CC_EINVAL, "ctx is NULL");
+  if (engine != CC_SURROGATE_MMA_SYNC && engine != CC_SURROGATE_TCGEN05)
+    return set_error(CC_EINVAL, "engine must be CC_SURROGATE_MMA_SYNC or CC_SURROGATE_TCGEN05");
+  ctx->sur_engine = engine;
+  return CC_OK;
+}
+
+int cc_surrogate_train(cc_ctx* ctx, const void* hess, int32_t dtype, int64_t n, int64_t plane_stride, double sigma,
+                       const cc_train_config* cfg, cc_train_report* report, void* stream) {
+  if (!ctx || !hess || !cfg) return set_error(CC_EINVAL, "ctx, hess and cfg are required");
+  if (cfg->steps < 1 || cfg->batch < 64 || cfg->batch % 64 || !(cfg->lr > 0.0f) || !(cfg->val_fraction > 0.0f) ||
+      !(cfg->val_fraction < 0.5f))
+    return set_error(CC_EINVAL, "train config: steps >= 1, batch a multiple of 64, lr > 0, 0 < val_fraction < 0.5");
+  TrainSet ts;
+  if (int rc = build_training_set(ctx, hess, dtype, n, plane_stride, sigma, cfg->val_fraction, ts, stream)) return rc;
+  if (ts.ntrain < cfg->batch || ts.nval < 32) return set_error(CC_EINVAL, "too few collapsing points to train on");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // ---- initial parameters: b4 = mean target of the first samples
+  std::vector<float4> head(static_cast<size_t>(std::min<int64_t>(ts.ntrain, 65536)));
+  if (int rc = check_cuda(cudaMemcpy(head.data(), ts.recs, sizeof(float4) * head.size(), cudaMemcpyDeviceToHost), "D2H head")) return rc;
+  double tmean = 0.0;
+  for (const auto& r : head) tmean += r.w;
+  tmean /= static_cast<double>(head.size());
+  std::vector<float> p0;
+  init_params(p0, cfg->seed, static_cast<float>(tmean));
+  float* P = ctx->d_mlp_param;
+  if (int rc = check_cuda(cudaMemcpyAsync(P, p0.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice, st), "H2D params")) return rc;
+  if (int rc = check_cuda(cudaMemsetAsync(P + NPARAM, 0, sizeof(float) * (3 * NPARAM + 8), st), "cudaMemsetAsync")) return rc;
+  sur_image_kernel<<<(NPARAM + 255) / 256, 256, 0, st>>>(P, ctx->d_mlp_img);
+  ctx->sur_cfg = *cfg;
+  ctx->sur_step = 0;
+  ctx->sur_schedule = cfg->steps;
+  for (int i = 0; i < 6; ++i) ctx->sur_hull[i] = ts.hull[i];
+  return train_and_validate(ctx, ts, cfg->steps, report, st);
+}
+
+int cc_surrogate_train_resume(cc_ctx* ctx, const void* hess, int32_t dtype, int64_t n, int64_t plane_stride,
+                              double sigma, int32_t steps, int32_t schedule_steps, cc_train_report* report,
+                              void* stream) {
+  if (!ctx || !hess) return set_error(CC_EINVAL, "ctx and hess are required");
+  if (!ctx->sur_trained) return set_error(CC_EINVAL, "no training state: call cc_surrogate_train or cc_surrogate_restore first");
+  if (steps < 1) return set_error(CC_EINVAL, "steps must be >= 1");
+  const int64_t until = ctx->sur_step + steps;
+  if (schedule_steps != 0 && schedule_steps < until)
+    return set_error(CC_EINVAL, "schedule_steps must be 0 or at least the steps taken plus the new ones");
+  TrainSet ts;
+  if (int rc = build_training_set(ctx, hess, dtype, n, plane_stride, sigma, ctx->sur_cfg.val_fraction, ts, stream)) return rc;
+  if (ts.ntrain < ctx->sur_cfg.batch || ts.nval < 32) return set_error(CC_EINVAL, "too few collapsing points to train on");
+  ctx->sur_schedule = schedule_steps != 0 ? schedule_steps : std::max<int64_t>(ctx->sur_schedule, until);
+  for (int i = 0; i < 3; ++i) {  // the hull covers every training set seen
+    ctx->sur_hull[i] = std::min(ctx->sur_hull[i], ts.hull[i]);
+    ctx->sur_hull[3 + i] = std::max(ctx->sur_hull[3 + i], ts.hull[3 + i]);
+  }
+  return train_and_validate(ctx, ts, steps, report, static_cast<cudaStream_t>(stream));
+}
+
+int cc_surrogate_checkpoint(const cc_ctx* ctx, void* blob, size_t* bytes) {
+  if (!ctx || !bytes) return set_error(CC_EINVAL, "ctx and bytes are required");
+  if (!blob) {
+    *bytes = kCkptBytes;
+    return CC_OK;
+  }
+  if (*bytes < kCkptBytes) return set_error(CC_EINVAL, "blob smaller than the checkpoint (query the size with blob = NULL)");
+  if (!ctx->sur_trained) return set_error(CC_EINVAL, "no training state: call cc_surrogate_train or cc_surrogate_restore first");
+  CkptHeader h{};
+  std::memcpy(h.magic, kCkptMagic, sizeof(h.magic));
+  h.version = kCkptVersion;
+  h.nparam = NPARAM;
+  h.step = ctx->sur_step;
+  h.schedule_steps = ctx->sur_schedule;
+  h.seed = ctx->sur_cfg.seed;
+  h.lr = ctx->sur_cfg.lr;
+  h.val_fraction = ctx->sur_cfg.val_fraction;
+  h.batch = ctx->sur_cfg.batch;
+  std::memcpy(h.hull, ctx->sur_hull, sizeof(h.hull));
+  if (int rc = select_device(ctx)) return rc;
+  unsigned char* out = static_cast<unsigned char*>(blob);
+  std::memcpy(out, &h, sizeof(h));
+  if (int rc = check_cuda(cudaMemcpy(out + sizeof(h), ctx->d_mlp_param, sizeof(float) * 3 * NPARAM, cudaMemcpyDeviceToHost),
+                          "D2H training state"))
+    return rc;
+  *bytes = kCkptBytes;
+  return CC_OK;
+}
+
+int cc_surrogate_restore(cc_ctx* ctx, const void* blob, size_t bytes) {
+  if (!ctx || !blob) return set_error(CC_EINVAL, "ctx and blob are required");
+  if (bytes < sizeof(CkptHeader)) return set_error(CC_EINVAL, "blob shorter than a checkpoint header");
+  CkptHeader h;
+  std::memcpy(&h, blob, sizeof(h));
+  if (std::memcmp(h.magic, kCkptMagic, sizeof(h.magic)) != 0) return set_error(CC_EINVAL, "not a surrogate checkpoint");
+  if (h.version != kCkptVersion) return set_error(CC_ENOTSUP, "checkpoint version not supported by this library");
+  if (h.nparam != static_cast<uint32_t>(NPARAM) || bytes != kCkptBytes)
+    return set_error(CC_EINVAL, "checkpoint size does not match the network");
+  if (h.step < 0 || h.schedule_steps < h.step || h.batch < 64 || h.batch % 64 || !(h.lr > 0.0f) ||
+      !(h.val_fraction > 0.0f) || !(h.val_fraction < 0.5f))
+    return set_error(CC_EINVAL, "checkpoint header out of range");
+  for (int i = 0; i < 3; ++i)
+    if (!(h.hull[i] <= h.hull[3 + i])) return set_error(CC_EINVAL, "checkpoint hull: lo <= hi per component");
+  const float* arr = reinterpret_cast<const float*>(static_cast<const unsigned char*>(blob) + sizeof(h));
+  std::vector<float> state(arr, arr + 3 * NPARAM);
+  for (float v : state)
+    if (!std::isfinite(v)) return set_error(CC_EINVAL, "checkpoint values must be finite");
+  if (int rc = select_device(ctx)) return rc;
+  if (int rc = ensure_surrogate(ctx)) return rc;
+  if (int rc = check_cuda(cudaMemcpy(ctx->d_mlp_param, state.data(), sizeof(float) * 3 * NPARAM, cudaMemcpyHostToDevice),
+                          "H2D training state"))
+    return rc;
+  sur_image_kernel<<<(NPARAM + 255) / 256, 256>>>(ctx->d_mlp_param, ctx->d_mlp_img);
+  if (int rc = check_cuda(cudaDeviceSynchronize(), "sur_image_kernel")) return rc;
+  ctx->sur_cfg.steps = static_cast<int32_t>(h.schedule_steps);
+  ctx->sur_cfg.batch = h.batch;
+  ctx->sur_cfg.lr = h.lr;
+  ctx->sur_cfg.seed = h.seed;
+  ctx->sur_cfg.val_fraction = h.val_fraction;
+  ctx->sur_step = h.step;
+  ctx->sur_schedule = h.schedule_steps;
+  std::memcpy(ctx->sur_hull, h.hull, sizeof(h.hull));
+  ctx->sur_trained = true;
+  ctx->sur_valid = true;
   return CC_OK;
 }
 
@@ -989,6 +1128,7 @@ int cc_load_surrogate(cc_ctx* ctx, const float* params, const float* hull) {
   if (int rc = check_cuda(cudaDeviceSynchronize(), "sur_image_kernel")) return rc;
   std::memcpy(ctx->sur_hull, hull, sizeof(float) * 6);
   ctx->sur_valid = true;
+  ctx->sur_trained = false;  // parameters without optimiser state: nothing to resume
   return CC_OK;
 }
 

@@ -115,14 +115,6 @@ __global__ void tab_query_kernel(TabDev td, const double* __restrict__ d, const 
     out[i] = tab_interp(td, s_ax, td.coef, d[i], fmax(x[i], 0.0), fmax(y[i], 0.0));
 }
 
-// single natural spline for the interpolation toy (one thread: n <= 4096)
-__global__ void spline_build_one_kernel(const double* __restrict__ xk, const double* __restrict__ yk, int n,
-                                        Coef4* __restrict__ coef, float* __restrict__ xkf, double* __restrict__ work) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  natural_spline_device(n, xk, yk, 1, coef, work);
-  for (int k = 0; k < n; ++k) xkf[k] = static_cast<float>(xk[k]);
-}
-
 // y(q) for m queries: FP32 binary search on the FP32 knots (C2 spline: the
 // neighbouring interval gives the same value to rounding), FP64 Horner.
 __global__ void spline_eval_kernel(const double* __restrict__ xk, const float* __restrict__ xkf,
@@ -298,18 +290,25 @@ int cc_spline_eval(cc_ctx* ctx, const double* xk, const double* yk, int32_t n, c
   if (m < 0 || (m > 0 && (!q || !out))) return set_error(CC_EINVAL, "bad query arrays");
   if (int rc = select_device(ctx)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // scratch: xk | yk | work (2n) | coef (n-1) | xkf (n)
-  const size_t bytes = sizeof(double) * 4 * n + sizeof(Coef4) * (n - 1) + sizeof(float) * n + 64;
-  if (int rc = grow(&ctx->d_spl, &ctx->spl_cap, bytes, "cudaMalloc(spline scratch)")) return rc;
-  double* dx = static_cast<double*>(ctx->d_spl);
-  double* dy = dx + n;
-  double* work = dy + n;
-  Coef4* coef = reinterpret_cast<Coef4*>(reinterpret_cast<uintptr_t>(work + 2 * n + 3) & ~uintptr_t{31});
-  float* xkf = reinterpret_cast<float*>(coef + (n - 1));
-  if (int rc = check_cuda(cudaMemcpyAsync(dx, xk, sizeof(double) * n, cudaMemcpyHostToDevice, st), "H2D knots")) return rc;
-  if (int rc = check_cuda(cudaMemcpyAsync(dy, yk, sizeof(double) * n, cudaMemcpyHostToDevice, st), "H2D values")) return rc;
-  spline_build_one_kernel<<<1, 1, 0, st>>>(dx, dy, n, coef, xkf, work);
-  if (int rc = check_cuda(cudaGetLastError(), "spline_build_one_kernel launch")) return rc;
+  // One spline is a serial O(n) tridiagonal solve: a single device thread
+  // took ~1.5 ms for 512 knots (dependent FP64 divisions), the host takes a
+  // few microseconds. Built on the host in FP64, uploaded as one image:
+  // coef (n-1) | xk (n) | xkf (n, FP32 copies for the interval search).
+  std::vector<double> img(4 * static_cast<size_t>(n - 1) + n + (n + 1) / 2);
+  std::vector<double> work(6 * static_cast<size_t>(n));
+  if (int rc = natural_spline_into(n, xk, yk, img.data(), work.data())) return set_error(rc, "spline build failed");
+  double* hx = img.data() + 4 * (n - 1);
+  std::memcpy(hx, xk, sizeof(double) * n);
+  float* hxf = reinterpret_cast<float*>(hx + n);
+  for (int k = 0; k < n; ++k) hxf[k] = static_cast<float>(xk[k]);
+  const size_t bytes = sizeof(double) * img.size();
+  if (int rc = grow(&ctx->d_spl, &ctx->spl_cap, bytes, "cudaMalloc(spline image)")) return rc;
+  // pageable source: the call returns once the image is staged
+  if (int rc = check_cuda(cudaMemcpyAsync(ctx->d_spl, img.data(), bytes, cudaMemcpyHostToDevice, st), "H2D spline"))
+    return rc;
+  const Coef4* coef = static_cast<const Coef4*>(ctx->d_spl);
+  const double* dx = reinterpret_cast<const double*>(coef + (n - 1));
+  const float* xkf = reinterpret_cast<const float*>(dx + n);
   if (m == 0) return CC_OK;
   const int64_t need = (m + 255) / 256;
   const int grid = static_cast<int>(std::min<int64_t>(need, static_cast<int64_t>(ctx->num_sms) * 8));

@@ -364,3 +364,58 @@ def test_surrogate_invalid_arguments_are_rejected(ctx):
         assert torch.all(torch.isfinite(out))
     finally:
         fresh.close()
+
+
+def test_checkpoint_restore_and_resume(ctx):
+    """Training state round trip and resumption: a checkpoint restored into a
+    fresh context reproduces the blob byte for byte and the network's outputs
+    exactly; training resumed from it continues the loss curve (its first
+    minibatch loss is near the last one before the checkpoint, far below a
+    fresh start's) and ends at least as well as the uninterrupted run; a
+    blob of another size, version or magic is refused."""
+    import ctypes
+
+    import hessgen.device as hdev
+    import paper_2510_02873_gb300 as cc
+    from paper_2510_02873_gb300 import _lib
+
+    h = torch.empty((6, 2 * 1024 * 1024), dtype=torch.float32, device="cuda")
+    hdev.fill(h, 777, 5, 0, 1.0)
+    rep1 = ctx.surrogate_train(h, 1.0, steps=200, batch=8192, lr=3e-3, seed=5)
+    blob = ctx.surrogate_checkpoint()
+    z = torch.from_numpy(sample_inputs(np.random.default_rng(8), 4096)).cuda()
+    f_a = torch.empty(4096, dtype=torch.float32, device="cuda")
+    ctx.surrogate_eval(z, f_a)
+    with cc.Context(0.3, 0.7, 512, 1e-3, 1.0, device=0) as c2:
+        c2.surrogate_restore(blob)
+        assert c2.surrogate_checkpoint() == blob
+        f_b = torch.empty_like(f_a)
+        c2.surrogate_eval(z, f_b)
+        torch.cuda.synchronize()
+        assert torch.equal(f_a, f_b)
+        rep2 = c2.surrogate_train_resume(h, 1.0, steps=100, schedule_steps=300)
+        # a continuation, not a restart
+        assert rep2["loss_first"] < 3.0 * rep1["loss_last"] + 1e-4
+        assert rep2["loss_first"] < 0.1 * rep1["loss_first"]
+        assert rep2["val_rms"] <= 1.2 * rep1["val_rms"]
+        assert len(c2.surrogate_checkpoint()) == len(blob)
+        # refused blobs
+        L = _lib.load()
+        bad = bytearray(blob)
+        bad[0] = ord("X")
+        for b, code in ((bytes(bad), _lib.CC_EINVAL), (blob[:-4], _lib.CC_EINVAL)):
+            buf = ctypes.create_string_buffer(b, len(b))
+            assert L.cc_surrogate_restore(c2.handle, buf, len(b)) == code
+        ver = bytearray(blob)
+        ver[8] = 99  # version field
+        buf = ctypes.create_string_buffer(bytes(ver), len(ver))
+        assert L.cc_surrogate_restore(c2.handle, buf, len(ver)) == _lib.CC_ENOTSUP
+    # loading bare parameters leaves nothing to resume
+    params, hull = ctx.surrogate_params()
+    ctx.load_surrogate(params, hull)
+    with pytest.raises(cc.CollapseError):
+        ctx.surrogate_checkpoint()
+    with pytest.raises(cc.CollapseError):
+        ctx.surrogate_train_resume(h, 1.0, steps=10)
+    print("checkpoint", len(blob), "bytes; loss", rep1["loss_first"], rep1["loss_last"], "-> resumed",
+          rep2["loss_first"], rep2["loss_last"], "val rms", rep1["val_rms"], rep2["val_rms"])
