@@ -45,10 +45,13 @@ FP64_FLOPS_PER_EVAL_MIXED = 8.1
 # whatever the instruction, so this count, not the flop count, sets the time.
 FP64_PIPE_INST_PER_EVAL = {"fp64": 41.9, "mixed": 5.1}
 FP64_LANES_PER_CLK_PER_SM = 2.0
-# DRAM bytes (read + write) of one full launch of the default workload, scaled
-# from the 128^3 x 4 capture of the same kernel: plane reads by evaluations,
-# F_max/idx reads and writes by points (the full launch is not captured).
-TRAFFIC_BYTES_DEFAULT = None
+# DRAM bytes (read + write) of a launch, scaled from the 128^3 x 4 ncu capture
+# of the FP64 kernel (dram__bytes_read 424.128512 MB, write 27.236864 MB for
+# 8,388,608 evaluations of 2,097,152 points): the planes are read once, 48 B
+# per evaluation; the rest (F_max/idx read and written for collapsed points)
+# scales with the points. The full 20 GB launch is not captured.
+TRAFFIC_PLANE_BYTES_PER_EVAL = 48.0
+TRAFFIC_OUT_BYTES_PER_POINT = (424.128512e6 - 48.0 * 8388608 + 27.236864e6) / 2097152
 # FP64 FMA rate of one GB300 SM: 1.25 TFLOP/s nominal at 2070 MHz over 152 SMs
 # = 3.97 flop/clk/SM, i.e. 2 DFMA per clock per SM (confirmed by a DFMA-chain probe).
 FP64_FLOP_PER_CLK_PER_SM = 4.0
@@ -1230,8 +1233,10 @@ def main():
         "evals_per_s_kernel": evals_launch / kern_avg_s,
         "kernel_ms": statistics.mean(kernel_ms),
         "kernel_ms_stats": timing_stats(kernel_ms),
-        "traffic": TRAFFIC_BYTES_DEFAULT if ((args.grid, R) == (GRID, N_RADII) and args.mode == "fp64") else None,
-        "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one full launch",
+        "traffic": (TRAFFIC_PLANE_BYTES_PER_EVAL * evals_launch + TRAFFIC_OUT_BYTES_PER_POINT * n)
+        if args.mode == "fp64" else None,
+        "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 128^3 x 4 launch of the same "
+                         "kernel, scaled to this launch: plane reads by evaluations, F_max/idx traffic by points",
         "algorithmic_bytes": 48.0 * evals_launch + 12.0 * 2 * n,
     }
     ipe = FP64_PIPE_INST_PER_EVAL.get(args.mode)
