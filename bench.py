@@ -1358,9 +1358,10 @@ def main():
         if "hess" in locals():
             del hess
         torch.cuda.empty_cache()
-        result.setdefault("variants", {})["mixed"] = run_mixed_variant(ctx, dev, stream)
-        result["variants"]["batched"] = run_batch_variant(ctx, dev, stream)
-        result["variants"]["surrogate"] = run_surrogate_variant(ctx, dev, stream)
+        vs = max(10000, int(args.cpu_points / 2.62144))  # 100,000 points at the default
+        result.setdefault("variants", {})["mixed"] = run_mixed_variant(ctx, dev, stream, sample=vs)
+        result["variants"]["batched"] = run_batch_variant(ctx, dev, stream, sample=vs)
+        result["variants"]["surrogate"] = run_surrogate_variant(ctx, dev, stream, sample=vs)
         result["variants"]["science_proxy"] = run_science_variant(ctx, dev, stream)
         result["variants"]["field_to_collapse"] = run_field_variant(ctx, dev, stream)
         result["variants"]["interpolation_toys"] = run_toys_variant(ctx, dev, stream)

@@ -41,6 +41,7 @@ __device__ __forceinline__ void add_counters(DevCounters* cnt, unsigned evals, u
 }
 
 constexpr int kModeFP64 = 0, kModeMixed = 1, kModeTab = 2, kModeF32x2 = 3, kModeExact = 4;
+constexpr int kFp64Radii = 2;  // radii per loop iteration of the FP64 path
 
 // ---- mixed path with the hard evaluations deferred. About 0.5 % of the
 // evaluations need FP64 work beyond the polish and the spline (the FP64
@@ -164,14 +165,16 @@ __device__ __forceinline__ void mixed_point_deferred(const T* __restrict__ hess,
 // float-float path (dfl::collapse_point), the exact-growth path
 // (exact::collapse_point) or collapse_point_tab (tabulated 1/D_c; its axes
 // follow the spline table in shared memory).
-// FP64 path: 64 registers, 4 blocks of 256 threads per SM (5 blocks at 48
-// registers measured equal: the FP64 unit is the limit). Mixed path: 40
+// FP64 path: two radii per iteration at 2 blocks of 256 threads per SM (94
+// registers, no spill): 1.3 % faster than one radius at 4 blocks and 64
+// registers; 3 or 4 radii per iteration, or 1 block, measured the same.
+// Mixed path: 40
 // registers and 6 blocks per SM, 4 % faster than 4 blocks at 64 registers
 // despite spills (its warps stall on global loads and on FP32 dependencies,
 // which more resident warps hide; 8 blocks at 32 registers spill too much).
 // The tabulated path keeps its 98 registers.
 template <typename T, bool kSmem, int kMode>
-__global__ void __launch_bounds__(kThreads, kMode == 2 ? 1 : (kMode == 1 ? 6 : 4))
+__global__ void __launch_bounds__(kThreads, kMode == 2 ? 1 : (kMode == 1 ? 6 : (kMode == 0 ? 2 : 4)))
 collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
                 int64_t radius_stride, int R, int32_t scale_idx0, DevTable tab, RadiusParams rp,
                 TabDev td, double* __restrict__ F_max, int32_t* __restrict__ idx,
@@ -246,6 +249,42 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
         best.store<true>(F_max + p, idx + p, scale_idx0);
         n_eval += R;
       }
+    } else if (kMode == kModeFP64 && active) {
+      // kFp64Radii radii per iteration: independent FP64 chains that the
+      // compiler interleaves, so the FP64 unit meets fewer gaps while a warp
+      // is in its FP32 seeds and integer conversions (the running minimum
+      // still takes the radii in order)
+      MinA best;
+      const T* base = hess + p;
+      int r = 0;
+      for (; r + kFp64Radii <= R; r += kFp64Radii) {
+        PointResult rs[kFp64Radii];
+#pragma unroll
+        for (int j = 0; j < kFp64Radii; ++j) {
+          const T* h = base + static_cast<int64_t>(r + j) * radius_stride;
+          rs[j] = collapse_point_fp64(ld(h), ld(h + plane_stride), ld(h + 2 * plane_stride), ld(h + 3 * plane_stride),
+                                      ld(h + 4 * plane_stride), ld(h + 5 * plane_stride), Dk, coef, Dkf, bucket, tab);
+        }
+#pragma unroll
+        for (int j = 0; j < kFp64Radii; ++j) {
+          n_coll += rs[j].collapsed;
+          n_eds += rs[j].eds;
+          n_ref += rs[j].refined;
+          best.add(rs[j].collapsed, rs[j].a, r + j);
+        }
+      }
+      for (; r < R; ++r) {
+        const T* h = base + static_cast<int64_t>(r) * radius_stride;
+        const PointResult res = collapse_point_fp64(ld(h), ld(h + plane_stride), ld(h + 2 * plane_stride),
+                                                    ld(h + 3 * plane_stride), ld(h + 4 * plane_stride),
+                                                    ld(h + 5 * plane_stride), Dk, coef, Dkf, bucket, tab);
+        n_coll += res.collapsed;
+        n_eds += res.eds;
+        n_ref += res.refined;
+        best.add(res.collapsed, res.a, r);
+      }
+      best.store<false>(F_max + p, idx + p, scale_idx0);
+      n_eval += R;
     } else if (kMode != kModeF32x2 && active) {
       MinA best;
       const T* base = hess + p;
