@@ -38,20 +38,23 @@ WORKLOAD = "collapse 256^3 grid x 25 radii, FP64 SoA Hessian planes (20.1 GB res
 # kernel: ncu thread-instruction counters (dadd + dmul + 2 dfma) of one launch
 # of the 128^3 x 4 case divided by its evaluations (the FP64 and mixed kernels
 # as they stand; re-taken whenever either kernel changes).
-FP64_FLOPS_PER_EVAL = 73.0
+FP64_FLOPS_PER_EVAL = 67.0
 FP64_FLOPS_PER_EVAL_MIXED = 8.1
 # FP64-pipe thread instructions of every kind (DFMA, DMUL, DADD, DSETP) per
 # evaluation, from the same captures: the FP64 unit issues one per lane slot
 # whatever the instruction, so this count, not the flop count, sets the time.
-FP64_PIPE_INST_PER_EVAL = {"fp64": 41.9, "mixed": 5.1}
+# For the mixed kernel, whose FP64 instructions often run with idle lanes, the
+# lane slots the pipe was busy for (its busy fraction x 2 lanes/clk/SM x SM
+# cycles / evaluations) instead of the 4.1 thread instructions.
+FP64_PIPE_INST_PER_EVAL = {"fp64": 38.9, "mixed": 4.9}
 FP64_LANES_PER_CLK_PER_SM = 2.0
 # DRAM bytes (read + write) of a launch, scaled from the 128^3 x 4 ncu capture
-# of the FP64 kernel (dram__bytes_read 424.128512 MB, write 27.236864 MB for
+# of the FP64 kernel (dram__bytes_read 420.726016 MB, write 22.859776 MB for
 # 8,388,608 evaluations of 2,097,152 points): the planes are read once, 48 B
 # per evaluation; the rest (F_max/idx read and written for collapsed points)
 # scales with the points. The full 20 GB launch is not captured.
 TRAFFIC_PLANE_BYTES_PER_EVAL = 48.0
-TRAFFIC_OUT_BYTES_PER_POINT = (424.128512e6 - 48.0 * 8388608 + 27.236864e6) / 2097152
+TRAFFIC_OUT_BYTES_PER_POINT = (420.726016e6 - 48.0 * 8388608 + 22.859776e6) / 2097152
 # FP64 FMA rate of one GB300 SM: 1.25 TFLOP/s nominal at 2070 MHz over 152 SMs
 # = 3.97 flop/clk/SM, i.e. 2 DFMA per clock per SM (confirmed by a DFMA-chain probe).
 FP64_FLOP_PER_CLK_PER_SM = 4.0

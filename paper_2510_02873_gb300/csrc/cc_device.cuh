@@ -65,6 +65,20 @@ __device__ __forceinline__ double to_f64_normal(float f) {
   return __hiloint2double(static_cast<int>(hi), static_cast<int>(u << 29));
 }
 
+// tail_f32: v - hi as an FP32 value, where hi = to_f32_trunc(v): the 29
+// mantissa bits of v below hi's 23, of which the top 23 are kept (relative
+// error 2^-23 of the tail, 2^-46 of v), scaled by hi's exponent - 23. Built
+// as the FP32 number 2^k (1 + m 2^-23) minus 2^k, both with v's sign, so the
+// subtraction is exact. Zero where hi's biased exponent is 23 or less
+// (|v| < 2^-103, or hi = 0).
+__device__ __forceinline__ float tail_f32(double v, float hi) {
+  const unsigned hb = __float_as_uint(hi);
+  const unsigned base = (hb & 0xff800000u) - (23u << 23);
+  const unsigned mant = (static_cast<unsigned>(__double_as_longlong(v)) >> 6) & 0x007fffffu;
+  const float t = __fsub_rn(__uint_as_float(base | mant), __uint_as_float(base));
+  return ((hb & 0x7f800000u) > (23u << 23)) ? t : 0.0f;
+}
+
 // Re-solve l1 >= l2 when they are nearly equal: l3 (isolated) gives an
 // eigenvector v3 as the largest cross product of two rows of A - l3 I; A
 // restricted to the plane orthogonal to v3 is a 2x2 symmetric matrix whose
@@ -189,8 +203,9 @@ struct EigenTop {
 };
 
 // Largest eigenvalue l1 = q + x of the symmetric matrix in FP64 (FP32 trigonometric
-// seed, two FP64 Newton steps on the depressed characteristic cubic, deflation
-// when l1 ~ l2) together with the invariants the collapse condition needs.
+// seed, two FP32 Newton steps and one FP64 Newton step on the depressed
+// characteristic cubic, deflation when l1 ~ l2) together with the invariants
+// the collapse condition needs.
 __device__ __forceinline__ EigenTop eigen_top_fp64(double xx, double yy, double zz, double xy, double xz,
                                                    double yz) {
   EigenTop e;
@@ -211,27 +226,45 @@ __device__ __forceinline__ EigenTop eigen_top_fp64(double xx, double yy, double 
   double p2x3 = fma(a, -c, fma(b, b, off));  // 3 p^2 = |M|_F^2 / 2
   p2x3 = bits(p2x3) < 0 ? 0.0 : p2x3;
   const double det = fma(xz, fma(xy, yz, -b * xz), fma(a, fma(b, c, -yz2), -xy * fma(xy, c, -yz * xz)));
+  // ---- FP32 heads and tails: 3 p^2 = Ph + Pl, det = Dh + Dl, p^2 = p2f + p2l
+  // (fmaf(-3, p2f, Ph) is the exact remainder of Ph / 3)
+  const float Ph = to_f32_trunc(p2x3), Pl = tail_f32(p2x3, Ph);
+  const float Dh = to_f32_trunc(det), Dl = tail_f32(det, Dh);
+  const float p2f = Ph * (1.0f / 3.0f);
+  const float p2l = __fmul_rn(__fadd_rn(fmaf(-3.0f, p2f, Ph), Pl), 1.0f / 3.0f);
   // ---- FP32 trigonometric seed
-  const float p2f = to_f32_trunc(p2x3) * (1.0f / 3.0f);
-  const float detf = to_f32_trunc(det);
   const float pf = sqrt_seed(p2f);
-  float rf = (p2f > 0.0f) ? __fdividef(detf, 2.0f * p2f * pf) : 0.0f;
+  float rf = (p2f > 0.0f) ? __fdividef(Dh, 2.0f * p2f * pf) : 0.0f;
   rf = fminf(1.0f, fmaxf(-1.0f, rf));
   float sn, cs;
   __sincosf(acos_seed(rf) * (1.0f / 3.0f), &sn, &cs);
   const float x1f = 2.0f * pf * cs;                   // l1 - q
   const float x3f = -pf * fmaf(kSqrt3f, sn, cs);      // l3 - q
-  // ---- FP64 Newton on g(x) = x (x^2 - 3p^2) - det; each step takes its
-  // derivative 3 (x^2 - p^2) in FP32 at the current iterate
-  double x = to_f64(x1f);
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const float xf = (it == 0) ? x1f : to_f32_trunc(x);
+  // ---- Newton on g(x) = x (x^2 - 3p^2) - det: one FP32 step on the heads, one
+  // FP32 step on the float-float residual (x^2 exact as h2 + l2, x^2 - 3p^2
+  // by TwoSum, x s1 exact as mh + ml; mh - Dh is exact near the root, where
+  // x s1 ~ det), which lands within FP32 rounding of the root, then one FP64
+  // step. Derivatives 3 (x^2 - p^2) in FP32 from p2f + p2l.
+  float xf = x1f;
+  {
     const float gpf = 3.0f * fmaf(xf, xf, -p2f);
-    const double yg = to_f64((gpf != 0.0f) ? __fdividef(1.0f, gpf) : 0.0f);
-    const double g = fma(x, fma(x, x, -p2x3), -det);
-    x = fma(-g, yg, x);
+    xf = (gpf != 0.0f) ? xf - __fdividef(fmaf(xf, fmaf(xf, xf, -Ph), -Dh), gpf) : xf;
   }
+  {
+    const float h2 = __fmul_rn(xf, xf), l2 = fmaf(xf, xf, -h2);
+    const float s1 = __fsub_rn(h2, Ph), bb = __fsub_rn(s1, h2);
+    const float e1 = __fadd_rn(__fsub_rn(h2, __fsub_rn(s1, bb)), __fsub_rn(-Ph, bb));
+    const float ul = __fadd_rn(e1, __fsub_rn(l2, Pl));
+    const float mh = __fmul_rn(xf, s1);
+    const float ml = fmaf(xf, ul, fmaf(xf, s1, -mh));
+    const float gf = __fadd_rn(__fsub_rn(mh, Dh), __fsub_rn(ml, Dl));
+    const float gpf = 3.0f * __fsub_rn(fmaf(xf, xf, -p2f), p2l);
+    xf = (gpf != 0.0f) ? __fsub_rn(xf, __fdividef(gf, gpf)) : xf;
+  }
+  const float gpf = 3.0f * __fsub_rn(fmaf(xf, xf, -p2f), p2l);
+  const double x0 = to_f64(xf);
+  const double x = fma(-fma(x0, fma(x0, x0, -p2x3), -det), to_f64((gpf != 0.0f) ? rcp_seed(gpf) : 0.0f), x0);
+  double xr = x;
   e.refined = (1.0f + rf) < kPairTauF && p2f > 0.0f;
   if (e.refined) {
     // l1 ~ l2: refine the isolated l3 by Newton (FP64 derivative), then deflate
@@ -243,11 +276,11 @@ __device__ __forceinline__ EigenTop eigen_top_fp64(double xx, double yy, double 
     }
     double l1r = q + x, l2r = 0.0;
     refine_top_pair(xx, yy, zz, xy, xz, yz, q + x3, l1r, l2r);
-    x = l1r - q;
+    xr = l1r - q;
   }
   e.s = s;
   e.q = q;
-  e.x = x;
+  e.x = xr;
   e.p2x3 = p2x3;
   e.det = det;
   e.p2f = p2f;
@@ -357,8 +390,10 @@ __device__ __forceinline__ double spline_a_t(const Coef4& cf, double t, bool eds
 // FP64 collapse value of one point, F = 1/a_c (0 when there is no collapse).
 //   eigenvalues: invariants of M = A - qI in FP64 (s = tr, q = s/3,
 //     |M|_F^2 = 6 p^2, det M); l1 = q + x with x the largest root of
-//     x^3 - 3 p^2 x - det M = 0, seeded by the FP32 trigonometric solution and
-//     corrected by two FP64 Newton steps (FP32 derivative at each iterate);
+//     x^3 - 3 p^2 x - det M = 0, seeded by the FP32 trigonometric solution,
+//     brought to FP32 rounding of the root by two FP32 Newton steps (the second
+//     on the float-float residual from FP32 heads and tails of 3 p^2 and
+//     det M) and corrected by one FP64 Newton step (FP32 derivative);
 //   collapse: A_1(D) = 1 - l1 D + c2 D^2 + c3 D^3 from the centred invariants
 //     (w = x^2 - 3p^2 = (l2 - q)(l3 - q), l2 l3 = q (q - x) + w,
 //     c2 = -3/7 l2 l3, c3 = l1 K with 63 K = -23 l2 l3 + 15 (3 w - 3p^2), which is
@@ -457,8 +492,9 @@ struct MixedEigen {
   bool fp64;                      // the FP64 eigenvalue refinement ran
 };
 
-// The FP32 part: invariants, trigonometric eigenvalues, two FP32 Newton
-// steps, and the flags that send a point to the FP64 refinement or to the
+// The FP32 part: invariants, trigonometric eigenvalues, one FP32 Newton
+// step (the seed's error of ~3e-5 p drops to FP32 rounding of the cubic's
+// coefficients; a second step measured no change), and the flags that send a point to the FP64 refinement or to the
 // whole FP64 path.
 __device__ __forceinline__ MixedEigen mixed_eigen_f32(float xx, float yy, float zz, float xy, float xz, float yz,
                                                       float tri_thr) {
@@ -478,7 +514,7 @@ __device__ __forceinline__ MixedEigen mixed_eigen_f32(float xx, float yy, float 
   const float x2 = pf * fmaf(kSqrt3f, sn, -cs);
   const float x3 = -pf * fmaf(kSqrt3f, sn, cs);
 #pragma unroll
-  for (int it = 0; it < 2; ++it) {  // FP32 Newton on x (x^2 - 3p^2) - det
+  for (int it = 0; it < 1; ++it) {  // FP32 Newton on x (x^2 - 3p^2) - det
     const float gp = 3.0f * fmaf(x, x, -p2);
     x = (gp != 0.0f) ? x - __fdividef(fmaf(x, fmaf(x, x, -p2x3), -det), gp) : x;
   }
@@ -619,9 +655,11 @@ __device__ __forceinline__ MixedResult collapse_point_mixed(
   const MixedEigen m = mixed_eigen(xx, yy, zz, xy, xz, yz, tri_thr);
   if (m.full) return full_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
   const MixedCoef k = mixed_coef(m);
-  // FP32 closed-form root of u^3 - l1 u^2 + c2 u + c3 (u = 1/D), two FP32 Newton steps on A_1
+  // FP32 closed-form root of u^3 - l1 u^2 + c2 u + c3 (u = 1/D), one FP32
+  // Newton step on A_1 (the seed is within ~1e-5, one step within ~2e-7, and
+  // the FP64 polish squares that)
   const float uf = cubic_largest_root_seed(-k.l1f, k.c2f, k.c3f);
-  const float Df = newton_f32<2>(k, __fdividef(1.0f, uf));
+  const float Df = newton_f32<1>(k, __fdividef(1.0f, uf));
   return mixed_finish(m, k, Df, coef, Dkf, bucket, tab);
 }
 

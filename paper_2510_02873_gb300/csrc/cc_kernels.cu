@@ -133,7 +133,7 @@ __device__ __forceinline__ void mixed_point_deferred(const T* __restrict__ hess,
         if (!hard) {
           const MixedCoef k = mixed_coef(m);
           const float uf = cubic_largest_root_seed(-k.l1f, k.c2f, k.c3f);
-          const float Df = newton_f32<2>(k, __fdividef(1.0f, uf));
+          const float Df = newton_f32<1>(k, __fdividef(1.0f, uf));
           const MixedResult res = mixed_finish(m, k, Df, coef, Dkf, bucket, tab);
           cn.add(res);
           best.add(res.collapsed, res.a, r);

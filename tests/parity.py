@@ -93,3 +93,19 @@ def compare_reduced(F, idx, F_all, flags_all, tol=REL_TOL_REDUCED):
     assert np.all(np.isfinite(F)) and np.all(F >= 0)
     return {"max_rel_err": worst, "rms_rel_err": float(np.sqrt(np.mean(err[ok] ** 2))) if ok.any() else 0.0,
             "ambiguous": int(amb.sum()), "edge": int(edge.sum()), "ties": int(tie.sum())}
+
+
+def near_pair_corner_planes(n: int, seed: int) -> np.ndarray:
+    """(1, 6, n) planes of the spectra hardest for a single FP64 Newton step on
+    l1: l1 - l2 just above the deflation threshold (1 + r between 1e-4 and
+    ~3e-3), small l1 (0.03 .. 3) against a large negative l3 (gap 1 .. 32),
+    where the FP32 rounding of the characteristic cubic's coefficients moves
+    the FP32 root most and D_c is most sensitive to l1. Random frames."""
+    rng = np.random.default_rng(seed)
+    base = 10.0 ** rng.uniform(-1.5, 0.5, n)
+    gap = 10.0 ** rng.uniform(0.0, 1.5, n)
+    d = 10.0 ** rng.uniform(np.log10(0.012), np.log10(0.06), n) * gap / 3.0
+    lam = np.stack([base + d, base, base - gap], axis=1)
+    Q = np.linalg.qr(rng.normal(size=(n, 3, 3)))[0]
+    M = np.einsum("nij,nj,nkj->nik", Q, lam, Q)
+    return np.stack([M[:, 0, 0], M[:, 1, 1], M[:, 2, 2], M[:, 0, 1], M[:, 0, 2], M[:, 1, 2]])[None]

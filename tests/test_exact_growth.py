@@ -6,7 +6,7 @@ import pytest
 
 import hessgen
 import oracle
-from parity import compare_max
+from parity import compare_max, near_pair_corner_planes
 
 pytestmark = pytest.mark.gpu
 
@@ -96,6 +96,16 @@ def test_exact_growth_special_spectra(ctx, rtables):
     F_all, fl = oracle_exact_per_radius(rtables, planes)
     F, idx = gpu_multi(ctx, planes, [1.0])
     compare_max(F, idx, F_all, fl)
+
+
+def test_exact_growth_near_pair_threshold_corner(ctx, rtables):
+    """Spectra just above the deflation threshold with small l1 against a
+    large negative l3 (the FP64 eigenvalue stage's weakest case)."""
+    planes = near_pair_corner_planes(2000, 29)
+    F_all, fl = oracle_exact_per_radius(rtables, planes)
+    F, idx = gpu_multi(ctx, planes, [1.0])
+    compare_max(F, idx, F_all, fl)
+    assert (F > 0).sum() > 1000
 
 
 def test_exact_growth_in_eds_is_the_rlpt_path():

@@ -6,7 +6,7 @@ import pytest
 
 import hessgen
 import oracle
-from parity import REL_TOL_FP64, compare_max, oracle_per_radius, rel_err, running_max
+from parity import REL_TOL_FP64, compare_max, near_pair_corner_planes, oracle_per_radius, rel_err, running_max
 
 pytestmark = pytest.mark.gpu
 
@@ -133,6 +133,18 @@ def test_degenerate_and_special_spectra(ctx, tables, mode):
     F_all, fl = oracle_per_radius(tables, stack)
     F, idx = gpu_multi(ctx, stack, [1.0], mode=mode)
     compare_max(F, idx, F_all, fl)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_near_pair_threshold_corner(ctx, tables, mode):
+    """Spectra just above the deflation threshold with small l1 against a
+    large negative l3 (the FP64 eigenvalue stage's weakest case); most collapse."""
+    stack = near_pair_corner_planes(3000, 23)
+    F_all, fl = oracle_per_radius(tables, stack)
+    F, idx = gpu_multi(ctx, stack, [1.0], mode=mode)
+    s = compare_max(F, idx, F_all, fl)
+    assert (F > 0).sum() > 1500
+    print("near-pair corner", mode, s)
 
 
 @pytest.mark.parametrize("mode", MODES)

@@ -4,7 +4,7 @@ import pytest
 
 import hessgen
 import oracle
-from parity import REL_TOL_FP64, compare_max, rel_err, running_max
+from parity import REL_TOL_FP64, compare_max, near_pair_corner_planes, rel_err, running_max
 
 pytestmark = pytest.mark.gpu
 
@@ -66,6 +66,17 @@ def run_tab(ctx, stack, sig, plane_stride=None):
     ctx.collapse_multi(buf[:, :, :n], sig, F, idx, mode="tabulated")
     torch.cuda.synchronize()
     return F.cpu().numpy(), idx.cpu().numpy(), ctx.stats()
+
+
+def test_tabulated_near_pair_threshold_corner(ctx, tables, table):
+    """Spectra just above the deflation threshold with small l1 against a
+    large negative l3: inside the table and, beyond it, the R-LPT fallback."""
+    tab, _ = table
+    stack = near_pair_corner_planes(2000, 31)
+    F_all, fl = oracle_tab_per_radius(tables, tab, stack)
+    F, idx, st = run_tab(ctx, stack, [1.0])
+    compare_max(F, idx, F_all, fl)
+    assert (F > 0).sum() > 1000
 
 
 def test_tabulated_32cube_x8(ctx, tables, table):
