@@ -65,6 +65,21 @@ __device__ __forceinline__ double to_f64_normal(float f) {
   return __hiloint2double(static_cast<int>(hi), static_cast<int>(u << 29));
 }
 
+// to_f64_pos / to_f64_neg: the widening of an FP32 number known to be
+// positive (negative) wherever the result is used, in three integer
+// instructions: the logical shift moves a positive number's exponent and
+// mantissa into place and the constant rebiases the exponent; for a negative
+// number it also turns the shifted sign (bit 28) into bit 31. Any other input
+// gives a finite number of no meaning.
+__device__ __forceinline__ double to_f64_pos(float f) {
+  const unsigned u = __float_as_uint(f);
+  return __hiloint2double(static_cast<int>((u >> 3) + (896u << 20)), static_cast<int>(u << 29));
+}
+__device__ __forceinline__ double to_f64_neg(float f) {
+  const unsigned u = __float_as_uint(f);
+  return __hiloint2double(static_cast<int>((u >> 3) + 0xa8000000u), static_cast<int>(u << 29));
+}
+
 // tail_f32: v - hi as an FP32 value, where hi = to_f32_trunc(v): the 29
 // mantissa bits of v below hi's 23, of which the top 23 are kept (relative
 // error 2^-23 of the tail, 2^-46 of v), scaled by hi's exponent - 23. Built
@@ -529,7 +544,7 @@ __device__ __forceinline__ MixedEigen mixed_eigen_f32(float xx, float yy, float 
   m.p2 = p2;
   m.p2x3 = p2x3;
   m.lam1f = lam1f;
-  m.lam1 = to_f64_normal(lam1f);  // exact wherever l1 > 0 can collapse (a normal lam1f)
+  m.lam1 = to_f64_pos(lam1f);  // exact wherever l1 > 0 can collapse (a positive normal lam1f)
   return m;
 }
 
@@ -538,7 +553,7 @@ __device__ __forceinline__ MixedEigen mixed_eigen_f32(float xx, float yy, float 
 // two FP32 numbers are exact in FP64).
 __device__ __forceinline__ void mixed_refine64(MixedEigen& m, float xx, float yy, float zz, float xy, float xz,
                                                float yz) {
-  const double lam1 = m.lam1;
+  const double lam1 = to_f64_normal(m.lam1f);
   const double dxx = to_f64(xx) - lam1, dyy = to_f64(yy) - lam1;
   const double dzz = to_f64(zz) - lam1;
   const double dxy = to_f64(xy), dxz = to_f64(xz), dyz = to_f64(yz);
@@ -604,9 +619,12 @@ __device__ __forceinline__ float newton_f32(const MixedCoef& k, float Df) {
 //   the collapse and EdS tests take Df: the FP32 and the polished root fall on
 //     the same side of D_top or D_0 except within ~1e-7 of them, where the two
 //     sides give the same a (a_max at D_top; the spline is continuous at D_0);
-//   FP32 -> FP64 by to_f64_normal: for a collapsing point Df, A_1'(Df) and v
-//     are normal numbers, and a zero t0, c3 Df + c2 or lo(a_0 / D_0) D shifts
-//     t, A_1 or a by less than 2^-126.
+//   FP32 -> FP64: for a collapsing point Df and v are positive normal
+//     numbers and A_1'(Df) a negative one (A_1 falls through zero at its
+//     first root), so they take the three-instruction to_f64_pos / to_f64_neg
+//     (a result that is not used may be any finite number); t0, c3 Df + c2
+//     and lo(a_0 / D_0) D take to_f64_normal, where a zero shifts t, A_1 or a
+//     by less than 2^-126.
 __device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const MixedCoef& k, float Df,
                                                     const Coef4* __restrict__ coef, const float* __restrict__ Dkf,
                                                     const unsigned short* __restrict__ bucket, const DevTable& tab) {
@@ -614,7 +632,7 @@ __device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const M
   res.refined = false;
   res.fp64 = m.fp64;
   const float dAf = fmaf(fmaf(3.0f * k.c3f, Df, 2.0f * k.c2f), Df, -k.l1f);
-  const double D0 = to_f64_normal(Df);
+  const double D0 = to_f64_pos(Df);
   const double A1 = fma(fma(to_f64_normal(fmaf(k.c3f, Df, k.c2f)), D0, -m.lam1), D0, 1.0);
   res.collapsed = m.lam1f > 0.0f && Df > 0.0f && Df <= tab.Dtopf;
   const float Dcf = res.collapsed ? Df : tab.Dtopf;
@@ -625,8 +643,8 @@ __device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const M
   const float t0 = res.eds ? Dcf : __fsub_rn(__fsub_rn(Dcf, s1.z), s1.w);
   const float v = res.eds ? tab.eds_hi : fmaf(fmaf(s1.y, t0, s1.x), t0, s0.z);
   const double head = res.eds ? to_f64_normal(tab.eds_lo * Dcf) : coef[kk].c0;
-  const double t = fma(-A1, to_f64_normal(rcp_seed(dAf)), to_f64_normal(t0));
-  const double av = fma(to_f64_normal(v), t, head);
+  const double t = fma(-A1, to_f64_neg(rcp_seed(dAf)), to_f64_normal(t0));
+  const double av = fma(to_f64_pos(v), t, head);
   res.a = res.collapsed ? av : kInf;
   res.F = res.collapsed ? to_f64(1.0f / to_f32_trunc(av)) : 0.0;
   return res;
