@@ -27,7 +27,16 @@
  *   - Return value: CC_OK (0) or a CC_E* code; no exceptions, no exit().
  *     cc_strerror() names the code; cc_last_error_message() gives detail.
  *   - One context per device; a context is not thread-safe (serialise calls
- *     on one context, or use one context per host thread).
+ *     on one context, or use one context per host thread). Device work of
+ *     calls on one context that use its workspaces (CC_MODE_MIXED, which
+ *     keeps records of the points with FP64-heavy radii between its two
+ *     kernels; cc_collapse_multi_host; the surrogate's training) must not
+ *     overlap on the GPU: enqueue them on one stream or order the streams.
+ *     CC_MODE_MIXED allocates that workspace on first use at a size (24 B
+ *     per record, for at most n (0.006 R + 0.02) + 1024 records, R capped at
+ *     256): the first call at a new size is not asynchronous.
+ *   - F_max/idx entries hold what cc_reset_max or an earlier collapse call
+ *     left (F_max >= 0; idx = -1, or a scale index >= 0).
  *   - Supported input range: eigenvalue magnitudes of H up to 1e6 (in units
  *     where D(a = 1) = 1; collapse needs at least ~0.7, and points with l1 <= 0
  *     never collapse). The FP32 seeds of every path form sixth powers of the

@@ -57,6 +57,44 @@ int check_outputs(const double* F_max, const int32_t* idx, int64_t n) {
   return CC_OK;
 }
 
+// Records of the mixed path's points with hard radii (cc::HardRec). On
+// isotropic-field Hessians ~0.5 % of evaluations are hard, so ~1 - 0.995^R of
+// the points need a record; the capacity allows n (0.006 R + 0.02) + 1024
+// (at most n), and points beyond it are recomputed in radius order by the
+// second kernel instead. Record indices travel as 32-bit numbers, so the
+// capacity is also below 2^32. Grows on demand; never shrinks.
+int ensure_hard_records(cc_ctx* ctx, int64_t n, int R) {
+  const int Rl = R < kMaxRadiiPerLaunch ? R : kMaxRadiiPerLaunch;
+  const double frac = 0.006 * Rl + 0.02;
+  int64_t want = frac >= 1.0 ? n : static_cast<int64_t>(static_cast<double>(n) * frac) + 1024;
+  if (want > n) want = n;
+  if (want > static_cast<int64_t>(UINT32_MAX)) want = static_cast<int64_t>(UINT32_MAX);
+  if (!ctx->d_hard_ctr) {
+    if (int rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&ctx->d_hard_ctr),
+                                       kHardCounters * sizeof(unsigned long long)),
+                            "cudaMalloc(hard record counters)"))
+      return rc;
+  }
+  if (want <= ctx->hard_cap) return CC_OK;
+  if (ctx->d_hard) {
+    cudaFree(ctx->d_hard);
+    ctx->d_hard = nullptr;
+    ctx->hard_cap = 0;
+  }
+  if (ctx->d_hard_full) {
+    cudaFree(ctx->d_hard_full);
+    ctx->d_hard_full = nullptr;
+  }
+  if (int rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&ctx->d_hard), sizeof(HardRec) * static_cast<size_t>(want)),
+                          "cudaMalloc(hard records)"))
+    return rc;
+  if (int rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&ctx->d_hard_full), sizeof(uint32_t) * static_cast<size_t>(want)),
+                          "cudaMalloc(hard record list)"))
+    return rc;
+  ctx->hard_cap = want;
+  return CC_OK;
+}
+
 int run_collapse(cc_ctx* ctx, cc_mode mode, const void* hess, int32_t dtype, int64_t n,
                  int64_t plane_stride, int64_t radius_stride, const double* sigma, int32_t R,
                  double* F_max, int32_t* idx, int32_t scale_idx0, void* stream) {
@@ -76,8 +114,10 @@ int run_collapse(cc_ctx* ctx, cc_mode mode, const void* hess, int32_t dtype, int
   switch (mode) {
     case CC_MODE_FP64:
       return launch_fp64(a, ctx->tab);
-    case CC_MODE_MIXED:
-      return launch_mixed(a, ctx->tab, sigma);
+    case CC_MODE_MIXED: {
+      if (int rc = ensure_hard_records(ctx, n, R)) return rc;
+      return launch_mixed(a, ctx->tab, sigma, HardWork{ctx->d_hard, ctx->hard_cap, ctx->d_hard_ctr, ctx->d_hard_full});
+    }
     case CC_MODE_TABULATED:
       return launch_tab_checked(ctx, a);
     case CC_MODE_SURROGATE:
@@ -293,6 +333,9 @@ void cc_destroy(cc_ctx* ctx) {
   if (ctx->d_table) cudaFree(ctx->d_table);
   if (ctx->d_ratio) cudaFree(ctx->d_ratio);
   if (ctx->d_counters) cudaFree(ctx->d_counters);
+  if (ctx->d_hard) cudaFree(ctx->d_hard);
+  if (ctx->d_hard_full) cudaFree(ctx->d_hard_full);
+  if (ctx->d_hard_ctr) cudaFree(ctx->d_hard_ctr);
   for (int b = 0; b < 2; ++b) {
     if (ctx->d_stage[b]) cudaFree(ctx->d_stage[b]);
     if (ctx->ev_copied[b]) cudaEventDestroy(ctx->ev_copied[b]);

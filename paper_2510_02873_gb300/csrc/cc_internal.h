@@ -157,8 +157,35 @@ struct LaunchArgs {
   cudaStream_t stream;
   int num_sms;
 };
+// Mixed path: points with evaluations that need FP64 work beyond the polish
+// and the spline (the FP64 refinement of l1, or the whole FP64 path near
+// degeneracy) leave the main kernel as records; a second kernel evaluates
+// those radii and finishes the point. A record holds the point, the running
+// minimum of a_c over its other radii and the radius it came from, and the
+// hard radii below 32 as a bit mask (bit 16 of r1 flags hard radii >= 32,
+// which the second kernel finds again).
+struct HardRec {
+  int64_t p;
+  double a;       // running minimum of a_c over the point's other radii (+inf: none collapsed)
+  uint32_t mask;  // hard radii 0..31
+  int32_t r1;     // (radius of a) + 1 in bits 0..15; bit 16: hard radii >= 32
+};
+static_assert(sizeof(HardRec) == 24, "record layout");
+// the records of one launch: capacity, and ctr[0] = records requested,
+// ctr[1] = nonzero when some did not fit (those points carry idx = -(idx + 3)
+// and are recomputed in radius order by the second kernel), ctr[2] = entries
+// of `full`: the records that still have radii needing the whole FP64 path
+// after the second kernel (the third kernel finishes them)
+struct HardWork {
+  HardRec* rec;
+  int64_t cap;
+  unsigned long long* ctr;
+  uint32_t* full;
+};
+constexpr int kHardCounters = 3;
+
 int launch_fp64(const LaunchArgs& a, const DevTable& tab);
-int launch_mixed(const LaunchArgs& a, const DevTable& tab, const double* sigma);
+int launch_mixed(const LaunchArgs& a, const DevTable& tab, const double* sigma, const HardWork& hw);
 int launch_tab(const LaunchArgs& a, const DevTable& tab, const TabDev& td);
 int launch_f32x2(const LaunchArgs& a, const DevTable& tab);
 int launch_exact(const LaunchArgs& a, const DevTable& tab);
@@ -216,4 +243,10 @@ struct cc_ctx {
   // interpolation toy (cc_spline_eval)
   void* d_spl = nullptr;
   size_t spl_cap = 0;
+  // mixed path: records of points with hard evaluations (allocated on first
+  // use at a size; see cc::HardRec) and their two counters
+  cc::HardRec* d_hard = nullptr;
+  uint32_t* d_hard_full = nullptr;
+  int64_t hard_cap = 0;
+  unsigned long long* d_hard_ctr = nullptr;
 };

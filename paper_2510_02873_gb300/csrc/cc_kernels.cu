@@ -43,17 +43,17 @@ __device__ __forceinline__ void add_counters(DevCounters* cnt, unsigned evals, u
 constexpr int kModeFP64 = 0, kModeMixed = 1, kModeTab = 2, kModeF32x2 = 3, kModeExact = 4;
 constexpr int kFp64Radii = 2;  // radii per loop iteration of the FP64 path
 
-// ---- mixed path with the hard evaluations deferred. About 0.5 % of the
-// evaluations need FP64 work beyond the polish and the spline (the FP64
-// refinement of l1, or the whole FP64 path near degeneracy); run in place,
-// one such lane makes its warp issue that FP64 code for all 32 lanes, and
-// with 32 lanes one warp in six does so at every radius. Instead the lane
-// queues (lane, radius) in shared memory and drops out of that radius; the
-// warp runs the queued evaluations 32 at a time, all lanes busy, when the
-// queue fills and after the last radius, and hands each result to the lane
-// that owns the point. The results are those of collapse_point_mixed; the
-// running minimum takes them out of radius order (ties to the smaller radius).
-constexpr int kDeferQ = 64;  // queue entries per warp: lane << 8 | radius
+// ---- mixed path. About 0.5 % of the evaluations need FP64 work beyond the
+// polish and the spline (the FP64 refinement of l1, or the whole FP64 path
+// near degeneracy). That code beside the radius loop, run in place or from a
+// per-warp queue, takes the loop's registers: at 40 registers the loop alone
+// does not spill, with the FP64 path inlined next to it 220 bytes spill and
+// the kernel runs 14 % slower. So the main kernel only marks those radii
+// (a bit per radius below 32, a flag for the others) and, for a point that
+// has any, writes a record (HardRec) instead of its result; mixed_hard_kernel
+// evaluates the marked radii with collapse_point_mixed and finishes the
+// point. The running minimum merges them out of radius order with ties to
+// the smaller radius, so F_max and idx are those of the in-order loop.
 
 struct MixedCounts {
   unsigned coll = 0, eds = 0, ref = 0, fp64 = 0;
@@ -65,119 +65,214 @@ struct MixedCounts {
   }
 };
 
-template <typename T>
-__device__ __forceinline__ void mixed_flush(const T* __restrict__ warp_base, int64_t plane_stride, int64_t radius_stride,
-                                            const RadiusParams& rp, const unsigned short* q, int count,
-                                            const double* __restrict__ Dk, const Coef4* __restrict__ coef,
-                                            const float* __restrict__ Dkf, const unsigned short* __restrict__ bucket,
-                                            const DevTable& tab, MinA& best, MixedCounts& cn) {
-  const int lane = threadIdx.x & 31;
-  __syncwarp();
-  for (int base = 0; base < count; base += 32) {
-    const int i = base + lane;
-    double av = kInf;
-    int rr = -1, owner = -1, coll = 0;
-    if (i < count) {
-      const unsigned e = q[i];
-      owner = static_cast<int>(e >> 8);
-      rr = static_cast<int>(e & 255u);
-      CC_DBG_CLAMP(owner, 0, 31, tab.dbg);
-      const T* h = warp_base + owner + static_cast<int64_t>(rr) * radius_stride;
-      const float xx = ldf(h), yy = ldf(h + plane_stride), zz = ldf(h + 2 * plane_stride);
-      const float xy = ldf(h + 3 * plane_stride), xz = ldf(h + 4 * plane_stride);
-      const float yz = ldf(h + 5 * plane_stride);
-      const MixedResult res = collapse_point_mixed(xx, yy, zz, xy, xz, yz, rp.tri_thr[rr], Dk, coef, Dkf, bucket, tab);
-      cn.add(res);
-      av = res.a;
-      coll = res.collapsed;
-    }
-    const int m = min(32, count - base);
-    for (int j = 0; j < m; ++j) {
-      const int o = __shfl_sync(0xffffffffu, owner, j);
-      const double a_j = __shfl_sync(0xffffffffu, av, j);
-      const int r_j = __shfl_sync(0xffffffffu, rr, j);
-      const int c_j = __shfl_sync(0xffffffffu, coll, j);
-      if (lane == o) best.add_any_order(c_j != 0, a_j, r_j);
-    }
-  }
-  __syncwarp();
+// One radius that needs nothing beyond the FP32 stages, the FP64 polish and
+// the spline (m from mixed_eigen_f32 with neither m.full nor m.need64): the
+// same steps, and so the same result, as collapse_point_mixed.
+__device__ __forceinline__ MixedResult mixed_easy(const MixedEigen& m, const Coef4* __restrict__ coef,
+                                                  const float* __restrict__ Dkf,
+                                                  const unsigned short* __restrict__ bucket, const DevTable& tab) {
+  const MixedCoef k = mixed_coef(m);
+  const float uf = cubic_largest_root_seed(-k.l1f, k.c2f, k.c3f);
+  const float Df = newton_f32<1>(k, __fdividef(1.0f, uf));
+  return mixed_finish(m, k, Df, coef, Dkf, bucket, tab);
 }
 
-// All 32 lanes of the warp call this together (inactive lanes with active = false).
-template <typename T>
-__device__ __forceinline__ void mixed_point_deferred(const T* __restrict__ hess, int64_t p, bool active, int R,
-                                                     int64_t plane_stride, int64_t radius_stride,
-                                                     const RadiusParams& rp, const double* __restrict__ Dk,
-                                                     const Coef4* __restrict__ coef, const float* __restrict__ Dkf,
-                                                     const unsigned short* __restrict__ bucket, const DevTable& tab,
-                                                     unsigned short* q, MinA& best, MixedCounts& cn) {
-  const int lane = threadIdx.x & 31;
-  const unsigned below = (1u << lane) - 1u;
-  const T* warp_base = hess + (p - lane);
-  int count = 0;  // warp-uniform
-  int r = 0;
-  // one call site of the flush (it inlines the whole FP64 path): the radius
-  // loop stops when radius r's hard lanes do not fit, the queue is run, and
-  // those lanes become the first entries of the next round
-  for (;;) {
-    unsigned pending = 0;
-    for (; r < R; ++r) {
-      bool hard = false;
-      if (active) {
-        const T* h = hess + p + static_cast<int64_t>(r) * radius_stride;
-        const float xx = ldf(h), yy = ldf(h + plane_stride), zz = ldf(h + 2 * plane_stride);
-        const float xy = ldf(h + 3 * plane_stride), xz = ldf(h + 4 * plane_stride);
-        const float yz = ldf(h + 5 * plane_stride);
-        const MixedEigen m = mixed_eigen_f32(xx, yy, zz, xy, xz, yz, rp.tri_thr[r]);
-        hard = m.full || m.need64;
-        if (!hard) {
-          const MixedCoef k = mixed_coef(m);
-          const float uf = cubic_largest_root_seed(-k.l1f, k.c2f, k.c3f);
-          const float Df = newton_f32<1>(k, __fdividef(1.0f, uf));
-          const MixedResult res = mixed_finish(m, k, Df, coef, Dkf, bucket, tab);
-          cn.add(res);
-          best.add(res.collapsed, res.a, r);
-        }
-      }
-      const unsigned hb = __ballot_sync(0xffffffffu, hard);
-      if (hb) {
-        if (count + __popc(hb) > kDeferQ) {
-          pending = hb;
-          break;
-        }
-        int slot = count + __popc(hb & below);
-        CC_DBG_CLAMP(slot, 0, kDeferQ - 1, tab.dbg);
-        if (hard) q[slot] = static_cast<unsigned short>((lane << 8) | r);
-        count += __popc(hb);
+constexpr int32_t kHardHigh = 0x10000;  // HardRec::r1: hard radii >= 32
+
+// End of a point in the main kernel. All 32 lanes of the warp call this. A
+// point without hard radii stores its result; the others take consecutive
+// record slots (one atomic per warp). A point whose slot is beyond the
+// capacity keeps F_max and marks idx as -(idx + 3) (idx is -1 or a radius
+// index, so the mark is <= -2) for the second kernel to recompute in order.
+__device__ __forceinline__ void mixed_record_or_store(bool active, int64_t p, const MinA& best, uint32_t mask,
+                                                      bool hi, const HardWork& hw, double* __restrict__ F_max,
+                                                      int32_t* __restrict__ idx, int32_t scale_idx0) {
+  const bool need = active && (mask != 0u || hi);
+  const unsigned bal = __ballot_sync(0xffffffffu, need);
+  if (bal != 0u) {
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(bal) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(hw.ctr, static_cast<unsigned long long>(__popc(bal)));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (need) {
+      const unsigned long long slot = base + static_cast<unsigned>(__popc(bal & ((1u << lane) - 1u)));
+      if (slot < static_cast<unsigned long long>(hw.cap)) {
+        HardRec rec;
+        rec.p = p;
+        rec.a = best.a;
+        rec.mask = mask;
+        rec.r1 = (best.r + 1) | (hi ? kHardHigh : 0);
+        hw.rec[slot] = rec;
+      } else {
+        idx[p] = -idx[p] - 3;
+        atomicOr(hw.ctr + 1, 1ull);
       }
     }
-    mixed_flush(warp_base, plane_stride, radius_stride, rp, q, count, Dk, coef, Dkf, bucket, tab, best, cn);
-    if (!pending) break;
-    if ((pending >> lane) & 1u) q[__popc(pending & below)] = static_cast<unsigned short>((lane << 8) | r);
-    count = __popc(pending);
-    ++r;
   }
+  if (active && !need) best.store<true>(F_max + p, idx + p, scale_idx0);
+}
+
+constexpr int kHardThreads = 128;
+
+template <typename T>
+struct Planes6 {
+  float xx, yy, zz, xy, xz, yz;
+  __device__ __forceinline__ Planes6(const T* h, int64_t ps)
+      : xx(ldf(h)), yy(ldf(h + ps)), zz(ldf(h + 2 * ps)), xy(ldf(h + 3 * ps)), xz(ldf(h + 4 * ps)),
+        yz(ldf(h + 5 * ps)) {}
+};
+
+// The recorded points (second kernel), one thread per record: each hard radius
+// gets mixed_eigen (with the FP64 refinement of l1 where flagged) and the
+// mixed path's finish; radii that need the whole FP64 path are left in the
+// record (its mask and running minimum updated) and the record joins the
+// `full` list for mixed_full_kernel, so that the few lanes on that path do
+// not hold up a warp of short evaluations. Points marked after an overflow
+// are recomputed here in radius order, every path in place. Counts what the
+// main kernel left out: collapses, EdS and FP64 evaluations of the hard radii
+// (the evaluations themselves were counted there).
+template <typename T>
+__global__ void __launch_bounds__(kHardThreads)
+mixed_hard_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride, int64_t radius_stride, int R,
+                  int32_t scale_idx0, DevTable tab, RadiusParams rp, HardWork hw, double* __restrict__ F_max,
+                  int32_t* __restrict__ idx, DevCounters* __restrict__ cnt) {
+  const unsigned long long req = hw.ctr[0];
+  const int64_t nrec = req < static_cast<unsigned long long>(hw.cap) ? static_cast<int64_t>(req) : hw.cap;
+  const bool overflow = hw.ctr[1] != 0ull;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  MixedCounts cn;
+  for (int64_t i = t0; i < nrec; i += stride) {
+    HardRec rec = hw.rec[i];
+    CC_DBG_CLAMP(rec.p, static_cast<int64_t>(0), n - 1, tab.dbg);
+    MinA best;
+    best.a = rec.a;
+    best.r = (rec.r1 & 0xffff) - 1;
+    const T* base = hess + rec.p;
+    uint32_t full = 0;
+    bool full_hi = false;
+    for (uint32_t m = rec.mask; m != 0u; m &= m - 1u) {
+      const int r = __ffs(m) - 1;
+      const Planes6<T> v(base + static_cast<int64_t>(r) * radius_stride, plane_stride);
+      const MixedEigen me = mixed_eigen(v.xx, v.yy, v.zz, v.xy, v.xz, v.yz, rp.tri_thr[r]);
+      if (me.full) {
+        full |= 1u << r;
+        continue;
+      }
+      const MixedResult res = mixed_easy(me, tab.coef, tab.Df, tab.bucket, tab);
+      cn.add(res);
+      best.add_any_order(res.collapsed, res.a, r);
+    }
+    if (rec.r1 & kHardHigh) {
+      for (int r = 32; r < R; ++r) {
+        const Planes6<T> v(base + static_cast<int64_t>(r) * radius_stride, plane_stride);
+        const MixedEigen me = mixed_eigen_f32(v.xx, v.yy, v.zz, v.xy, v.xz, v.yz, rp.tri_thr[r]);
+        if (me.full) {
+          full_hi = true;
+        } else if (me.need64) {
+          MixedEigen mr = me;
+          mixed_refine64(mr, v.xx, v.yy, v.zz, v.xy, v.xz, v.yz);
+          const MixedResult res = mixed_easy(mr, tab.coef, tab.Df, tab.bucket, tab);
+          cn.add(res);
+          best.add_any_order(res.collapsed, res.a, r);
+        }
+      }
+    }
+    if (full != 0u || full_hi) {
+      rec.a = best.a;
+      rec.mask = full;
+      rec.r1 = (best.r + 1) | (full_hi ? kHardHigh : 0);
+      hw.rec[i] = rec;
+      int64_t k = static_cast<int64_t>(atomicAdd(hw.ctr + 2, 1ull));
+      CC_DBG_CLAMP(k, static_cast<int64_t>(0), hw.cap - 1, tab.dbg);
+      hw.full[k] = static_cast<uint32_t>(i);
+    } else {
+      best.store<true>(F_max + rec.p, idx + rec.p, scale_idx0);
+    }
+  }
+  if (overflow) {
+    for (int64_t p = t0; p < n; p += stride) {
+      const int32_t mark = idx[p];
+      if (mark > -2) continue;
+      idx[p] = -mark - 3;
+      MinA best;
+      for (int r = 0; r < R; ++r) {
+        const Planes6<T> v(hess + p + static_cast<int64_t>(r) * radius_stride, plane_stride);
+        const MixedEigen me = mixed_eigen_f32(v.xx, v.yy, v.zz, v.xy, v.xz, v.yz, rp.tri_thr[r]);
+        MixedResult res;
+        if (me.full || me.need64) {
+          res = collapse_point_mixed(v.xx, v.yy, v.zz, v.xy, v.xz, v.yz, rp.tri_thr[r], tab.D, tab.coef, tab.Df,
+                                     tab.bucket, tab);
+          cn.add(res);
+        } else {
+          res = mixed_easy(me, tab.coef, tab.Df, tab.bucket, tab);
+        }
+        best.add(res.collapsed, res.a, r);
+      }
+      best.store<true>(F_max + p, idx + p, scale_idx0);
+    }
+  }
+  add_counters(cnt, 0u, cn.coll, cn.eds, cn.ref, cn.fp64);
+}
+
+// The records left with radii on the whole FP64 path (third kernel): those
+// radii through full_fp64 (what collapse_point_mixed runs for them), merged
+// into the record's running minimum; then the point's result is stored.
+template <typename T>
+__global__ void __launch_bounds__(kHardThreads)
+mixed_full_kernel(const T* __restrict__ hess, int64_t plane_stride, int64_t radius_stride, int R,
+                  int32_t scale_idx0, DevTable tab, RadiusParams rp, HardWork hw, double* __restrict__ F_max,
+                  int32_t* __restrict__ idx, DevCounters* __restrict__ cnt) {
+  const int64_t nfull = static_cast<int64_t>(hw.ctr[2]);
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  MixedCounts cn;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nfull; i += stride) {
+    int64_t ri = hw.full[i];
+    CC_DBG_CLAMP(ri, static_cast<int64_t>(0), hw.cap - 1, tab.dbg);
+    const HardRec rec = hw.rec[ri];
+    MinA best;
+    best.a = rec.a;
+    best.r = (rec.r1 & 0xffff) - 1;
+    const T* base = hess + rec.p;
+    for (uint32_t m = rec.mask; m != 0u; m &= m - 1u) {
+      const int r = __ffs(m) - 1;
+      const Planes6<T> v(base + static_cast<int64_t>(r) * radius_stride, plane_stride);
+      const MixedResult res = full_fp64(v.xx, v.yy, v.zz, v.xy, v.xz, v.yz, tab.D, tab.coef, tab.Df, tab.bucket, tab);
+      cn.add(res);
+      best.add_any_order(res.collapsed, res.a, r);
+    }
+    if (rec.r1 & kHardHigh) {
+      for (int r = 32; r < R; ++r) {
+        const Planes6<T> v(base + static_cast<int64_t>(r) * radius_stride, plane_stride);
+        if (!mixed_eigen_f32(v.xx, v.yy, v.zz, v.xy, v.xz, v.yz, rp.tri_thr[r]).full) continue;
+        const MixedResult res = full_fp64(v.xx, v.yy, v.zz, v.xy, v.xz, v.yz, tab.D, tab.coef, tab.Df, tab.bucket, tab);
+        cn.add(res);
+        best.add_any_order(res.collapsed, res.a, r);
+      }
+    }
+    best.store<true>(F_max + rec.p, idx + rec.p, scale_idx0);
+  }
+  add_counters(cnt, 0u, cn.coll, cn.eds, cn.ref, cn.fp64);
 }
 
 // One thread per point (grid-stride), all R radii of the launch in registers.
 // kMode selects collapse_point_fp64, the mixed path (FP32 bulk, its rare
-// FP64-heavy evaluations deferred through mixed_point_deferred), the
+// FP64-heavy radii left to mixed_hard_kernel through records), the
 // float-float path (dfl::collapse_point), the exact-growth path
 // (exact::collapse_point) or collapse_point_tab (tabulated 1/D_c; its axes
 // follow the spline table in shared memory).
 // FP64 path: two radii per iteration at 2 blocks of 256 threads per SM (94
 // registers, no spill): 1.3 % faster than one radius at 4 blocks and 64
 // registers; 3 or 4 radii per iteration, or 1 block, measured the same.
-// Mixed path: 40
-// registers and 6 blocks per SM, 4 % faster than 4 blocks at 64 registers
-// despite spills (its warps stall on global loads and on FP32 dependencies,
-// which more resident warps hide; 8 blocks at 32 registers spill too much).
+// Mixed path: 40 registers and 6 blocks per SM (its warps stall on global
+// loads and on FP32 dependencies, which more resident warps hide).
 // The tabulated path keeps its 98 registers.
 template <typename T, bool kSmem, int kMode>
 __global__ void __launch_bounds__(kThreads, kMode == 2 ? 1 : (kMode == 1 ? 6 : (kMode == 0 ? 2 : 4)))
 collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
                 int64_t radius_stride, int R, int32_t scale_idx0, DevTable tab, RadiusParams rp,
-                TabDev td, double* __restrict__ F_max, int32_t* __restrict__ idx,
+                TabDev td, HardWork hw, double* __restrict__ F_max, int32_t* __restrict__ idx,
                 DevCounters* __restrict__ cnt) {
   extern __shared__ Coef4 smem_tab[];
   const Coef4* coef = tab.coef;
@@ -236,19 +331,32 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
       best.store(F_max + p, idx + p, scale_idx0);
       n_eval += R;
     } else if constexpr (kMode == kModeMixed) {
-      __shared__ unsigned short defer_q[kThreads / 32][kDeferQ];
       MinA best;
       MixedCounts cn;
-      mixed_point_deferred(hess, p, active, R, plane_stride, radius_stride, rp, Dk, coef, Dkf, bucket, tab,
-                           defer_q[threadIdx.x >> 5], best, cn);
-      n_coll += cn.coll;
-      n_eds += cn.eds;
-      n_ref += cn.ref;
-      n_fp64 += cn.fp64;
+      uint32_t mask = 0;
+      bool hi = false;
       if (active) {
-        best.store<true>(F_max + p, idx + p, scale_idx0);
+        for (int r = 0; r < R; ++r) {
+          const T* h = hess + p + static_cast<int64_t>(r) * radius_stride;
+          const float xx = ldf(h), yy = ldf(h + plane_stride), zz = ldf(h + 2 * plane_stride);
+          const float xy = ldf(h + 3 * plane_stride), xz = ldf(h + 4 * plane_stride);
+          const float yz = ldf(h + 5 * plane_stride);
+          const MixedEigen m = mixed_eigen_f32(xx, yy, zz, xy, xz, yz, rp.tri_thr[r]);
+          if (!(m.full || m.need64)) {
+            const MixedResult res = mixed_easy(m, coef, Dkf, bucket, tab);
+            cn.add(res);
+            best.add(res.collapsed, res.a, r);
+          } else if (r < 32) {
+            mask |= 1u << r;
+          } else {
+            hi = true;
+          }
+        }
         n_eval += R;
       }
+      n_coll += cn.coll;
+      n_eds += cn.eds;
+      mixed_record_or_store(active, p, best, mask, hi, hw, F_max, idx, scale_idx0);
     } else if (kMode == kModeFP64 && active) {
       // kFp64Radii radii per iteration: independent FP64 chains that the
       // compiler interleaves, so the FP64 unit meets fewer gaps while a warp
@@ -354,7 +462,8 @@ __global__ void reset_max_kernel(double* __restrict__ F_max, int32_t* __restrict
 }
 
 template <typename T, bool kSmem, int kMode>
-int launch_typed(const LaunchArgs& a, const DevTable& tab, const RadiusParams& rp, const TabDev& td) {
+int launch_typed(const LaunchArgs& a, const DevTable& tab, const RadiusParams& rp, const TabDev& td,
+                 const HardWork& hw) {
   auto kern = collapse_kernel<T, kSmem, kMode>;
   size_t smem = kSmem ? ((tab.bytes() + 15) / 16) * 16 : 0;
   if (kMode == kModeTab) smem = ((tab.bytes() + 15) / 16) * 16 + ((td.axes_bytes() + 15) / 16) * 16;
@@ -386,23 +495,36 @@ int launch_typed(const LaunchArgs& a, const DevTable& tab, const RadiusParams& r
   TabDev tdl = td;
   tdl.dbg = t.dbg;
   kern<<<grid, kThreads, smem, a.stream>>>(static_cast<const T*>(a.hess), a.n, a.plane_stride,
-                                           a.radius_stride, a.R, a.scale_idx0, t, rp, tdl, a.F_max,
+                                           a.radius_stride, a.R, a.scale_idx0, t, rp, tdl, hw, a.F_max,
                                            a.idx, a.counters);
-  return check_cuda(cudaGetLastError(), "collapse_kernel launch");
+  if (int rc = check_cuda(cudaGetLastError(), "collapse_kernel launch")) return rc;
+  if constexpr (kMode == kModeMixed) {
+    // the recorded points: a grid of a few blocks per SM strides over them
+    mixed_hard_kernel<T><<<4 * a.num_sms, kHardThreads, 0, a.stream>>>(
+        static_cast<const T*>(a.hess), a.n, a.plane_stride, a.radius_stride, a.R, a.scale_idx0, t, rp, hw,
+        a.F_max, a.idx, a.counters);
+    if (int rc = check_cuda(cudaGetLastError(), "mixed_hard_kernel launch")) return rc;
+    mixed_full_kernel<T><<<4 * a.num_sms, kHardThreads, 0, a.stream>>>(
+        static_cast<const T*>(a.hess), a.plane_stride, a.radius_stride, a.R, a.scale_idx0, t, rp, hw, a.F_max,
+        a.idx, a.counters);
+    return check_cuda(cudaGetLastError(), "mixed_full_kernel launch");
+  }
+  return CC_OK;
 }
 
 template <int kMode>
-int launch_mode(const LaunchArgs& a, const DevTable& tab, const RadiusParams& rp, const TabDev& td) {
+int launch_mode(const LaunchArgs& a, const DevTable& tab, const RadiusParams& rp, const TabDev& td,
+                const HardWork& hw = HardWork{}) {
   const size_t staged = (kMode == kModeF32x2) ? ((tab.bytes() + 15) / 16) * 16 + sizeof(float4) * 2 * (tab.n - 1)
                                                : tab.bytes();
   const bool smem = staged <= static_cast<size_t>(kSmemTableMaxBytes);
   if (kMode == kModeTab) {  // the tabulated kernel always stages both images
-    if (a.dtype == CC_F64) return launch_typed<double, true, kMode>(a, tab, rp, td);
-    return launch_typed<float, true, kMode>(a, tab, rp, td);
+    if (a.dtype == CC_F64) return launch_typed<double, true, kMode>(a, tab, rp, td, hw);
+    return launch_typed<float, true, kMode>(a, tab, rp, td, hw);
   }
   if (a.dtype == CC_F64)
-    return smem ? launch_typed<double, true, kMode>(a, tab, rp, td) : launch_typed<double, false, kMode>(a, tab, rp, td);
-  return smem ? launch_typed<float, true, kMode>(a, tab, rp, td) : launch_typed<float, false, kMode>(a, tab, rp, td);
+    return smem ? launch_typed<double, true, kMode>(a, tab, rp, td, hw) : launch_typed<double, false, kMode>(a, tab, rp, td, hw);
+  return smem ? launch_typed<float, true, kMode>(a, tab, rp, td, hw) : launch_typed<float, false, kMode>(a, tab, rp, td, hw);
 }
 
 }  // namespace
@@ -426,7 +548,7 @@ int launch_tab(const LaunchArgs& a, const DevTable& tab, const TabDev& td) {
   return launch_mode<kModeTab>(a, tab, RadiusParams{}, td);
 }
 
-int launch_mixed(const LaunchArgs& a, const DevTable& tab, const double* sigma) {
+int launch_mixed(const LaunchArgs& a, const DevTable& tab, const double* sigma, const HardWork& hw) {
   // at most kMaxRadiiPerLaunch radii per launch (their thresholds ride in the
   // kernel parameters); longer radius lists run as consecutive launches
   for (int r0 = 0; r0 < a.R; r0 += kMaxRadiiPerLaunch) {
@@ -436,7 +558,10 @@ int launch_mixed(const LaunchArgs& a, const DevTable& tab, const double* sigma) 
     c.scale_idx0 = a.scale_idx0 + r0;
     RadiusParams rp;
     for (int r = 0; r < c.R; ++r) rp.tri_thr[r] = static_cast<float>(1e-4 * sigma[r0 + r]);
-    if (int rc = launch_mode<kModeMixed>(c, tab, rp, TabDev{})) return rc;
+    if (int rc = check_cuda(cudaMemsetAsync(hw.ctr, 0, kHardCounters * sizeof(unsigned long long), a.stream),
+                            "cudaMemsetAsync(hard records)"))
+      return rc;
+    if (int rc = launch_mode<kModeMixed>(c, tab, rp, TabDev{}, hw)) return rc;
   }
   return CC_OK;
 }

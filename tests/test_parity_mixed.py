@@ -175,10 +175,10 @@ def _degenerate_matrices(rng, scales=(0.5, 2.0, 8.0)):
 
 
 def test_mixed_deferred_queue_overflow_and_ties(ctx, tables):
-    """Warps whose lanes are mostly 'hard' (FP64 refinement or the whole FP64
-    path) at every radius: the per-warp queue of deferred evaluations fills
-    several times per point, and the same matrices at every radius make every
-    collapsing point an exact tie, which the earliest radius must win."""
+    """Points that are mostly 'hard' (FP64 refinement or the whole FP64 path)
+    at every radius, so nearly every point leaves the main kernel as a record,
+    and the same matrices at every radius make every collapsing point an exact
+    tie, which the earliest radius must win."""
     rng = np.random.default_rng(23)
     hard = _degenerate_matrices(rng)                      # 6 x 87
     easy = hessgen.hessian_stack(31, 0, [1.0], 100)[0]    # 6 x 100 (FP64)
@@ -197,14 +197,14 @@ def test_mixed_deferred_queue_overflow_and_ties(ctx, tables):
     assert np.all(idx[F > 0] == 0), "exact ties must keep the earliest radius"
     assert np.all(idx[F == 0] == -1)
     assert st["evaluations"] == planes.shape[1] * R
-    # the hard share is large: many deferred evaluations per warp and radius
+    # the hard share is large: most points carry hard radii
     assert st["fp64_branch"] > 0.15 * planes.shape[1] * R
 
 
 def test_mixed_deferred_mixed_radii(ctx, tables):
     """Hard matrices scattered over random (point, radius) cells of a random
-    field: deferred and in-place evaluations of one point meet in the running
-    maximum out of radius order."""
+    field: a point's hard radii (second kernel) and its other radii (main
+    kernel) meet in the running maximum out of radius order."""
     rng = np.random.default_rng(29)
     n, R = 3000, 9
     sig = hessgen.sigma_schedule(R, 0.3, 5.0)
@@ -217,7 +217,77 @@ def test_mixed_deferred_mixed_radii(ctx, tables):
     F_all, fl = oracle_per_radius(tables, stack)
     F, idx, st = run_mixed(ctx, stack, sig, plane_stride=n + 4)
     s = compare_mixed(F, idx, F_all, fl)
-    print("mixed deferred, scattered hard cells", s, "fp64 fraction", st["fp64_branch"] / (n * R))
+    print("mixed, scattered hard cells", s, "fp64 fraction", st["fp64_branch"] / (n * R))
+
+
+def _batch_mixed(ctx, stack, sig, ps):
+    """The same planes through the batched kernel, which evaluates hard radii in
+    place and in radius order: F_max, idx and the counters to compare with."""
+    import paper_2510_02873_gb300 as cc
+    R, _, n = stack.shape
+    buf = torch.zeros((R, 6, ps), dtype=torch.float32, device="cuda")
+    buf[:, :, :n] = torch.from_numpy(stack).cuda()
+    F = torch.zeros(n, dtype=torch.float64, device="cuda")
+    idx = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    b = cc.Batch(ctx, [(buf[:, :, :n], sig, F, idx, 0)], mode="mixed")
+    ctx.reset_stats()
+    b.run()
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    b.close()
+    return F.cpu().numpy(), idx.cpu().numpy(), st
+
+
+def test_mixed_hard_record_overflow(ctx, tables):
+    """24,000 points that nearly all have hard radii against a record capacity
+    of 2,368 (n (0.006 R + 0.02) + 1024 at R = 6): most points are marked and
+    recomputed in radius order by the second kernel. Bit-identical to the
+    batched kernel's in-place evaluation, with the same counters, and within
+    3e-5 of the oracle."""
+    rng = np.random.default_rng(37)
+    hard = _degenerate_matrices(rng)
+    n, R = 24000, 6
+    sig = [0.6, 1.0, 1.4, 2.0, 2.8, 4.0]
+    cols = rng.integers(0, hard.shape[1], (R, n))
+    stack = np.stack([hard[:, cols[r]] * sig[r] for r in range(R)]).astype(np.float32)
+    easy = hessgen.hessian_stack(41, 0, sig, n, dtype=np.float32)
+    mix = rng.random((R, n)) < 0.2
+    stack = np.where(mix[:, None, :], easy, stack).astype(np.float32)
+    ps = n + 4
+    F, idx, st = run_mixed(ctx, stack, sig, plane_stride=ps)
+    Fb, ib, stb = _batch_mixed(ctx, stack, sig, ps)
+    assert np.array_equal(F, Fb) and np.array_equal(idx, ib)
+    for k in ("evaluations", "collapsed", "eds_branch", "refined", "fp64_branch"):
+        assert st[k] == stb[k], (k, st[k], stb[k])
+    assert st["fp64_branch"] > 0.1 * n * R  # most points carry hard radii: far beyond the capacity
+    F_all, fl = oracle_per_radius(tables, stack)
+    s = compare_mixed(F, idx, F_all, fl)
+    print("mixed, record overflow", s, st)
+
+
+def test_mixed_hard_radii_above_32(ctx, tables):
+    """40 radii with hard matrices on both sides of radius 32: radii below 32
+    travel as bits of the record, the others are found again by the second
+    kernel. Bit-identical to the batched kernel and within 3e-5 of the oracle."""
+    rng = np.random.default_rng(43)
+    n, R = 2500, 40
+    sig = hessgen.sigma_schedule(R, 0.3, 5.0)
+    stack = hessgen.hessian_stack(2543, 0, sig, n, dtype=np.float32)
+    hard = _degenerate_matrices(rng).astype(np.float32)
+    for _ in range(3000):
+        p = int(rng.integers(0, n))
+        r = int(rng.integers(24, R))
+        stack[r, :, p] = hard[:, int(rng.integers(0, hard.shape[1]))] * np.float32(sig[r])
+    ps = n + 4
+    F, idx, st = run_mixed(ctx, stack, sig, plane_stride=ps)
+    Fb, ib, stb = _batch_mixed(ctx, stack, sig, ps)
+    assert np.array_equal(F, Fb) and np.array_equal(idx, ib)
+    for k in ("evaluations", "collapsed", "eds_branch", "refined", "fp64_branch"):
+        assert st[k] == stb[k], (k, st[k], stb[k])
+    F_all, fl = oracle_per_radius(tables, stack)
+    s = compare_mixed(F, idx, F_all, fl)
+    assert (idx >= 32).sum() > 100
+    print("mixed, hard radii above 32", s, st)
 
 
 def test_mixed_eds_segment_below_first_knot(ctx, tables):
