@@ -625,6 +625,10 @@ __device__ __forceinline__ float newton_f32(const MixedCoef& k, float Df) {
 //     (a result that is not used may be any finite number); t0, c3 Df + c2
 //     and lo(a_0 / D_0) D take to_f64_normal, where a zero shifts t, A_1 or a
 //     by less than 2^-126.
+// kEds = false: the caller sends EdS collapses (res.eds) elsewhere and uses
+// only the other results, so the EdS operand selects are left out; every
+// result with res.eds false is the same as with kEds = true.
+template <bool kEds = true>
 __device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const MixedCoef& k, float Df,
                                                     const Coef4* __restrict__ coef, const float* __restrict__ Dkf,
                                                     const unsigned short* __restrict__ bucket, const DevTable& tab) {
@@ -640,9 +644,10 @@ __device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const M
   res.eds = res.collapsed && Df < Dkf[0];
   const float4 s0 = __ldg(tab.dfseg + 2 * kk);      // {hi(c0), lo(c0), hi(c1), lo(c1)}
   const float4 s1 = __ldg(tab.dfseg + 2 * kk + 1);  // {c2, c3, hi(D_k), lo(D_k)}
-  const float t0 = res.eds ? Dcf : __fsub_rn(__fsub_rn(Dcf, s1.z), s1.w);
-  const float v = res.eds ? tab.eds_hi : fmaf(fmaf(s1.y, t0, s1.x), t0, s0.z);
-  const double head = res.eds ? to_f64_normal(tab.eds_lo * Dcf) : coef[kk].c0;
+  const bool eds = kEds && res.eds;
+  const float t0 = eds ? Dcf : __fsub_rn(__fsub_rn(Dcf, s1.z), s1.w);
+  const float v = eds ? tab.eds_hi : fmaf(fmaf(s1.y, t0, s1.x), t0, s0.z);
+  const double head = eds ? to_f64_normal(tab.eds_lo * Dcf) : coef[kk].c0;
   const double t = fma(-A1, to_f64_neg(rcp_seed(dAf)), to_f64_normal(t0));
   const double av = fma(to_f64_pos(v), t, head);
   res.a = res.collapsed ? av : kInf;

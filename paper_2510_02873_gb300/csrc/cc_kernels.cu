@@ -68,13 +68,14 @@ struct MixedCounts {
 // One radius that needs nothing beyond the FP32 stages, the FP64 polish and
 // the spline (m from mixed_eigen_f32 with neither m.full nor m.need64): the
 // same steps, and so the same result, as collapse_point_mixed.
+template <bool kEds = true>
 __device__ __forceinline__ MixedResult mixed_easy(const MixedEigen& m, const Coef4* __restrict__ coef,
                                                   const float* __restrict__ Dkf,
                                                   const unsigned short* __restrict__ bucket, const DevTable& tab) {
   const MixedCoef k = mixed_coef(m);
   const float uf = cubic_largest_root_seed(-k.l1f, k.c2f, k.c3f);
   const float Df = newton_f32<1>(k, __fdividef(1.0f, uf));
-  return mixed_finish(m, k, Df, coef, Dkf, bucket, tab);
+  return mixed_finish<kEds>(m, k, Df, coef, Dkf, bucket, tab);
 }
 
 constexpr int32_t kHardHigh = 0x10000;  // HardRec::r1: hard radii >= 32
@@ -170,13 +171,15 @@ mixed_hard_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride, i
         const MixedEigen me = mixed_eigen_f32(v.xx, v.yy, v.zz, v.xy, v.xz, v.yz, rp.tri_thr[r]);
         if (me.full) {
           full_hi = true;
-        } else if (me.need64) {
-          MixedEigen mr = me;
-          mixed_refine64(mr, v.xx, v.yy, v.zz, v.xy, v.xz, v.yz);
-          const MixedResult res = mixed_easy(mr, tab.coef, tab.Df, tab.bucket, tab);
-          cn.add(res);
-          best.add_any_order(res.collapsed, res.a, r);
+          continue;
         }
+        // every other radius: the main kernel left out the refined ones and
+        // the EdS ones; merging one it kept again leaves the minimum as it is
+        MixedEigen mr = me;
+        if (me.need64) mixed_refine64(mr, v.xx, v.yy, v.zz, v.xy, v.xz, v.yz);
+        const MixedResult res = mixed_easy(mr, tab.coef, tab.Df, tab.bucket, tab);
+        if (me.need64 || res.eds) cn.add(res);
+        best.add_any_order(res.collapsed, res.a, r);
       }
     }
     if (full != 0u || full_hi) {
@@ -342,20 +345,23 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
           const float xy = ldf(h + 3 * plane_stride), xz = ldf(h + 4 * plane_stride);
           const float yz = ldf(h + 5 * plane_stride);
           const MixedEigen m = mixed_eigen_f32(xx, yy, zz, xy, xz, yz, rp.tri_thr[r]);
-          if (!(m.full || m.need64)) {
-            const MixedResult res = mixed_easy(m, coef, Dkf, bucket, tab);
-            cn.add(res);
-            best.add(res.collapsed, res.a, r);
-          } else if (r < 32) {
-            mask |= 1u << r;
-          } else {
-            hi = true;
+          bool later = m.full || m.need64;
+          if (!later) {
+            // collapse before the first knot (the EdS segment) also goes to
+            // the second kernel, so that this loop carries no EdS selects
+            const MixedResult res = mixed_easy<false>(m, coef, Dkf, bucket, tab);
+            later = res.eds;
+            cn.coll += res.collapsed && !later;
+            best.add(res.collapsed && !later, res.a, r);
+          }
+          if (later) {
+            if (r < 32) mask |= 1u << r;
+            else hi = true;
           }
         }
         n_eval += R;
       }
       n_coll += cn.coll;
-      n_eds += cn.eds;
       mixed_record_or_store(active, p, best, mask, hi, hw, F_max, idx, scale_idx0);
     } else if (kMode == kModeFP64 && active) {
       // kFp64Radii radii per iteration: independent FP64 chains that the
