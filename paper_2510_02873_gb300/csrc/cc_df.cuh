@@ -138,7 +138,7 @@ __device__ __forceinline__ Result collapse_point(const T* __restrict__ h, int64_
   const float pf = sqrt_seed(p2f);
   float rf = (p2f > 0.0f) ? __fdividef(det.hi, 2.0f * p2f * pf) : 0.0f;
   rf = fminf(1.0f, fmaxf(-1.0f, rf));
-  const float x1f = 2.0f * pf * __cosf(acos_seed(rf) * (1.0f / 3.0f));
+  const float x1f = 2.0f * pf * cos_third_acos(rf);
   // ---- two Newton corrections on x (x^2 - 3p^2) - det (FP32 derivative at each iterate)
   f2 x;
   {
