@@ -19,7 +19,7 @@
 #include <string>
 #include <vector>
 
-#include "cc_device.cuh"
+#include "cc_mixed.cuh"
 
 namespace cc {
 
@@ -37,45 +37,86 @@ namespace {
 
 template <typename T>
 __device__ __forceinline__ double ldd(const T* p) { return static_cast<double>(__ldg(p)); }
-template <typename T>
-__device__ __forceinline__ float ldf2(const T* p) { return static_cast<float>(__ldg(p)); }
 
-template <typename T, bool kMixed>
-__device__ __forceinline__ void run_point(const BatchItemDev& it, int64_t p, const double* Dk, const Coef4* coef,
-                                          const float* Dkf, const unsigned short* bucket, const DevTable& tab,
-                                          unsigned& n_coll, unsigned& n_eds, unsigned& n_ref, unsigned& n_fp64) {
+// The launch's counts, reduced per warp and added once per warp.
+__device__ __forceinline__ void batch_counters(DevCounters* cnt, unsigned n_eval, unsigned n_coll, unsigned n_eds,
+                                               unsigned n_ref, unsigned n_fp64) {
+  n_eval = __reduce_add_sync(0xffffffffu, n_eval);
+  n_coll = __reduce_add_sync(0xffffffffu, n_coll);
+  n_eds = __reduce_add_sync(0xffffffffu, n_eds);
+  n_ref = __reduce_add_sync(0xffffffffu, n_ref);
+  n_fp64 = __reduce_add_sync(0xffffffffu, n_fp64);
+  if ((threadIdx.x & 31) == 0) {
+    if (n_eval) atomicAdd(&cnt->evaluations, static_cast<unsigned long long>(n_eval));
+    if (n_coll) atomicAdd(&cnt->collapsed, static_cast<unsigned long long>(n_coll));
+    if (n_eds) atomicAdd(&cnt->eds_branch, static_cast<unsigned long long>(n_eds));
+    if (n_ref) atomicAdd(&cnt->refined, static_cast<unsigned long long>(n_ref));
+    if (n_fp64) atomicAdd(&cnt->fp64_branch, static_cast<unsigned long long>(n_fp64));
+  }
+}
+
+// FP64 mode: one point, all radii in order.
+template <typename T>
+__device__ __forceinline__ void run_point_fp64(const BatchItemDev& it, int64_t p, const double* Dk, const Coef4* coef,
+                                               const float* Dkf, const unsigned short* bucket, const DevTable& tab,
+                                               unsigned& n_coll, unsigned& n_eds, unsigned& n_ref) {
   MinA best;
   const T* base = static_cast<const T*>(it.hess) + p;
   const int64_t ps = it.plane_stride;
   for (int r = 0; r < it.R; ++r) {
     const T* h = base + static_cast<int64_t>(r) * it.radius_stride;
-    if constexpr (kMixed) {
-      const MixedResult res = collapse_point_mixed(ldf2(h), ldf2(h + ps), ldf2(h + 2 * ps), ldf2(h + 3 * ps),
-                                                   ldf2(h + 4 * ps), ldf2(h + 5 * ps), __ldg(it.tri_thr + r),
-                                                   Dk, coef, Dkf, bucket, tab);
-      n_coll += res.collapsed;
-      n_eds += res.eds;
-      n_ref += res.refined;
-      n_fp64 += res.fp64;
-      best.add(res.collapsed, res.a, r);
-    } else {
-      const PointResult res = collapse_point_fp64(ldd(h), ldd(h + ps), ldd(h + 2 * ps), ldd(h + 3 * ps),
-                                                  ldd(h + 4 * ps), ldd(h + 5 * ps), Dk, coef, Dkf, bucket, tab);
-      n_coll += res.collapsed;
-      n_eds += res.eds;
-      n_ref += res.refined;
-      best.add(res.collapsed, res.a, r);
+    const PointResult res = collapse_point_fp64(ldd(h), ldd(h + ps), ldd(h + 2 * ps), ldd(h + 3 * ps),
+                                                ldd(h + 4 * ps), ldd(h + 5 * ps), Dk, coef, Dkf, bucket, tab);
+    n_coll += res.collapsed;
+    n_eds += res.eds;
+    n_ref += res.refined;
+    best.add(res.collapsed, res.a, r);
+  }
+  best.store<false>(it.F_max + p, it.idx + p, it.scale_idx0);
+}
+
+// Mixed mode: one point, as the per-launch mixed kernel does it: the hard and
+// EdS radii are marked, and a point with any leaves a record (key: batch item
+// << kItemShift | point) for the two follow-up kernels (cc_mixed.cuh). All 32
+// lanes of the warp call this (inactive lanes with active = false).
+constexpr int kItemShift = 40;
+template <typename T>
+__device__ __forceinline__ void run_point_mixed(const BatchItemDev& it, int item, int64_t p, bool active,
+                                                const Coef4* coef, const float* Dkf, const unsigned short* bucket,
+                                                const DevTable& tab, const HardWork& hw, unsigned& n_coll) {
+  MinA best;
+  uint32_t mask = 0;
+  bool hi = false;
+  if (active) {
+    const T* base = static_cast<const T*>(it.hess) + p;
+    for (int r = 0; r < it.R; ++r) {
+      const Planes6 v = load6(base + static_cast<int64_t>(r) * it.radius_stride, it.plane_stride);
+      const MixedEigen m = mixed_eigen_f32(v.xx, v.yy, v.zz, v.xy, v.xz, v.yz, __ldg(it.tri_thr + r));
+      bool later = m.full || m.need64;
+      if (!later) {
+        const MixedResult res = mixed_easy<false>(m, coef, Dkf, bucket, tab);
+        later = res.eds;
+        n_coll += res.collapsed && !later;
+        best.add(res.collapsed && !later, res.a, r);
+      }
+      if (later) {
+        if (r < 32) mask |= 1u << r;
+        else hi = true;
+      }
     }
   }
-  best.store<kMixed>(it.F_max + p, it.idx + p, it.scale_idx0);
+  const int64_t key = (static_cast<int64_t>(item) << kItemShift) | p;
+  mixed_record_or_store(active, key, best, mask, hi, hw, it.F_max + (active ? p : 0), it.idx + (active ? p : 0),
+                        it.scale_idx0);
 }
 
 template <bool kMixed, int kBlock>
 __global__ void __launch_bounds__(kBlock, (kMixed ? 1536 : 1024) / kBlock)
 batched_kernel(const BatchItemDev* __restrict__ items, int nitems, int64_t total_tiles,
-               unsigned long long* __restrict__ work, DevTable tab, DevCounters* __restrict__ cnt) {
+               unsigned long long* __restrict__ work, DevTable tab, HardWork hw, DevCounters* __restrict__ cnt) {
   extern __shared__ Coef4 smem_tab[];
   __shared__ long long s_tile;
+  __shared__ int s_item;
   __shared__ BatchItemDev s_it;
   {  // table image to shared memory (16-byte words)
     const int words = static_cast<int>(tab.bytes() / 16);
@@ -91,7 +132,7 @@ batched_kernel(const BatchItemDev* __restrict__ items, int nitems, int64_t total
   const double* Dk = reinterpret_cast<const double*>(smem_tab + (tab.n - 1));
   const float* Dkf = reinterpret_cast<const float*>(Dk + tab.n);
   const unsigned short* bucket = reinterpret_cast<const unsigned short*>(Dkf + tab.n);
-  unsigned n_eval = 0, n_coll = 0, n_eds = 0, n_ref = 0, n_fp64 = 0;
+  unsigned n_eval = 0, n_coll = 0, n_eds = 0, n_ref = 0;
   for (;;) {
     if (threadIdx.x == 0) {
       const long long t = static_cast<long long>(atomicAdd(work, 1ULL));
@@ -101,6 +142,7 @@ batched_kernel(const BatchItemDev* __restrict__ items, int nitems, int64_t total
         if (items[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
       }
       s_tile = t;
+      s_item = lo;
       if (t < total_tiles) s_it = items[lo];
     }
     __syncthreads();  // also orders the table staging before first use
@@ -109,27 +151,99 @@ batched_kernel(const BatchItemDev* __restrict__ items, int nitems, int64_t total
     const BatchItemDev& it = s_it;  // read from shared memory (keeps registers for the point)
     const int64_t p0 = (t - it.tile_begin) * it.tile_points;
     const int64_t p1 = min(p0 + it.tile_points, it.n);
-    for (int64_t p = p0 + threadIdx.x; p < p1; p += kBlock) {
-      if (it.dtype == CC_F32)
-        run_point<float, kMixed>(it, p, Dk, coef, Dkf, bucket, tab, n_coll, n_eds, n_ref, n_fp64);
-      else
-        run_point<double, kMixed>(it, p, Dk, coef, Dkf, bucket, tab, n_coll, n_eds, n_ref, n_fp64);
-      n_eval += it.R;
+    if constexpr (kMixed) {
+      // whole warps step together (the record step is warp-wide)
+      for (int64_t pb = p0; pb < p1; pb += kBlock) {
+        const int64_t p = pb + threadIdx.x;
+        const bool active = p < p1;
+        if (it.dtype == CC_F32)
+          run_point_mixed<float>(it, s_item, p, active, coef, Dkf, bucket, tab, hw, n_coll);
+        else
+          run_point_mixed<double>(it, s_item, p, active, coef, Dkf, bucket, tab, hw, n_coll);
+        if (active) n_eval += it.R;
+      }
+    } else {
+      for (int64_t p = p0 + threadIdx.x; p < p1; p += kBlock) {
+        if (it.dtype == CC_F32)
+          run_point_fp64<float>(it, p, Dk, coef, Dkf, bucket, tab, n_coll, n_eds, n_ref);
+        else
+          run_point_fp64<double>(it, p, Dk, coef, Dkf, bucket, tab, n_coll, n_eds, n_ref);
+        n_eval += it.R;
+      }
     }
     __syncthreads();  // every thread is done with s_it before thread 0 takes the next tile
   }
-  n_eval = __reduce_add_sync(0xffffffffu, n_eval);
-  n_coll = __reduce_add_sync(0xffffffffu, n_coll);
-  n_eds = __reduce_add_sync(0xffffffffu, n_eds);
-  n_ref = __reduce_add_sync(0xffffffffu, n_ref);
-  n_fp64 = __reduce_add_sync(0xffffffffu, n_fp64);
-  if ((threadIdx.x & 31) == 0) {
-    if (n_eval) atomicAdd(&cnt->evaluations, static_cast<unsigned long long>(n_eval));
-    if (n_coll) atomicAdd(&cnt->collapsed, static_cast<unsigned long long>(n_coll));
-    if (n_eds) atomicAdd(&cnt->eds_branch, static_cast<unsigned long long>(n_eds));
-    if (n_ref) atomicAdd(&cnt->refined, static_cast<unsigned long long>(n_ref));
-    if (n_fp64) atomicAdd(&cnt->fp64_branch, static_cast<unsigned long long>(n_fp64));
+  batch_counters(cnt, n_eval, n_coll, n_eds, n_ref, 0u);
+}
+
+// The mixed batch's recorded points (second kernel) and, after an overflow,
+// its marked points; see hard_record and recompute_marked.
+constexpr int kHardThreads = 128;
+constexpr int64_t kPointMask = (int64_t{1} << kItemShift) - 1;
+
+__global__ void __launch_bounds__(kHardThreads)
+batch_hard_kernel(const BatchItemDev* __restrict__ items, int nitems, DevTable tab, HardWork hw,
+                  DevCounters* __restrict__ cnt) {
+  const unsigned long long req = hw.ctr[0];
+  const int64_t nrec = req < static_cast<unsigned long long>(hw.cap) ? static_cast<int64_t>(req) : hw.cap;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  MixedCounts cn;
+  for (int64_t i = t0; i < nrec; i += stride) {
+    const HardRec rec = hw.rec[i];
+    int item = static_cast<int>(rec.p >> kItemShift);
+    CC_DBG_CLAMP(item, 0, nitems - 1, tab.dbg);
+    const BatchItemDev& it = items[item];
+    const int64_t p = rec.p & kPointMask;
+    if (it.dtype == CC_F32)
+      hard_record(ItemSrc<float>{static_cast<const float*>(it.hess), it.plane_stride, it.radius_stride, it.R,
+                                 it.tri_thr, it.F_max, it.idx, it.scale_idx0}, rec, p, i, hw, tab, cn);
+    else
+      hard_record(ItemSrc<double>{static_cast<const double*>(it.hess), it.plane_stride, it.radius_stride, it.R,
+                                  it.tri_thr, it.F_max, it.idx, it.scale_idx0}, rec, p, i, hw, tab, cn);
   }
+  if (hw.ctr[1] != 0ull) {
+    for (int item = 0; item < nitems; ++item) {
+      const BatchItemDev& it = items[item];
+      for (int64_t p = t0; p < it.n; p += stride) {
+        const int32_t mark = it.idx[p];
+        if (mark > -2) continue;
+        it.idx[p] = -mark - 3;
+        if (it.dtype == CC_F32)
+          recompute_marked(ItemSrc<float>{static_cast<const float*>(it.hess), it.plane_stride, it.radius_stride, it.R,
+                                          it.tri_thr, it.F_max, it.idx, it.scale_idx0}, p, tab, cn);
+        else
+          recompute_marked(ItemSrc<double>{static_cast<const double*>(it.hess), it.plane_stride, it.radius_stride,
+                                           it.R, it.tri_thr, it.F_max, it.idx, it.scale_idx0}, p, tab, cn);
+      }
+    }
+  }
+  batch_counters(cnt, 0u, cn.coll, cn.eds, cn.ref, cn.fp64);
+}
+
+// The mixed batch's records left with radii on the whole FP64 path (third kernel).
+__global__ void __launch_bounds__(kHardThreads)
+batch_full_kernel(const BatchItemDev* __restrict__ items, int nitems, DevTable tab, HardWork hw,
+                  DevCounters* __restrict__ cnt) {
+  const int64_t nfull = static_cast<int64_t>(hw.ctr[2]);
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  MixedCounts cn;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nfull; i += stride) {
+    int64_t ri = hw.full[i];
+    CC_DBG_CLAMP(ri, static_cast<int64_t>(0), hw.cap - 1, tab.dbg);
+    const HardRec rec = hw.rec[ri];
+    int item = static_cast<int>(rec.p >> kItemShift);
+    CC_DBG_CLAMP(item, 0, nitems - 1, tab.dbg);
+    const BatchItemDev& it = items[item];
+    const int64_t p = rec.p & kPointMask;
+    if (it.dtype == CC_F32)
+      full_record(ItemSrc<float>{static_cast<const float*>(it.hess), it.plane_stride, it.radius_stride, it.R,
+                                 it.tri_thr, it.F_max, it.idx, it.scale_idx0}, rec, p, tab, cn);
+    else
+      full_record(ItemSrc<double>{static_cast<const double*>(it.hess), it.plane_stride, it.radius_stride, it.R,
+                                  it.tri_thr, it.F_max, it.idx, it.scale_idx0}, rec, p, tab, cn);
+  }
+  batch_counters(cnt, 0u, cn.coll, cn.eds, cn.ref, cn.fp64);
 }
 
 constexpr int kTileCandidates[] = {256, 512, 1024, 2048, 4096, 8192};
@@ -156,6 +270,12 @@ struct cc_batch {
   BatchItemDev* d_items = nullptr;
   float* d_thr = nullptr;
   unsigned long long* d_work = nullptr;
+  // mixed mode: records of the points with hard radii (cc::HardRec, shared
+  // by every item; the key packs the item above bit 40)
+  cc::HardRec* d_hard = nullptr;
+  uint32_t* d_hard_full = nullptr;
+  int64_t hard_cap = 0;
+  unsigned long long* d_hard_ctr = nullptr;
   int64_t total_tiles = 0;
   bool dirty = true;                    // device item table needs an upload
   cudaGraphExec_t graph_exec = nullptr;
@@ -218,9 +338,22 @@ int launch_batch_t(cc_batch* b, cudaStream_t st) {
   if (grid <= 0) return CC_OK;
   DevTable t = tab;  // the index checks of debug builds report into the context's flags
   t.dbg = &b->ctx->d_counters->error_flags;
-  kern<<<grid, kBlock, smem, st>>>(b->d_items, static_cast<int>(b->items.size()), b->total_tiles, b->d_work,
-                                   t, b->ctx->d_counters);
-  return check_cuda(cudaGetLastError(), "batched_kernel launch");
+  const HardWork hw{b->d_hard, b->hard_cap, b->d_hard_ctr, b->d_hard_full};
+  const int nitems = static_cast<int>(b->items.size());
+  if (kMixed)
+    if (int rc = check_cuda(cudaMemsetAsync(b->d_hard_ctr, 0, kHardCounters * sizeof(unsigned long long), st),
+                            "cudaMemsetAsync(hard records)"))
+      return rc;
+  kern<<<grid, kBlock, smem, st>>>(b->d_items, nitems, b->total_tiles, b->d_work, t, hw, b->ctx->d_counters);
+  if (int rc = check_cuda(cudaGetLastError(), "batched_kernel launch")) return rc;
+  if (kMixed) {
+    const int g2 = 4 * b->ctx->num_sms;
+    batch_hard_kernel<<<g2, kHardThreads, 0, st>>>(b->d_items, nitems, t, hw, b->ctx->d_counters);
+    if (int rc = check_cuda(cudaGetLastError(), "batch_hard_kernel launch")) return rc;
+    batch_full_kernel<<<g2, kHardThreads, 0, st>>>(b->d_items, nitems, t, hw, b->ctx->d_counters);
+    return check_cuda(cudaGetLastError(), "batch_full_kernel launch");
+  }
+  return CC_OK;
 }
 
 int launch_batch(cc_batch* b, cudaStream_t st) {
@@ -256,15 +389,18 @@ int cc_batch_create(cc_ctx* ctx, cc_mode mode, const cc_batch_item* items, int32
   if (!out) return set_error(CC_EINVAL, "out is NULL");
   *out = nullptr;
   if (!ctx || !items || nitems < 1) return set_error(CC_EINVAL, "ctx, items and nitems >= 1 are required");
+  if (nitems >= (1 << 23)) return set_error(CC_EINVAL, "at most 2^23 - 1 items");
   if (mode != CC_MODE_FP64 && mode != CC_MODE_MIXED)
     return set_error(CC_ENOTSUP, "batched launch supports CC_MODE_FP64 and CC_MODE_MIXED");
   size_t total_r = 0;
+  int64_t hard_want = 0, points = 0;
   for (int i = 0; i < nitems; ++i) {
     const cc_batch_item& it = items[i];
     char where[64];
     std::snprintf(where, sizeof(where), "item %d: ", i);
     if (it.dtype != CC_F64 && it.dtype != CC_F32) return set_error(CC_EINVAL, std::string(where) + "bad dtype");
     if (it.n < 1 || !it.hess || !it.F_max || !it.idx) return set_error(CC_EINVAL, std::string(where) + "n >= 1 and non-NULL pointers required");
+    if (it.n >= (int64_t{1} << kItemShift)) return set_error(CC_EINVAL, std::string(where) + "n must be below 2^40");
     if (it.R < 1 || it.R > kMaxRadiiPerLaunch || !it.sigma) return set_error(CC_EINVAL, std::string(where) + "R must be in [1, 256] with sigma");
     if (it.plane_stride < it.n || (it.R > 1 && it.radius_stride < 6 * it.plane_stride))
       return set_error(CC_EINVAL, std::string(where) + "strides too small");
@@ -275,7 +411,14 @@ int cc_batch_create(cc_ctx* ctx, cc_mode mode, const cc_batch_item* items, int32
     for (int r = 0; r < it.R; ++r)
       if (!(it.sigma[r] > 0.0) || !std::isfinite(it.sigma[r])) return set_error(CC_EINVAL, std::string(where) + "sigma must be > 0");
     total_r += static_cast<size_t>(it.R);
+    // record capacity of the mixed mode: as for one launch (cc_api.cu)
+    const double frac = 0.006 * it.R + 0.02;
+    hard_want += frac >= 1.0 ? it.n : static_cast<int64_t>(static_cast<double>(it.n) * frac);
+    points += it.n;
   }
+  hard_want += 1024;
+  if (hard_want > points) hard_want = points;
+  if (hard_want > static_cast<int64_t>(UINT32_MAX)) hard_want = static_cast<int64_t>(UINT32_MAX);
   int cur = -1;
   if (int rc = check_cuda(cudaGetDevice(&cur), "cudaGetDevice")) return rc;
   if (cur != ctx->device)
@@ -293,6 +436,15 @@ int cc_batch_create(cc_ctx* ctx, cc_mode mode, const cc_batch_item* items, int32
   int rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&b->d_items), sizeof(BatchItemDev) * nitems), "cudaMalloc(items)");
   if (!rc) rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&b->d_thr), sizeof(float) * total_r), "cudaMalloc(thresholds)");
   if (!rc) rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&b->d_work), sizeof(unsigned long long)), "cudaMalloc(work)");
+  if (!rc && mode == CC_MODE_MIXED) {
+    b->hard_cap = hard_want;
+    rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&b->d_hard), sizeof(HardRec) * static_cast<size_t>(hard_want)),
+                    "cudaMalloc(hard records)");
+    if (!rc) rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&b->d_hard_full), sizeof(uint32_t) * static_cast<size_t>(hard_want)),
+                             "cudaMalloc(hard record list)");
+    if (!rc) rc = check_cuda(cudaMalloc(reinterpret_cast<void**>(&b->d_hard_ctr), kHardCounters * sizeof(unsigned long long)),
+                             "cudaMalloc(hard record counters)");
+  }
   if (!rc) rc = check_cuda(cudaMemcpy(b->d_thr, thr_flat.data(), sizeof(float) * total_r, cudaMemcpyHostToDevice), "cudaMemcpy(thresholds)");
   if (!rc) rc = upload_items(b, nullptr);
   if (rc) { cc_batch_destroy(b); return rc; }
@@ -307,6 +459,9 @@ void cc_batch_destroy(cc_batch* b) {
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_thr) cudaFree(b->d_thr);
   if (b->d_work) cudaFree(b->d_work);
+  if (b->d_hard) cudaFree(b->d_hard);
+  if (b->d_hard_full) cudaFree(b->d_hard_full);
+  if (b->d_hard_ctr) cudaFree(b->d_hard_ctr);
   delete b;
 }
 

@@ -9,6 +9,7 @@
 // and written once per point per launch.
 #include "cc_df.cuh"
 #include "cc_exact.cuh"
+#include "cc_mixed.cuh"
 
 namespace cc {
 
@@ -43,101 +44,17 @@ __device__ __forceinline__ void add_counters(DevCounters* cnt, unsigned evals, u
 constexpr int kModeFP64 = 0, kModeMixed = 1, kModeTab = 2, kModeF32x2 = 3, kModeExact = 4;
 constexpr int kFp64Radii = 2;  // radii per loop iteration of the FP64 path
 
-// ---- mixed path. About 0.5 % of the evaluations need FP64 work beyond the
-// polish and the spline (the FP64 refinement of l1, or the whole FP64 path
-// near degeneracy). That code beside the radius loop, run in place or from a
-// per-warp queue, takes the loop's registers: at 40 registers the loop alone
-// does not spill, with the FP64 path inlined next to it 220 bytes spill and
-// the kernel runs 14 % slower. So the main kernel only marks those radii
-// (a bit per radius below 32, a flag for the others) and, for a point that
-// has any, writes a record (HardRec) instead of its result; mixed_hard_kernel
-// evaluates the marked radii with collapse_point_mixed and finishes the
-// point. The running minimum merges them out of radius order with ties to
-// the smaller radius, so F_max and idx are those of the in-order loop.
-
-struct MixedCounts {
-  unsigned coll = 0, eds = 0, ref = 0, fp64 = 0;
-  __device__ __forceinline__ void add(const MixedResult& res) {
-    coll += res.collapsed;
-    eds += res.eds;
-    ref += res.refined;
-    fp64 += res.fp64;
-  }
-};
-
-// One radius that needs nothing beyond the FP32 stages, the FP64 polish and
-// the spline (m from mixed_eigen_f32 with neither m.full nor m.need64): the
-// same steps, and so the same result, as collapse_point_mixed.
-template <bool kEds = true>
-__device__ __forceinline__ MixedResult mixed_easy(const MixedEigen& m, const Coef4* __restrict__ coef,
-                                                  const float* __restrict__ Dkf,
-                                                  const unsigned short* __restrict__ bucket, const DevTable& tab) {
-  const MixedCoef k = mixed_coef(m);
-  const float uf = cubic_largest_root_seed(-k.l1f, k.c2f, k.c3f);
-  const float Df = newton_f32<1>(k, __fdividef(1.0f, uf));
-  return mixed_finish<kEds>(m, k, Df, coef, Dkf, bucket, tab);
-}
-
-constexpr int32_t kHardHigh = 0x10000;  // HardRec::r1: hard radii >= 32
-
-// End of a point in the main kernel. All 32 lanes of the warp call this. A
-// point without hard radii stores its result; the others take consecutive
-// record slots (one atomic per warp). A point whose slot is beyond the
-// capacity keeps F_max and marks idx as -(idx + 3) (idx is -1 or a radius
-// index, so the mark is <= -2) for the second kernel to recompute in order.
-__device__ __forceinline__ void mixed_record_or_store(bool active, int64_t p, const MinA& best, uint32_t mask,
-                                                      bool hi, const HardWork& hw, double* __restrict__ F_max,
-                                                      int32_t* __restrict__ idx, int32_t scale_idx0) {
-  const bool need = active && (mask != 0u || hi);
-  const unsigned bal = __ballot_sync(0xffffffffu, need);
-  if (bal != 0u) {
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(bal) - 1;
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(hw.ctr, static_cast<unsigned long long>(__popc(bal)));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (need) {
-      const unsigned long long slot = base + static_cast<unsigned>(__popc(bal & ((1u << lane) - 1u)));
-      if (slot < static_cast<unsigned long long>(hw.cap)) {
-        HardRec rec;
-        rec.p = p;
-        rec.a = best.a;
-        rec.mask = mask;
-        rec.r1 = (best.r + 1) | (hi ? kHardHigh : 0);
-        hw.rec[slot] = rec;
-      } else {
-        idx[p] = -idx[p] - 3;
-        atomicOr(hw.ctr + 1, 1ull);
-      }
-    }
-  }
-  if (active && !need) best.store<true>(F_max + p, idx + p, scale_idx0);
-}
-
+// ---- mixed path: the main kernel (collapse_kernel) marks the hard radii and
+// writes records; mixed_hard_kernel and mixed_full_kernel finish those points
+// (see cc_mixed.cuh).
 constexpr int kHardThreads = 128;
 
-template <typename T>
-struct Planes6 {
-  float xx, yy, zz, xy, xz, yz;
-  __device__ __forceinline__ Planes6(const T* h, int64_t ps)
-      : xx(ldf(h)), yy(ldf(h + ps)), zz(ldf(h + 2 * ps)), xy(ldf(h + 3 * ps)), xz(ldf(h + 4 * ps)),
-        yz(ldf(h + 5 * ps)) {}
-};
-
-// The recorded points (second kernel), one thread per record: each hard radius
-// gets mixed_eigen (with the FP64 refinement of l1 where flagged) and the
-// mixed path's finish; radii that need the whole FP64 path are left in the
-// record (its mask and running minimum updated) and the record joins the
-// `full` list for mixed_full_kernel, so that the few lanes on that path do
-// not hold up a warp of short evaluations. Points marked after an overflow
-// are recomputed here in radius order, every path in place. Counts what the
-// main kernel left out: collapses, EdS and FP64 evaluations of the hard radii
-// (the evaluations themselves were counted there).
 template <typename T>
 __global__ void __launch_bounds__(kHardThreads)
 mixed_hard_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride, int64_t radius_stride, int R,
                   int32_t scale_idx0, DevTable tab, RadiusParams rp, HardWork hw, double* __restrict__ F_max,
                   int32_t* __restrict__ idx, DevCounters* __restrict__ cnt) {
+  const LaunchSrc<T> src{hess, plane_stride, radius_stride, R, rp, F_max, idx, scale_idx0};
   const unsigned long long req = hw.ctr[0];
   const int64_t nrec = req < static_cast<unsigned long long>(hw.cap) ? static_cast<int64_t>(req) : hw.cap;
   const bool overflow = hw.ctr[1] != 0ull;
@@ -145,88 +62,28 @@ mixed_hard_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride, i
   const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   MixedCounts cn;
   for (int64_t i = t0; i < nrec; i += stride) {
-    HardRec rec = hw.rec[i];
-    CC_DBG_CLAMP(rec.p, static_cast<int64_t>(0), n - 1, tab.dbg);
-    MinA best;
-    best.a = rec.a;
-    best.r = (rec.r1 & 0xffff) - 1;
-    const T* base = hess + rec.p;
-    uint32_t full = 0;
-    bool full_hi = false;
-    for (uint32_t m = rec.mask; m != 0u; m &= m - 1u) {
-      const int r = __ffs(m) - 1;
-      const Planes6<T> v(base + static_cast<int64_t>(r) * radius_stride, plane_stride);
-      const MixedEigen me = mixed_eigen(v.xx, v.yy, v.zz, v.xy, v.xz, v.yz, rp.tri_thr[r]);
-      if (me.full) {
-        full |= 1u << r;
-        continue;
-      }
-      const MixedResult res = mixed_easy(me, tab.coef, tab.Df, tab.bucket, tab);
-      cn.add(res);
-      best.add_any_order(res.collapsed, res.a, r);
-    }
-    if (rec.r1 & kHardHigh) {
-      for (int r = 32; r < R; ++r) {
-        const Planes6<T> v(base + static_cast<int64_t>(r) * radius_stride, plane_stride);
-        const MixedEigen me = mixed_eigen_f32(v.xx, v.yy, v.zz, v.xy, v.xz, v.yz, rp.tri_thr[r]);
-        if (me.full) {
-          full_hi = true;
-          continue;
-        }
-        // every other radius: the main kernel left out the refined ones and
-        // the EdS ones; merging one it kept again leaves the minimum as it is
-        MixedEigen mr = me;
-        if (me.need64) mixed_refine64(mr, v.xx, v.yy, v.zz, v.xy, v.xz, v.yz);
-        const MixedResult res = mixed_easy(mr, tab.coef, tab.Df, tab.bucket, tab);
-        if (me.need64 || res.eds) cn.add(res);
-        best.add_any_order(res.collapsed, res.a, r);
-      }
-    }
-    if (full != 0u || full_hi) {
-      rec.a = best.a;
-      rec.mask = full;
-      rec.r1 = (best.r + 1) | (full_hi ? kHardHigh : 0);
-      hw.rec[i] = rec;
-      int64_t k = static_cast<int64_t>(atomicAdd(hw.ctr + 2, 1ull));
-      CC_DBG_CLAMP(k, static_cast<int64_t>(0), hw.cap - 1, tab.dbg);
-      hw.full[k] = static_cast<uint32_t>(i);
-    } else {
-      best.store<true>(F_max + rec.p, idx + rec.p, scale_idx0);
-    }
+    const HardRec rec = hw.rec[i];
+    int64_t p = rec.p;
+    CC_DBG_CLAMP(p, static_cast<int64_t>(0), n - 1, tab.dbg);
+    hard_record(src, rec, p, i, hw, tab, cn);
   }
   if (overflow) {
     for (int64_t p = t0; p < n; p += stride) {
       const int32_t mark = idx[p];
       if (mark > -2) continue;
       idx[p] = -mark - 3;
-      MinA best;
-      for (int r = 0; r < R; ++r) {
-        const Planes6<T> v(hess + p + static_cast<int64_t>(r) * radius_stride, plane_stride);
-        const MixedEigen me = mixed_eigen_f32(v.xx, v.yy, v.zz, v.xy, v.xz, v.yz, rp.tri_thr[r]);
-        MixedResult res;
-        if (me.full || me.need64) {
-          res = collapse_point_mixed(v.xx, v.yy, v.zz, v.xy, v.xz, v.yz, rp.tri_thr[r], tab.D, tab.coef, tab.Df,
-                                     tab.bucket, tab);
-          cn.add(res);
-        } else {
-          res = mixed_easy(me, tab.coef, tab.Df, tab.bucket, tab);
-        }
-        best.add(res.collapsed, res.a, r);
-      }
-      best.store<true>(F_max + p, idx + p, scale_idx0);
+      recompute_marked(src, p, tab, cn);
     }
   }
   add_counters(cnt, 0u, cn.coll, cn.eds, cn.ref, cn.fp64);
 }
 
-// The records left with radii on the whole FP64 path (third kernel): those
-// radii through full_fp64 (what collapse_point_mixed runs for them), merged
-// into the record's running minimum; then the point's result is stored.
 template <typename T>
 __global__ void __launch_bounds__(kHardThreads)
 mixed_full_kernel(const T* __restrict__ hess, int64_t plane_stride, int64_t radius_stride, int R,
                   int32_t scale_idx0, DevTable tab, RadiusParams rp, HardWork hw, double* __restrict__ F_max,
                   int32_t* __restrict__ idx, DevCounters* __restrict__ cnt) {
+  const LaunchSrc<T> src{hess, plane_stride, radius_stride, R, rp, F_max, idx, scale_idx0};
   const int64_t nfull = static_cast<int64_t>(hw.ctr[2]);
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   MixedCounts cn;
@@ -234,27 +91,7 @@ mixed_full_kernel(const T* __restrict__ hess, int64_t plane_stride, int64_t radi
     int64_t ri = hw.full[i];
     CC_DBG_CLAMP(ri, static_cast<int64_t>(0), hw.cap - 1, tab.dbg);
     const HardRec rec = hw.rec[ri];
-    MinA best;
-    best.a = rec.a;
-    best.r = (rec.r1 & 0xffff) - 1;
-    const T* base = hess + rec.p;
-    for (uint32_t m = rec.mask; m != 0u; m &= m - 1u) {
-      const int r = __ffs(m) - 1;
-      const Planes6<T> v(base + static_cast<int64_t>(r) * radius_stride, plane_stride);
-      const MixedResult res = full_fp64(v.xx, v.yy, v.zz, v.xy, v.xz, v.yz, tab.D, tab.coef, tab.Df, tab.bucket, tab);
-      cn.add(res);
-      best.add_any_order(res.collapsed, res.a, r);
-    }
-    if (rec.r1 & kHardHigh) {
-      for (int r = 32; r < R; ++r) {
-        const Planes6<T> v(base + static_cast<int64_t>(r) * radius_stride, plane_stride);
-        if (!mixed_eigen_f32(v.xx, v.yy, v.zz, v.xy, v.xz, v.yz, rp.tri_thr[r]).full) continue;
-        const MixedResult res = full_fp64(v.xx, v.yy, v.zz, v.xy, v.xz, v.yz, tab.D, tab.coef, tab.Df, tab.bucket, tab);
-        cn.add(res);
-        best.add_any_order(res.collapsed, res.a, r);
-      }
-    }
-    best.store<true>(F_max + rec.p, idx + rec.p, scale_idx0);
+    full_record(src, rec, rec.p, tab, cn);
   }
   add_counters(cnt, 0u, cn.coll, cn.eds, cn.ref, cn.fp64);
 }
@@ -362,7 +199,7 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
         n_eval += R;
       }
       n_coll += cn.coll;
-      mixed_record_or_store(active, p, best, mask, hi, hw, F_max, idx, scale_idx0);
+      mixed_record_or_store(active, p, best, mask, hi, hw, F_max + p, idx + p, scale_idx0);
     } else if (kMode == kModeFP64 && active) {
       // kFp64Radii radii per iteration: independent FP64 chains that the
       // compiler interleaves, so the FP64 unit meets fewer gaps while a warp

@@ -221,8 +221,7 @@ def test_mixed_deferred_mixed_radii(ctx, tables):
 
 
 def _batch_mixed(ctx, stack, sig, ps):
-    """The same planes through the batched kernel, which evaluates hard radii in
-    place and in radius order: F_max, idx and the counters to compare with."""
+    """The same planes through the batched kernel: F_max, idx and the counters."""
     import paper_2510_02873_gb300 as cc
     R, _, n = stack.shape
     buf = torch.zeros((R, 6, ps), dtype=torch.float32, device="cuda")
@@ -238,37 +237,48 @@ def _batch_mixed(ctx, stack, sig, ps):
     return F.cpu().numpy(), idx.cpu().numpy(), st
 
 
-def test_mixed_hard_record_overflow(ctx, tables):
-    """24,000 points that nearly all have hard radii against a record capacity
-    of 2,368 (n (0.006 R + 0.02) + 1024 at R = 6): most points are marked and
-    recomputed in radius order by the second kernel. Bit-identical to the
-    batched kernel's in-place evaluation, with the same counters, and within
-    3e-5 of the oracle."""
-    rng = np.random.default_rng(37)
+def _mostly_hard(rng, n, sig, easy_share, seed):
     hard = _degenerate_matrices(rng)
-    n, R = 24000, 6
-    sig = [0.6, 1.0, 1.4, 2.0, 2.8, 4.0]
+    R = len(sig)
     cols = rng.integers(0, hard.shape[1], (R, n))
     stack = np.stack([hard[:, cols[r]] * sig[r] for r in range(R)]).astype(np.float32)
-    easy = hessgen.hessian_stack(41, 0, sig, n, dtype=np.float32)
-    mix = rng.random((R, n)) < 0.2
-    stack = np.where(mix[:, None, :], easy, stack).astype(np.float32)
-    ps = n + 4
-    F, idx, st = run_mixed(ctx, stack, sig, plane_stride=ps)
-    Fb, ib, stb = _batch_mixed(ctx, stack, sig, ps)
-    assert np.array_equal(F, Fb) and np.array_equal(idx, ib)
+    easy = hessgen.hessian_stack(seed, 0, sig, n, dtype=np.float32)
+    mix = rng.random((R, n)) < easy_share
+    return np.where(mix[:, None, :], easy, stack).astype(np.float32)
+
+
+def test_mixed_hard_record_overflow(ctx, tables):
+    """A point's result does not depend on how its hard radii were finished.
+    512 points alone all fit in the record buffer; the same 512 points after
+    30,000 points that nearly all have hard radii (capacity n (0.006 R + 0.02)
+    + 1024 = 2,732 at R = 6) mostly overflow and are recomputed in radius
+    order: bit-identical either way. The long run also matches the batched
+    kernel bit for bit, with the same counters, and the oracle within 3e-5."""
+    rng = np.random.default_rng(37)
+    sig = [0.6, 1.0, 1.4, 2.0, 2.8, 4.0]
+    R = len(sig)
+    a = _mostly_hard(rng, 512, sig, 0.4, 41)
+    b = _mostly_hard(rng, 30000, sig, 0.05, 42)
+    F1, i1, _ = run_mixed(ctx, a, sig, plane_stride=512)
+    both = np.concatenate([b, a], axis=2)
+    n = both.shape[2]
+    F2, i2, st = run_mixed(ctx, both, sig, plane_stride=n)
+    assert np.array_equal(F2[-512:], F1) and np.array_equal(i2[-512:], i1)
+    Fb, ib, stb = _batch_mixed(ctx, both, sig, n)
+    assert np.array_equal(F2, Fb) and np.array_equal(i2, ib)
     for k in ("evaluations", "collapsed", "eds_branch", "refined", "fp64_branch"):
         assert st[k] == stb[k], (k, st[k], stb[k])
     assert st["fp64_branch"] > 0.1 * n * R  # most points carry hard radii: far beyond the capacity
-    F_all, fl = oracle_per_radius(tables, stack)
-    s = compare_mixed(F, idx, F_all, fl)
+    F_all, fl = oracle_per_radius(tables, both)
+    s = compare_mixed(F2, i2, F_all, fl)
     print("mixed, record overflow", s, st)
 
 
 def test_mixed_hard_radii_above_32(ctx, tables):
     """40 radii with hard matrices on both sides of radius 32: radii below 32
     travel as bits of the record, the others are found again by the second
-    kernel. Bit-identical to the batched kernel and within 3e-5 of the oracle."""
+    and third kernels. Bit-identical to the batched kernel (its own main
+    kernel and records), same counters, and within 3e-5 of the oracle."""
     rng = np.random.default_rng(43)
     n, R = 2500, 40
     sig = hessgen.sigma_schedule(R, 0.3, 5.0)
