@@ -350,7 +350,11 @@ typedef struct cc_batch cc_batch;
 
 /* Validate the items and build a plan: the item table, per-radius parameters
  * and a work counter are copied to device memory owned by the plan (allocated
- * here). The device buffers the items point to must outlive the plan. */
+ * here). The device buffers the items point to must outlive the plan.
+ * CC_MODE_MIXED plans also own the record buffer for the points with
+ * FP64-heavy radii (24 B per record, for at most sum_i n_i (0.006 R_i + 0.02)
+ * + 1024 records), so runs of one plan must not overlap on the GPU. Limits:
+ * nitems < 2^23, n < 2^40 per item. */
 CC_API int cc_batch_create(cc_ctx *ctx, cc_mode mode, const cc_batch_item *items, int32_t nitems,
                            cc_batch **out);
 
@@ -362,7 +366,9 @@ CC_API int cc_batch_create(cc_ctx *ctx, cc_mode mode, const cc_batch_item *items
  * name, mode and class. Synchronises `stream`. */
 CC_API int cc_batch_autotune(cc_batch *b, const char *cache_path, void *stream);
 
-/* One persistent launch over all items on `stream` (work-counter reset + kernel). */
+/* One persistent launch over all items on `stream` (work-counter reset + kernel;
+ * CC_MODE_MIXED: then the record-counter reset and two kernels for the
+ * recorded points). */
 CC_API int cc_batch_run(cc_batch *b, void *stream);
 
 /* The same launch through a CUDA graph that the plan captures on first use
