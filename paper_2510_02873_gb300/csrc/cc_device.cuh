@@ -711,7 +711,9 @@ __device__ __forceinline__ double tab_interp(const TabDev& td, const double* __r
   const double* yg = xg + td.nx;
   const double* ihx = yg + td.ny;
   const double* ihy = ihx + (td.nx - 1);
-  const float* dgf = reinterpret_cast<const float*>(ihy + (td.ny - 1));
+  const double* cx = ihy + (td.ny - 1);  // -x_i / h_i
+  const double* cy = cx + (td.nx - 1);
+  const float* dgf = reinterpret_cast<const float*>(cy + (td.ny - 1));
   const long long bx = bits(x), by = bits(y);
   int ix = 0, iy = 0, kd = 0;
   for (int step = td.x_steps; step > 0; step >>= 1) {
@@ -738,8 +740,10 @@ __device__ __forceinline__ double tab_interp(const TabDev& td, const double* __r
   const double z10 = horner(tcoef[s00 + sx], t);
   const double z01 = horner(tcoef[s00 + nseg], t);
   const double z11 = horner(tcoef[s00 + sx + nseg], t);
-  const double tx = (x - xg[ix]) * ihx[ix];
-  const double ty = (y - yg[iy]) * ihy[iy];
+  // (x - x_i) / h_i in one FMA from the cell's 1/h_i and -x_i / h_i (the
+  // offset's rounding is eps x_i / h_i, far below the table's own error)
+  const double tx = fma(x, ihx[ix], cx[ix]);
+  const double ty = fma(y, ihy[iy], cy[iy]);
   const double z0 = fma(tx, z10 - z00, z00);
   const double z1 = fma(tx, z11 - z01, z01);
   return fma(ty, z1 - z0, z0);
@@ -770,20 +774,25 @@ __device__ __forceinline__ TabResult collapse_point_tab(
   const float Sf = to_f32_trunc(S);
   const float d2_scale = fmaf(Sf, Sf, fmaf(4.0f, fabsf(to_f32_trunc(Pp)), to_f32_trunc(p2x3)));
   double l2, l3;
-  if (to_f32_trunc(D2) < 1e-10f * d2_scale) {
+  const float D2f = to_f32_trunc(D2);
+  if (D2f < 1e-10f * d2_scale) {
     l2 = 0.5 * S;
     l3 = 0.5 * S;
     refine_top_pair(xx, yy, zz, xy, xz, yz, lam1, l2, l3);
     res.refined = true;
   } else {
-    const double yv = sqrt(D2);
-    l2 = 0.5 * (S + yv);
-    l3 = 0.5 * (S - yv);
+    // sqrt(D2): FP32 seed, one FP64 Newton step (relative error ~1e-13)
+    const float yf = sqrt_seed(D2f);
+    const double y0 = to_f64(yf);
+    const double yv = fma(fma(-y0, y0, D2), to_f64(0.5f * rcp_seed(yf)), y0);
+    const double hS = 0.5 * S;
+    l2 = fma(yv, 0.5, hS);  // 0.5 (S + yv), the same rounding
+    l3 = fma(yv, -0.5, hS);
   }
   double yv = l2 - l3, xv = lam1 - l2;
   yv = bits(yv) > 0 ? yv : 0.0;
   xv = bits(xv) > 0 ? xv : 0.0;
-  const double delta = xx + yy + zz;
+  const double delta = e.s;  // the trace
   // inside the hull [d_0, d_last] x [x_0, x_last] x [y_0, y_last]: xv, yv and
   // the axis bounds are >= 0, so their bit patterns order like their values
   res.outside = !(delta >= td.d_lo && delta <= td.d_hi && bits(xv) >= bits(td.x_lo) && bits(xv) <= bits(td.x_hi) &&

@@ -96,14 +96,14 @@ struct DevTable {
 constexpr int kTabMaxD = 256;
 constexpr int kTabMaxXY = 256;
 struct TabDev {
-  const double* axes;  // image: dg[nd] | xg[nx] | yg[ny] | 1/hx[nx-1] | 1/hy[ny-1] | dgf (float)[nd]
+  const double* axes;  // image: dg[nd] | xg[nx] | yg[ny] | 1/hx[nx-1] | 1/hy[ny-1] | -xg/hx[nx-1] | -yg/hy[ny-1] | dgf (float)[nd]
   const Coef4* coef;   // [(ix * ny + iy) * (nd - 1) + k]
   int nd, nx, ny;
   int d_steps, x_steps, y_steps;  // largest power of two <= n - 2 (branch-free searches)
   double d_lo, d_hi, x_lo, x_hi, y_lo, y_hi;  // the table's hull (first and last knot of each axis)
   unsigned int* dbg;                          // the launch's error flags (index checks of debug builds)
   __host__ __device__ size_t axes_bytes() const {
-    return sizeof(double) * (nd + nx + ny + (nx - 1) + (ny - 1)) + sizeof(float) * nd;
+    return sizeof(double) * (nd + nx + ny + 2 * (nx - 1) + 2 * (ny - 1)) + sizeof(float) * nd;
   }
 };
 

@@ -210,7 +210,11 @@ int cc_set_table(cc_ctx* ctx, const double* dgrid, int32_t nd, const double* xgr
   std::memcpy(p + nd + nx, ygrid, sizeof(double) * ny);
   for (int i = 0; i + 1 < nx; ++i) p[nd + nx + ny + i] = 1.0 / (xgrid[i + 1] - xgrid[i]);
   for (int i = 0; i + 1 < ny; ++i) p[nd + nx + ny + (nx - 1) + i] = 1.0 / (ygrid[i + 1] - ygrid[i]);
-  float* pf = reinterpret_cast<float*>(p + nd + nx + ny + (nx - 1) + (ny - 1));
+  // cell offsets: the bilinear weight (x - x_i) / h_i as one FMA, x (1/h_i) + (-x_i / h_i)
+  for (int i = 0; i + 1 < nx; ++i) p[nd + nx + ny + (nx - 1) + (ny - 1) + i] = -(xgrid[i] * p[nd + nx + ny + i]);
+  for (int i = 0; i + 1 < ny; ++i)
+    p[nd + nx + ny + 2 * (nx - 1) + (ny - 1) + i] = -(ygrid[i] * p[nd + nx + ny + (nx - 1) + i]);
+  float* pf = reinterpret_cast<float*>(p + nd + nx + ny + 2 * (nx - 1) + 2 * (ny - 1));
   for (int k = 0; k < nd; ++k) pf[k] = static_cast<float>(dgrid[k]);
   ctx->tab_valid = false;
   // pageable sources: each call returns once its data is staged
