@@ -4,14 +4,16 @@
 // second- and third-order growth factors in their EdS ratios to D1, this mode
 // takes them from their ODEs in the actual background).
 //
-//   A_1(D) = 1 - l1 D + r2(D) l2 l3 D^2 + [r3a(D) u3 + r3b(D) v3] D^3,
-//   u3 = -l1 l2 l3 / 3,  v3 = -l1 (l2^2 + l3^2) / 2,
+//   A_1(D) = 1 - l1 D + r2(D) l2 l3 D^2 + l1 [r3a'(D) l2 l3 + r3b'(D) (l2^2 + l3^2)] D^3,
+//   r3a' = -r3a / 3,  r3b' = -r3b / 2,
 // with r2 = D2/D1^2, r3a = D3a/D1^3, r3b = D3b/D1^3 natural splines in D over
-// the growth-table knots (EdS values below the first knot, the last value
-// beyond the last knot, where no root counts as a collapse). The root starts
-// from the EdS root (closed form, FP32), takes three FP32 Newton steps with the
-// FP32 ratio splines and their derivatives, then one FP64 Newton step with the
-// FP64 splines; the a(D) spline follows as in the FP64 path.
+// the growth-table knots, stored already scaled (EdS values below the first
+// knot, the last value beyond the last knot, where no root counts as a
+// collapse). In EdS r3a' = 1/9 and r3b' = -5/21, the R-LPT coefficients. The
+// root starts from the EdS root (closed form, FP32), takes three FP32 Newton
+// steps with the FP32 ratio splines and their derivatives, then one FP64 Newton
+// step with the FP64 splines that yields t = D - e_k for the a(D) spline
+// directly, as in the FP64 path.
 #pragma once
 
 #include "cc_device.cuh"
@@ -19,18 +21,19 @@
 namespace cc {
 namespace exact {
 
-// EdS ratios (below the first knot)
-constexpr double kEds2 = -3.0 / 7.0, kEds3a = -1.0 / 3.0, kEds3b = 10.0 / 21.0;
+// EdS ratios (below the first knot): r2, r3a' = -r3a / 3, r3b' = -r3b / 2
+constexpr double kEds2 = -3.0 / 7.0, kEdsA = 1.0 / 9.0, kEdsB = -5.0 / 21.0;
 
-// A_1 and its derivative in FP32 at D (ratios from the FP32 splines)
+// A_1 and its derivative in FP32 at D (ratios from the FP32 splines);
+// u2 = l2 l3, Q = l2^2 + l3^2
 __device__ __forceinline__ void stretch_f32(const DevTable& tab, const float* __restrict__ Dkf,
                                             const unsigned short* __restrict__ bucket, float D, float l1, float u2,
-                                            float u3, float v3, float& A, float& dA) {
+                                            float Q, float& A, float& dA) {
   float r[3], dr[3];
   if (D < Dkf[0]) {
     r[0] = static_cast<float>(kEds2);
-    r[1] = static_cast<float>(kEds3a);
-    r[2] = static_cast<float>(kEds3b);
+    r[1] = static_cast<float>(kEdsA);
+    r[2] = static_cast<float>(kEdsB);
     dr[0] = dr[1] = dr[2] = 0.0f;
   } else {
     // beyond the last knot the ratios are held at their last value: an
@@ -46,8 +49,8 @@ __device__ __forceinline__ void stretch_f32(const DevTable& tab, const float* __
       dr[o] = above ? 0.0f : fmaf(fmaf(3.0f * c.w, t, 2.0f * c.z), t, c.y);
     }
   }
-  const float w3 = fmaf(r[1], u3, r[2] * v3);
-  const float dw3 = fmaf(dr[1], u3, dr[2] * v3);
+  const float w3 = l1 * fmaf(r[1], u2, r[2] * Q);
+  const float dw3 = l1 * fmaf(dr[1], u2, dr[2] * Q);
   const float D2 = D * D;
   A = fmaf(fmaf(fmaf(w3, D, r[0] * u2), D, -l1), D, 1.0f);
   // d/dD [r2 u2 D^2 + w3 D^3] = (dr2 D^2 + 2 r2 D) u2 + dw3 D^3 + 3 w3 D^2
@@ -63,45 +66,48 @@ __device__ __forceinline__ Result collapse_point(double xx, double yy, double zz
                                                  const double* __restrict__ Dk, const Coef4* __restrict__ coef,
                                                  const float* __restrict__ Dkf,
                                                  const unsigned short* __restrict__ bucket, const DevTable& tab) {
+  (void)Dk;
   Result res;
   const EigenTop e = eigen_top_fp64(xx, yy, zz, xy, xz, yz);
   res.refined = e.refined;
-  const double q = e.q, x = e.x, p2x3 = e.p2x3;
-  const double lam1 = q + x;
-  const double Pp = fma(q, q - x, fma(x, x, -p2x3));  // l2 l3
-  const double S = fma(2.0, q, -x);                    // l2 + l3
-  const double Q = fma(S, S, -2.0 * Pp);               // l2^2 + l3^2
-  const double u3 = lam1 * (Pp * (-1.0 / 3.0));
-  const double v3 = lam1 * (Q * -0.5);
+  const double s = e.s, x = e.x, p2x3 = e.p2x3;
+  const double lam1 = fma(s, 1.0 / 3.0, x);
+  const double Pp = fma(e.q, fma(s, 1.0 / 3.0, -x), fma(x, x, -p2x3));  // l2 l3
+  const double S = fma(s, 2.0 / 3.0, -x);                               // l2 + l3
+  const double Q = fma(S, S, Pp * -2.0);                                // l2^2 + l3^2
   // ---- FP32: EdS root, then three Newton steps with the exact ratios
-  const float l1f = to_f32_trunc(lam1), u2f = to_f32_trunc(Pp), u3f = to_f32_trunc(u3), v3f = to_f32_trunc(v3);
-  const float c3f = fmaf(static_cast<float>(kEds3a), u3f, static_cast<float>(kEds3b) * v3f);
+  const float l1f = to_f32_trunc(lam1), u2f = to_f32_trunc(Pp), Qf = to_f32_trunc(Q);
+  const float c3f = l1f * fmaf(static_cast<float>(kEdsA), u2f, static_cast<float>(kEdsB) * Qf);
   const float uf = cubic_largest_root_seed(-l1f, static_cast<float>(kEds2) * u2f, c3f);
   float Df = __fdividef(1.0f, uf);
   float A, dA;
 #pragma unroll
   for (int it = 0; it < 3; ++it) {
-    stretch_f32(tab, Dkf, bucket, Df, l1f, u2f, u3f, v3f, A, dA);
+    stretch_f32(tab, Dkf, bucket, Df, l1f, u2f, Qf, A, dA);
     Df -= __fdividef(A, dA);
   }
-  stretch_f32(tab, Dkf, bucket, Df, l1f, u2f, u3f, v3f, A, dA);
+  stretch_f32(tab, Dkf, bucket, Df, l1f, u2f, Qf, A, dA);
   // ---- one FP64 Newton step with the FP64 ratio splines (FP32 derivative)
   const double D0 = to_f64(Df);
+  const int k = spline_interval(Dkf, bucket, tab, Df);
+  const bool below = Df < Dkf[0];
   double r[3];
-  if (Df < Dkf[0]) {
+  if (below) {
     r[0] = kEds2;
-    r[1] = kEds3a;
-    r[2] = kEds3b;
+    r[1] = kEdsA;
+    r[2] = kEdsB;
   } else {
     // r = c0 + t (c1 + t (c2 + c3 t)): c2 + c3 t in FP32 (the FP32 copies of
-    // the coefficients, t from the FP32 root and knot), the rest in FP64. Over
-    // one interval a ratio moves by at most 4.4e-4 of its value, nearly all of
-    // it in the c1 term; the FP32 part moves r by ~1e-12 relative at most.
+    // the coefficients), the rest in FP64. Over one interval a ratio moves by
+    // at most 4.4e-4 of its value, nearly all of it in the c1 term; the FP32
+    // part moves r by ~1e-12 relative at most. t = D0 - e_k is exact in FP32
+    // (the splines are expanded about the FP32 knots e_k); beyond the last
+    // knot the ratios are taken at the FP32 D_top (no collapse there, but an
+    // FP64 step may land back within ~1e-7 of it: a point then on the a_max
+    // edge, where F ~ 1 either way).
     const bool above = Df > tab.Dtopf;
-    const float Dr = above ? tab.Dtopf : Df;
-    const int k = spline_interval(Dkf, bucket, tab, Dr);
-    const double t = (above ? tab.Dtop : D0) - Dk[k];
-    const float tf = Dr - Dkf[k];
+    const float tf = (above ? tab.Dtopf : Df) - Dkf[k];
+    const double t = to_f64(tf);
 #pragma unroll
     for (int o = 0; o < 3; ++o) {
       const float4 cf = __ldg(tab.rc32 + o * (tab.n - 1) + k);
@@ -109,16 +115,15 @@ __device__ __forceinline__ Result collapse_point(double xx, double yy, double zz
       r[o] = fma(fma(to_f64(fmaf(cf.w, tf, cf.z)), t, c.c1), t, c.c0);
     }
   }
-  const double w3 = fma(r[1], u3, r[2] * v3);
+  const double w3 = lam1 * fma(r[1], Pp, r[2] * Q);
   const double A1 = fma(fma(fma(w3, D0, r[0] * Pp), D0, -lam1), D0, 1.0);
-  const double D = fma(-A1, to_f64(__fdividef(1.0f, dA)), D0);
-  // ---- collapse test, a(D) as in the FP64 path
-  const long long bD = bits(D);
-  res.collapsed = bits(lam1) > 0 && bD > 0 && bD <= bits(tab.Dtop);
-  const double Dc = res.collapsed ? D : tab.Dtop;
-  const int kk = spline_interval(Dkf, bucket, tab, res.collapsed ? to_f32_trunc(D) : tab.Dtopf);
-  res.eds = res.collapsed && bits(Dc) < bits(tab.D0);
-  const double av = spline_a(coef[kk], Dk[kk], Dc, res.eds, tab);
+  // ---- the step lands on t = D - e_k (on the EdS segment t = D), and the
+  // collapse test and a(D) follow as in collapse_point_fp64
+  const float t0 = below ? Df : __fsub_rn(Df, Dkf[k]);
+  const double t = fma(-A1, to_f64(rcp_seed(dA)), to_f64_normal(t0));
+  res.collapsed = bits(lam1) > 0 && Df > 0.0f && (k < tab.n - 2 || bits(t) <= bits(tab.Dtop_t)) && finite_bits(t);
+  res.eds = below && res.collapsed;
+  const double av = spline_a_t(coef[k], t, res.eds, tab);
   res.a = res.collapsed ? av : kInf;
   return res;
 }

@@ -77,9 +77,10 @@ struct DevTable {
   // the table image at offset round_up(bytes(), 16); nullptr when absent
   const float4* dfseg;
   float Dtop_hi, Dtop_lo, D0_hi, D0_lo, eds_hi, eds_lo;  // float-float constants
-  // exact-background growth ratios r2, r3a, r3b as natural splines in D over
-  // the same knots (CC_MODE_EXACT_GROWTH): rc64[o * (n - 1) + k] (FP64) and
-  // rc32[...] (FP32 copies, {c0, c1, c2, c3}); nullptr when absent
+  // exact-background growth ratios as natural splines in D over the same
+  // knots (CC_MODE_EXACT_GROWTH), stored as r2, -r3a / 3 and -r3b / 2:
+  // rc64[o * (n - 1) + k] (FP64) and rc32[...] (FP32 copies, {c0, c1, c2,
+  // c3}); nullptr when absent
   const Coef4* rc64;
   const float4* rc32;
   unsigned int* dbg;              // the launch's error flags (index checks of debug builds)
