@@ -221,22 +221,17 @@ int cc_create(cc_ctx** out, const cc_cosmology* cosmo, int device) {
   if ((rc = check_cuda(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device),
                        "cudaDeviceGetAttribute"))) { delete ctx; return rc; }
   const int n = cosmo->n_knots;
-  // FP32 interval search: uniform buckets in log2 D, each holding the largest
-  // knot index k with D_k <= the bucket's lower edge
-  const int nb = kBucketsPerKnot * n;
-  const double l2lo = std::log2(ctx->D_k[0]), l2hi = std::log2(ctx->D_k[n - 1]);
-  const double width = (l2hi - l2lo) / nb;
-  std::vector<unsigned short> bucket(nb);
-  {
-    int k = 0;
-    for (int b = 0; b < nb; ++b) {
-      const double edge = std::exp2(l2lo + width * b);
-      while (k + 1 <= n - 2 && ctx->D_k[k + 1] <= edge) ++k;
-      bucket[b] = static_cast<unsigned short>(k);
-    }
-  }
+  // FP32 interval search: buckets over the FP32 bit patterns of D, each holding
+  // the largest knot index k with D_k <= the bucket's lower edge
   std::vector<float> df(n);
   for (int k = 0; k < n; ++k) df[k] = static_cast<float>(ctx->D_k[k]);
+  std::vector<unsigned short> bucket(kBucketsPerKnot * n);
+  int nb = 0, b_shift = 0;
+  unsigned b0 = 0;
+  if (bit_buckets_into(n, df.data(), kBucketsPerKnot * n, bucket.data(), &nb, &b_shift, &b0) != CC_OK) {
+    delete ctx;
+    return set_error(CC_EINVAL, "growth-table knots too irregular for the interval search buckets");
+  }
   // device layout: coef[n-1] (32-byte aligned) | D[n] | Df[n] | bucket[nb]
   const size_t coef_bytes = sizeof(Coef4) * (n - 1);
   const size_t d_bytes = sizeof(double) * n;
@@ -285,8 +280,8 @@ int cc_create(cc_ctx** out, const cc_cosmology* cosmo, int device) {
   t.bucket = reinterpret_cast<const unsigned short*>(base + coef_bytes + d_bytes + df_bytes);
   t.n = n;
   t.n_buckets = nb;
-  t.log2_D0 = static_cast<float>(l2lo);
-  t.inv_bucket_width = static_cast<float>(1.0 / width);
+  t.b0 = b0;
+  t.b_shift = b_shift;
   t.a0 = ctx->a_k[0];
   t.D0 = ctx->D_k[0];
   t.Dtop = ctx->D_k[n - 1];

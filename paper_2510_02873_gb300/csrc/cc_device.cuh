@@ -192,17 +192,17 @@ __device__ __forceinline__ float cubic_largest_root_seed(float b, float c, float
   return t - b3;
 }
 
-// Interval of the a(D) spline holding D (FP32 search on FP32 knots): a bucket
-// of the uniform grid in log2 D gives a first interval, two predicated steps
-// finish. Near a knot the FP32 decision may pick the neighbouring interval;
-// the spline is C2 there, so the value changes only by |jump of c3| |t|^3,
-// far below FP64 rounding.
+// Interval of the a(D) spline holding D (FP32 search on FP32 knots): positive
+// FP32 numbers order like their bit patterns, so the bucket (bits(D) - bits(D_0))
+// >> b_shift is exact; it holds the largest k with D_k at or below its lower
+// edge, and no bucket holds more than two knots, so two predicated steps end
+// on the interval with D_k <= D < D_{k+1} (clamped to the first and last
+// interval; D below D_0, negative or NaN lands in one of those).
 __device__ __forceinline__ int spline_interval(const float* __restrict__ Dkf,
                                                const unsigned short* __restrict__ bucket,
                                                const DevTable& tab, float Df) {
-  float fb = (__log2f(Df) - tab.log2_D0) * tab.inv_bucket_width;
-  fb = fminf(fmaxf(fb, 0.0f), static_cast<float>(tab.n_buckets - 1));
-  int b = static_cast<int>(fb);
+  int b = static_cast<int>(__float_as_uint(Df) - tab.b0) >> tab.b_shift;
+  b = min(max(b, 0), tab.n_buckets - 1);
   CC_DBG_CLAMP(b, 0, tab.n_buckets - 1, tab.dbg);
   int k = bucket[b];
   CC_DBG_CLAMP(k, 0, tab.n - 2, tab.dbg);
@@ -625,11 +625,12 @@ __device__ __forceinline__ float newton_f32(const MixedCoef& k, float Df) {
 //     the same side of D_top or D_0 except within ~1e-7 of them, where the two
 //     sides give the same a (a_max at D_top; the spline is continuous at D_0);
 //   FP32 -> FP64: for a collapsing point Df and v are positive normal
-//     numbers and A_1'(Df) a negative one (A_1 falls through zero at its
-//     first root), so they take the three-instruction to_f64_pos / to_f64_neg
-//     (a result that is not used may be any finite number); t0, c3 Df + c2
-//     and lo(a_0 / D_0) D take to_f64_normal, where a zero shifts t, A_1 or a
-//     by less than 2^-126.
+//     numbers, A_1'(Df) a negative one (A_1 falls through zero at its first
+//     root) and t0 >= 0 (the interval search is exact, D_k = e_k, and on the
+//     EdS segment t0 = Df), so they take the three-instruction to_f64_pos /
+//     to_f64_neg (a result that is not used may be any finite number; a zero
+//     t0 becomes 2^-127); c3 Df + c2 and lo(a_0 / D_0) D take to_f64_normal,
+//     where a zero shifts A_1 or a by less than 2^-126.
 // kEds = false: the caller sends EdS collapses (res.eds) elsewhere and uses
 // only the other results, so the EdS operand selects are left out; every
 // result with res.eds false is the same as with kEds = true.
@@ -653,7 +654,7 @@ __device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const M
   const float t0 = eds ? Dcf : __fsub_rn(__fsub_rn(Dcf, s1.z), s1.w);
   const float v = eds ? tab.eds_hi : fmaf(fmaf(s1.y, t0, s1.x), t0, s0.z);
   const double head = eds ? to_f64_normal(tab.eds_lo * Dcf) : coef[kk].c0;
-  const double t = fma(-A1, to_f64_neg(rcp_seed(dAf)), to_f64_normal(t0));
+  const double t = fma(-A1, to_f64_neg(rcp_seed(dAf)), to_f64_pos(t0));
   const double av = fma(to_f64_pos(v), t, head);
   res.a = res.collapsed ? av : kInf;
   res.F = res.collapsed ? to_f64(1.0f / to_f32_trunc(av)) : 0.0;

@@ -66,8 +66,9 @@ struct DevTable {
   const float* Df;                // FP32 copy of the knots (interval search)
   const unsigned short* bucket;   // n_buckets: largest k with D_k <= bucket's lower edge
   int n;
-  int n_buckets;                  // uniform buckets in log2 D over [D_0, D_top]
-  float log2_D0, inv_bucket_width;
+  int n_buckets;                  // uniform buckets in the FP32 bit pattern of D over [D_0, D_top]
+  unsigned b0;                    // FP32 bit pattern of the first knot
+  int b_shift;                    // bucket = (bits(D) - b0) >> b_shift
   double a0, D0, Dtop;            // first scale factor, first and last knot
   double eds_slope;               // a0 / D0
   float Dtopf;                    // D_top rounded to FP32 (interval search)
@@ -125,6 +126,13 @@ int growth_ratios_into(const cc_cosmology& c, double* r2, double* r3a, double* r
 int f32_knots_within_factor2(int n, const double* x);
 // re-expand the n - 1 cubics c0 + c1 t + c2 t^2 + c3 t^3 (t = D - x_k) about e_k
 void expand_about_f32_knots(int n, const double* x, double* coef);
+// Interval search buckets over the FP32 knots xf (positive, increasing):
+// bucket b covers the FP32 bit patterns [b0 + (b << shift), b0 + ((b + 1) << shift))
+// of D and holds the largest k <= n - 2 with xf[k] <= its lower edge; shift is
+// the largest with at most two knots x_1 .. x_{n-2} in any bucket, so two
+// predicated steps always reach the interval. CC_EINVAL when that needs more
+// than max_nb buckets.
+int bit_buckets_into(int n, const float* xf, int max_nb, unsigned short* bucket, int* nb, int* shift, unsigned* b0);
 
 // error reporting (cc_api.cu)
 int set_error(int code, const std::string& msg);

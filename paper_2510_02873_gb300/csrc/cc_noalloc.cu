@@ -55,6 +55,8 @@ DeviceState g_state[kMaxDevices];
 double g_a[kStaticMaxKnots], g_D[kStaticMaxKnots];
 double g_coef[4 * (kStaticMaxKnots - 1)];
 double g_work[6 * kStaticMaxKnots];
+float g_scratch_f[kStaticMaxKnots];
+unsigned short g_bucket[kStaticMaxBuckets];
 alignas(32) unsigned char g_image[kStaticTableBytes];
 
 bool same_cosmology(const cc_cosmology& a, const cc_cosmology& b) {
@@ -70,9 +72,11 @@ int build_image(const cc_cosmology& c, unsigned char* base, DevTable& tab, size_
   if (int rc = natural_spline_into(n, g_D, g_a, g_coef, g_work)) return rc;
   if (int rc = f32_knots_within_factor2(n, g_D)) return rc;
   expand_about_f32_knots(n, g_D, g_coef);  // the device polynomials are expanded about the FP32 knots
-  const int nb = kBucketsPerKnot * n;
-  const double l2lo = std::log2(g_D[0]), l2hi = std::log2(g_D[n - 1]);
-  const double width = (l2hi - l2lo) / nb;
+  float* df = g_scratch_f;
+  for (int k = 0; k < n; ++k) df[k] = static_cast<float>(g_D[k]);
+  int nb = 0, b_shift = 0;
+  unsigned b0 = 0;
+  if (int rc = bit_buckets_into(n, df, kBucketsPerKnot * n, g_bucket, &nb, &b_shift, &b0)) return rc;
   const size_t coef_bytes = sizeof(Coef4) * (n - 1);
   const size_t d_bytes = sizeof(double) * n;
   const size_t df_bytes = sizeof(float) * n;
@@ -80,23 +84,16 @@ int build_image(const cc_cosmology& c, unsigned char* base, DevTable& tab, size_
   std::memcpy(g_image, g_coef, coef_bytes);
   double* e = reinterpret_cast<double*>(g_image + coef_bytes);
   for (int k = 0; k < n; ++k) e[k] = static_cast<double>(static_cast<float>(g_D[k]));
-  float* df = reinterpret_cast<float*>(g_image + coef_bytes + d_bytes);
-  for (int k = 0; k < n; ++k) df[k] = static_cast<float>(g_D[k]);
-  unsigned short* bucket = reinterpret_cast<unsigned short*>(g_image + coef_bytes + d_bytes + df_bytes);
-  int k = 0;
-  for (int b = 0; b < nb; ++b) {
-    const double edge = std::exp2(l2lo + width * b);
-    while (k + 1 <= n - 2 && g_D[k + 1] <= edge) ++k;
-    bucket[b] = static_cast<unsigned short>(k);
-  }
+  std::memcpy(g_image + coef_bytes + d_bytes, df, df_bytes);
+  std::memcpy(g_image + coef_bytes + d_bytes + df_bytes, g_bucket, sizeof(unsigned short) * nb);
   tab.coef = reinterpret_cast<const Coef4*>(base);
   tab.D = reinterpret_cast<const double*>(base + coef_bytes);
   tab.Df = reinterpret_cast<const float*>(base + coef_bytes + d_bytes);
   tab.bucket = reinterpret_cast<const unsigned short*>(base + coef_bytes + d_bytes + df_bytes);
   tab.n = n;
   tab.n_buckets = nb;
-  tab.log2_D0 = static_cast<float>(l2lo);
-  tab.inv_bucket_width = static_cast<float>(1.0 / width);
+  tab.b0 = b0;
+  tab.b_shift = b_shift;
   tab.a0 = g_a[0];
   tab.D0 = g_D[0];
   tab.Dtop = g_D[n - 1];

@@ -17,6 +17,7 @@
 #include "cc_internal.h"
 
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 namespace cc {
@@ -222,6 +223,41 @@ void expand_about_f32_knots(int n, const double* x, double* coef) {
     c[1] = c1 + d * (2.0 * c2 + 3.0 * d * c3);
     c[2] = c2 + 3.0 * d * c3;
   }
+}
+
+int bit_buckets_into(int n, const float* xf, int max_nb, unsigned short* bucket, int* nb_out, int* shift_out,
+                     unsigned* b0_out) {
+  // positive FP32 numbers order like their bit patterns, so bucket
+  // b = (bits(x) - bits(x_0)) >> shift is exact: pick the largest shift
+  // (fewest buckets) at which no bucket holds more than two of the knots a
+  // search can step to (x_1 .. x_{n-2})
+  std::vector<uint32_t> kb(n);
+  for (int k = 0; k < n; ++k) std::memcpy(&kb[k], &xf[k], sizeof(uint32_t));
+  const uint32_t b0 = kb[0], range = kb[n - 1] - kb[0];
+  for (int shift = 31; shift >= 0; --shift) {
+    const int64_t nb = static_cast<int64_t>(range >> shift) + 1;
+    if (nb > max_nb) break;  // finer shifts only add buckets
+    int worst = 0, run = 0;
+    int64_t cur = -1;
+    for (int k = 1; k <= n - 2; ++k) {
+      const int64_t b = static_cast<int64_t>((kb[k] - b0) >> shift);
+      run = (b == cur) ? run + 1 : 1;
+      cur = b;
+      worst = run > worst ? run : worst;
+    }
+    if (worst > 2) continue;
+    int k = 0;
+    for (int64_t i = 0; i < nb; ++i) {
+      const uint64_t edge = static_cast<uint64_t>(b0) + (static_cast<uint64_t>(i) << shift);
+      while (k + 1 <= n - 2 && kb[k + 1] <= edge) ++k;
+      bucket[i] = static_cast<unsigned short>(k);
+    }
+    *nb_out = static_cast<int>(nb);
+    *shift_out = shift;
+    *b0_out = b0;
+    return CC_OK;
+  }
+  return CC_EINVAL;
 }
 
 int build_natural_spline(const std::vector<double>& x, const std::vector<double>& y,
