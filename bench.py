@@ -1272,8 +1272,9 @@ def main():
                    "value_at_median_step": float(n) * R * world / (statistics.median(step_ms) * 1e-3),
                    "basis": "CUDA events on the launching stream around each timed step (reset + fused "
                             "launch) and around each fused launch; value is the whole timed region"},
-        # per step: the reset kernel and the collapse kernel (mixed: its second kernel for the hard radii too)
-        "gpu_launches": (3 if args.mode == "mixed" else 2) * args.steps,
+        # per step: the reset kernel and the collapse kernel (mixed: also its two
+        # kernels for the recorded points)
+        "gpu_launches": (4 if args.mode == "mixed" else 2) * args.steps,
         "clocks": clk,
         "stats": {k: stats[k] for k in ("evaluations", "collapsed", "eds_branch", "refined", "error_flags")},
     }
@@ -1357,7 +1358,7 @@ def main():
         }
         F_check = F.cpu()
         assert torch.equal(Fh, F_check), "e2e result differs from the device-resident run"
-        result["gpu_launches"] += (2 if args.mode == "mixed" else 1) * R * args.steps
+        result["gpu_launches"] += (3 if args.mode == "mixed" else 1) * R * args.steps
     if rank == 0 and not args.no_variants and (args.grid, R) == (GRID, N_RADII) and args.mode == "fp64":
         if "hess" in locals():
             del hess
