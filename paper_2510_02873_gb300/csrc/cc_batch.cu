@@ -94,7 +94,7 @@ __device__ __forceinline__ void run_point_mixed(const BatchItemDev& it, int item
       const MixedEigen m = mixed_eigen_f32(v.xx, v.yy, v.zz, v.xy, v.xz, v.yz, __ldg(it.tri_thr + r));
       bool later = m.full || m.need64;
       if (!later) {
-        const MixedResult res = mixed_easy<false>(m, coef, Dkf, bucket, tab);
+        const MixedResult res = mixed_easy<false>(m, coef, Dkf, bucket, tab, tab.dfseg);
         later = res.eds;
         n_coll += res.collapsed && !later;
         best.add(res.collapsed && !later, res.a, r);

@@ -637,7 +637,8 @@ __device__ __forceinline__ float newton_f32(const MixedCoef& k, float Df) {
 template <bool kEds = true>
 __device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const MixedCoef& k, float Df,
                                                     const Coef4* __restrict__ coef, const float* __restrict__ Dkf,
-                                                    const unsigned short* __restrict__ bucket, const DevTable& tab) {
+                                                    const unsigned short* __restrict__ bucket, const DevTable& tab,
+                                                    const float4* __restrict__ seg) {
   MixedResult res;
   res.refined = false;
   res.fp64 = m.fp64;
@@ -648,8 +649,8 @@ __device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const M
   const float Dcf = res.collapsed ? Df : tab.Dtopf;
   const int kk = spline_interval(Dkf, bucket, tab, Dcf);
   res.eds = res.collapsed && Df < Dkf[0];
-  const float4 s0 = __ldg(tab.dfseg + 2 * kk);      // {hi(c0), lo(c0), hi(c1), lo(c1)}
-  const float4 s1 = __ldg(tab.dfseg + 2 * kk + 1);  // {c2, c3, hi(D_k), lo(D_k)}
+  const float4 s0 = seg[2 * kk];      // {hi(c0), lo(c0), hi(c1), lo(c1)}
+  const float4 s1 = seg[2 * kk + 1];  // {c2, c3, hi(D_k), lo(D_k)}
   const bool eds = kEds && res.eds;
   const float t0 = eds ? Dcf : __fsub_rn(__fsub_rn(Dcf, s1.z), s1.w);
   const float v = eds ? tab.eds_hi : fmaf(fmaf(s1.y, t0, s1.x), t0, s0.z);
@@ -689,7 +690,7 @@ __device__ __forceinline__ MixedResult collapse_point_mixed(
   // the FP64 polish squares that)
   const float uf = cubic_largest_root_seed(-k.l1f, k.c2f, k.c3f);
   const float Df = newton_f32<1>(k, __fdividef(1.0f, uf));
-  return mixed_finish(m, k, Df, coef, Dkf, bucket, tab);
+  return mixed_finish(m, k, Df, coef, Dkf, bucket, tab, tab.dfseg);
 }
 
 // ---------------------------------------------------------------------------

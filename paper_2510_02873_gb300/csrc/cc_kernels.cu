@@ -105,11 +105,13 @@ mixed_full_kernel(const T* __restrict__ hess, int64_t plane_stride, int64_t radi
 // FP64 path: two radii per iteration at 2 blocks of 256 threads per SM (94
 // registers, no spill): 1.3 % faster than one radius at 4 blocks and 64
 // registers; 3 or 4 radii per iteration, or 1 block, measured the same.
-// Mixed path: 40 registers and 6 blocks per SM (its warps stall on global
-// loads and on FP32 dependencies, which more resident warps hide).
+// Mixed path: 5 blocks per SM at 48 registers, each staging the table image
+// and the FP32 segment image (the finish's two float4 per evaluation) in
+// shared memory, 39 KB (2 % faster than 6 blocks at 40 registers reading the
+// segments through L1; 8 blocks at 32 registers spill and run 4 % slower).
 // The tabulated path keeps its 98 registers.
 template <typename T, bool kSmem, int kMode>
-__global__ void __launch_bounds__(kThreads, kMode == 2 ? 1 : (kMode == 1 ? 6 : (kMode == 0 ? 2 : 4)))
+__global__ void __launch_bounds__(kThreads, kMode == 2 ? 1 : (kMode == 1 ? 5 : (kMode == 0 ? 2 : 4)))
 collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
                 int64_t radius_stride, int R, int32_t scale_idx0, DevTable tab, RadiusParams rp,
                 TabDev td, HardWork hw, double* __restrict__ F_max, int32_t* __restrict__ idx,
@@ -123,12 +125,12 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
   if constexpr (kSmem) {
     // the table image (coef | D | Df | bucket [| pad | float-float image]) is
     // contiguous: copy it in 16-byte words
-    const int words = (kMode == kModeF32x2) ? static_cast<int>((tab.bytes() + 15) / 16) + 2 * (tab.n - 1)
+    const int words = (kMode == kModeF32x2 || kMode == kModeMixed) ? static_cast<int>((tab.bytes() + 15) / 16) + 2 * (tab.n - 1)
                                             : static_cast<int>(tab.bytes() / 16);
     const uint4* src = reinterpret_cast<const uint4*>(tab.coef);
     uint4* dst = reinterpret_cast<uint4*>(smem_tab);
     for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
-    if constexpr (kMode != kModeF32x2) {
+    if constexpr (kMode != kModeF32x2 && kMode != kModeMixed) {
       const size_t tail = tab.bytes() & 15;
       if (threadIdx.x < tail)
         reinterpret_cast<unsigned char*>(dst + words)[threadIdx.x] =
@@ -186,7 +188,7 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
           if (!later) {
             // collapse before the first knot (the EdS segment) also goes to
             // the second kernel, so that this loop carries no EdS selects
-            const MixedResult res = mixed_easy<false>(m, coef, Dkf, bucket, tab);
+            const MixedResult res = mixed_easy<false>(m, coef, Dkf, bucket, tab, seg);
             later = res.eds;
             cn.coll += res.collapsed && !later;
             best.add(res.collapsed && !later, res.a, r);
@@ -310,7 +312,7 @@ int launch_typed(const LaunchArgs& a, const DevTable& tab, const RadiusParams& r
   auto kern = collapse_kernel<T, kSmem, kMode>;
   size_t smem = kSmem ? ((tab.bytes() + 15) / 16) * 16 : 0;
   if (kMode == kModeTab) smem = ((tab.bytes() + 15) / 16) * 16 + ((td.axes_bytes() + 15) / 16) * 16;
-  if (kMode == kModeF32x2 && kSmem) smem = ((tab.bytes() + 15) / 16) * 16 + sizeof(float4) * 2 * (tab.n - 1);
+  if ((kMode == kModeF32x2 || kMode == kModeMixed) && kSmem) smem = ((tab.bytes() + 15) / 16) * 16 + sizeof(float4) * 2 * (tab.n - 1);
   // resident blocks per SM, cached per shared-memory size (tables differ between contexts)
   static thread_local int occ = 0;
   static thread_local size_t occ_smem = ~size_t{0};
@@ -358,7 +360,7 @@ int launch_typed(const LaunchArgs& a, const DevTable& tab, const RadiusParams& r
 template <int kMode>
 int launch_mode(const LaunchArgs& a, const DevTable& tab, const RadiusParams& rp, const TabDev& td,
                 const HardWork& hw = HardWork{}) {
-  const size_t staged = (kMode == kModeF32x2) ? ((tab.bytes() + 15) / 16) * 16 + sizeof(float4) * 2 * (tab.n - 1)
+  const size_t staged = (kMode == kModeF32x2 || kMode == kModeMixed) ? ((tab.bytes() + 15) / 16) * 16 + sizeof(float4) * 2 * (tab.n - 1)
                                                : tab.bytes();
   const bool smem = staged <= static_cast<size_t>(kSmemTableMaxBytes);
   if (kMode == kModeTab) {  // the tabulated kernel always stages both images

@@ -44,11 +44,12 @@ struct MixedCounts {
 template <bool kEds = true>
 __device__ __forceinline__ MixedResult mixed_easy(const MixedEigen& m, const Coef4* __restrict__ coef,
                                                   const float* __restrict__ Dkf,
-                                                  const unsigned short* __restrict__ bucket, const DevTable& tab) {
+                                                  const unsigned short* __restrict__ bucket, const DevTable& tab,
+                                                  const float4* __restrict__ seg) {
   const MixedCoef k = mixed_coef(m);
   const float uf = cubic_largest_root_seed(-k.l1f, k.c2f, k.c3f);
   const float Df = newton_f32<1>(k, __fdividef(1.0f, uf));
-  return mixed_finish<kEds>(m, k, Df, coef, Dkf, bucket, tab);
+  return mixed_finish<kEds>(m, k, Df, coef, Dkf, bucket, tab, seg);
 }
 
 constexpr int32_t kHardHigh = 0x10000;  // HardRec::r1: marked radii >= 32
@@ -151,7 +152,7 @@ __device__ __forceinline__ void hard_record(const Src& src, HardRec rec, int64_t
       full |= 1u << r;
       continue;
     }
-    const MixedResult res = mixed_easy(me, tab.coef, tab.Df, tab.bucket, tab);
+    const MixedResult res = mixed_easy(me, tab.coef, tab.Df, tab.bucket, tab, tab.dfseg);
     cn.add(res);
     best.add_any_order(res.collapsed, res.a, r);
   }
@@ -165,7 +166,7 @@ __device__ __forceinline__ void hard_record(const Src& src, HardRec rec, int64_t
       }
       MixedEigen mr = me;
       if (me.need64) mixed_refine64(mr, v.xx, v.yy, v.zz, v.xy, v.xz, v.yz);
-      const MixedResult res = mixed_easy(mr, tab.coef, tab.Df, tab.bucket, tab);
+      const MixedResult res = mixed_easy(mr, tab.coef, tab.Df, tab.bucket, tab, tab.dfseg);
       if (me.need64 || res.eds) cn.add(res);
       best.add_any_order(res.collapsed, res.a, r);
     }
@@ -225,7 +226,7 @@ __device__ __forceinline__ void recompute_marked(const Src& src, int64_t p, cons
                                  tab);
       cn.add(res);
     } else {
-      res = mixed_easy(me, tab.coef, tab.Df, tab.bucket, tab);
+      res = mixed_easy(me, tab.coef, tab.Df, tab.bucket, tab, tab.dfseg);
       if (res.eds) cn.add(res);
     }
     best.add(res.collapsed, res.a, r);

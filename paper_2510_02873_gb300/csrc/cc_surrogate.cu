@@ -467,7 +467,7 @@ __device__ __forceinline__ MixedResult sur_finish(const MixedEigen& m, float f, 
       ok = Df > 0.0f && isfinite(Df) && fabsf(Af) <= kCertTol * fabsf(dAf * Df);
     }
     if (ok) {
-      res = mixed_finish(m, k, Df, coef, Dkf, bucket, tab);
+      res = mixed_finish(m, k, Df, coef, Dkf, bucket, tab, tab.dfseg);
     } else {
       res = full_fp64(xx, yy, zz, xy, xz, yz, Dk, coef, Dkf, bucket, tab);
       ++n_fb;
