@@ -55,6 +55,35 @@ def test_histogram_is_exact(ctx, n, edges):
     assert np.array_equal(gpu_hist(ctx, F, edges), oracle.histogram(F, edges))
 
 
+STRESS_EDGES = {
+    # 1024 edges (the most cc_histogram takes) over 600 decades: one bucket
+    # table spans every binade
+    "1024 log edges": np.logspace(-300.0, 300.0, 1024),
+    # 500 edges within 5e-10 of 1 and one far edge: the table's resolution
+    # leaves the cluster in one bucket, which the kernel's scan then crosses
+    "clustered": np.concatenate([1.0 + 1e-12 * np.arange(500), [1e6]]),
+    "one bin": np.array([0.5, 2.0]),
+    # edges a few bit patterns apart (subnormal, and consecutive doubles):
+    # buckets finer than 2^32 patterns, counted on whole 64-bit patterns
+    "subnormal": np.array([5e-324, 1e-323, 1.5e-323]),
+    "adjacent doubles": np.array([1.0, np.nextafter(1.0, 2.0), np.nextafter(np.nextafter(1.0, 2.0), 2.0)]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(STRESS_EDGES))
+def test_histogram_exact_around_every_edge(ctx, name):
+    """Values on every edge and one ulp either side of it, zeros of both
+    signs, and values far beyond the last edge: bit-exact counts."""
+    edges = STRESS_EDGES[name]
+    rng = np.random.default_rng(len(edges))
+    F = np.concatenate([edges, np.nextafter(edges, 0.0), np.nextafter(edges, np.inf),
+                        [0.0, -0.0, 1e308, edges[0] * 0.5, edges[-1] * 2.0],
+                        rng.uniform(edges[0], edges[-1], 20000),
+                        edges[rng.integers(0, len(edges), 5000)]])
+    F = F[rng.permutation(len(F))]
+    assert np.array_equal(gpu_hist(ctx, F, edges), oracle.histogram(F, edges))
+
+
 def test_histogram_rejects_bad_edges(ctx):
     import paper_2510_02873_gb300 as cc
     Fd = torch.zeros(10, dtype=torch.float64, device="cuda")
