@@ -194,8 +194,8 @@ CC_API int cc_collapse_multi_host(cc_ctx *ctx, cc_mode mode, const void *hess_ho
  * the counters are cleared at the start of each call, and the table is copied
  * in again when the cosmology changes. Calls that overlap on the GPU (other
  * streams, or another cosmology in flight) race on it. The first call on each
- * device looks up the array's address and uploads the table: make it before
- * any stream capture begins. */
+ * device looks up the array's address (with that device current) and uploads
+ * the table. */
 CC_API int cc_collapse_multi_noalloc(const cc_cosmology *cosmo, cc_mode mode, const void *hess,
                               int32_t dtype, int64_t n, int64_t plane_stride,
                               int64_t radius_stride, const double *sigma, int32_t R,

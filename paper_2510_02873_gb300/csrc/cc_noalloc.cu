@@ -17,8 +17,7 @@
 // in flight at once) race on the array.
 //
 // The first call on each device looks up the array's device address with
-// cudaGetSymbolAddress (that device current) and uploads the table; make that
-// first call before any stream capture begins.
+// cudaGetSymbolAddress (that device current) and uploads the table.
 #include <cmath>
 #include <cstring>
 #include <mutex>
