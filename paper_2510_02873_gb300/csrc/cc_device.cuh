@@ -533,15 +533,15 @@ __device__ __forceinline__ MixedEigen mixed_eigen_f32(float xx, float yy, float 
   float x = 2.0f * pf * cs;
   const float x2 = pf * fmaf(kSqrt3f, sn, -cs);
   const float x3 = -pf * fmaf(kSqrt3f, sn, cs);
-#pragma unroll
-  for (int it = 0; it < 1; ++it) {  // FP32 Newton on x (x^2 - 3p^2) - det
-    const float gp = 3.0f * fmaf(x, x, -p2);
-    x = (gp != 0.0f) ? x - __fdividef(fmaf(x, fmaf(x, x, -p2x3), -det), gp) : x;
-  }
+  // one FP32 Newton step on x (x^2 - 3p^2) - det; its derivative
+  // 3 (x^2 - p^2) equals (x - x2)(x - x3) (Vieta: x + x2 + x3 = 0,
+  // x x2 + x x3 + x2 x3 = -3 p^2), the product the estimate below needs
+  const float gp = 3.0f * fmaf(x, x, -p2);
+  x = (gp != 0.0f) ? x - __fdividef(fmaf(x, fmaf(x, x, -p2x3), -det), gp) : x;
   m.full = ((1.0f + rf) < kPairTauF && p2 > 0.0f) || (x - x3) < tri_thr;
   const float lam1f = q + x;
   // the estimate over |l1| against kMixedEstTau, compared as a product (no division)
-  m.need64 = !m.full && kMixedEstCoef * p2 * pf > kMixedEstTau * fmaxf((x - x2) * (x - x3) * fabsf(lam1f), 1e-30f);
+  m.need64 = !m.full && kMixedEstCoef * p2 * pf > kMixedEstTau * fmaxf(gp * fabsf(lam1f), 1e-30f);
   m.q = q;
   m.x = x;
   m.x2 = x2;
@@ -595,6 +595,20 @@ __device__ __forceinline__ MixedCoef mixed_coef(const MixedEigen& m) {
   return k;
 }
 
+// One FP32 Newton step on A_1 that also returns the reciprocal of the
+// derivative it took (at the iterate before the step). The FP64 polish reuses
+// it: A_1' moves by ~1e-5 relative over that step (the seed's error), which
+// moves the polish's correction (~1e-7 D) by ~1e-12 D.
+struct RootF32 {
+  float D, rdA;
+};
+__device__ __forceinline__ RootF32 newton_f32_r(const MixedCoef& k, float Df) {
+  const float Af = fmaf(fmaf(fmaf(k.c3f, Df, k.c2f), Df, -k.l1f), Df, 1.0f);
+  const float dAf = fmaf(fmaf(3.0f * k.c3f, Df, 2.0f * k.c2f), Df, -k.l1f);
+  const float r = rcp_seed(dAf);
+  return RootF32{fmaf(-Af, r, Df), r};
+}
+
 // FP32 Newton steps on A_1(D) = 1 - l1 D + c2 D^2 + c3 D^3 from Df
 template <int kSteps>
 __device__ __forceinline__ float newton_f32(const MixedCoef& k, float Df) {
@@ -625,8 +639,9 @@ __device__ __forceinline__ float newton_f32(const MixedCoef& k, float Df) {
 //     the same side of D_top or D_0 except within ~1e-7 of them, where the two
 //     sides give the same a (a_max at D_top; the spline is continuous at D_0);
 //   FP32 -> FP64: for a collapsing point Df and v are positive normal
-//     numbers, A_1'(Df) a negative one (A_1 falls through zero at its first
-//     root) and t0 >= 0 (the interval search is exact, D_k = e_k, and on the
+//     numbers, 1/A_1' a negative one (A_1 is strictly decreasing on D > 0
+//     when l1 > 0, so A_1' < 0 at Df and at the positive iterate before it)
+//     and t0 >= 0 (the interval search is exact, D_k = e_k, and on the
 //     EdS segment t0 = Df), so they take the three-instruction to_f64_pos /
 //     to_f64_neg (a result that is not used may be any finite number; a zero
 //     t0 becomes 2^-127); c3 Df + c2 and lo(a_0 / D_0) D take to_f64_normal,
@@ -634,15 +649,15 @@ __device__ __forceinline__ float newton_f32(const MixedCoef& k, float Df) {
 // kEds = false: the caller sends EdS collapses (res.eds) elsewhere and uses
 // only the other results, so the EdS operand selects are left out; every
 // result with res.eds false is the same as with kEds = true.
+// rdA: the reciprocal of A_1' near Df (newton_f32_r's, or at Df itself).
 template <bool kEds = true>
-__device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const MixedCoef& k, float Df,
-                                                    const Coef4* __restrict__ coef, const float* __restrict__ Dkf,
-                                                    const unsigned short* __restrict__ bucket, const DevTable& tab,
-                                                    const float4* __restrict__ seg) {
+__device__ __forceinline__ MixedResult mixed_finish_r(const MixedEigen& m, const MixedCoef& k, float Df, float rdA,
+                                                      const Coef4* __restrict__ coef, const float* __restrict__ Dkf,
+                                                      const unsigned short* __restrict__ bucket, const DevTable& tab,
+                                                      const float4* __restrict__ seg) {
   MixedResult res;
   res.refined = false;
   res.fp64 = m.fp64;
-  const float dAf = fmaf(fmaf(3.0f * k.c3f, Df, 2.0f * k.c2f), Df, -k.l1f);
   const double D0 = to_f64_pos(Df);
   const double A1 = fma(fma(to_f64_normal(fmaf(k.c3f, Df, k.c2f)), D0, -m.lam1), D0, 1.0);
   res.collapsed = m.lam1f > 0.0f && Df > 0.0f && Df <= tab.Dtopf;
@@ -655,11 +670,21 @@ __device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const M
   const float t0 = eds ? Dcf : __fsub_rn(__fsub_rn(Dcf, s1.z), s1.w);
   const float v = eds ? tab.eds_hi : fmaf(fmaf(s1.y, t0, s1.x), t0, s0.z);
   const double head = eds ? to_f64_normal(tab.eds_lo * Dcf) : coef[kk].c0;
-  const double t = fma(-A1, to_f64_neg(rcp_seed(dAf)), to_f64_pos(t0));
+  const double t = fma(-A1, to_f64_neg(rdA), to_f64_pos(t0));
   const double av = fma(to_f64_pos(v), t, head);
   res.a = res.collapsed ? av : kInf;
   res.F = res.collapsed ? to_f64(1.0f / to_f32_trunc(av)) : 0.0;
   return res;
+}
+
+// The same with A_1' taken at Df.
+template <bool kEds = true>
+__device__ __forceinline__ MixedResult mixed_finish(const MixedEigen& m, const MixedCoef& k, float Df,
+                                                    const Coef4* __restrict__ coef, const float* __restrict__ Dkf,
+                                                    const unsigned short* __restrict__ bucket, const DevTable& tab,
+                                                    const float4* __restrict__ seg) {
+  const float dAf = fmaf(fmaf(3.0f * k.c3f, Df, 2.0f * k.c2f), Df, -k.l1f);
+  return mixed_finish_r<kEds>(m, k, Df, rcp_seed(dAf), coef, Dkf, bucket, tab, seg);
 }
 
 __device__ __forceinline__ MixedResult full_fp64(float xx, float yy, float zz, float xy, float xz, float yz,
@@ -689,8 +714,8 @@ __device__ __forceinline__ MixedResult collapse_point_mixed(
   // Newton step on A_1 (the seed is within ~1e-5, one step within ~2e-7, and
   // the FP64 polish squares that)
   const float uf = cubic_largest_root_seed(-k.l1f, k.c2f, k.c3f);
-  const float Df = newton_f32<1>(k, __fdividef(1.0f, uf));
-  return mixed_finish(m, k, Df, coef, Dkf, bucket, tab, tab.dfseg);
+  const RootF32 rt = newton_f32_r(k, __fdividef(1.0f, uf));
+  return mixed_finish_r(m, k, rt.D, rt.rdA, coef, Dkf, bucket, tab, tab.dfseg);
 }
 
 // ---------------------------------------------------------------------------

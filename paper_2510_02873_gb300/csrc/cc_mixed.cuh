@@ -48,8 +48,8 @@ __device__ __forceinline__ MixedResult mixed_easy(const MixedEigen& m, const Coe
                                                   const float4* __restrict__ seg) {
   const MixedCoef k = mixed_coef(m);
   const float uf = cubic_largest_root_seed(-k.l1f, k.c2f, k.c3f);
-  const float Df = newton_f32<1>(k, __fdividef(1.0f, uf));
-  return mixed_finish<kEds>(m, k, Df, coef, Dkf, bucket, tab, seg);
+  const RootF32 rt = newton_f32_r(k, __fdividef(1.0f, uf));
+  return mixed_finish_r<kEds>(m, k, rt.D, rt.rdA, coef, Dkf, bucket, tab, seg);
 }
 
 constexpr int32_t kHardHigh = 0x10000;  // HardRec::r1: marked radii >= 32
