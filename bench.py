@@ -39,14 +39,14 @@ WORKLOAD = "collapse 256^3 grid x 25 radii, FP64 SoA Hessian planes (20.1 GB res
 # of the 128^3 x 4 case divided by its evaluations (the FP64 and mixed kernels
 # as they stand; re-taken whenever either kernel changes).
 FP64_FLOPS_PER_EVAL = 67.0
-FP64_FLOPS_PER_EVAL_MIXED = 8.1
+FP64_FLOPS_PER_EVAL_MIXED = 7.96
 # FP64-pipe thread instructions of every kind (DFMA, DMUL, DADD, DSETP) per
 # evaluation, from the same captures: the FP64 unit issues one per lane slot
 # whatever the instruction, so this count, not the flop count, sets the time.
-# For the mixed kernel, whose FP64 instructions often run with idle lanes, the
-# lane slots the pipe was busy for (its busy fraction x 2 lanes/clk/SM x SM
-# cycles / evaluations) instead of the 4.1 thread instructions.
-FP64_PIPE_INST_PER_EVAL = {"fp64": 38.9, "mixed": 4.9}
+# For the mixed kernel, the lane slots the pipe was busy for (its busy
+# fraction x 2 lanes/clk/SM x active SM cycles / evaluations): 4.0 against
+# 3.98 DFMA thread instructions, its FP64 instructions running on full warps.
+FP64_PIPE_INST_PER_EVAL = {"fp64": 38.9, "mixed": 4.0}
 FP64_LANES_PER_CLK_PER_SM = 2.0
 # DRAM bytes (read + write) of a launch, scaled from the 128^3 x 4 ncu capture
 # of the FP64 kernel (dram__bytes_read 420.709632 MB, write 23.129344 MB for
