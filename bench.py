@@ -1111,6 +1111,21 @@ def run_config1_leg(ctx, dev) -> dict:
     return oracle_leg(stack, F.cpu().numpy(), idx.cpu().numpy(), 1e-10, False, single_points=4096)
 
 
+# Bound on every collective of a multi-rank run: a rank that dies or stops
+# answering surfaces on the others as an error at their next collective
+# (barrier or all_reduce) within this time instead of a hang.
+PG_TIMEOUT_S = 600.0
+
+
+def init_ranks(backend: str, timeout_s: float = PG_TIMEOUT_S) -> None:
+    """Join the process group (RANK, WORLD_SIZE, MASTER_ADDR/PORT from the
+    environment) with a bounded collective timeout."""
+    import datetime
+
+    import torch.distributed as dist
+    dist.init_process_group(backend, timeout=datetime.timedelta(seconds=timeout_s))
+
+
 def job_rate(elapsed_ms: float, evals: float, world: int, device) -> tuple:
     """Whole-job throughput over ranks: every rank's evaluations divided by the
     slowest rank's time (max over ranks)."""
@@ -1164,7 +1179,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
-        dist.init_process_group("nccl")
+        init_ranks("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     cc.buildlib.build() if hasattr(cc, "buildlib") else None
