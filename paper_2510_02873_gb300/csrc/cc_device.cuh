@@ -790,33 +790,29 @@ __device__ __forceinline__ TabResult collapse_point_tab(
   res.refined = e.refined;
   const double q = e.q, x = e.x, p2x3 = e.p2x3;
   const double lam1 = q + x;
-  const double Pp = fma(q, q - x, fma(x, x, -p2x3));  // l2 l3
-  const double S = fma(2.0, q, -x);                    // l2 + l3
-  // y = l2 - l3 from (l2 + l3)^2 - 4 l2 l3; near l2 = l3 that difference
-  // cancels: its rounding is ~eps (S^2 + 4 |l2 l3|), which for a nearly
-  // isotropic matrix (p -> 0) is not small next to p^2. Below 1e-10 of those
-  // scales the pair is re-solved by deflation around the isolated l1 (and
-  // stays S/2 each when no eigenvalue is isolated); the test is in FP32.
-  const double D2 = fma(S, S, -4.0 * Pp);
-  const float Sf = to_f32_trunc(S);
-  const float d2_scale = fmaf(Sf, Sf, fmaf(4.0f, fabsf(to_f32_trunc(Pp)), to_f32_trunc(p2x3)));
-  double l2, l3;
+  // x = l1 - l2 and y = l2 - l3 from the traceless part alone: the other two
+  // roots of x^3 - 3p^2 x - det are (-x +- y) / 2 with
+  // y^2 = (x2 - x3)^2 = (x2 + x3)^2 - 4 x2 x3 = x^2 - 4 (x^2 - 3p^2) = 4 (3p^2) - 3x^2
+  // (Vieta), so nothing cancels against the trace; x = 1.5 x - y / 2. Near
+  // x2 = x3 (y below ~3.5e-5 p, where y^2 cancels) the pair is re-solved by
+  // deflation around the isolated l1 (and stays at (l2 + l3) / 2 each when no
+  // eigenvalue is isolated, p = 0 included); the test is in FP32.
+  const double D2 = fma(x * -3.0, x, 4.0 * p2x3);
   const float D2f = to_f32_trunc(D2);
-  if (D2f < 1e-10f * d2_scale) {
-    l2 = 0.5 * S;
-    l3 = 0.5 * S;
+  double yv, xv;
+  if (D2f <= 1e-10f * (4.0f * to_f32_trunc(p2x3))) {
+    double l2 = 0.5 * fma(2.0, q, -x), l3 = l2;
     refine_top_pair(xx, yy, zz, xy, xz, yz, lam1, l2, l3);
     res.refined = true;
+    yv = l2 - l3;
+    xv = lam1 - l2;
   } else {
     // sqrt(D2): FP32 seed, one FP64 Newton step (relative error ~1e-13)
     const float yf = sqrt_seed(D2f);
     const double y0 = to_f64(yf);
-    const double yv = fma(fma(-y0, y0, D2), to_f64(0.5f * rcp_seed(yf)), y0);
-    const double hS = 0.5 * S;
-    l2 = fma(yv, 0.5, hS);  // 0.5 (S + yv), the same rounding
-    l3 = fma(yv, -0.5, hS);
+    yv = fma(fma(-y0, y0, D2), to_f64(0.5f * rcp_seed(yf)), y0);
+    xv = fma(yv, -0.5, 1.5 * x);
   }
-  double yv = l2 - l3, xv = lam1 - l2;
   yv = bits(yv) > 0 ? yv : 0.0;
   xv = bits(xv) > 0 ? xv : 0.0;
   const double delta = e.s;  // the trace
@@ -832,7 +828,8 @@ __device__ __forceinline__ TabResult collapse_point_tab(
     D = fma(r0, fma(-u, r0, 1.0), r0);  // 1/u: FP32 reciprocal + one FP64 Newton step
     root = bits(u) > 0;
   } else {
-    D = rlpt_root_fp64(lam1, Pp, S).D;
+    const double Pp = fma(q, q - x, fma(x, x, -p2x3));  // l2 l3
+    D = rlpt_root_fp64(lam1, Pp, fma(2.0, q, -x)).D;    // l2 + l3
   }
   const long long bD = bits(D);
   res.collapsed = bits(lam1) > 0 && root && bD > 0 && bD <= bits(tab.Dtop);

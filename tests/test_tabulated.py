@@ -109,6 +109,9 @@ def test_tabulated_degenerate_spectra(ctx, tables, table):
         spectra += [[s, s, s], [s, 0, 0], [s, 0.2 * s, 0.2 * s], [s, -s, -s], [0.05 * s, -s, -s]]
         for eps in (1e-3, 1e-6, 1e-9, 1e-12):
             spectra += [[s, s * (1 - eps), -0.4 * s], [s, 0.2 * s, 0.2 * s * (1 - eps)]]
+    # a small l2 - l3 on a large trace (l2 + l3 >> l2 - l3): the cell
+    # coordinates come from the traceless part, so nothing cancels against it
+    spectra += [[10.5, 10.2, 10.0], [13.1, 13.0, 12.95], [13.0, 12.9, 12.9 - 1e-7]]
     Ms = np.array([(lambda Q: Q @ np.diag(l) @ Q.T)(np.linalg.qr(rng.normal(size=(3, 3)))[0]) for l in spectra])
     planes = np.stack([Ms[:, 0, 0], Ms[:, 1, 1], Ms[:, 2, 2], Ms[:, 0, 1], Ms[:, 0, 2], Ms[:, 1, 2]])
     stack = planes[None]
