@@ -11,7 +11,9 @@
 // planes, per radius as one batched plan writing straight into the caller's
 // planes); the k-space products are this file's kernels. The Gaussian factor is
 // separable, G = g(k_x) g(k_y) g(k_z), so the per-mode work is products of
-// three table entries (host FP64 exp per axis) instead of an exp per mode.
+// three table entries (host FP64 exp per axis) instead of an exp per mode. The
+// rms s(R) sums over shells of equal k^2 (weighted mode counts per shell, built
+// once) instead of over modes.
 #include <cufft.h>
 
 #include <algorithm>
@@ -115,21 +117,35 @@ struct AxisTables32 {
   float kz0;
 };
 
-// sum over the full k grid of P(k) G(kR)^2 (half grid, modes 0 < iz < N/2 counted twice)
-__global__ void sigma_kernel(const AxisTables t, int64_t nc, double A, double n_idx, double k_cut, double R,
-                             double* __restrict__ acc) {
-  double s = 0.0;
+// P(k) G(kR)^2 depends on a mode only through the integer
+// n2 = sx^2 + sy^2 + sz^2 of its signed frequencies (k^2 = (2 pi / box)^2 n2).
+// shell_count_kernel adds each mode's weight over the full grid (modes with
+// 0 < iz < N/2 stand for their mirror images too, so 2; iz = 0 counts 1;
+// Nyquist modes and k = 0 are excluded) to its shell n2, once per field;
+// sigma_shell_kernel then sums one term per shell for each R.
+__global__ void shell_count_kernel(int64_t nc, int N, int Nz, unsigned long long* __restrict__ cnt) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int h = N / 2;
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nc; i += stride) {
     int ix, iy, iz;
-    decompose(i, t.N, t.Nz, ix, iy, iz);
-    const int h = t.N / 2;
+    decompose(i, N, Nz, ix, iy, iz);
     if (ix == h || iy == h || iz == h) continue;
-    const double kx = t.k[ix], ky = t.k[iy], kz = t.kz0 * iz;
-    const double k2 = fma(kx, kx, fma(ky, ky, kz * kz));
-    if (!(k2 > 0.0)) continue;
-    const double p = A * pow(sqrt(k2), n_idx) * exp(-k2 / (k_cut * k_cut)) * exp(-k2 * R * R);
-    s += (iz == 0) ? p : 2.0 * p;
+    const int sx = ix < h ? ix : ix - N, sy = iy < h ? iy : iy - N;
+    const int n2 = sx * sx + sy * sy + iz * iz;
+    if (n2 == 0) continue;
+    atomicAdd(cnt + n2, iz == 0 ? 1ull : 2ull);
+  }
+}
+
+__global__ void sigma_shell_kernel(const unsigned long long* __restrict__ cnt, int n_shells, double kf2, double A,
+                                   double n_idx, double k_cut, double R, double* __restrict__ acc) {
+  double s = 0.0;
+  const int stride = gridDim.x * blockDim.x;
+  for (int n2 = blockIdx.x * blockDim.x + threadIdx.x; n2 < n_shells; n2 += stride) {
+    const unsigned long long c = cnt[n2];
+    if (c == 0ull) continue;
+    const double k2 = kf2 * n2;
+    s += static_cast<double>(c) * (A * pow(sqrt(k2), n_idx) * exp(-k2 / (k_cut * k_cut)) * exp(-k2 * R * R));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
@@ -154,6 +170,8 @@ struct cc_field {
   void* work = nullptr;           // six k-space products
   size_t work_bytes = 0;
   double* acc = nullptr;          // sigma accumulator
+  unsigned long long* shells = nullptr;  // weighted mode count per n2 (built at the first sigma call)
+  int n_shells = 0;
   std::map<std::pair<int, int64_t>, cufftHandle> inv_plans;  // (dtype, plane_stride) -> batched inverse
 };
 
@@ -231,11 +249,29 @@ int cc_field_sigma(cc_field* f, double R, double* sigma, void* stream) {
   if (!(R >= 0.0) || !std::isfinite(R)) return set_error(CC_EINVAL, "R must be finite and >= 0");
   if (int rc = select_device(f->ctx)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!f->shells) {
+    const int h = f->N / 2;
+    const int n_shells = 3 * (h - 1) * (h - 1) + 1;  // largest n2 of a non-Nyquist mode, plus one
+    unsigned long long* cnt = nullptr;
+    if (int rc = check_cuda(cudaMalloc(&cnt, sizeof(unsigned long long) * n_shells), "cudaMalloc(shell counts)"))
+      return rc;
+    int rc = check_cuda(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * n_shells, st), "cudaMemsetAsync");
+    if (!rc) {
+      shell_count_kernel<<<grid_for(f->nc, f->ctx->num_sms), 256, 0, st>>>(f->nc, f->N, h + 1, cnt);
+      rc = check_cuda(cudaGetLastError(), "shell_count_kernel launch");
+    }
+    if (rc) {
+      cudaFree(cnt);
+      return rc;
+    }
+    f->shells = cnt;
+    f->n_shells = n_shells;
+  }
   if (int rc = check_cuda(cudaMemsetAsync(f->acc, 0, sizeof(double), st), "cudaMemsetAsync")) return rc;
-  const AxisTables t = axis_tables(f, 0.0);
-  sigma_kernel<<<grid_for(f->nc, f->ctx->num_sms), 256, 0, st>>>(t, f->nc, f->spec.amplitude, f->spec.index,
-                                                                  f->spec.k_cut, R, f->acc);
-  if (int rc = check_cuda(cudaGetLastError(), "sigma_kernel launch")) return rc;
+  const double kf = 2.0 * 3.14159265358979323846 / f->spec.box;
+  sigma_shell_kernel<<<grid_for(f->n_shells, f->ctx->num_sms), 256, 0, st>>>(
+      f->shells, f->n_shells, kf * kf, f->spec.amplitude, f->spec.index, f->spec.k_cut, R, f->acc);
+  if (int rc = check_cuda(cudaGetLastError(), "sigma_shell_kernel launch")) return rc;
   double s = 0.0;
   if (int rc = check_cuda(cudaMemcpyAsync(&s, f->acc, sizeof(double), cudaMemcpyDeviceToHost, st), "D2H sigma")) return rc;
   if (int rc = check_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize")) return rc;
@@ -312,6 +348,7 @@ void cc_field_destroy(cc_field* f) {
   if (f->dk) cudaFree(f->dk);
   if (f->work) cudaFree(f->work);
   if (f->acc) cudaFree(f->acc);
+  if (f->shells) cudaFree(f->shells);
   delete f;
 }
 
