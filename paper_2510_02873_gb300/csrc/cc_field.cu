@@ -12,8 +12,8 @@
 // planes); the k-space products are this file's kernels. The Gaussian factor is
 // separable, G = g(k_x) g(k_y) g(k_z), so the per-mode work is products of
 // three table entries (host FP64 exp per axis) instead of an exp per mode. The
-// rms s(R) sums over shells of equal k^2 (weighted mode counts per shell, built
-// once) instead of over modes.
+// colouring and the rms s(R) work on shells of equal k^2 (sqrt(P) per shell;
+// weighted mode counts per shell, built once) instead of on every mode.
 #include <cufft.h>
 
 #include <algorithm>
@@ -52,25 +52,32 @@ __device__ __forceinline__ void decompose(int64_t idx, int N, int Nz, int& ix, i
   ix = static_cast<int>(r / N);
 }
 
-// delta_k = DFT(w) sqrt(P(k)); Nyquist modes and k = 0 zeroed
-__global__ void color_kernel(double2* __restrict__ dk, int64_t nc, const AxisTables t, double A, double n_idx,
-                             double k_cut) {
+// sqrt(P(k)) per shell n2 (k^2 = kf2 n2; shell 0, k = 0, gets 0)
+__global__ void shell_amp_kernel(int n_shells, double kf2, double A, double n_idx, double k_cut,
+                                 double* __restrict__ amp) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int n2 = blockIdx.x * blockDim.x + threadIdx.x; n2 < n_shells; n2 += stride) {
+    const double k2 = kf2 * n2;
+    amp[n2] = (n2 > 0) ? sqrt(A * pow(sqrt(k2), n_idx) * exp(-k2 / (k_cut * k_cut))) : 0.0;
+  }
+}
+
+// delta_k = DFT(w) sqrt(P(k)) from the shell table; Nyquist modes zeroed
+__global__ void color_kernel(double2* __restrict__ dk, int64_t nc, int N, int Nz,
+                             const double* __restrict__ amp) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int h = N / 2;
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < nc; i += stride) {
     int ix, iy, iz;
-    decompose(i, t.N, t.Nz, ix, iy, iz);
-    const int h = t.N / 2;
-    const bool nyq = ix == h || iy == h || iz == h;
-    const double kx = t.k[ix], ky = t.k[iy], kz = t.kz0 * iz;
-    const double k2 = fma(kx, kx, fma(ky, ky, kz * kz));
-    double amp = 0.0;
-    if (!nyq && k2 > 0.0) {
-      const double k = sqrt(k2);
-      amp = sqrt(A * pow(k, n_idx) * exp(-k2 / (k_cut * k_cut)));
+    decompose(i, N, Nz, ix, iy, iz);
+    double a = 0.0;
+    if (ix != h && iy != h && iz != h) {
+      const int sx = ix < h ? ix : ix - N, sy = iy < h ? iy : iy - N;
+      a = __ldg(amp + (sx * sx + sy * sy + iz * iz));
     }
     double2 v = dk[i];
-    v.x *= amp;
-    v.y *= amp;
+    v.x *= a;
+    v.y *= a;
     dk[i] = v;
   }
 }
@@ -225,17 +232,28 @@ int cc_field_create(cc_ctx* ctx, const double* white, int32_t N, const cc_spectr
   // an out-of-place real-to-complex transform leaves its input unchanged
   if (!rc) rc = check_cufft(cufftExecD2Z(fwd, const_cast<double*>(white), reinterpret_cast<cufftDoubleComplex*>(f->dk)),
                             "cufftExecD2Z");
+  // sqrt(P) per shell n2 of the non-Nyquist modes (the shells of s(R))
+  const int h = N / 2;
+  const int n_shells = 3 * (h - 1) * (h - 1) + 1;
+  double* amp = nullptr;
+  if (!rc) rc = check_cuda(cudaMalloc(&amp, sizeof(double) * n_shells), "cudaMalloc(shell amplitudes)");
   if (!rc) {
-    const AxisTables t = axis_tables(f, 0.0);
-    color_kernel<<<grid_for(f->nc, ctx->num_sms), 256, 0, st>>>(f->dk, f->nc, t, spec->amplitude, spec->index,
-                                                                 spec->k_cut);
+    const double kf = 2.0 * 3.14159265358979323846 / spec->box;
+    shell_amp_kernel<<<grid_for(n_shells, ctx->num_sms), 256, 0, st>>>(n_shells, kf * kf, spec->amplitude,
+                                                                        spec->index, spec->k_cut, amp);
+    rc = check_cuda(cudaGetLastError(), "shell_amp_kernel launch");
+  }
+  if (!rc) {
+    color_kernel<<<grid_for(f->nc, ctx->num_sms), 256, 0, st>>>(f->dk, f->nc, N, h + 1, amp);
     rc = check_cuda(cudaGetLastError(), "color_kernel launch");
   }
-  if (have_plan) {
-    // the plan may be released only after the transform has run
-    if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize");
-    cufftDestroy(fwd);
+  // the plan and the shell table may be released only after the kernels have run
+  if (have_plan || amp) {
+    const int rs = check_cuda(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    if (!rc) rc = rs;
   }
+  if (have_plan) cufftDestroy(fwd);
+  if (amp) cudaFree(amp);
   if (rc) {
     cc_field_destroy(f);
     return rc;
