@@ -68,6 +68,28 @@ def test_planes_match_oracle(ctx, white, R):
     f.close()
 
 
+@pytest.mark.parametrize("n_side", [4, 6, 10])
+def test_small_and_uneven_grids(ctx, n_side):
+    """The smallest grid and even sides that are not powers of two: planes and
+    s(R) (whose shell tables are sized from the side) against the oracle."""
+    import paper_2510_02873_gb300 as cc
+    spec = dict(SPEC, box=2.0 * n_side)
+    w = hessgen.white_noise(2600 + n_side, 0, n_side ** 3)
+    f = cc.Field(ctx, torch.from_numpy(w).cuda(), **spec)
+    dk = oracle.field_delta_k(w.reshape(n_side, n_side, n_side), **spec)
+    for R in (0.0, 1.5):
+        want = oracle.hessian_from_delta_k(dk, n_side, spec["box"], R)
+        planes = torch.empty((6, n_side ** 3), dtype=torch.float64, device="cuda")
+        f.hessian(R, planes)
+        torch.cuda.synchronize()
+        got = planes.cpu().numpy()
+        assert np.abs(got - want).max() <= 1e-13 * max(np.abs(want).max(), 1e-300)
+        s = f.sigma(R)
+        want_s = oracle.field_sigma(n_side, spec["box"], spec["amplitude"], spec["index"], spec["k_cut"], R)
+        assert abs(s - want_s) <= 1e-12 * want_s
+    f.close()
+
+
 def test_sigma_matches_oracle(ctx, white):
     f = make_field(ctx, white)
     for R in (0.5, 1.0, 4.0, 12.0):
