@@ -19,6 +19,8 @@
 // near-degenerate eigenvalue pair and the EdS range below the table.
 #pragma once
 
+#include <cstring>
+
 #include "cc_internal.h"
 
 namespace cc {
@@ -723,6 +725,18 @@ __device__ __forceinline__ MixedResult collapse_point_mixed(
 // delta at the four (x, y) corners of the cell, bilinear blend). The table holds
 // u = 1/D_c; outside it the R-LPT root is used.
 
+// An integer that orders like the FP64 value v (NaN aside): the bit pattern b
+// for b >= 0; for b < 0, minus its magnitude bits, so -0.0 and +0.0 both give 0.
+__host__ __device__ __forceinline__ long long order_key(double v) {
+#ifdef __CUDA_ARCH__
+  const long long b = __double_as_longlong(v);
+#else
+  long long b;
+  std::memcpy(&b, &v, sizeof(b));
+#endif
+  return b < 0 ? -static_cast<long long>(static_cast<unsigned long long>(b) - 0x8000000000000000ull) : b;
+}
+
 __device__ __forceinline__ double horner(const Coef4& c, double t) {
   return fma(fma(fma(c.c3, t, c.c2), t, c.c1), t, c.c0);
 }
@@ -817,8 +831,10 @@ __device__ __forceinline__ TabResult collapse_point_tab(
   xv = bits(xv) > 0 ? xv : 0.0;
   const double delta = e.s;  // the trace
   // inside the hull [d_0, d_last] x [x_0, x_last] x [y_0, y_last]: xv, yv and
-  // the axis bounds are >= 0, so their bit patterns order like their values
-  res.outside = !(delta >= td.d_lo && delta <= td.d_hi && bits(xv) >= bits(td.x_lo) && bits(xv) <= bits(td.x_hi) &&
+  // the axis bounds are >= 0, so their bit patterns order like their values;
+  // delta by its order key (a NaN of either sign falls outside)
+  const long long dkey = order_key(delta);
+  res.outside = !(dkey >= td.d_lo_key && dkey <= td.d_hi_key && bits(xv) >= bits(td.x_lo) && bits(xv) <= bits(td.x_hi) &&
                   bits(yv) >= bits(td.y_lo) && bits(yv) <= bits(td.y_hi));
   double D;
   bool root = true;

@@ -103,6 +103,7 @@ struct TabDev {
   int nd, nx, ny;
   int d_steps, x_steps, y_steps;  // largest power of two <= n - 2 (branch-free searches)
   double d_lo, d_hi, x_lo, x_hi, y_lo, y_hi;  // the table's hull (first and last knot of each axis)
+  long long d_lo_key, d_hi_key;                // order keys of d_lo, d_hi (order_key in cc_device.cuh)
   unsigned int* dbg;                          // the launch's error flags (index checks of debug builds)
   __host__ __device__ size_t axes_bytes() const {
     return sizeof(double) * (nd + nx + ny + 2 * (nx - 1) + 2 * (ny - 1)) + sizeof(float) * nd;

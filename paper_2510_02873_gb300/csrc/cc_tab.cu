@@ -235,6 +235,10 @@ int cc_set_table(cc_ctx* ctx, const double* dgrid, int32_t nd, const double* xgr
   td.y_steps = pow2_steps(ny);
   td.d_lo = dgrid[0];
   td.d_hi = dgrid[nd - 1];
+  // integer keys that order like the values: the hull test on delta takes
+  // no FP64 compare
+  td.d_lo_key = order_key(td.d_lo);
+  td.d_hi_key = order_key(td.d_hi);
   td.x_lo = xgrid[0];
   td.x_hi = xgrid[nx - 1];
   td.y_lo = ygrid[0];
