@@ -46,7 +46,7 @@ FP64_FLOPS_PER_EVAL_MIXED = 7.96
 # For the mixed kernel, the lane slots the pipe was busy for (its busy
 # fraction x 2 lanes/clk/SM x active SM cycles / evaluations): 4.0 against
 # 3.98 DFMA thread instructions, its FP64 instructions running on full warps.
-FP64_PIPE_INST_PER_EVAL = {"fp64": 38.9, "mixed": 4.0}
+FP64_PIPE_INST_PER_EVAL = {"fp64": 38.5, "mixed": 4.0}
 FP64_LANES_PER_CLK_PER_SM = 2.0
 # DRAM bytes (read + write) of a launch, scaled from the 128^3 x 4 ncu capture
 # of the FP64 kernel (dram__bytes_read 420.709632 MB, write 23.129344 MB for

@@ -397,9 +397,14 @@ struct MinA {
   }
 };
 
-// Finiteness of an FP64 value from its bit pattern (exponent not all ones).
+// Finiteness of an FP64 value from its bit pattern (exponent not all ones),
+// on the integer pipes: the high word comes from an opaque move, because the
+// compiler recognises the masked 64-bit test as a floating-point class check
+// and issues an FP64 compare, which this GPU runs on its FP64 unit.
 __device__ __forceinline__ bool finite_bits(double v) {
-  return (bits(v) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+  unsigned lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(v));
+  return (hi & 0x7ff00000u) != 0x7ff00000u;
 }
 
 // a on the spline interval whose polynomial is expanded about the FP32 knot
