@@ -49,12 +49,12 @@ FP64_FLOPS_PER_EVAL_MIXED = 7.96
 FP64_PIPE_INST_PER_EVAL = {"fp64": 38.5, "mixed": 4.0}
 FP64_LANES_PER_CLK_PER_SM = 2.0
 # DRAM bytes (read + write) of a launch, scaled from the 128^3 x 4 ncu capture
-# of the FP64 kernel (dram__bytes_read 420.709632 MB, write 23.129344 MB for
+# of the FP64 kernel (dram__bytes_read 420.716544 MB, write 23.085056 MB for
 # 8,388,608 evaluations of 2,097,152 points): the planes are read once, 48 B
 # per evaluation; the rest (F_max/idx read and written for collapsed points)
 # scales with the points. The full 20 GB launch is not captured.
 TRAFFIC_PLANE_BYTES_PER_EVAL = 48.0
-TRAFFIC_OUT_BYTES_PER_POINT = (420.709632e6 - 48.0 * 8388608 + 23.129344e6) / 2097152
+TRAFFIC_OUT_BYTES_PER_POINT = (420.716544e6 - 48.0 * 8388608 + 23.085056e6) / 2097152
 # FP64 FMA rate of one GB300 SM: 1.25 TFLOP/s nominal at 2070 MHz over 152 SMs
 # = 3.97 flop/clk/SM, i.e. 2 DFMA per clock per SM (confirmed by a DFMA-chain probe).
 FP64_FLOP_PER_CLK_PER_SM = 4.0
