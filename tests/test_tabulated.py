@@ -208,6 +208,38 @@ def test_tabulated_hull_with_axes_above_zero(tables):
     print("tabulated hull x, y >= 0.3", s, "outside", int(out.sum()))
 
 
+def test_tabulated_delta_hull_at_signed_zero(tables):
+    """A delta axis that starts at 0: a point whose trace is exactly -0.0 (all
+    three diagonal entries -0.0) is treated as one with trace +0.0 and the
+    same off-diagonal entries (inside the table, as the FP64 comparison with
+    the axis end has it; the oracle, whose trace comes from its eigenvalues,
+    flags both as on the hull's edge), and points with a trace of -1e-3 lie
+    outside (R-LPT root)."""
+    import paper_2510_02873_gb300 as cc
+    _, xg, yg = table_axes()
+    dg = np.linspace(0.0, 40.0, 64)
+    val = oracle.tab_node_values(dg, xg, yg)
+    tab = oracle.Tab(dg, xg, yg, val)
+    rng = np.random.default_rng(47)
+    m = 1000
+    off = rng.normal(size=(3, m)) * 0.8
+    neg0 = np.concatenate([np.full((3, m), -0.0), off])
+    pos0 = np.concatenate([np.zeros((3, m)), off])
+    shifted = pos0.copy()
+    shifted[0] = -1e-3
+    planes = np.concatenate([neg0, pos0, shifted], axis=1)
+    assert np.all(np.signbit((planes[0] + planes[1] + planes[2])[:m]))  # the trace is -0.0 there
+    stack = planes[None]
+    F_all, fl = oracle_tab_per_radius(tables, tab, stack)
+    assert np.all((fl[0, 2 * m:] & oracle.FLAG_HULL_OUT) != 0)
+    with cc.Context(0.3, 0.7, 512, 1e-3, 1.0, device=0) as c:
+        c.set_table(dg, xg, yg, val)
+        F, idx, st = run_tab(c, stack, [1.0])
+    assert np.array_equal(F[:m], F[m:2 * m]) and np.array_equal(idx[:m], idx[m:2 * m])
+    assert (F[:m] > 0).sum() > m // 2
+    compare_max(F, idx, F_all, fl)
+
+
 def test_table_query_toy(ctx, table):
     """The spline x bilinear routine on its own (the paper's 64 x 64 grid with a
     128-knot spline per node), against the oracle's query."""
