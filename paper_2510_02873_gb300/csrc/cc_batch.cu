@@ -87,6 +87,7 @@ __device__ __forceinline__ void run_point_mixed(const BatchItemDev& it, int item
   MinA best;
   uint32_t mask = 0;
   bool hi = false;
+  const double F_old = active ? it.F_max[p] : 0.0;
   if (active) {
     const T* base = static_cast<const T*>(it.hess) + p;
     for (int r = 0; r < it.R; ++r) {
@@ -107,7 +108,7 @@ __device__ __forceinline__ void run_point_mixed(const BatchItemDev& it, int item
   }
   const int64_t key = (static_cast<int64_t>(item) << kItemShift) | p;
   mixed_record_or_store(active, key, best, mask, hi, hw, it.F_max + (active ? p : 0), it.idx + (active ? p : 0),
-                        it.scale_idx0);
+                        it.scale_idx0, F_old);
 }
 
 template <bool kMixed, int kBlock>

@@ -384,6 +384,16 @@ struct MinA {
       r = radius;
     }
   }
+  // the same merge against a value of F_max read earlier by this thread
+  template <bool kF32Recip>
+  __device__ __forceinline__ void store_vs(double F_old, double* F_max, int32_t* idx, int32_t scale_idx0) const {
+    if (r < 0) return;
+    const double F = kF32Recip ? to_f64(1.0f / to_f32_trunc(a)) : recip_fp64(a);
+    if (bits(F) > bits(F_old)) {
+      *F_max = F;
+      *idx = scale_idx0 + r;
+    }
+  }
   // merge into the stored maximum: F = 1/a (FP64, or through the FP32
   // reciprocal for the reduced-precision modes), strict '>' against F_max
   template <bool kF32Recip>

@@ -177,6 +177,7 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
       MixedCounts cn;
       uint32_t mask = 0;
       bool hi = false;
+      const double F_old = active ? F_max[p] : 0.0;
       if (active) {
         for (int r = 0; r < R; ++r) {
           const T* h = hess + p + static_cast<int64_t>(r) * radius_stride;
@@ -201,7 +202,7 @@ collapse_kernel(const T* __restrict__ hess, int64_t n, int64_t plane_stride,
         n_eval += R;
       }
       n_coll += cn.coll;
-      mixed_record_or_store(active, p, best, mask, hi, hw, F_max + p, idx + p, scale_idx0);
+      mixed_record_or_store(active, p, best, mask, hi, hw, F_max + p, idx + p, scale_idx0, F_old);
     } else if (kMode == kModeFP64 && active) {
       // kFp64Radii radii per iteration: independent FP64 chains that the
       // compiler interleaves, so the FP64 unit meets fewer gaps while a warp

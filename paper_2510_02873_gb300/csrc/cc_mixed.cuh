@@ -68,9 +68,11 @@ __device__ __forceinline__ Planes6 load6(const T* h, int64_t ps) {
 // slots (one atomic per warp) under `key` (the point, or the point and its
 // batch item). A point whose slot is beyond the capacity keeps F_max and marks
 // idx as -(idx + 3) (idx is -1 or a scale index, so the mark is <= -2).
+// F_old: the point's F_max, read before its radii so that the load's latency
+// is hidden behind them (only this thread reads or writes that entry).
 __device__ __forceinline__ void mixed_record_or_store(bool active, int64_t key, const MinA& best, uint32_t mask,
                                                       bool hi, const HardWork& hw, double* __restrict__ F_max,
-                                                      int32_t* __restrict__ idx, int32_t scale_idx0) {
+                                                      int32_t* __restrict__ idx, int32_t scale_idx0, double F_old) {
   const bool need = active && (mask != 0u || hi);
   const unsigned bal = __ballot_sync(0xffffffffu, need);
   if (bal != 0u) {
@@ -94,7 +96,7 @@ __device__ __forceinline__ void mixed_record_or_store(bool active, int64_t key, 
       }
     }
   }
-  if (active && !need) best.store<true>(F_max, idx, scale_idx0);
+  if (active && !need) best.store_vs<true>(F_old, F_max, idx, scale_idx0);
 }
 
 // Where the record workers find a point's planes, thresholds and outputs.
