@@ -99,6 +99,7 @@ int run_collapse(cc_ctx* ctx, cc_mode mode, const void* hess, int32_t dtype, int
                  int64_t plane_stride, int64_t radius_stride, const double* sigma, int32_t R,
                  double* F_max, int32_t* idx, int32_t scale_idx0, void* stream) {
   if (ctx == nullptr) return set_error(CC_EINVAL, "ctx is NULL");
+  if (mode < CC_MODE_FP64 || mode > CC_MODE_EXACT_GROWTH) return set_error(CC_EINVAL, "unknown mode");
   if (R < 1) return set_error(CC_EINVAL, "R must be >= 1");
   if (sigma == nullptr) return set_error(CC_EINVAL, "sigma is NULL");
   for (int r = 0; r < R; ++r)

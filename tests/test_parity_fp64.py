@@ -1,6 +1,8 @@
 """GPU parity of the FP64-accurate collapse paths (C-ABI through the binding) against the
 oracle: CC_MODE_FP64 (FP64 unit) and CC_MODE_F32X2 (the same steps in float-float
 arithmetic), both held to 1e-10 relative."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -221,8 +223,12 @@ def test_invalid_arguments_are_rejected(ctx):
     assert L.cc_collapse_scale(h, 0, p, 8, n, n, 1.0, F.data_ptr(), idx.data_ptr(), -1, s) == _lib.CC_EINVAL
     assert L.cc_collapse_scale(h, 7, p, 8, n, n, 1.0, F.data_ptr(), idx.data_ptr(), 0, s) == _lib.CC_EINVAL
     assert L.cc_collapse_scale(h, 0, p, 8, n, n, 1.0, None, idx.data_ptr(), 0, s) == _lib.CC_EINVAL
-    # empty input is a no-op
-    assert L.cc_collapse_scale(h, 0, None, 8, 0, 0, 1.0, None, None, 0, s) == _lib.CC_OK
+    # empty input is a no-op in every mode, and an unknown mode is rejected even then
+    for mode in range(6):
+        assert L.cc_collapse_scale(h, mode, None, 8, 0, 0, 1.0, None, None, 0, s) == _lib.CC_OK
+        sig2 = (ctypes.c_double * 2)(1.0, 2.0)
+        assert L.cc_collapse_multi(h, mode, None, 4, 0, 0, 0, sig2, 2, None, None, 0, s) == _lib.CC_OK
+    assert L.cc_collapse_scale(h, 7, None, 8, 0, 0, 1.0, None, None, 0, s) == _lib.CC_EINVAL
     with pytest.raises(cc.CollapseError):  # 8-byte plane stride
         ctx.collapse_scale(buf[:6 * (n + 1)].view(6, n + 1)[:, :n], 1.0, F, idx, 0)
 
