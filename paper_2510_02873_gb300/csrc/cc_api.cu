@@ -303,10 +303,13 @@ int cc_create(cc_ctx** out, const cc_cosmology* cosmo, int device) {
     for (int o = 0; o < 3 && !rc; ++o)
       rc = natural_spline_into(n, ctx->D_k.data(), r.data() + o * n, c64.data() + o * 4 * (n - 1), work.data());
     for (int o = 0; o < 3 && !rc; ++o) expand_about_f32_knots(n, ctx->D_k.data(), c64.data() + o * 4 * (n - 1));
-    // stored as r2, -r3a / 3 and -r3b / 2: the third-order term is then
-    // l1 (r3a' l2 l3 + r3b' (l2^2 + l3^2)) (see cc_exact.cuh)
+    // stored as r2, ra = -r3a / 3 + r3b and rb = -r3b / 2 (splines are linear
+    // in their node values, so these are the splines of those combinations):
+    // with r3a' = -r3a / 3 and r3b' = -r3b / 2 the third-order term
+    // l1 (r3a' l2 l3 + r3b' (l2^2 + l3^2)) is l1 (ra l2 l3 + rb (l2 + l3)^2)
+    // (see cc_exact.cuh)
     for (size_t i = 0; i < 4 * static_cast<size_t>(n - 1); ++i) {
-      c64[4 * (n - 1) + i] *= -1.0 / 3.0;
+      c64[4 * (n - 1) + i] = c64[4 * (n - 1) + i] * (-1.0 / 3.0) + c64[8 * (n - 1) + i];
       c64[8 * (n - 1) + i] *= -0.5;
     }
     if (rc) { cc_destroy(ctx); return set_error(rc, "growth ratio tables failed"); }

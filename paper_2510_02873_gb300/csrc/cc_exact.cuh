@@ -6,10 +6,12 @@
 //
 //   A_1(D) = 1 - l1 D + r2(D) l2 l3 D^2 + l1 [r3a'(D) l2 l3 + r3b'(D) (l2^2 + l3^2)] D^3,
 //   r3a' = -r3a / 3,  r3b' = -r3b / 2,
-// with r2 = D2/D1^2, r3a = D3a/D1^3, r3b = D3b/D1^3 natural splines in D over
-// the growth-table knots, stored already scaled (EdS values below the first
-// knot, the last value beyond the last knot, where no root counts as a
-// collapse). In EdS r3a' = 1/9 and r3b' = -5/21, the R-LPT coefficients. The
+// with r2 = D2/D1^2, r3a = D3a/D1^3, r3b = D3b/D1^3. With
+// l2^2 + l3^2 = (l2 + l3)^2 - 2 l2 l3 the bracket is ra l2 l3 + rb (l2 + l3)^2,
+// ra = r3a' - 2 r3b', rb = r3b': r2, ra and rb are natural splines in D over
+// the growth-table knots (EdS values below the first knot, the last value
+// beyond the last knot, where no root counts as a collapse). In EdS
+// r3a' = 1/9 and r3b' = -5/21, the R-LPT coefficients, so ra = 37/63. The
 // root starts from the EdS root (closed form, FP32), takes three FP32 Newton
 // steps with the FP32 ratio splines and their derivatives, then one FP64 Newton
 // step with the FP64 splines that yields t = D - e_k for the a(D) spline
@@ -21,11 +23,11 @@
 namespace cc {
 namespace exact {
 
-// EdS ratios (below the first knot): r2, r3a' = -r3a / 3, r3b' = -r3b / 2
-constexpr double kEds2 = -3.0 / 7.0, kEdsA = 1.0 / 9.0, kEdsB = -5.0 / 21.0;
+// EdS ratios (below the first knot): r2, ra = r3a' - 2 r3b', rb = r3b'
+constexpr double kEds2 = -3.0 / 7.0, kEdsA = 37.0 / 63.0, kEdsB = -5.0 / 21.0;
 
 // A_1 and its derivative in FP32 at D (ratios from the FP32 splines);
-// u2 = l2 l3, Q = l2^2 + l3^2
+// u2 = l2 l3, Q = (l2 + l3)^2
 __device__ __forceinline__ void stretch_f32(const DevTable& tab, const float* __restrict__ Dkf,
                                             const unsigned short* __restrict__ bucket, float D, float l1, float u2,
                                             float Q, float& A, float& dA) {
@@ -74,7 +76,7 @@ __device__ __forceinline__ Result collapse_point(double xx, double yy, double zz
   const double lam1 = fma(s, 1.0 / 3.0, x);
   const double Pp = fma(e.q, fma(s, 1.0 / 3.0, -x), fma(x, x, -p2x3));  // l2 l3
   const double S = fma(s, 2.0 / 3.0, -x);                               // l2 + l3
-  const double Q = fma(S, S, Pp * -2.0);                                // l2^2 + l3^2
+  const double Q = S * S;                                               // (l2 + l3)^2
   // ---- FP32: EdS root, then three Newton steps with the exact ratios
   const float l1f = to_f32_trunc(lam1), u2f = to_f32_trunc(Pp), Qf = to_f32_trunc(Q);
   const float c3f = l1f * fmaf(static_cast<float>(kEdsA), u2f, static_cast<float>(kEdsB) * Qf);

@@ -79,7 +79,7 @@ struct DevTable {
   const float4* dfseg;
   float Dtop_hi, Dtop_lo, D0_hi, D0_lo, eds_hi, eds_lo;  // float-float constants
   // exact-background growth ratios as natural splines in D over the same
-  // knots (CC_MODE_EXACT_GROWTH), stored as r2, -r3a / 3 and -r3b / 2:
+  // knots (CC_MODE_EXACT_GROWTH), stored as r2, -r3a / 3 + r3b and -r3b / 2:
   // rc64[o * (n - 1) + k] (FP64) and rc32[...] (FP32 copies, {c0, c1, c2,
   // c3}); nullptr when absent
   const Coef4* rc64;
