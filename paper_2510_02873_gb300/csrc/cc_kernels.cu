@@ -102,7 +102,7 @@ mixed_full_kernel(const T* __restrict__ hess, int64_t plane_stride, int64_t radi
 // float-float path (dfl::collapse_point), the exact-growth path
 // (exact::collapse_point) or collapse_point_tab (tabulated 1/D_c; its axes
 // follow the spline table in shared memory).
-// FP64 path: two radii per iteration at 2 blocks of 256 threads per SM (92
+// FP64 path: two radii per iteration at 2 blocks of 256 threads per SM (94
 // registers, no spill): 1.3 % faster than one radius at 4 blocks and 64
 // registers; 3 or 4 radii per iteration, or 1 block, measured the same.
 // Mixed path: 5 blocks per SM at 48 registers, each staging the table image
