@@ -27,11 +27,13 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-GRID = 256
-N_RADII = 25
-S_LO, S_HI = 0.2, 6.0
-SEED = 2512
-COSMO = dict(omega_m=0.3, omega_l=0.7, n_knots=512, a_min=1e-3, a_max=1.0)
+from paper_2510_02873_gb300 import configs as CFG  # noqa: E402  (the workloads as data)
+
+GRID = CFG.FP64.grid
+N_RADII = CFG.FP64.radii
+S_LO, S_HI = CFG.FP64.s_lo, CFG.FP64.s_hi
+SEED = CFG.FP64.seed
+COSMO = CFG.COSMOLOGY.kwargs()
 WORKLOAD = "collapse 256^3 grid x 25 radii, FP64 SoA Hessian planes (20.1 GB resident), 512-knot a(D) spline"
 
 # FP64 floating-point operations per (point, radius) evaluation of the FP64
@@ -774,7 +776,7 @@ def run_toys_variant(ctx, dev, stream, reps: int = 10, max_queries: int = 10 ** 
 
 
 # ----------------------------------------------------------------------------- mixed variant
-MIXED_GRID, MIXED_RADII = 512, 30
+MIXED_GRID, MIXED_RADII = CFG.MIXED.grid, CFG.MIXED.radii
 
 
 def run_mixed_variant(ctx, dev, stream, reps: int = 3, sample: int = 100000) -> dict:
@@ -793,7 +795,7 @@ def run_mixed_variant(ctx, dev, stream, reps: int = 3, sample: int = 100000) -> 
     clk_mhz = clk_mhz_default(dev)
     hess = torch.empty((R, 6, n), dtype=torch.float32, device=dev)
     for r in range(R):
-        hdev.fill(hess[r], SEED + 1, 0, r, sig[r])
+        hdev.fill(hess[r], CFG.MIXED.seed, 0, r, sig[r])
     out = {}
     F = {}
     for mode in ("fp64", "mixed"):
@@ -864,8 +866,8 @@ def run_mixed_variant(ctx, dev, stream, reps: int = 3, sample: int = 100000) -> 
 
 
 # ----------------------------------------------------------------------------- batched variant
-BATCH_SEED, BATCH_N = 2514, 48
-BATCH_GRIDS = (64, 96, 128, 192, 256, 384)
+BATCH_SEED, BATCH_N = CFG.BATCHED.seed, CFG.BATCHED.realizations
+BATCH_GRIDS = CFG.BATCHED.grids
 
 
 def merge_parity(reports: list) -> dict:
@@ -899,7 +901,7 @@ def run_batch_variant(ctx, dev, stream, reps: int = 3, grids=BATCH_GRIDS, n_item
     rng = np.random.default_rng(BATCH_SEED)
     grid_choice = grids
     grids = rng.choice(grid_choice, n_items)
-    radii = rng.integers(8, 41, n_items)
+    radii = rng.integers(CFG.BATCHED.radii_range[0], CFG.BATCHED.radii_range[1] + 1, n_items)
     items = []
     for k, (g, R) in enumerate(zip(grids, radii)):
         n, R = int(g) ** 3, int(R)
@@ -986,8 +988,8 @@ def run_batch_variant(ctx, dev, stream, reps: int = 3, grids=BATCH_GRIDS, n_item
 
 
 # ----------------------------------------------------------------------------- surrogate variant
-SUR_GRID, SUR_RADII = 768, 40
-SUR_TRAIN_POINTS = 40 * 1024 * 1024  # ~2e7 collapsing samples at s = 1
+SUR_GRID, SUR_RADII = CFG.SURROGATE.grid, CFG.SURROGATE.radii
+SUR_TRAIN_POINTS = CFG.SURROGATE_TRAIN_POINTS  # ~2e7 collapsing samples at s = 1
 
 
 def run_surrogate_variant(ctx, dev, stream, steps: int = 3000, sample: int = 100000) -> dict:
@@ -1023,7 +1025,7 @@ def run_surrogate_variant(ctx, dev, stream, steps: int = 3000, sample: int = 100
     pi = torch.from_numpy(pts).to(dev)
     sample_planes = np.empty((R, 6, len(pts)), dtype=np.float32)
     for r in range(R):
-        hdev.fill(planes, SEED + 6, 0, r, sig[r])
+        hdev.fill(planes, CFG.SURROGATE.seed, 0, r, sig[r])
         sample_planes[r] = planes.index_select(1, pi).cpu().numpy()
         for m, (F, idx) in outs.items():
             ctx.reset_stats()
@@ -1099,9 +1101,10 @@ def run_config1_leg(ctx, dev) -> dict:
 
     import hessgen
 
-    n, R = 32 ** 3, 8
-    sig = hessgen.sigma_schedule(R, 0.3, 4.0)
-    stack = hessgen.hessian_stack(2511, 0, sig, n)
+    w = CFG.SMALL_FP64
+    n, R = w.points, w.radii
+    sig = hessgen.sigma_schedule(R, w.s_lo, w.s_hi)
+    stack = hessgen.hessian_stack(w.seed, 0, sig, n)
     hess = torch.from_numpy(stack).to(dev)
     F = torch.empty(n, dtype=torch.float64, device=dev)
     idx = torch.empty(n, dtype=torch.int32, device=dev)

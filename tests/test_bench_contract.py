@@ -73,3 +73,21 @@ def test_gpu_arm_json_line_small_case():
     assert d["gpu_launches"] > 0 and d["value"] > 0 and d["e2e"]["h2d_bytes_per_step"] > 0
     assert "workload" in d["config"]
 
+
+
+def test_workloads_as_data():
+    """The five workloads the bench and the tests use, from one module: the
+    shapes, plane types, modes and s(R) ranges the benchmark is specified
+    with, and the bench's own constants taken from them."""
+    import bench
+    from paper_2510_02873_gb300 import configs as cfg
+    assert (cfg.SMALL_FP64.grid, cfg.SMALL_FP64.radii, cfg.SMALL_FP64.s_lo, cfg.SMALL_FP64.s_hi) == (32, 8, 0.3, 4.0)
+    assert (cfg.FP64.grid, cfg.FP64.radii, cfg.FP64.planes, cfg.FP64.mode) == (256, 25, "f64", "fp64")
+    assert (cfg.MIXED.grid, cfg.MIXED.radii, cfg.MIXED.planes, cfg.MIXED.mode) == (512, 30, "f32", "mixed")
+    assert cfg.BATCHED.realizations == 48 and cfg.BATCHED.grids == (64, 96, 128, 192, 256, 384)
+    assert cfg.BATCHED.radii_range == (8, 40)
+    assert (cfg.SURROGATE.grid, cfg.SURROGATE.radii, cfg.SURROGATE.planes) == (768, 40, "f32")
+    assert cfg.FP64.evaluations == 256 ** 3 * 25
+    assert (bench.GRID, bench.N_RADII, bench.MIXED_GRID, bench.SUR_GRID) == (256, 25, 512, 768)
+    assert bench.COSMO == dict(omega_m=0.3, omega_l=0.7, n_knots=512, a_min=1e-3, a_max=1.0)
+    assert len(cfg.WORKLOADS) == 5
