@@ -4,11 +4,14 @@
 // HBM-bound reduction: 8 bytes read per point. F >= 0 and the edges are
 // positive, so bins are found on the FP64 bit patterns as integers (integer
 // order is value order for non-negative doubles): no FP64 instruction. A
-// point's bucket, (bits(F) - bits(edge_0)) >> shift, gives the number of
-// edges at or below the bucket's lower end; a short scan over the edges
-// inside the bucket finishes the count (the host picks the largest shift
-// that leaves at most two edges in a bucket; only edges clustered within
-// 1/2048 of their bit-pattern range make a bucket hold more).
+// point's bucket, (bits(F) - kb) >> shift with kb the first edge's pattern
+// rounded down to a multiple of 2^shift, gives the number of edges at or
+// below the bucket's lower end, and the edges inside the bucket finish the
+// count. The host picks the largest shift that leaves at most two edges in a
+// bucket; when that shift is 32 or more the kernel takes the bucket from the
+// top 32 bits of F and finishes with two predicated steps, otherwise (edges
+// a few patterns apart, or clustered within 1/2048 of their range) it takes
+// the whole pattern and scans.
 // Each block counts with shared-memory atomics and adds its counts to the
 // global ones once. (Per-thread private rows and warp-aggregated atomics were
 // both measured slower at 16.8M points.)
